@@ -1,0 +1,216 @@
+"""FP64 CPU oracle of the SBR radar simulator (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: the slow, plain reference that the CUDA library is
+compared against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+bench's ``cpu_baseline`` / ``--impl reference`` legs may import it.  It shares
+no code with the CUDA path; its only common dependency is the seeded input
+module ``sbr_inputs``.
+
+Layout:
+  sbr_oracle.c   brute-force FP64 trace (every ray x every triangle), direct FP64
+                 Eq. 8 synthesis and its Eq. 11-12 adjoint (OpenMP over rays/outputs)
+  __init__.py    loader, ray paths -> per-antenna (tau, A), synthesis wrappers
+  pointcloud.py  direct O(N^2) DFTs, angle DFT, CA-CFAR, soft detection, points,
+                 Chamfer and Laplacian terms, frozen-structure evaluators for FD
+
+Readings of passages the paper leaves open (amplitude constants, ray grid,
+bounce count, the signal-processing chain T of Eq. 16) are written next to the
+function that takes them.  "Parity unpinned": the amplitude constants and the
+point-cloud chain beyond the closed-form special cases pinned by
+``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+import subprocess
+
+import numpy as np
+
+from sbr_inputs import C_LIGHT
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sbr_oracle.c")
+_LIB = None
+
+TMIN = 1e-9        # m, minimum accepted hit distance
+EDGE_EPS = 1e-6    # barycentric edge band excluded from index parity
+TIE_REL = 1e-9     # relative t band treated as a tie between surfaces
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "_build", f"liboracle_{platform.machine()}.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (-O2, OpenMP, no FP contraction)."""
+    out = lib_path()
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        lib.orc_trace.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  P, P, P, P, P, P, P]
+        lib.orc_synth.argtypes = [P, P, ctypes.c_long, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_int, P, P]
+        lib.orc_synth_grad.argtypes = [P, P, ctypes.c_long, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P, P, P]
+        _LIB = lib
+    return _LIB
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def grid_array(grid) -> np.ndarray:
+    return np.concatenate([grid.origin, grid.axis, grid.u_axis, grid.v_axis,
+                           [grid.tan_half]]).astype(np.float64)
+
+
+# ----------------------------------------------------------------------------
+# Trace (Section 3.2.1, Eq. 2-3)
+# ----------------------------------------------------------------------------
+
+
+def trace(verts, faces, grid, max_bounces: int, ray_ids=None, tmin=TMIN, edge_eps=EDGE_EPS,
+          tie_rel=TIE_REL) -> dict:
+    """Brute-force FP64 trace of the G x G grid (or of ``ray_ids``).
+
+    Returns arrays indexed [ray, bounce]: tri (-1 = no hit), t/u/v, hit point,
+    incident direction, unit normal; per ray omega (solid-angle weight) and flag
+    (first ambiguous bounce, 1-based, 0 if none)."""
+    v = np.ascontiguousarray(verts, dtype=np.float32)
+    f = np.ascontiguousarray(faces, dtype=np.int32)
+    g = grid_array(grid)
+    ids = None if ray_ids is None else np.ascontiguousarray(ray_ids, dtype=np.int32)
+    n = grid.n_rays if ids is None else int(ids.shape[0])
+    K = int(max_bounces)
+    tri = np.empty((n, K), np.int32)
+    tuv = np.empty((n, K, 3), np.float64)
+    hit = np.empty((n, K, 3), np.float64)
+    din = np.empty((n, K, 3), np.float64)
+    nrm = np.empty((n, K, 3), np.float64)
+    omega = np.empty(n, np.float64)
+    flag = np.empty(n, np.int32)
+    rc = _lib().orc_trace(_ptr(v), v.shape[0], _ptr(f), f.shape[0], _ptr(g), grid.G, _ptr(ids), n, K,
+                          tmin, edge_eps, tie_rel, _ptr(tri), _ptr(tuv), _ptr(hit), _ptr(din),
+                          _ptr(nrm), _ptr(omega), _ptr(flag))
+    if rc != 0:
+        raise ValueError(f"orc_trace rejected its input (code {rc})")
+    return dict(tri=tri, tuv=tuv, hit=hit, din=din, nrm=nrm, omega=omega, flag=flag,
+                ray_ids=(np.arange(n, dtype=np.int32) if ids is None else ids), K=K)
+
+
+def paths(tr: dict, radar) -> dict:
+    """Per-path, per-virtual-antenna delay tau and strength A (the I^t, I^s of Section 3.2.1).
+
+    Reading (the paper gives no constants): every hit k of a ray emits one path
+    per virtual antenna (t, r), v = t * n_rx + r, with
+      L_in  = |h_1 - Tx_t| + sum_{j=2..k} |h_j - h_{j-1}|
+      L_out = |Rx_r - h_k|
+      tau   = (L_in + L_out) / c
+      A     = omega * (-1)^(k-1) * |d_k . n_k| / (4 pi L_in L_out)
+    (per-interaction reflection -1 of a perfect conductor, the cos term and the
+    1/(4 pi .) spreading of Eq. 1).  Paths are ordered ray-major, bounce-minor.
+    """
+    tri, hit, din, nrm, omega = tr["tri"], tr["hit"], tr["din"], tr["nrm"], tr["omega"]
+    n, K = tri.shape
+    valid = tri >= 0
+    ray_of, k_of = np.nonzero(valid)              # row-major => ray-major, bounce-minor
+    seg = np.zeros((n, K), np.float64)
+    if K > 1:
+        seg[:, 1:] = np.sqrt(((hit[:, 1:] - hit[:, :-1]) ** 2).sum(-1)) * valid[:, 1:]
+    interior = np.cumsum(seg, axis=1)             # interior[i,k] = sum_{j<=k} |h_j - h_{j-1}|
+    h1 = hit[ray_of, 0]
+    hk = hit[ray_of, k_of]
+    cos = np.abs((din[ray_of, k_of] * nrm[ray_of, k_of]).sum(-1))
+    sign = np.where(k_of % 2 == 0, 1.0, -1.0)
+    I = interior[ray_of, k_of]
+    V = radar.n_virt
+    P = ray_of.shape[0]
+    tau = np.empty((V, P))
+    amp = np.empty((V, P))
+    lin = np.empty((V, P))
+    lout = np.empty((V, P))
+    for t in range(radar.n_tx):
+        li = np.sqrt(((h1 - radar.tx[t]) ** 2).sum(-1)) + I
+        for r in range(radar.n_rx):
+            lo = np.sqrt(((radar.rx[r] - hk) ** 2).sum(-1))
+            v = t * radar.n_rx + r
+            lin[v], lout[v] = li, lo
+            tau[v] = (li + lo) / C_LIGHT
+            amp[v] = omega[ray_of] * sign * cos / (4.0 * np.pi * li * lo)
+    return dict(tau=tau, amp=amp, ray=ray_of.astype(np.int32), bounce=k_of.astype(np.int32),
+                lin=lin, lout=lout, cos=cos, P=P)
+
+
+# ----------------------------------------------------------------------------
+# Synthesis (Section 3.2.2, Eq. 8) and its adjoint (Eq. 11-12)
+# ----------------------------------------------------------------------------
+
+
+def chirp_constants(radar):
+    mu = radar.bandwidth / radar.chirp_time
+    fs = radar.n_samples / radar.chirp_time
+    return mu, fs
+
+
+def synthesize(tau, amp, radar) -> np.ndarray:
+    """IF cube [V, C, N_s] complex128 by the direct FP64 sum of Eq. 8.
+
+    Reading: t_n = n / f_s with f_s = N_s / T (no ADC offset); the sum runs over
+    every (hit, antenna) path; the scene is static, so every chirp is equal."""
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    amp = np.ascontiguousarray(amp, dtype=np.float64)
+    V, P = tau.shape
+    mu, fs = chirp_constants(radar)
+    Ns = radar.n_samples
+    re = np.empty((V, Ns))
+    im = np.empty((V, Ns))
+    rc = _lib().orc_synth(_ptr(tau), _ptr(amp), P, V, radar.f0, mu, fs, Ns, _ptr(re), _ptr(im))
+    if rc:
+        raise ValueError("orc_synth rejected its input")
+    s = re + 1j * im
+    return np.repeat(s[:, None, :], radar.n_chirps, axis=1)
+
+
+def synthesize_grad(tau, amp, radar, g_cube):
+    """(dL/dtau, dL/dA) [V, P] for upstream gradient g_cube [V, C, N_s] (Eq. 11-12).
+
+    The static cube repeats one chirp C times, so the per-chirp gradients add."""
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    amp = np.ascontiguousarray(amp, dtype=np.float64)
+    V, P = tau.shape
+    mu, fs = chirp_constants(radar)
+    g = np.asarray(g_cube).sum(axis=1)
+    gr = np.ascontiguousarray(g.real, dtype=np.float64)
+    gi = np.ascontiguousarray(g.imag, dtype=np.float64)
+    gtau = np.empty((V, P))
+    gamp = np.empty((V, P))
+    rc = _lib().orc_synth_grad(_ptr(tau), _ptr(amp), P, V, radar.f0, mu, fs, radar.n_samples,
+                               _ptr(gr), _ptr(gi), _ptr(gtau), _ptr(gamp))
+    if rc:
+        raise ValueError("orc_synth_grad rejected its input")
+    return gtau, gamp
+
+
+def simulate_cube(wl, ray_ids=None) -> tuple:
+    """Trace + paths + synthesis of a workload; returns (cube, trace, paths)."""
+    tr = trace(wl.verts, wl.faces, wl.grid, wl.max_bounces, ray_ids)
+    pa = paths(tr, wl.radar)
+    return synthesize(pa["tau"], pa["amp"], wl.radar), tr, pa

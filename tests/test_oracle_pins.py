@@ -1,0 +1,420 @@
+"""Pins of the FP64 oracle against closed forms, invariants and special cases.
+
+Each test fixes a fact that the paper or plain geometry/mathematics determines,
+chosen so that a plausible slip in the oracle (a dropped term, a wrong sign or
+index, a transposed operand) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import pointcloud as pc
+from sbr_inputs import (C_LIGHT, RayGrid, icosphere, merge_meshes, radar_mimo_3x4, radar_single_tx,
+                        ray_grid_for_sphere)
+
+
+def square(corner, e1, e2):
+    """Planar quad corner, corner+e1, corner+e1+e2, corner+e2 as two triangles."""
+    c = np.asarray(corner, float)
+    e1, e2 = np.asarray(e1, float), np.asarray(e2, float)
+    v = np.array([c, c + e1, c + e1 + e2, c + e2], dtype=np.float32)
+    f = np.array([[0, 1, 2], [0, 2, 3]], dtype=np.int32)
+    return v, f
+
+
+def axis_grid(G, tan_half, axis=(0.0, 0.0, 1.0), origin=(0.0, 0.0, 0.0)):
+    a = np.asarray(axis, float)
+    a = a / np.linalg.norm(a)
+    up = np.array([0.0, 1.0, 0.0]) if abs(a[1]) < 0.9 else np.array([1.0, 0.0, 0.0])
+    u = np.cross(up, a)
+    u /= np.linalg.norm(u)
+    v = np.cross(a, u)
+    return RayGrid(G, np.asarray(origin, float), a, u, v, tan_half)
+
+
+# --------------------------------------------------------------------------
+# Geometry
+# --------------------------------------------------------------------------
+
+def test_flat_plate_path_length_and_amplitude():
+    """Plate z = D normal to boresight: t = D / cos(psi), L = |h - Tx| + |Rx - h| exactly."""
+    D = 1.25   # exactly representable in the float32 vertex array
+    v, f = square((-2.0, -2.0, D), (4.0, 0, 0), (0, 4.0, 0))
+    grid = axis_grid(24, 0.35)
+    radar = radar_mimo_3x4(256, 1)
+    tr = oracle.trace(v, f, grid, 2)
+    assert (tr["tri"][:, 0] >= 0).all() and (tr["tri"][:, 1] < 0).all()
+    d = tr["din"][:, 0]
+    cos_psi = d[:, 2]
+    np.testing.assert_allclose(tr["tuv"][:, 0, 0], D / cos_psi, rtol=1e-13)
+    h = D * d / cos_psi[:, None]
+    np.testing.assert_allclose(tr["hit"][:, 0], h, rtol=0, atol=1e-13)
+    pa = oracle.paths(tr, radar)
+    for t in range(radar.n_tx):
+        for r in range(radar.n_rx):
+            vv = t * radar.n_rx + r
+            lin = np.linalg.norm(h - radar.tx[t], axis=1)
+            lout = np.linalg.norm(h - radar.rx[r], axis=1)
+            np.testing.assert_allclose(pa["tau"][vv] * C_LIGHT, lin + lout, rtol=1e-14)
+            # |d.n| = cos(psi) on a plate normal to z; A = omega cos / (4 pi L_in L_out)
+            np.testing.assert_allclose(pa["amp"][vv], tr["omega"] * cos_psi / (4 * np.pi * lin * lout),
+                                       rtol=1e-13)
+    # monostatic element (Tx0 = Rx0 = origin): L = 2 D / cos(psi)
+    np.testing.assert_allclose(pa["tau"][0] * C_LIGHT, 2 * D / cos_psi, rtol=1e-14)
+
+
+def test_flat_plate_range_peak():
+    """A narrow cone onto a plate at D: the strongest point lies at range D (nearest bin)."""
+    D = 1.0
+    v, f = square((-1.0, -1.0, D), (2.0, 0, 0), (0, 2.0, 0))
+    grid = axis_grid(32, 0.02)
+    radar = radar_single_tx(256, 1)
+    tr = oracle.trace(v, f, grid, 1)
+    pa = oracle.paths(tr, radar)
+    cube = oracle.synthesize(pa["tau"], pa["amp"], radar)
+    out = pc.pointcloud(cube, radar)
+    binw = C_LIGHT / (2 * radar.bandwidth)
+    k = out["k"][0]
+    assert k == int(round(D / binw))
+    top = out["points"][0]
+    assert abs(math.hypot(top[0], top[2]) - D) < 0.25 * binw
+    assert abs(top[0]) < 0.05 * D
+
+
+def test_sphere_icosphere_within_sagitta():
+    """Icosphere (inscribed) hits agree with the analytic sphere within the facet sagitta."""
+    R, c = 0.2, np.array([0.0, 0.0, 1.0])
+    v, f = icosphere(3, R, c)
+    grid = ray_grid_for_sphere(c, R, 48)
+    tr = oracle.trace(v, f, grid, 1)
+    d = tr["din"][:, 0]
+    b = d @ c
+    disc = b * b - (c @ c - R * R)
+    hit_sphere = disc >= 0
+    t_s = b - np.sqrt(np.maximum(disc, 0))
+    hit_ico = tr["tri"][:, 0] >= 0
+    assert not (hit_ico & ~hit_sphere).any()         # the polyhedron lies inside the sphere
+    # deepest facet point: a triangle of circumradius rho <= e / sqrt(3) sits at most
+    # R - sqrt(R^2 - rho^2) below the sphere, its normal within asin(rho / R) of the radius
+    e = np.linalg.norm(v[f[:, [0, 1, 2]]] - v[f[:, [1, 2, 0]]], axis=2).max()
+    phi = math.asin(e / (math.sqrt(3) * R))
+    sag = R * (1 - math.cos(phi))
+    # rays well inside the silhouette (impact parameter below the inradius) must hit
+    r_in = R - sag
+    impact = np.sqrt(np.maximum(c @ c - b * b, 0))
+    assert hit_ico[impact < 0.95 * r_in].all()
+    ok = hit_ico & (impact < 0.8 * R)
+    inc = np.arcsin(impact[ok] / R)
+    dt = tr["tuv"][ok, 0, 0] - t_s[ok]
+    assert (dt >= -1e-12).all()
+    assert (dt <= sag / np.cos(inc + phi) + 1e-9).all()
+
+
+def corner_reflector(C, s):
+    cx, cy, cz = C
+    p1 = square((cx - s, cy - s, cz), (s, 0, 0), (0, s, 0))           # z = cz
+    p2 = square((cx, cy - s, cz - s), (0, s, 0), (0, 0, s))           # x = cx
+    p3 = square((cx - s, cy, cz - s), (s, 0, 0), (0, 0, s))           # y = cy
+    return merge_meshes(p1, p2, p3)
+
+
+def test_trihedral_corner_retroreflects():
+    """Three mutually perpendicular plates: after 3 hits the ray leaves along -d and the
+    total length to the plane through the origin normal to d is 2 (C - o).d."""
+    C = np.array([0.25, 0.125, 2.0])      # float32-exact corner
+    v, f = corner_reflector(C, 0.75)
+    grid = axis_grid(40, 0.12, axis=C)
+    tr = oracle.trace(v, f, grid, 3)
+    three = (tr["tri"] >= 0).all(axis=1)
+    assert three.sum() > 100
+    d1 = tr["din"][three, 0]
+    h = tr["hit"][three]
+    n3 = tr["nrm"][three, 2]
+    d3 = tr["din"][three, 2]
+    out = d3 - 2 * (d3 * n3).sum(-1, keepdims=True) * n3
+    np.testing.assert_allclose(out, -d1, atol=1e-12)
+    L = (np.linalg.norm(h[:, 0], axis=1) + np.linalg.norm(h[:, 1] - h[:, 0], axis=1)
+         + np.linalg.norm(h[:, 2] - h[:, 1], axis=1) + (h[:, 2] * d1).sum(-1))
+    np.testing.assert_allclose(L, 2 * (d1 @ C), rtol=1e-12)
+    # the oracle's own path records agree: tau (monostatic) of the 3rd hit
+    radar = radar_single_tx(256, 1)
+    pa = oracle.paths(tr, radar)
+    sel = (pa["bounce"] == 2) & three[pa["ray"]]
+    lin = pa["lin"][0, sel]
+    np.testing.assert_allclose(lin, np.linalg.norm(h[:, 0], axis=1) + np.linalg.norm(h[:, 1] - h[:, 0], axis=1)
+                               + np.linalg.norm(h[:, 2] - h[:, 1], axis=1), rtol=1e-13)
+    # reflection sign (-1)^(k-1): third interaction positive, second negative
+    assert (pa["amp"][0, sel] > 0).all()
+    assert (pa["amp"][0, (pa["bounce"] == 1)] < 0).all()
+
+
+def test_dihedral_two_bounce_direction():
+    """Planes x = cx and y = cy: after two hits the direction is (-dx, -dy, dz)."""
+    C = np.array([0.2, 0.15, 0.0])
+    pz = 3.0
+    a = square((C[0], C[1] - 1.0, 1.0), (0, 1.0, 0), (0, 0, pz))
+    b = square((C[0] - 1.0, C[1], 1.0), (1.0, 0, 0), (0, 0, pz))
+    v, f = merge_meshes(a, b)
+    grid = axis_grid(32, 0.1, axis=(C[0], C[1], 2.0))
+    tr = oracle.trace(v, f, grid, 3)
+    two = (tr["tri"][:, :2] >= 0).all(axis=1) & (tr["tri"][:, 2] < 0)
+    assert two.sum() > 50
+    d1 = tr["din"][two, 0]
+    d3 = tr["din"][two, 2]     # incident direction stored for the (missed) third slot
+    np.testing.assert_allclose(d3, d1 * np.array([-1.0, -1.0, 1.0]), atol=1e-12)
+
+
+def test_permutation_invariance():
+    """Reordering triangles (and their corners) does not change any hit."""
+    R, c = 0.2, np.array([0.05, -0.02, 1.1])
+    v1, f1 = icosphere(2, R, c)
+    v2, f2 = square((-1.0, -0.3, 0.5), (2.0, 0, 0), (0, 0, 2.0))   # wall below: second bounces
+    v, f = merge_meshes((v1, f1), (v2, f2))
+    grid = ray_grid_for_sphere(c, R, 40)
+    tr = oracle.trace(v, f, grid, 3)
+    rng = np.random.default_rng(7)
+    perm = rng.permutation(f.shape[0])
+    fp = np.roll(f[perm], 1, axis=1)        # rotate corners too (orientation preserved)
+    tr2 = oracle.trace(v, fp, grid, 3)
+    ok = tr["flag"] == 0
+    mapped = np.where(tr2["tri"] >= 0, perm[np.maximum(tr2["tri"], 0)], -1)
+    np.testing.assert_array_equal(mapped[ok], tr["tri"][ok])
+    np.testing.assert_allclose(tr2["hit"][ok], tr["hit"][ok], atol=1e-12)
+    assert (tr["tri"][:, 1] >= 0).sum() > 0
+
+
+def test_exact_tie_lower_index_and_edge_flag():
+    """A duplicated triangle is an exact tie: the lower index wins and the ray is flagged.
+    Rays along the shared diagonal of a square are edge-near and flagged."""
+    v, f = square((-1.0, -1.0, 1.0), (2.0, 0, 0), (0, 2.0, 0))
+    f_dup = np.concatenate([f, f[:1]])
+    grid = axis_grid(8, 0.3)
+    tr = oracle.trace(v, f_dup, grid, 1)
+    hit0 = tr["tri"][:, 0]
+    assert not (hit0 == 2).any()
+    assert (tr["flag"][hit0 == 0] == 1).all()           # tie with the duplicate
+    # diagonal (row == col) lies on the shared edge of the two triangles
+    tr = oracle.trace(v, f, grid, 1)
+    rows, cols = np.divmod(np.arange(64), 8)
+    assert (tr["flag"][rows == cols] == 1).all()
+    assert (tr["flag"][np.abs(rows - cols) >= 2] == 0).all()
+
+
+def test_ray_grid_solid_angle_converges():
+    """Sum of cell weights -> exact solid angle of the square, 4 atan(t^2 / sqrt(1 + 2 t^2)),
+    with midpoint-rule O(1/G^2) error."""
+    t = 0.4
+    exact = 4 * math.atan(t * t / math.sqrt(1 + 2 * t * t))
+    errs = []
+    for G in (16, 32, 64):
+        grid = axis_grid(G, t)
+        tr = oracle.trace(np.zeros((3, 3), np.float32), np.zeros((0, 3), np.int32), grid, 1)
+        errs.append(abs(tr["omega"].sum() - exact) / exact)
+    assert errs[2] < 1e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_reciprocity_swap_tx_rx():
+    """Swapping the Tx and Rx positions leaves tau and A of every 1-bounce path unchanged."""
+    R, c = 0.25, np.array([0.1, 0.0, 1.5])
+    v, f = icosphere(2, R, c)
+    grid = ray_grid_for_sphere(c, R, 32)
+    tr = oracle.trace(v, f, grid, 1)
+    r1 = radar_single_tx()
+    r1.tx = np.array([[0.003, 0.001, 0.0]])
+    r1.rx = np.array([[0.011, -0.002, 0.0]])
+    r2 = radar_single_tx()
+    r2.tx, r2.rx = r1.rx.copy(), r1.tx.copy()
+    p1, p2 = oracle.paths(tr, r1), oracle.paths(tr, r2)
+    # first legs are recomputed from Tx, so the swap must be exact for 1-bounce paths
+    np.testing.assert_allclose(p1["tau"], p2["tau"], rtol=1e-15)
+    np.testing.assert_allclose(p1["amp"], p2["amp"], rtol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Synthesis (Eq. 8) and its adjoint (Eq. 11-12)
+# --------------------------------------------------------------------------
+
+def test_point_scatterer_tone_high_precision():
+    """Eq. 8 for one path at 20 m against a 50-digit evaluation (phase reduction mod 1)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    radar = radar_single_tx(1024, 1)
+    tau = np.array([[2 * 20.0123456789 / C_LIGHT]])
+    amp = np.array([[0.7]])
+    s = oracle.synthesize(tau, amp, radar)[0, 0]
+    mu = mp.mpf(radar.bandwidth) / mp.mpf(radar.chirp_time)
+    fs = mp.mpf(radar.n_samples) / mp.mpf(radar.chirp_time)
+    t = mp.mpf(float(tau[0, 0]))
+    for n in (0, 1, 511, 1023):
+        ph = 2 * mp.pi * (mp.mpf(radar.f0) * t + mu * t * n / fs)
+        ref = complex(mp.mpf("0.7") * mp.expj(ph))
+        assert abs(s[n] - ref) < 1e-9
+
+
+def test_point_scatterer_dft_is_dirichlet():
+    """DFT of the Eq. 8 tone of one path = closed-form Dirichlet kernel peaking at B tau."""
+    radar = radar_single_tx(256, 1)
+    tau = np.array([[2 * 1.2345 / C_LIGHT]])
+    amp = np.array([[1.3]])
+    X = pc.dft(oracle.synthesize(tau, amp, radar), axis=2)[0, 0]
+    N = radar.n_samples
+    beta = radar.bandwidth * tau[0, 0]          # beat frequency in bins: mu tau N / f_s
+    phi0 = 2 * np.pi * radar.f0 * tau[0, 0]
+    k = np.arange(N)
+    z = np.exp(2j * np.pi * (beta - k) / N)
+    ref = 1.3 * np.exp(1j * phi0) * (1 - z ** N) / (1 - z)
+    np.testing.assert_allclose(X, ref, rtol=1e-9, atol=1e-9 * abs(ref).max())
+    assert np.argmax(np.abs(X)) == int(round(beta)) % N
+
+
+def test_synthesis_linearity_and_integer_phase():
+    radar = radar_single_tx(128, 2)
+    rng = np.random.default_rng(3)
+    tau = rng.uniform(5e-9, 2e-8, size=(2, 40))
+    amp = rng.normal(size=(2, 40))
+    s_all = oracle.synthesize(tau, amp, radar)
+    s_a = oracle.synthesize(tau[:, :17], amp[:, :17], radar)
+    s_b = oracle.synthesize(tau[:, 17:], amp[:, 17:], radar)
+    np.testing.assert_allclose(s_all, s_a + s_b, atol=1e-12)
+    np.testing.assert_array_equal(s_all[:, 0], s_all[:, 1])       # static: chirps equal
+    # f0 tau and B tau both integers -> every sample equals A exactly (up to rounding)
+    r = radar_single_tx(64, 1)
+    r.f0, r.bandwidth = 7.7e10, 4e9
+    tau1 = np.array([[1.6e-8]])                       # f0 tau = 1232, per-sample mu tau / f_s = 1
+    s = oracle.synthesize(tau1, np.array([[2.5]]), r)[0, 0]
+    mu, fs = oracle.chirp_constants(r)
+    assert abs(mu * tau1[0, 0] / fs - 1.0) < 1e-12
+    np.testing.assert_allclose(s, 2.5, atol=1e-9)
+
+
+def test_synthesis_adjoint_matches_central_differences():
+    """Eq. 11-12 adjoint vs FP64 central differences of L = Re sum conj(g) S."""
+    radar = radar_single_tx(64, 3)
+    rng = np.random.default_rng(11)
+    V, P = 2, 5
+    tau = rng.uniform(6e-9, 1.4e-8, size=(V, P))
+    amp = rng.normal(size=(V, P))
+    g = rng.normal(size=(V, 3, 64)) + 1j * rng.normal(size=(V, 3, 64))
+
+    def L(t, a):
+        return float(np.real(np.conj(g) * oracle.synthesize(t, a, radar)).sum())
+
+    gt, ga = oracle.synthesize_grad(tau, amp, radar, g)
+    ht, ha = 2e-17, 1e-6
+    for v in range(V):
+        for p in range(P):
+            tp, tm = tau.copy(), tau.copy()
+            tp[v, p] += ht
+            tm[v, p] -= ht
+            fd_t = (L(tp, amp) - L(tm, amp)) / (2 * ht)
+            ap, am = amp.copy(), amp.copy()
+            ap[v, p] += ha
+            am[v, p] -= ha
+            fd_a = (L(tau, ap) - L(tau, am)) / (2 * ha)
+            assert abs(gt[v, p] - fd_t) <= 1e-6 * abs(fd_t) + 1e-9 * np.abs(gt).max()
+            assert abs(ga[v, p] - fd_a) <= 1e-8 * max(abs(fd_a), 1.0)
+
+
+# --------------------------------------------------------------------------
+# Signal processing chain
+# --------------------------------------------------------------------------
+
+def test_direct_dft_matches_fft_and_parseval():
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(3, 4, 128)) + 1j * rng.normal(size=(3, 4, 128))
+    X = pc.dft(x, axis=2)
+    np.testing.assert_allclose(X, np.fft.fft(x, axis=2), rtol=1e-12, atol=1e-12 * abs(X).max())
+    np.testing.assert_allclose((abs(X) ** 2).sum(2), 128 * (abs(x) ** 2).sum(2), rtol=1e-12)
+    Y = pc.dft(x, axis=1)
+    np.testing.assert_allclose(Y, np.fft.fft(x, axis=1), atol=1e-12 * abs(Y).max())
+    # inverse: conj(DFT(conj(X)))/N recovers x
+    np.testing.assert_allclose(np.conj(pc.dft(np.conj(X), axis=2)) / 128, x, atol=1e-12)
+
+
+def point_target_cube(radar, targets):
+    """IF cube of ideal point targets [(position, amplitude)] through the oracle's Eq. 8."""
+    tau = np.zeros((radar.n_virt, len(targets)))
+    amp = np.zeros_like(tau)
+    for j, (p, a) in enumerate(targets):
+        p = np.asarray(p, float)
+        for t in range(radar.n_tx):
+            for r in range(radar.n_rx):
+                tau[t * radar.n_rx + r, j] = (np.linalg.norm(p - radar.tx[t]) + np.linalg.norm(p - radar.rx[r])) / C_LIGHT
+                amp[t * radar.n_rx + r, j] = a
+    return oracle.synthesize(tau, amp, radar)
+
+
+def test_angle_and_range_of_point_scatterer():
+    """A point target at (r0, theta0): strongest point at u = sin(theta0), r = r0."""
+    radar = radar_mimo_3x4(256, 2)
+    for r0, th in ((2.4, 0.3), (3.1, -0.5), (1.7, 0.05)):
+        p = (r0 * math.sin(th), 0.0, r0 * math.cos(th))
+        out = pc.pointcloud(point_target_cube(radar, [(p, 1.0)]), radar)
+        top = out["points"][0]
+        rr = math.hypot(top[0], top[2])
+        assert abs(top[0] / rr - math.sin(th)) < 0.01
+        # 3-point log-parabola on an unwindowed (Dirichlet) range peak: bias up to ~0.2 bin
+        assert abs(rr - r0) < 0.25 * C_LIGHT / (2 * radar.bandwidth)
+        assert top[3] > 0.99
+        # every other detection is at least 10 dB weaker than the target's cell
+        Pw = out["Pw"]
+        a, k = out["a"], out["k"]
+        assert (Pw[a[1:], k[1:]] < 0.1 * Pw[a[0], k[0]]).all()
+
+
+def test_two_scatterers_and_empty_scene():
+    radar = radar_mimo_3x4(256, 1)
+    p1, p2 = (0.0, 0.0, 1.5), (0.8, 0.0, 2.6)
+    out = pc.pointcloud(point_target_cube(radar, [(p1, 1.0), (p2, 1.0)]), radar)
+    # the two strongest detections (by cell power) sit at the two targets
+    order = np.argsort(-out["Pw"][out["a"], out["k"]])[:2]
+    strong = out["points"][order]
+    rr = np.hypot(strong[:, 0], strong[:, 2])
+    uu = strong[:, 0] / rr
+    i = np.argsort(rr)
+    binw = C_LIGHT / (2 * radar.bandwidth)
+    np.testing.assert_allclose(rr[i], [1.5, math.hypot(0.8, 2.6)], atol=0.25 * binw)
+    np.testing.assert_allclose(uu[i], [0.0, 0.8 / math.hypot(0.8, 2.6)], atol=0.01)
+    assert (strong[:, 3] > 0.95).all()
+    empty = pc.pointcloud(np.zeros((12, 1, 256), complex), radar)
+    assert empty["points"].shape[0] == 0
+
+
+def test_cfar_noise_edges_and_local_max_ties():
+    Pw = np.arange(20, dtype=float)[None, :].repeat(3, 0)
+    n = pc.cfar_noise(Pw, 2, 8)
+    # k = 0: training cells 3..10 only
+    assert n[0, 0] == pytest.approx(np.mean(np.arange(3, 11)))
+    assert n[0, 10] == pytest.approx(np.mean(list(range(0, 8)) + list(range(13, 20))))
+    flat = np.ones((3, 4))
+    m = pc.local_max(flat)
+    assert m.sum() == 1 and m[0, 0]             # equal values: the lowest linear index
+
+
+def test_chamfer_and_laplacian_definitions():
+    rng = np.random.default_rng(2)
+    P = np.concatenate([rng.normal(size=(30, 3)), np.ones((30, 1))], 1)
+    assert pc.chamfer_parity(P, P) == 0.0
+    Q = P.copy()
+    Q[:, 0] += 1e-3
+    assert pc.chamfer_parity(P, Q) == pytest.approx(1e-3, rel=1e-9)
+    # a planar regular grid has zero uniform Laplacian at interior vertices
+    n = 6
+    xs, ys = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    v = np.stack([xs.ravel(), ys.ravel(), np.zeros(n * n)], 1).astype(np.float64)
+    f = []
+    for i in range(n - 1):
+        for j in range(n - 1):
+            a, b, c, d = i * n + j, (i + 1) * n + j, (i + 1) * n + j + 1, i * n + j + 1
+            f += [(a, b, c), (a, c, d)]
+    f = np.array(f)
+    nb = pc.mesh_neighbours(f, n * n)
+    interior = [i * n + j for i in range(1, n - 1) for j in range(1, n - 1)]
+    for i in interior:
+        assert np.allclose(v[i] - v[nb[i]].mean(0), 0)
+    # icosphere: every vertex sits off its ring centroid by the same radial amount pattern (> 0)
+    vi, fi = icosphere(1, 1.0)
+    assert pc.laplacian(vi, fi) > 0
