@@ -1,0 +1,296 @@
+/*
+ * sbr.h -- C ABI of libsbr, a GB300 (sm_103a) shooting-and-bouncing-rays (SBR)
+ * FMCW radar simulator with hand-written adjoints.
+ *
+ * The library follows the paper's statement of the problem (Section 3.4,
+ * Eq. 14: a simulator S : Theta -> Y) split into its three stages:
+ *
+ *   sbr_trace       mesh, radar, ray grid -> paths      (Section 3.2.1, Eq. 2-3:
+ *                   Monte-Carlo ray tracing; the path records are the time of
+ *                   flight I^t and signal strength I^s named there)
+ *   sbr_synthesize  paths -> IF cube [V, C, N_s]        (Section 3.2.2, Eq. 8)
+ *   sbr_pointcloud  IF cube -> radar point cloud        (Section 3.4, Eq. 16: the
+ *                   signal-processing map T; range FFT, Doppler FFT, angle DFT,
+ *                   soft CA-CFAR, sub-bin refine)
+ *
+ * plus the adjoint of each stage (Section 3.3, Eq. 13 chain rule; Eq. 11-12
+ * for synthesis) and the loss / optimiser kernels of the reconstruction loop
+ * (Section 3.4, Eq. 14-15).
+ *
+ * Conventions (every entry point):
+ *  - Returns sbr_status; SBR_OK = 0.  Nothing aborts, throws across the ABI or
+ *    traps on the device.  sbr_last_error() gives a message for the calling
+ *    thread's last failure.
+ *  - Work is enqueued asynchronously on the given stream (NULL = legacy default
+ *    stream); argument checks that need no device data happen before anything
+ *    is enqueued and fail without side effects.
+ *  - Every device pointer is owned by the caller, must stay valid until the
+ *    enqueued work completes, and must be 256-byte aligned when it is the base
+ *    of a region carved by a *_bind function.  The library performs no device
+ *    allocation of its own; *_bytes functions give the sizes to allocate.
+ *  - Frame: metres, seconds, Hz.  Radar frame origin at the ray origin,
+ *    boresight +z, array along +x.
+ *  - Sizes are device-side where they depend on data (e.g. the number of valid
+ *    paths P, the number of detected points): kernels read them from device
+ *    memory, so no call synchronises the host.
+ */
+#ifndef SBR_H_
+#define SBR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* sbr_stream; /* identical to cudaStream_t */
+
+typedef enum {
+  SBR_OK = 0,
+  SBR_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or configuration */
+  SBR_ERR_OOM = 2,         /* caller-provided region smaller than *_bytes() */
+  SBR_ERR_TIMEOUT = 3,     /* a bounded device wait gave up (status word) */
+  SBR_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has the name) */
+  SBR_ERR_UNSUPPORTED = 5  /* configuration outside the compiled kernels' range */
+} sbr_status;
+
+#define SBR_MAX_TX 16
+#define SBR_MAX_RX 16
+#define SBR_MAX_VIRT 64
+
+/* FMCW radar (Section 3.2.2, Eq. 8: carrier f_c, sweep B over chirp time T,
+ * mu = B / T).  Samples t_n = n T / N_s, n = 0..N_s-1.  Virtual antenna
+ * v = t * n_rx + r pairs Tx t with Rx r. */
+typedef struct {
+  double f0;          /* carrier f_c [Hz] */
+  double bandwidth;   /* sweep B [Hz] */
+  double chirp_time;  /* chirp duration T [s] */
+  double chirp_rep;   /* chirp repetition interval [s] (static scene: unused) */
+  int32_t n_samples;  /* N_s, power of two in [32, 4096] */
+  int32_t n_chirps;   /* C, power of two in [1, 512] */
+  int32_t n_tx, n_rx; /* n_tx * n_rx <= SBR_MAX_VIRT */
+  double tx[SBR_MAX_TX][3];
+  double rx[SBR_MAX_RX][3];
+} sbr_radar_cfg;
+
+/* Stratified G x G ray grid: the Monte-Carlo sample set of Eq. 3.  Ray
+ * index = row * G + col; direction = normalize(axis + a u_axis + b v_axis),
+ * a = tan_half (2 (col + 1/2) / G - 1), b likewise with row; weight = cell
+ * solid angle (2 tan_half / G)^2 cos^3 of the direction's angle to axis. */
+typedef struct {
+  int32_t G;
+  int32_t _pad;
+  double origin[3];
+  double axis[3];   /* unit */
+  double u_axis[3]; /* unit, orthogonal to axis */
+  double v_axis[3]; /* unit, orthogonal to axis and u_axis */
+  double tan_half;
+} sbr_ray_grid;
+
+/* Soft CA-CFAR and point extraction (the map T of Eq. 16; parameters are
+ * this library's reading: the paper names T only as "a signal processing
+ * algorithm").  Angle bins u_a = -1 + 2a / n_theta. */
+typedef struct {
+  int32_t n_theta; /* angle bins, power of two in [8, 256] */
+  int32_t guard;   /* CFAR guard cells each side along range */
+  int32_t train;   /* CFAR training cells each side beyond the guard */
+  int32_t k_max;   /* maximum points returned */
+  float alpha;     /* CFAR scale (linear power) */
+  float floor_rel; /* absolute floor as a fraction of the map's maximum power */
+  float beta;      /* sigmoid temperature in natural-log power units */
+  float w_min;     /* minimum soft weight for a point to be kept */
+} sbr_cfar_cfg;
+
+typedef enum {
+  SBR_PHASE_SPLIT = 0, /* tau in FP64, phase anchors in hi/lo FP32, FP32 rotation */
+  SBR_PHASE_FP64 = 1,  /* per-sample carrier phase f_c tau + mu tau t_n in FP64 */
+  SBR_PHASE_NAIVE = 2  /* tau, f_c tau and mu tau t_n all in FP32 */
+} sbr_phase_mode;
+
+/* One surface interaction of a ray (16 B).  tri = original triangle index or
+ * -1 (no hit; every later bounce of that ray is -1 too). */
+typedef struct {
+  int32_t tri;
+  float t, u, v;
+} sbr_hit;
+
+const char* sbr_version(void);
+/* Copies the calling thread's last error message (NUL-terminated, truncated to n). */
+void sbr_last_error(char* buf, size_t n);
+
+/* ------------------------------------------------------------------------ */
+/* Scene: triangle mesh + LBVH (Section 3.1: the mesh is the scene          */
+/* representation whose vertices are the optimised parameters).             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sbr_scene sbr_scene; /* opaque host-side handle */
+
+/* Device bytes a scene of nt triangles needs (triangle records, BVH nodes,
+ * sort and refit scratch). */
+size_t sbr_scene_bytes(int32_t nt);
+
+/* Packs the mesh and builds its LBVH (Morton codes of centroids, radix sort,
+ * binary radix tree, bottom-up AABB refit) in d_mem.  d_verts [nv][3] float32,
+ * d_faces [nt][3] int32 stay owned by the caller and are read, not kept.
+ * Face indices must lie in [0, nv): out-of-range faces make the build set an
+ * error word that the next sbr_scene_check() reports; d_mem must hold
+ * sbr_scene_bytes(nt) bytes.  *out is a host handle released by
+ * sbr_scene_destroy (which does not touch d_mem). */
+sbr_status sbr_scene_create(const float* d_verts, int32_t nv, const int32_t* d_faces,
+                            int32_t nt, void* d_mem, size_t mem_bytes, sbr_stream stream,
+                            sbr_scene** out);
+/* Rebuilds the scene for new vertex positions of the same topology (the
+ * per-iteration update of the reconstruction loop). */
+sbr_status sbr_scene_update(sbr_scene* scene, const float* d_verts, sbr_stream stream);
+/* Synchronises the stream and reports a device-side error word set by the build. */
+sbr_status sbr_scene_check(const sbr_scene* scene, sbr_stream stream);
+void sbr_scene_destroy(sbr_scene* scene);
+
+/* ------------------------------------------------------------------------ */
+/* Trace (Section 3.2.1, Eq. 2-3) and path preparation                      */
+/* ------------------------------------------------------------------------ */
+
+/* Caller-owned path records, carved from one region by sbr_paths_bind.
+ * R rays x K bounces slots; P <= R*K valid paths are compacted ray-major,
+ * bounce-minor; per path and virtual antenna v the synthesis record is at
+ * prep[v * path_cap + p]. */
+typedef struct {
+  int32_t n_rays, max_bounces, n_virt, _pad;
+  int64_t path_cap;   /* = n_rays * max_bounces */
+  sbr_hit* hits;      /* [R*K] nearest hits */
+  double* hit_pos;    /* [R*K*4] FP64 hit point xyz and |d_k . n_k| */
+  float* ray_weight;  /* [R] solid-angle weight omega */
+  int32_t* ray_first; /* [R+1] first path of each ray (exclusive scan); [R] = P */
+  int32_t* path_ray;  /* [path_cap] ray of path p */
+  float* prep;        /* [V*path_cap*4] {phi0, delta_hi, delta_lo, A} per (v, p) */
+  double* tau64;      /* [V*path_cap] FP64 delay per (v, p) */
+  int32_t* count;     /* [1] P (device) */
+  void* scratch;      /* scan scratch */
+} sbr_paths;
+
+size_t sbr_paths_bytes(int32_t n_rays, int32_t max_bounces, int32_t n_virt);
+sbr_status sbr_paths_bind(void* d_mem, size_t bytes, int32_t n_rays, int32_t max_bounces,
+                          int32_t n_virt, sbr_paths* out);
+
+/* Traces the grid's rays (all G*G when n_ids < 0; otherwise the n_ids ray
+ * indices in d_ray_ids, each in [0, G*G), any order, n_ids = 0 allowed) through up to max_bounces specular interactions with
+ * nearest-hit Moller-Trumbore tests (FP32 with a guarded FP64 fallback that
+ * makes the chosen triangle that of an FP64 brute-force search), skipping the
+ * previously hit triangle; refines every hit in FP64, and writes per path and
+ * virtual antenna the FP64 delay tau = (|h_1 - Tx_t| + sum |h_j - h_{j-1}| +
+ * |Rx_r - h_k|) / c, its phase terms frac(f_c tau), frac(mu tau T / N_s) split
+ * hi/lo, and the strength A = omega (-1)^(k-1) |d_k . n_k| / (4 pi L_in L_out).
+ * paths must come from sbr_paths_bind with n_rays = (n_ids < 0 ? G*G : n_ids). */
+sbr_status sbr_trace(const sbr_scene* scene, const sbr_radar_cfg* radar,
+                     const sbr_ray_grid* grid, const int32_t* d_ray_ids, int32_t n_ids,
+                     int32_t max_bounces, const sbr_paths* paths, sbr_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Synthesis (Section 3.2.2, Eq. 8)                                         */
+/* ------------------------------------------------------------------------ */
+
+/* Scratch bytes for sbr_synthesize / sbr_synthesize_bwd. */
+size_t sbr_synth_ws_bytes(const sbr_radar_cfg* radar, int64_t path_cap);
+
+/* d_cube [V][C][N_s] complex64 (interleaved re, im) =
+ *   sum_p A_{p,v} exp(j 2 pi (f_c tau_{p,v} + mu tau_{p,v} t_n)),
+ * broadcast over the C chirps of a static scene.  Deterministic: partial sums
+ * per CTA are reduced in a fixed order.  SBR_PHASE_FP64 needs paths->tau64. */
+sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg* radar,
+                          sbr_phase_mode mode, float* d_cube, void* d_ws, size_t ws_bytes,
+                          sbr_stream stream);
+
+/* Adjoint through Eq. 11-12: for upstream d_gcube = dL/dRe + j dL/dIm of the
+ * cube, writes d_gtau [V*path_cap] = dL/dtau (per metre of path length, i.e.
+ * dL/dtau / c) and d_gamp [V*path_cap] = dL/dA. */
+sbr_status sbr_synthesize_bwd(const sbr_paths* paths, const sbr_radar_cfg* radar,
+                              const float* d_gcube, float* d_glen, float* d_gamp,
+                              void* d_ws, size_t ws_bytes, sbr_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Point cloud (the map T of Eq. 16)                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Saved state of one point-cloud evaluation (needed by its adjoint) and its
+ * scratch, carved from one region by sbr_pc_bind. */
+typedef struct {
+  int32_t n_virt, n_chirps, n_samples, n_theta, k_max, _pad;
+  float* spec;        /* [V*C*N_s*2] range+Doppler spectrum X */
+  float* power;       /* [n_theta*N_s] power map Pw */
+  int32_t* peak_cell; /* [k_max] linear cell a*N_s+k of each output point */
+  int32_t* n_points;  /* [1] number of points written (device) */
+  int32_t* argmax;    /* [1] cell of max Pw */
+  void* scratch;
+} sbr_pc_state;
+
+size_t sbr_pc_bytes(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar);
+sbr_status sbr_pc_bind(void* d_mem, size_t bytes, const sbr_radar_cfg* radar,
+                       const sbr_cfar_cfg* cfar, sbr_pc_state* out);
+
+/* d_points [k_max][4] = (x, y, z, w) ordered by (w desc, cell asc); rows at
+ * and beyond *n_points are zero. */
+sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* radar,
+                          const sbr_cfar_cfg* cfar, float* d_points, sbr_pc_state* state,
+                          sbr_stream stream);
+
+/* Adjoint: d_gpoints [k_max][4] -> d_gcube [V][C][N_s] complex (overwritten). */
+sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar,
+                              const sbr_pc_state* state, const float* d_gpoints,
+                              float* d_gcube, sbr_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Trace adjoint (Section 3.3, Eq. 13; interior derivative, Eq. 4-5)        */
+/* ------------------------------------------------------------------------ */
+
+/* Accumulates dL/dverts [nv][3] (added to d_gverts) from per-path gradients
+ * d_glen (dL/d path length, [V*path_cap]) and d_gamp (dL/dA) through the
+ * hit points, reflection directions and |d.n| of every bounce; triangle
+ * indices stay those of the forward trace (visibility is held fixed).
+ * d_verts are the vertices the scene was built from; d_ray_ids is the
+ * forward call's ray list (NULL when it traced the whole grid).  Gradients
+ * are added with float atomics (order-dependent in the last bits).
+ * max_bounces <= 8. */
+sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts, const sbr_radar_cfg* radar,
+                         const sbr_ray_grid* grid, const int32_t* d_ray_ids,
+                         const sbr_paths* paths, const float* d_glen, const float* d_gamp,
+                         float* d_gverts, sbr_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Reconstruction loss and optimiser (Section 3.4: Eq. 14 objective and the */
+/* Eq. 15 gradient step; the loss terms and Adam are this library's choice) */
+/* ------------------------------------------------------------------------ */
+
+/* Weighted squared Chamfer distance between predicted points d_pred
+ * [pred_cap][4] (x, y, z, w; the first *d_n_pred rows valid) and target
+ * points d_target [n_target][4]:
+ *   L = sum_i w_i |p_i - q_nn(i)|^2 / sum_i w_i + sum_j u_j |q_j - p_nn(j)|^2 / sum_j u_j.
+ * Writes *d_loss and d_gpred [pred_cap][4] = dL/d(x, y, z, w) (zero rows past
+ * the valid count).  Both sides at most 2048 points; deterministic. */
+sbr_status sbr_chamfer(const float* d_pred, const int32_t* d_n_pred, int32_t pred_cap,
+                       const float* d_target, int32_t n_target, float* d_loss, float* d_gpred,
+                       sbr_stream stream);
+
+/* Host helper: CSR vertex adjacency (unique undirected mesh edges) of a host
+ * face array.  With h_adj == NULL only *n_adj is computed (size query);
+ * h_off has nv + 1 entries. */
+sbr_status sbr_mesh_adjacency(const int32_t* h_faces, int32_t nt, int32_t nv, int32_t* h_off,
+                              int32_t* h_adj, int32_t adj_cap, int32_t* n_adj);
+
+size_t sbr_laplacian_ws_bytes(int32_t nv);
+/* Uniform Laplacian smoothness, weight * mean_i |v_i - mean_{j in N(i)} v_j|^2:
+ * ADDS the term to *d_loss and its gradient to d_gverts [nv][3]. */
+sbr_status sbr_laplacian(const float* d_verts, int32_t nv, const int32_t* d_off, const int32_t* d_adj,
+                         float weight, float* d_loss, float* d_gverts, void* d_ws, size_t ws_bytes,
+                         sbr_stream stream);
+
+/* One bias-corrected Adam step on n parameters in place.  *d_step (device)
+ * counts completed steps: the update uses t = *d_step + 1 and the call then
+ * increments it, so a captured CUDA graph of the loop stays correct. */
+sbr_status sbr_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v, int64_t n,
+                         int32_t* d_step, float lr, float beta1, float beta2, float eps, sbr_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBR_H_ */

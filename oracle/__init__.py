@@ -214,3 +214,48 @@ def simulate_cube(wl, ray_ids=None) -> tuple:
     tr = trace(wl.verts, wl.faces, wl.grid, wl.max_bounces, ray_ids)
     pa = paths(tr, wl.radar)
     return synthesize(pa["tau"], pa["amp"], wl.radar), tr, pa
+
+
+# ----------------------------------------------------------------------------
+# Frozen-structure evaluation (finite-difference references of the adjoints)
+# ----------------------------------------------------------------------------
+
+
+def trace_frozen(verts, faces, tr_ref: dict, grid) -> dict:
+    """Re-evaluate the geometry of ``tr_ref``'s rays in FP64 for new vertex positions
+    with every ray's triangle sequence held fixed (the visibility structure of the
+    reference trace).  Hit k is the intersection of the ray with the plane of its
+    recorded triangle (Moller-Trumbore's t), then specular reflection as in ``trace``.
+    The interior derivative of Eq. 4-5 is the derivative of this function."""
+    v = np.asarray(verts, dtype=np.float64)
+    f = np.asarray(faces)
+    tri = tr_ref["tri"]
+    n, K = tri.shape
+    o = np.repeat(np.asarray(grid.origin, np.float64)[None], n, axis=0)
+    d = tr_ref["din"][:, 0].copy()
+    hit = np.zeros((n, K, 3))
+    din = np.zeros((n, K, 3))
+    nrm = np.zeros((n, K, 3))
+    tuv = np.zeros((n, K, 3))
+    alive = np.ones(n, bool)
+    for k in range(K):
+        din[:, k] = d
+        ok = alive & (tri[:, k] >= 0)
+        alive = ok
+        if not ok.any():
+            continue
+        idx = np.where(ok)[0]
+        fa = f[tri[idx, k]]
+        a, b, c = v[fa[:, 0]], v[fa[:, 1]], v[fa[:, 2]]
+        N = np.cross(b - a, c - a)
+        t = (N * (a - o[idx])).sum(-1) / (N * d[idx]).sum(-1)
+        h = o[idx] + t[:, None] * d[idx]
+        nh = N / np.linalg.norm(N, axis=1, keepdims=True)
+        hit[idx, k] = h
+        nrm[idx, k] = nh
+        tuv[idx, k, 0] = t
+        dd = d[idx]
+        d[idx] = dd - 2.0 * (dd * nh).sum(-1, keepdims=True) * nh
+        o[idx] = h
+    return dict(tri=tri.copy(), tuv=tuv, hit=hit, din=din, nrm=nrm, omega=tr_ref["omega"].copy(),
+                flag=np.zeros(n, np.int32), ray_ids=tr_ref["ray_ids"], K=K)

@@ -32,27 +32,12 @@ clouds (Section 4).  The reading implemented here, step by step in FP64:
 """
 from __future__ import annotations
 
-import dataclasses
-
 import numpy as np
 
-from sbr_inputs import C_LIGHT
+from sbr_inputs import C_LIGHT, CfarParams
 
 
-@dataclasses.dataclass
-class CfarConfig:
-    n_theta: int = 64
-    guard: int = 2
-    train: int = 8
-    alpha_db: float = 12.0
-    floor_rel: float = 1e-4
-    beta: float = 0.5
-    w_min: float = 0.01
-    k_max: int = 2000
-
-    @property
-    def alpha(self) -> float:
-        return 10.0 ** (self.alpha_db / 10.0)
+CfarConfig = CfarParams  # the parameter set is an input shared with the CUDA path
 
 
 L_FLOOR = 1e-30

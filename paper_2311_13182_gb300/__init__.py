@@ -1,0 +1,17 @@
+"""GB300-native shooting-and-bouncing-rays FMCW radar simulator (arxiv 2311.13182 hot path).
+
+The compute path is libsbr (hand-written sm_103a CUDA behind the C ABI in
+``include/sbr.h``); this package builds it in-tree and marshals torch device
+memory and streams into it.  Importing the package does not build anything;
+``build.build()`` does, and ``_lib.load()`` raises if the library is missing.
+"""
+from . import build
+from ._lib import SbrError, load
+from .sim import (PHASE_FP64, PHASE_NAIVE, PHASE_SPLIT, Adjacency, PathBuffers, PcState, Scene, adam_step,
+                  cfar_struct, chamfer, grid_struct, laplacian, pointcloud, pointcloud_bwd, radar_struct,
+                  synth_ws_bytes, synthesize, synthesize_bwd, trace, trace_bwd)
+
+__all__ = ["build", "load", "SbrError", "Scene", "PathBuffers", "PcState", "Adjacency", "trace", "synthesize",
+           "synthesize_bwd", "pointcloud", "pointcloud_bwd", "trace_bwd", "chamfer", "laplacian", "adam_step",
+           "synth_ws_bytes", "radar_struct", "grid_struct", "cfar_struct", "PHASE_SPLIT", "PHASE_FP64",
+           "PHASE_NAIVE"]

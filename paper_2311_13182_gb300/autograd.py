@@ -1,0 +1,83 @@
+"""Differentiable simulator: vertices -> radar point cloud with hand-written backward.
+
+``Simulator`` owns the device buffers of one scene/radar/grid configuration and
+chains the library calls (Section 3.3, Eq. 13):
+
+  forward   scene update -> sbr_trace -> sbr_synthesize -> sbr_pointcloud
+  backward  sbr_pointcloud_bwd -> sbr_synthesize_bwd -> sbr_trace_bwd
+
+With ``recompute=True`` the path records of the forward trace are not kept:
+their buffer is released after synthesis and the backward re-traces the same
+vertices (triangle sequences are a deterministic function of the vertices),
+trading one trace for the path memory (R x K x (48 + 24 V) bytes).
+``SimulateFn`` exposes it as a torch.autograd.Function.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import sim
+
+
+class Simulator:
+    def __init__(self, faces: np.ndarray, nv: int, radar, grid, max_bounces: int, cfar, ray_ids=None,
+                 phase_mode: int = sim.PHASE_SPLIT, recompute: bool = False, device="cuda"):
+        self.faces_np = np.ascontiguousarray(faces, dtype=np.int32)
+        self.faces = torch.from_numpy(self.faces_np).to(device)
+        self.nv, self.radar, self.grid, self.K, self.cfar = nv, radar, grid, max_bounces, cfar
+        self.ray_ids = None if ray_ids is None else torch.as_tensor(np.asarray(ray_ids, np.int32)).to(device)
+        self.n_rays = grid.G * grid.G if ray_ids is None else int(self.ray_ids.shape[0])
+        self.mode, self.recompute, self.device = phase_mode, recompute, device
+        self.scene = None
+        self.paths = None if recompute else sim.PathBuffers(self.n_rays, max_bounces, radar.n_virt, device)
+        cap = self.n_rays * max_bounces
+        self.synth_ws = torch.empty(sim.synth_ws_bytes(radar, cap), dtype=torch.uint8, device=device)
+        self.cube = torch.empty((radar.n_virt, radar.n_chirps, radar.n_samples, 2), dtype=torch.float32,
+                                device=device)
+        self.points = torch.empty((cfar.k_max, 4), dtype=torch.float32, device=device)
+        self.state = sim.PcState(radar, cfar, device)
+        self.gcube = torch.empty_like(self.cube)
+
+    def _trace(self, verts):
+        if self.scene is None:
+            self.scene = sim.Scene(verts, self.faces)
+        else:
+            self.scene.update(verts)
+        paths = self.paths if self.paths is not None else sim.PathBuffers(self.n_rays, self.K, self.radar.n_virt,
+                                                                        self.device)
+        sim.trace(self.scene, self.radar, self.grid, self.K, self.ray_ids, out=paths)
+        return paths
+
+    def forward(self, verts: torch.Tensor):
+        paths = self._trace(verts)
+        sim.synthesize(paths, self.radar, self.mode, out=self.cube, ws=self.synth_ws)
+        sim.pointcloud(self.cube, self.radar, self.cfar, state=self.state, out=self.points)
+        return self.points, self.state.n_points_tensor()
+
+    def backward(self, verts: torch.Tensor, gpoints: torch.Tensor, gverts: torch.Tensor):
+        """Adds dL/dverts to gverts for upstream dL/dpoints [k_max, 4]."""
+        paths = self.paths if self.paths is not None else self._trace(verts)
+        sim.pointcloud_bwd(self.state, gpoints.contiguous(), out=self.gcube)
+        glen, gamp = sim.synthesize_bwd(paths, self.radar, self.gcube, ws=self.synth_ws)
+        sim.trace_bwd(self.scene, verts, self.radar, self.grid, paths, glen, gamp, self.ray_ids, gverts=gverts)
+        return gverts
+
+
+class SimulateFn(torch.autograd.Function):
+    """points = SimulateFn.apply(verts, simulator); rows past n_points are zero."""
+
+    @staticmethod
+    def forward(ctx, verts, simulator):
+        v = verts.detach().contiguous()
+        pts, _ = simulator.forward(v)
+        ctx.sim = simulator
+        ctx.save_for_backward(v)
+        return pts.clone()
+
+    @staticmethod
+    def backward(ctx, gpoints):
+        (v,) = ctx.saved_tensors
+        g = torch.zeros_like(v)
+        ctx.sim.backward(v, gpoints.float(), g)
+        return g, None

@@ -1,0 +1,97 @@
+// Shared helpers of libsbr: status/error plumbing, region carving, small vector math.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "sbr.h"
+
+namespace sbr {
+
+void set_error(const char* fmt, ...);
+
+constexpr double kC = 299792458.0;  // m/s
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kAlign = 256;
+
+// Carves sub-regions out of one caller-provided device allocation.  Used twice:
+// once with base = nullptr to size the region, once to bind pointers.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+  size_t bytes() const { return (off + kAlign - 1) / kAlign * kAlign; }
+};
+
+inline bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+
+// ---- device scan / sort utilities (scan_sort.cu) --------------------------
+
+// Exclusive scan of n int32 (n from host, or from *d_n when d_n != nullptr with
+// n as the capacity).  out[n_actual] receives the total.  scratch needs
+// scan_scratch_bytes(capacity).
+size_t scan_scratch_bytes(int64_t capacity);
+cudaError_t exclusive_scan(const int32_t* in, int32_t* out, int64_t n, const int32_t* d_n,
+                           void* scratch, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
+// keys (4-bit digits).  Ping-pongs between the two buffers; the sorted result
+// ends in keys[0]/vals[0].  n from host, or from *d_n (n = capacity).
+size_t sort_scratch_bytes(int64_t capacity);
+cudaError_t radix_sort_pairs(uint32_t* keys[2], int32_t* vals[2], int64_t n, const int32_t* d_n,
+                             int bits, void* scratch, cudaStream_t s);
+
+// Argument validation shared by the entry points (trace.cu).
+sbr_status check_radar(const sbr_radar_cfg* r, const char* who);
+sbr_status check_grid(const sbr_ray_grid* g, const char* who);
+
+}  // namespace sbr
+
+#define SBR_ARG(cond, ...)                          \
+  do {                                              \
+    if (!(cond)) {                                  \
+      ::sbr::set_error(__VA_ARGS__);                \
+      return SBR_ERR_INVALID_ARG;                   \
+    }                                               \
+  } while (0)
+
+#define SBR_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      ::sbr::set_error("%s failed: %s", #call, cudaGetErrorString(e_));      \
+      return SBR_ERR_CUDA;                                                    \
+    }                                                                         \
+  } while (0)
+
+// ---- small vector math ------------------------------------------------------
+
+struct d3 {
+  double x, y, z;
+};
+__host__ __device__ inline d3 mk3(double x, double y, double z) { return d3{x, y, z}; }
+__host__ __device__ inline d3 operator-(d3 a, d3 b) { return d3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__host__ __device__ inline d3 operator+(d3 a, d3 b) { return d3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__host__ __device__ inline d3 operator*(d3 a, double s) { return d3{a.x * s, a.y * s, a.z * s}; }
+__host__ __device__ inline double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__host__ __device__ inline d3 cross(d3 a, d3 b) {
+  return d3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+__host__ __device__ inline float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__host__ __device__ inline float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__host__ __device__ inline float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__host__ __device__ inline float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__host__ __device__ inline float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__host__ __device__ inline float3 cross(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ inline float l1(float3 a) { return fabsf(a.x) + fabsf(a.y) + fabsf(a.z); }

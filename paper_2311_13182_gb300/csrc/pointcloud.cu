@@ -1,0 +1,664 @@
+// Radar point cloud from the IF cube: the signal-processing map T of Eq. 16
+// (Section 3.4), and its adjoint.
+//
+// The paper leaves T open ("a signal processing algorithm" producing a spatial
+// image; Section 4 shows radar point clouds).  This library reads it as:
+//   X = FFT_chirp(FFT_sample(cube))                     range and Doppler spectra
+//   Y[a,d,k] = sum_v W[a,v] X[v,d,k],  W = e^{+j 2 pi x_v u_a / lambda_c},
+//              u_a = -1 + 2a/N_theta, lambda_c = c / (f_c + B/2)      angle DFT
+//   Pw[a,k] = sum_d |Y[a,d,k]|^2                                     power map
+//   N[a,k]  = mean of Pw over `train` cells each side beyond `guard` (range) CA-CFAR
+//   w = sigmoid((ln Pw - ln(alpha N + floor_rel max Pw)) / beta)     soft detection
+//   peaks: 3x3 local maxima above the floor (ties: lower cell index), w >= w_min,
+//   ordered by (w desc, cell asc), at most k_max;
+//   sub-bin 3-point parabola on ln Pw per axis (clamped to +-1/2 bin);
+//   point = (r u, 0, r sqrt(1 - u^2)), r = (k + dk) c / (2B).
+// The adjoint routes dL/d(point) and dL/dw to dPw (sparse: the peak, its
+// refine neighbours, its CFAR training cells and the argmax cell), then
+// dY = 2 Y dPw, dX = W^H dY, and the two inverse FFTs (unnormalised: the
+// adjoint of a forward DFT).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace sbr {
+namespace {
+
+constexpr float kCf = 299792458.0f;
+
+__device__ inline float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ inline int bitrev(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }
+
+// In-place radix-2 DIT FFT of n points held in shared memory (already in
+// bit-reversed order), all threads of the block cooperating.  sign = -1 forward.
+__device__ void smem_fft(float2* s, int n, int logn, float sign, int lanes, int lane) {
+  for (int len = 2; len <= n; len <<= 1) {
+    const int half = len >> 1;
+    for (int u = lane; u < (n >> 1); u += lanes) {
+      const int grp = u / half, j = u - grp * half;
+      const int i0 = grp * len + j, i1 = i0 + half;
+      float sn, cs;
+      sincospif(sign * 2.f * (float)j / (float)len, &sn, &cs);
+      const float2 t = cmul(s[i1], make_float2(cs, sn));
+      const float2 a = s[i0];
+      s[i0] = make_float2(a.x + t.x, a.y + t.y);
+      s[i1] = make_float2(a.x - t.x, a.y - t.y);
+    }
+    __syncthreads();
+  }
+}
+
+// FFT along the contiguous last axis: one CTA per row of n points.
+__global__ void k_fft_rows(const float2* __restrict__ in, float2* __restrict__ out, int n, int logn,
+                           float sign) {
+  extern __shared__ float2 s[];
+  const size_t row = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s[bitrev(i, logn)] = in[row * n + i];
+  __syncthreads();
+  smem_fft(s, n, logn, sign, blockDim.x, threadIdx.x);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) out[row * n + i] = s[i];
+}
+
+constexpr int kColTile = 16;
+
+// FFT along the chirp axis of [V][C][N_s]: one CTA per (v, 16 consecutive k).
+__global__ void k_fft_cols(float2* __restrict__ x, int C, int logc, int Ns, float sign) {
+  extern __shared__ float2 s[];  // [kColTile][C]
+  const int tiles = Ns / kColTile;
+  const int v = blockIdx.x / tiles, k0 = (blockIdx.x - v * tiles) * kColTile;
+  float2* base = x + (size_t)v * C * Ns + k0;
+  for (int i = threadIdx.x; i < C * kColTile; i += blockDim.x) {
+    const int c = i / kColTile, kk = i - c * kColTile;
+    s[kk * C + bitrev(c, logc)] = base[(size_t)c * Ns + kk];
+  }
+  __syncthreads();
+  for (int len = 2; len <= C; len <<= 1) {
+    const int half = len >> 1;
+    for (int u = threadIdx.x; u < kColTile * (C >> 1); u += blockDim.x) {
+      const int col = u / (C >> 1), w = u - col * (C >> 1);
+      const int grp = w / half, j = w - grp * half;
+      float2* sc = s + col * C;
+      const int i0 = grp * len + j, i1 = i0 + half;
+      float sn, cs;
+      sincospif(sign * 2.f * (float)j / (float)len, &sn, &cs);
+      const float2 t = cmul(sc[i1], make_float2(cs, sn));
+      const float2 a = sc[i0];
+      sc[i0] = make_float2(a.x + t.x, a.y + t.y);
+      sc[i1] = make_float2(a.x - t.x, a.y - t.y);
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < C * kColTile; i += blockDim.x) {
+    const int c = i / kColTile, kk = i - c * kColTile;
+    base[(size_t)c * Ns + kk] = s[kk * C + c];
+  }
+}
+
+// x_v / lambda_c per virtual antenna, passed by value (no host-to-device copy,
+// so the entry points can be captured into CUDA graphs).
+struct Steer {
+  float xl[SBR_MAX_VIRT];
+};
+
+// Steering matrix W[a][v] into shared memory.
+__device__ inline void load_w(float2* sw, const Steer& xl, int A, int V) {
+  for (int i = threadIdx.x; i < A * V; i += blockDim.x) {
+    const int a = i / V, v = i - a * V;
+    const float u = -1.f + 2.f * (float)a / (float)A;
+    float sn, cs;
+    sincospif(2.f * xl.xl[v] * u, &sn, &cs);
+    sw[i] = make_float2(cs, sn);
+  }
+}
+
+constexpr int kKT = 32;  // ranges per CTA in the angle kernels
+
+// Partial power map over one group of Doppler bins: part[g][a][k] = sum_{d in g} |Y|^2.
+template <int APT>
+__global__ void __launch_bounds__(256) k_angle_power(const float2* __restrict__ X,
+                                                     const Steer xl, int V, int C,
+                                                     int Ns, int dpg, float* __restrict__ part) {
+  extern __shared__ float2 sm[];
+  constexpr int A = 8 * APT;
+  float2* sw = sm;                // [A][V]
+  float2* sx = sm + A * V;        // [V][kKT]
+  load_w(sw, xl, A, V);
+  const int kk = threadIdx.x & (kKT - 1), ag = threadIdx.x >> 5;
+  const int k0 = blockIdx.x * kKT, g = blockIdx.y;
+  float acc[APT];
+#pragma unroll
+  for (int i = 0; i < APT; ++i) acc[i] = 0.f;
+  for (int d = g * dpg; d < min(C, (g + 1) * dpg); ++d) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < V * kKT; i += blockDim.x) {
+      const int v = i / kKT, q = i - v * kKT;
+      sx[i] = X[((size_t)v * C + d) * Ns + k0 + q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < APT; ++i) {
+      const int a = ag * APT + i;
+      float yr = 0.f, yi = 0.f;
+      for (int v = 0; v < V; ++v) {
+        const float2 w = sw[a * V + v], x = sx[v * kKT + kk];
+        yr = fmaf(w.x, x.x, fmaf(-w.y, x.y, yr));
+        yi = fmaf(w.x, x.y, fmaf(w.y, x.x, yi));
+      }
+      acc[i] = fmaf(yr, yr, fmaf(yi, yi, acc[i]));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < APT; ++i) part[((size_t)g * A + ag * APT + i) * Ns + k0 + kk] = acc[i];
+}
+
+__global__ void k_power_reduce(const float* __restrict__ part, int groups, int cells,
+                               float* __restrict__ Pw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cells) return;
+  float s = 0.f;
+  for (int g = 0; g < groups; ++g) s += part[(size_t)g * cells + i];
+  Pw[i] = s;
+}
+
+// argmax of Pw (lowest index among equal maxima) with one CTA.
+__global__ void k_argmax(const float* __restrict__ Pw, int cells, int32_t* __restrict__ out) {
+  __shared__ unsigned long long red[32];
+  unsigned long long best = 0ull;
+  for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+    const unsigned long long key =
+        ((unsigned long long)__float_as_uint(fmaxf(Pw[i], 0.f)) << 32) | (0xffffffffu - (unsigned)i);
+    best = key > best ? key : best;
+  }
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+    best = y > best ? y : best;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    best = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ull;
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+      best = y > best ? y : best;
+    }
+    if (threadIdx.x == 0) *out = (int32_t)(0xffffffffu - (unsigned)(best & 0xffffffffull));
+  }
+}
+
+struct CfarArg {
+  int A, Ns, guard, train;
+  float alpha, floor_rel, beta, w_min;
+};
+
+__device__ inline float lnp(float p) { return logf(fmaxf(p, 1e-30f)); }
+
+__device__ inline void noise_cells(const CfarArg& c, int k, int& lo0, int& lo1, int& hi0, int& hi1) {
+  lo0 = max(k - c.guard - c.train, 0);
+  lo1 = k - c.guard;  // exclusive
+  hi0 = k + c.guard + 1;
+  hi1 = min(k + c.guard + c.train + 1, c.Ns);  // exclusive
+}
+
+__device__ inline float cfar_noise(const float* __restrict__ row, const CfarArg& c, int k, int* cnt) {
+  int lo0, lo1, hi0, hi1;
+  noise_cells(c, k, lo0, lo1, hi0, hi1);
+  float s = 0.f;
+  int n = 0;
+  for (int j = lo0; j < lo1; ++j, ++n) s += row[j];
+  for (int j = hi0; j < hi1; ++j, ++n) s += row[j];
+  *cnt = n;
+  return n ? s / (float)n : 0.f;
+}
+
+__device__ inline float soft_w(const float* __restrict__ Pw, const CfarArg& c, int a, int k, float floor_v,
+                               float* zout, float* nout, int* cnt) {
+  const float* row = Pw + (size_t)a * c.Ns;
+  const float N = cfar_noise(row, c, k, cnt);
+  const float z = (lnp(row[k]) - logf(c.alpha * N + floor_v)) / c.beta;
+  if (zout) *zout = z;
+  if (nout) *nout = N;
+  return 1.f / (1.f + expf(-z));
+}
+
+__global__ void k_detect(const float* __restrict__ Pw, CfarArg c, const int32_t* __restrict__ amax,
+                         int32_t* __restrict__ flag, uint32_t* __restrict__ key) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c.A * c.Ns) return;
+  const int a = i / c.Ns, k = i - a * c.Ns;
+  const float p = Pw[i];
+  const float floor_v = c.floor_rel * Pw[*amax];
+  bool peak = p > floor_v;
+  for (int da = -1; da <= 1 && peak; ++da)
+    for (int dk = -1; dk <= 1; ++dk) {
+      if (da == 0 && dk == 0) continue;
+      const int aa = a + da, kk = k + dk;
+      if (aa < 0 || aa >= c.A || kk < 0 || kk >= c.Ns) continue;
+      const float q = Pw[(size_t)aa * c.Ns + kk];
+      const bool earlier = da < 0 || (da == 0 && dk < 0);
+      if (earlier ? !(p > q) : !(p >= q)) {
+        peak = false;
+        break;
+      }
+    }
+  float w = 0.f;
+  if (peak) {
+    int cnt;
+    w = soft_w(Pw, c, a, k, floor_v, nullptr, nullptr, &cnt);
+  }
+  const bool keep = peak && w >= c.w_min;
+  flag[i] = keep ? 1 : 0;
+  key[i] = keep ? 0xffffffffu - __float_as_uint(w) : 0xffffffffu;
+}
+
+__global__ void k_compact(const int32_t* __restrict__ flag, const int32_t* __restrict__ off,
+                          const uint32_t* __restrict__ key, int cells, uint32_t* __restrict__ ko,
+                          int32_t* __restrict__ vo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cells || !flag[i]) return;
+  ko[off[i]] = key[i];
+  vo[off[i]] = i;
+}
+
+__device__ inline float refine(float lm, float l0, float lp, float* dm, float* d0, float* dp) {
+  const float den = lm - 2.f * l0 + lp;
+  *dm = *d0 = *dp = 0.f;
+  if (!(den < 0.f)) return 0.f;
+  const float d = 0.5f * (lm - lp) / den;
+  if (d <= -0.5f) return -0.5f;
+  if (d >= 0.5f) return 0.5f;
+  const float id2 = 1.f / (den * den);
+  *dm = (lp - l0) * id2;
+  *d0 = (lm - lp) * id2;
+  *dp = (l0 - lm) * id2;
+  return d;
+}
+
+struct PointArg {
+  CfarArg c;
+  int k_max;
+  float range_bin;  // c / (2B)
+};
+
+__global__ void k_points(const float* __restrict__ Pw, PointArg pa, const int32_t* __restrict__ amax,
+                         const int32_t* __restrict__ cand, const int32_t* __restrict__ n_cand,
+                         float4* __restrict__ pts, int32_t* __restrict__ cell_out,
+                         int32_t* __restrict__ n_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = min(*n_cand, pa.k_max);
+  if (i == 0) *n_out = n;
+  if (i >= pa.k_max) return;
+  if (i >= n) {
+    pts[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    cell_out[i] = -1;
+    return;
+  }
+  const CfarArg& c = pa.c;
+  const int cell = cand[i];
+  const int a = cell / c.Ns, k = cell - a * c.Ns;
+  const float floor_v = c.floor_rel * Pw[*amax];
+  int cnt;
+  const float w = soft_w(Pw, c, a, k, floor_v, nullptr, nullptr, &cnt);
+  const float* row = Pw + (size_t)a * c.Ns;
+  const float l0 = lnp(row[k]);
+  float t0, t1, t2, dk = 0.f, da = 0.f;
+  if (k > 0 && k < c.Ns - 1) dk = refine(lnp(row[k - 1]), l0, lnp(row[k + 1]), &t0, &t1, &t2);
+  if (a > 0 && a < c.A - 1)
+    da = refine(lnp(Pw[(size_t)(a - 1) * c.Ns + k]), l0, lnp(Pw[(size_t)(a + 1) * c.Ns + k]), &t0, &t1, &t2);
+  const float r = ((float)k + dk) * pa.range_bin;
+  const float u = fminf(fmaxf(-1.f + 2.f * ((float)a + da) / (float)c.A, -1.f), 1.f);
+  pts[i] = make_float4(r * u, 0.f, r * sqrtf(fmaxf(1.f - u * u, 0.f)), w);
+  cell_out[i] = cell;
+}
+
+// ---- adjoint ----------------------------------------------------------------
+
+__device__ inline void add_dl(float* dPw, const float* Pw, size_t cell, float dl) {
+  const float p = Pw[cell];
+  if (p > 1e-30f && dl != 0.f) atomicAdd(&dPw[cell], dl / p);
+}
+
+__global__ void k_points_bwd(const float* __restrict__ Pw, PointArg pa, const int32_t* __restrict__ amax,
+                             const int32_t* __restrict__ cells, const int32_t* __restrict__ n_pts,
+                             const float4* __restrict__ gpts, float* __restrict__ dPw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *n_pts) return;
+  const CfarArg& c = pa.c;
+  const int cell = cells[i];
+  const int a = cell / c.Ns, k = cell - a * c.Ns;
+  const int am = *amax;
+  const float floor_v = c.floor_rel * Pw[am];
+  const float4 g = gpts[i];
+  float z, N;
+  int cnt;
+  const float w = soft_w(Pw, c, a, k, floor_v, &z, &N, &cnt);
+  // soft weight: w = sigmoid(z), z = (l0 - ln(alpha N + F)) / beta
+  const float gz = g.w * w * (1.f - w) / c.beta;
+  const float den = c.alpha * N + floor_v;
+  float dl0 = gz;
+  const float dN = -gz * c.alpha / den;
+  const float dF = -gz / den;
+  atomicAdd(&dPw[am], dF * c.floor_rel);
+  if (cnt > 0) {
+    int lo0, lo1, hi0, hi1;
+    noise_cells(c, k, lo0, lo1, hi0, hi1);
+    const float e = dN / (float)cnt;
+    for (int j = lo0; j < lo1; ++j) atomicAdd(&dPw[(size_t)a * c.Ns + j], e);
+    for (int j = hi0; j < hi1; ++j) atomicAdd(&dPw[(size_t)a * c.Ns + j], e);
+  }
+  // position: r = (k + dk) bin, u = -1 + 2 (a + da) / A, p = (r u, 0, r sqrt(1 - u^2))
+  const float* row = Pw + (size_t)a * c.Ns;
+  const float l0 = lnp(row[k]);
+  float rm = 0.f, r0 = 0.f, rp = 0.f, am_ = 0.f, a0 = 0.f, ap = 0.f, dk = 0.f, da = 0.f;
+  if (k > 0 && k < c.Ns - 1) dk = refine(lnp(row[k - 1]), l0, lnp(row[k + 1]), &rm, &r0, &rp);
+  if (a > 0 && a < c.A - 1)
+    da = refine(lnp(Pw[(size_t)(a - 1) * c.Ns + k]), l0, lnp(Pw[(size_t)(a + 1) * c.Ns + k]), &am_, &a0, &ap);
+  const float r = ((float)k + dk) * pa.range_bin;
+  const float ur = -1.f + 2.f * ((float)a + da) / (float)c.A;
+  const float u = fminf(fmaxf(ur, -1.f), 1.f);
+  const float sq = sqrtf(fmaxf(1.f - u * u, 0.f));
+  const float dr = g.x * u + g.z * sq;
+  const float du = (ur > -1.f && ur < 1.f && sq > 0.f) ? (g.x * r - g.z * r * u / sq) : 0.f;
+  const float ddk = dr * pa.range_bin;
+  const float dda = du * 2.f / (float)c.A;
+  dl0 += ddk * r0 + dda * a0;
+  add_dl(dPw, Pw, (size_t)cell, dl0);
+  if (k > 0 && k < c.Ns - 1) {
+    add_dl(dPw, Pw, (size_t)cell - 1, ddk * rm);
+    add_dl(dPw, Pw, (size_t)cell + 1, ddk * rp);
+  }
+  if (a > 0 && a < c.A - 1) {
+    add_dl(dPw, Pw, (size_t)cell - c.Ns, dda * am_);
+    add_dl(dPw, Pw, (size_t)cell + c.Ns, dda * ap);
+  }
+}
+
+// dX[v,d,k] = sum_a conj(W[a,v]) 2 Y[a,d,k] dPw[a,k], Y recomputed from X.
+template <int APT>
+__global__ void __launch_bounds__(256) k_angle_bwd(const float2* __restrict__ X,
+                                                   const Steer xl,
+                                                   const float* __restrict__ dPw, int V, int C,
+                                                   int Ns, float2* __restrict__ dX) {
+  extern __shared__ float2 sm[];
+  constexpr int A = 8 * APT;
+  float2* sw = sm;               // [A][V]
+  float2* sx = sw + A * V;       // [V][kKT]
+  float2* sg = sx + V * kKT;     // [A][kKT]
+  load_w(sw, xl, A, V);
+  const int kk = threadIdx.x & (kKT - 1), ag = threadIdx.x >> 5;
+  const int k0 = blockIdx.x * kKT, d = blockIdx.y;
+  for (int i = threadIdx.x; i < V * kKT; i += blockDim.x) {
+    const int v = i / kKT, q = i - v * kKT;
+    sx[i] = X[((size_t)v * C + d) * Ns + k0 + q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < APT; ++i) {
+    const int a = ag * APT + i;
+    float yr = 0.f, yi = 0.f;
+    for (int v = 0; v < V; ++v) {
+      const float2 w = sw[a * V + v], x = sx[v * kKT + kk];
+      yr = fmaf(w.x, x.x, fmaf(-w.y, x.y, yr));
+      yi = fmaf(w.x, x.y, fmaf(w.y, x.x, yi));
+    }
+    const float s = 2.f * dPw[(size_t)a * Ns + k0 + kk];
+    sg[a * kKT + kk] = make_float2(s * yr, s * yi);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < V * kKT; i += blockDim.x) {
+    const int v = i / kKT, q = i - v * kKT;
+    float gr = 0.f, gi = 0.f;
+    for (int a = 0; a < A; ++a) {
+      const float2 w = sw[a * V + v], g = sg[a * kKT + q];  // conj(w) * g
+      gr = fmaf(w.x, g.x, fmaf(w.y, g.y, gr));
+      gi = fmaf(w.x, g.y, fmaf(-w.y, g.x, gi));
+    }
+    dX[((size_t)v * C + d) * Ns + k0 + q] = make_float2(gr, gi);
+  }
+}
+
+inline int ilog2(int x) {
+  int l = 0;
+  while ((1 << l) < x) ++l;
+  return l;
+}
+
+struct Layout {
+  float2* spec;
+  float* power;
+  int32_t* peak_cell;
+  int32_t* n_points;
+  int32_t* argmax;
+  float* part;
+  int32_t* flag;
+  int32_t* off;
+  uint32_t* key;
+  uint32_t* skeys[2];
+  int32_t* svals[2];
+  void* scan_scr;
+  void* sort_scr;
+  float* dpw;
+  int groups;
+};
+
+inline int dgroups(int C) { return C >= 8 ? C / 8 : 1; }
+
+size_t pc_layout(Layout* L, void* mem, const sbr_radar_cfg* r, const sbr_cfar_cfg* f) {
+  Carver c(mem);
+  const int V = r->n_tx * r->n_rx, C = r->n_chirps, Ns = r->n_samples, A = f->n_theta;
+  const int64_t cells = (int64_t)A * Ns;
+  L->groups = dgroups(C);
+  L->spec = c.take<float2>((size_t)V * C * Ns);
+  L->power = c.take<float>(cells);
+  L->peak_cell = c.take<int32_t>(f->k_max > 0 ? f->k_max : 1);
+  L->n_points = c.take<int32_t>(1);
+  L->argmax = c.take<int32_t>(1);
+  L->part = c.take<float>((size_t)L->groups * cells);
+  L->flag = c.take<int32_t>(cells);
+  L->off = c.take<int32_t>(cells + 1);
+  L->key = c.take<uint32_t>(cells);
+  L->skeys[0] = c.take<uint32_t>(cells);
+  L->skeys[1] = c.take<uint32_t>(cells);
+  L->svals[0] = c.take<int32_t>(cells);
+  L->svals[1] = c.take<int32_t>(cells);
+  L->scan_scr = c.take<char>(scan_scratch_bytes(cells));
+  L->sort_scr = c.take<char>(sort_scratch_bytes(cells));
+  L->dpw = c.take<float>(cells);
+  return c.bytes();
+}
+
+sbr_status check_cfar(const sbr_cfar_cfg* f, const sbr_radar_cfg* r, const char* who) {
+  SBR_ARG(f != nullptr, "%s: cfar is NULL", who);
+  const int V = r->n_tx * r->n_rx;
+  SBR_ARG(f->n_theta >= 8 && f->n_theta <= 256 && (f->n_theta & (f->n_theta - 1)) == 0,
+          "%s: n_theta=%d must be a power of two in [8, 256]", who, f->n_theta);
+  SBR_ARG(f->n_theta * V <= 4096, "%s: n_theta * V = %d above 4096", who, f->n_theta * V);
+  SBR_ARG(f->guard >= 0 && f->train >= 0 && f->guard + f->train < 4096, "%s: bad guard/train", who);
+  SBR_ARG(f->k_max >= 1 && f->k_max <= (1 << 20), "%s: k_max=%d outside [1, 2^20]", who, f->k_max);
+  SBR_ARG(f->alpha > 0.f && f->beta > 0.f && f->floor_rel >= 0.f, "%s: alpha, beta > 0 needed", who);
+  return SBR_OK;
+}
+
+// x_v / lambda_c per virtual antenna, uploaded into the state's small table.
+Steer steering_table(const sbr_radar_cfg* r) {
+  Steer s{};
+  const double lam = kC / (r->f0 + 0.5 * r->bandwidth);
+  for (int t = 0; t < r->n_tx; ++t)
+    for (int q = 0; q < r->n_rx; ++q) s.xl[t * r->n_rx + q] = (float)((r->tx[t][0] + r->rx[q][0]) / lam);
+  return s;
+}
+
+template <int APT>
+void launch_angle_power(const float2* X, const Steer& xl, int V, int C, int Ns, int groups, float* part,
+                        cudaStream_t st) {
+  const int A = 8 * APT;
+  const size_t sm = sizeof(float2) * ((size_t)A * V + (size_t)V * kKT);
+  dim3 grid(Ns / kKT, groups);
+  k_angle_power<APT><<<grid, 256, sm, st>>>(X, xl, V, C, Ns, (C + groups - 1) / groups, part);
+}
+
+template <int APT>
+void launch_angle_bwd(const float2* X, const Steer& xl, const float* dpw, int V, int C, int Ns, float2* dX,
+                      cudaStream_t st) {
+  const int A = 8 * APT;
+  const size_t sm = sizeof(float2) * ((size_t)A * V + (size_t)V * kKT + (size_t)A * kKT);
+  dim3 grid(Ns / kKT, C);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_angle_bwd<APT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_angle_bwd<APT><<<grid, 256, sm, st>>>(X, xl, dpw, V, C, Ns, dX);
+}
+
+cudaError_t fft_rows(const float2* in, float2* out, int rows, int n, float sign, cudaStream_t st) {
+  const int threads = n / 2 < 256 ? (n / 2 < 32 ? 32 : n / 2) : 256;
+  const size_t sm = sizeof(float2) * n;
+  k_fft_rows<<<rows, threads, sm, st>>>(in, out, n, ilog2(n), sign);
+  return cudaGetLastError();
+}
+
+cudaError_t fft_cols(float2* x, int V, int C, int Ns, float sign, cudaStream_t st) {
+  if (C == 1) return cudaSuccess;
+  const size_t sm = sizeof(float2) * C * kColTile;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_fft_cols<<<V * (Ns / kColTile), 256, sm, st>>>(x, C, ilog2(C), Ns, sign);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace sbr
+
+using namespace sbr;
+
+extern "C" size_t sbr_pc_bytes(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar) {
+  if (check_radar(radar, "sbr_pc_bytes") != SBR_OK || check_cfar(cfar, radar, "sbr_pc_bytes") != SBR_OK)
+    return 0;
+  Layout L;
+  return pc_layout(&L, nullptr, radar, cfar);
+}
+
+extern "C" sbr_status sbr_pc_bind(void* d_mem, size_t bytes, const sbr_radar_cfg* radar,
+                                  const sbr_cfar_cfg* cfar, sbr_pc_state* out) {
+  SBR_ARG(out != nullptr, "sbr_pc_bind: out is NULL");
+  sbr_status rs = check_radar(radar, "sbr_pc_bind");
+  if (rs != SBR_OK) return rs;
+  rs = check_cfar(cfar, radar, "sbr_pc_bind");
+  if (rs != SBR_OK) return rs;
+  SBR_ARG(d_mem && aligned256(d_mem), "sbr_pc_bind: d_mem NULL or not 256-byte aligned");
+  Layout L;
+  const size_t need = pc_layout(&L, nullptr, radar, cfar);
+  if (bytes < need) {
+    set_error("sbr_pc_bind: region of %zu bytes, %zu needed", bytes, need);
+    return SBR_ERR_OOM;
+  }
+  pc_layout(&L, d_mem, radar, cfar);
+  out->n_virt = radar->n_tx * radar->n_rx;
+  out->n_chirps = radar->n_chirps;
+  out->n_samples = radar->n_samples;
+  out->n_theta = cfar->n_theta;
+  out->k_max = cfar->k_max;
+  out->spec = reinterpret_cast<float*>(L.spec);
+  out->power = L.power;
+  out->peak_cell = L.peak_cell;
+  out->n_points = L.n_points;
+  out->argmax = L.argmax;
+  out->scratch = d_mem;
+  return SBR_OK;
+}
+
+namespace {
+sbr_status state_layout(const sbr_pc_state* s, const sbr_radar_cfg* r, const sbr_cfar_cfg* f, Layout* L,
+                        const char* who) {
+  SBR_ARG(s && s->scratch, "%s: state is NULL or unbound", who);
+  SBR_ARG(s->n_virt == r->n_tx * r->n_rx && s->n_chirps == r->n_chirps && s->n_samples == r->n_samples &&
+              s->n_theta == f->n_theta && s->k_max == f->k_max,
+          "%s: state bound for another configuration", who);
+  pc_layout(L, s->scratch, r, f);
+  return SBR_OK;
+}
+}  // namespace
+
+extern "C" sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* radar,
+                                     const sbr_cfar_cfg* cfar, float* d_points, sbr_pc_state* state,
+                                     sbr_stream stream) {
+  SBR_ARG(d_cube && d_points, "sbr_pointcloud: NULL cube or points");
+  sbr_status rs = check_radar(radar, "sbr_pointcloud");
+  if (rs != SBR_OK) return rs;
+  rs = check_cfar(cfar, radar, "sbr_pointcloud");
+  if (rs != SBR_OK) return rs;
+  Layout L;
+  rs = state_layout(state, radar, cfar, &L, "sbr_pointcloud");
+  if (rs != SBR_OK) return rs;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int V = radar->n_tx * radar->n_rx, C = radar->n_chirps, Ns = radar->n_samples, A = cfar->n_theta;
+  const int cells = A * Ns;
+  const Steer xl = steering_table(radar);
+  // 1-2: range FFT over samples, Doppler FFT over chirps
+  SBR_CUDA(fft_rows(reinterpret_cast<const float2*>(d_cube), L.spec, V * C, Ns, -1.f, st));
+  SBR_CUDA(fft_cols(L.spec, V, C, Ns, -1.f, st));
+  // 3-4: angle DFT and power map (partials per Doppler group, fixed-order sum)
+  switch (A / 8) {
+    case 1: launch_angle_power<1>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
+    case 2: launch_angle_power<2>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
+    case 4: launch_angle_power<4>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
+    case 8: launch_angle_power<8>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
+    case 16: launch_angle_power<16>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
+    case 32: launch_angle_power<32>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
+    default: set_error("sbr_pointcloud: n_theta=%d unsupported", A); return SBR_ERR_UNSUPPORTED;
+  }
+  SBR_CUDA(cudaGetLastError());
+  k_power_reduce<<<(cells + 255) / 256, 256, 0, st>>>(L.part, L.groups, cells, L.power);
+  k_argmax<<<1, 1024, 0, st>>>(L.power, cells, L.argmax);
+  // 5-7: soft CFAR, peaks, compaction in cell order, stable sort by weight
+  CfarArg ca{A, Ns, cfar->guard, cfar->train, cfar->alpha, cfar->floor_rel, cfar->beta, cfar->w_min};
+  k_detect<<<(cells + 255) / 256, 256, 0, st>>>(L.power, ca, L.argmax, L.flag, L.key);
+  SBR_CUDA(exclusive_scan(L.flag, L.off, cells, nullptr, L.scan_scr, st));
+  k_compact<<<(cells + 255) / 256, 256, 0, st>>>(L.flag, L.off, L.key, cells, L.skeys[0], L.svals[0]);
+  SBR_CUDA(radix_sort_pairs(L.skeys, L.svals, cells, L.off + cells, 32, L.sort_scr, st));
+  // 8-9: refine and emit points
+  PointArg pa{ca, cfar->k_max, (float)(kC / (2.0 * radar->bandwidth))};
+  k_points<<<(cfar->k_max + 255) / 256, 256, 0, st>>>(L.power, pa, L.argmax, L.svals[0], L.off + cells,
+                                                       reinterpret_cast<float4*>(d_points), L.peak_cell,
+                                                       L.n_points);
+  SBR_CUDA(cudaGetLastError());
+  return SBR_OK;
+}
+
+extern "C" sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar,
+                                         const sbr_pc_state* state, const float* d_gpoints,
+                                         float* d_gcube, sbr_stream stream) {
+  SBR_ARG(d_gpoints && d_gcube, "sbr_pointcloud_bwd: NULL gradient");
+  sbr_status rs = check_radar(radar, "sbr_pointcloud_bwd");
+  if (rs != SBR_OK) return rs;
+  rs = check_cfar(cfar, radar, "sbr_pointcloud_bwd");
+  if (rs != SBR_OK) return rs;
+  Layout L;
+  rs = state_layout(state, radar, cfar, &L, "sbr_pointcloud_bwd");
+  if (rs != SBR_OK) return rs;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int V = radar->n_tx * radar->n_rx, C = radar->n_chirps, Ns = radar->n_samples, A = cfar->n_theta;
+  const int cells = A * Ns;
+  const Steer xl = steering_table(radar);
+  SBR_CUDA(cudaMemsetAsync(L.dpw, 0, sizeof(float) * cells, st));
+  CfarArg ca{A, Ns, cfar->guard, cfar->train, cfar->alpha, cfar->floor_rel, cfar->beta, cfar->w_min};
+  PointArg pa{ca, cfar->k_max, (float)(kC / (2.0 * radar->bandwidth))};
+  k_points_bwd<<<(cfar->k_max + 255) / 256, 256, 0, st>>>(L.power, pa, L.argmax, L.peak_cell, L.n_points,
+                                                           reinterpret_cast<const float4*>(d_gpoints), L.dpw);
+  float2* g = reinterpret_cast<float2*>(d_gcube);
+  switch (A / 8) {
+    case 1: launch_angle_bwd<1>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    case 2: launch_angle_bwd<2>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    case 4: launch_angle_bwd<4>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    case 8: launch_angle_bwd<8>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    case 16: launch_angle_bwd<16>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    case 32: launch_angle_bwd<32>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    default: set_error("sbr_pointcloud_bwd: n_theta=%d unsupported", A); return SBR_ERR_UNSUPPORTED;
+  }
+  SBR_CUDA(cudaGetLastError());
+  // adjoint of the forward DFTs: unnormalised inverse transforms, in place
+  SBR_CUDA(fft_cols(g, V, C, Ns, +1.f, st));
+  SBR_CUDA(fft_rows(g, g, V * C, Ns, +1.f, st));
+  return SBR_OK;
+}

@@ -1,0 +1,33 @@
+// Scene layout shared by the LBVH builder, the traversal and the trace adjoint.
+#pragma once
+
+#include "common.cuh"
+
+namespace sbr {
+
+// BVH2 node with both child boxes stored in the parent (64 B, four float4
+// loads).  child >= 0: internal node index; child < 0: leaf ~child = position
+// of the triangle in sorted (Morton) order.
+struct __align__(16) Node {
+  float4 lxy;   // left  lo.x hi.x lo.y hi.y
+  float4 rxy;   // right lo.x hi.x lo.y hi.y
+  float4 lrz;   // left lo.z hi.z, right lo.z hi.z
+  int4 child;   // left, right, unused, unused
+};
+
+}  // namespace sbr
+
+struct sbr_scene {
+  int32_t nv, nt;
+  float4* tris;        // [nt*3] sorted: (v0, original id bits), (v1, 0), (v2, 0)
+  sbr::Node* nodes;    // [max(nt-1, 1)]
+  int32_t* parent;     // [2nt-1]: internal 0..nt-2, leaves nt-1..2nt-2
+  uint32_t* visits;    // [max(nt-1,1)] refit arrival counters
+  uint32_t* keys[2];   // [nt] Morton codes (sort ping-pong)
+  int32_t* vals[2];    // [nt] triangle ids (sort ping-pong)
+  int32_t* faces;      // [nt*3] copy of the topology
+  int32_t* bounds;     // [8] centroid box as ordered ints + pad
+  int32_t* err;        // [1] device error word (bit 0: face index out of range)
+  void* sort_scratch;
+  size_t bytes;
+};

@@ -1,0 +1,387 @@
+// FMCW IF synthesis (Section 3.2.2, Eq. 8) and its adjoint (Eq. 11-12).
+//
+// cube[v, c, n] = sum_p A_{p,v} exp(j 2 pi (f_c tau_{p,v} + mu tau_{p,v} t_n)),
+// t_n = n T / N_s, identical for every chirp c of a static scene.
+//
+// Forward kernel (persistent, one virtual antenna per CTA): the CTA's threads
+// own M consecutive samples each and together cover all N_s samples, so the
+// sum over paths accumulates in registers with no cross-thread reduction.
+// Paths stream through shared memory in chunks; per (path, thread) one
+// split-precision anchor phase (n0 delta_hi is exact in FP32, frac() before the
+// low part and phi0 are added) goes through one sincos, and the remaining M-1
+// samples follow by complex rotation with the per-path step e^{j 2 pi delta}
+// (4 FP32 multiply/FMA per sample instead of two transcendental ops).  Each CTA
+// writes its partial sums; a second kernel adds them in a fixed order, so the
+// result is bitwise reproducible.
+#include "common.cuh"
+
+namespace sbr {
+namespace {
+
+constexpr int kChunk = 256;
+constexpr float kTwoPiF = 6.28318530717958647692f;
+
+inline int threads_for(int Ns) {
+  int t = Ns / 4;
+  return t < 32 ? 32 : (t > 256 ? 256 : t);
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) k_synth_split(const float4* __restrict__ prep, int64_t cap,
+                                                     const int32_t* __restrict__ d_P, int V, int Q,
+                                                     int Ns, float2* __restrict__ partial) {
+  __shared__ float4 sp[kChunk];
+  __shared__ float2 sstep[kChunk];
+  const int v = blockIdx.x % V, q = blockIdx.x / V;
+  const int64_t P = *d_P;
+  const int n0 = threadIdx.x * M;
+  const float fn0 = (float)n0;
+  float accr[M], acci[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) accr[m] = acci[m] = 0.f;
+  const float4* pv = prep + (size_t)v * cap;
+  for (int64_t c0 = (int64_t)q * kChunk; c0 < P; c0 += (int64_t)Q * kChunk) {
+    const int cnt = (int)min((int64_t)kChunk, P - c0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+      const float4 r = pv[c0 + j];
+      sp[j] = r;
+      float s, c;
+      sincospif(2.f * (r.y + r.z), &s, &c);
+      sstep[j] = make_float2(c, s);
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int j = 0; j < cnt; ++j) {
+      const float4 r = sp[j];
+      const float2 st = sstep[j];
+      float x = fn0 * r.y;  // exact: delta_hi is a multiple of 2^-12 and n0 < 4096
+      x -= rintf(x);
+      x = fmaf(fn0, r.z, x) + r.x;
+      x -= rintf(x);
+      float s, c;
+      __sincosf(kTwoPiF * x, &s, &c);
+      float er = r.w * c, ei = r.w * s;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        accr[m] += er;
+        acci[m] += ei;
+        if (m + 1 < M) {
+          const float nr = fmaf(er, st.x, -ei * st.y);
+          const float ni = fmaf(er, st.y, ei * st.x);
+          er = nr;
+          ei = ni;
+        }
+      }
+    }
+  }
+  float2* out = partial + (size_t)blockIdx.x * Ns + n0;
+#pragma unroll
+  for (int m = 0; m < M; ++m) out[m] = make_float2(accr[m], acci[m]);
+}
+
+// Per-sample phase in FP64: x = f_c tau + (B / N_s) tau n, reduced mod 1.
+template <int M>
+__global__ void __launch_bounds__(256) k_synth_fp64(const float4* __restrict__ prep,
+                                                    const double* __restrict__ tau64, int64_t cap,
+                                                    const int32_t* __restrict__ d_P, int V, int Q,
+                                                    int Ns, double f0, double b_over_ns,
+                                                    float2* __restrict__ partial) {
+  __shared__ double2 sx[kChunk];
+  __shared__ float sa[kChunk];
+  const int v = blockIdx.x % V, q = blockIdx.x / V;
+  const int64_t P = *d_P;
+  const int n0 = threadIdx.x * M;
+  float accr[M], acci[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) accr[m] = acci[m] = 0.f;
+  for (int64_t c0 = (int64_t)q * kChunk; c0 < P; c0 += (int64_t)Q * kChunk) {
+    const int cnt = (int)min((int64_t)kChunk, P - c0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+      const double t = tau64[(size_t)v * cap + c0 + j];
+      const double x0 = f0 * t;
+      const double d = b_over_ns * t;
+      sx[j] = make_double2(x0 - rint(x0), d - rint(d));
+      sa[j] = prep[(size_t)v * cap + c0 + j].w;
+    }
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+      const double2 xd = sx[j];
+      const float a = sa[j];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        double x = fma((double)(n0 + m), xd.y, xd.x);
+        x -= rint(x);
+        float s, c;
+        __sincosf(kTwoPiF * (float)x, &s, &c);
+        accr[m] = fmaf(a, c, accr[m]);
+        acci[m] = fmaf(a, s, acci[m]);
+      }
+    }
+  }
+  float2* out = partial + (size_t)blockIdx.x * Ns + n0;
+#pragma unroll
+  for (int m = 0; m < M; ++m) out[m] = make_float2(accr[m], acci[m]);
+}
+
+// Everything in FP32: tau, f_c tau and mu tau t_n (no split, no FP64).
+template <int M>
+__global__ void __launch_bounds__(256) k_synth_naive(const float4* __restrict__ prep,
+                                                     const double* __restrict__ tau64, int64_t cap,
+                                                     const int32_t* __restrict__ d_P, int V, int Q,
+                                                     int Ns, float f0, float mu, float dt,
+                                                     float2* __restrict__ partial) {
+  __shared__ float2 sx[kChunk];
+  const int v = blockIdx.x % V, q = blockIdx.x / V;
+  const int64_t P = *d_P;
+  const int n0 = threadIdx.x * M;
+  float accr[M], acci[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) accr[m] = acci[m] = 0.f;
+  for (int64_t c0 = (int64_t)q * kChunk; c0 < P; c0 += (int64_t)Q * kChunk) {
+    const int cnt = (int)min((int64_t)kChunk, P - c0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x)
+      sx[j] = make_float2((float)tau64[(size_t)v * cap + c0 + j], prep[(size_t)v * cap + c0 + j].w);
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+      const float t = sx[j].x, a = sx[j].y;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        float x = fmaf(mu * t, (float)(n0 + m) * dt, f0 * t);
+        x -= rintf(x);
+        float s, c;
+        __sincosf(kTwoPiF * x, &s, &c);
+        accr[m] = fmaf(a, c, accr[m]);
+        acci[m] = fmaf(a, s, acci[m]);
+      }
+    }
+  }
+  float2* out = partial + (size_t)blockIdx.x * Ns + n0;
+#pragma unroll
+  for (int m = 0; m < M; ++m) out[m] = make_float2(accr[m], acci[m]);
+}
+
+__global__ void k_reduce(const float2* __restrict__ partial, int V, int Q, int Ns, int C,
+                         float2* __restrict__ cube) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V * Ns) return;
+  const int v = i / Ns, n = i - v * Ns;
+  float re = 0.f, im = 0.f;
+  for (int q = 0; q < Q; ++q) {
+    const float2 x = partial[((size_t)q * V + v) * Ns + n];
+    re += x.x;
+    im += x.y;
+  }
+  for (int c = 0; c < C; ++c) cube[((size_t)v * C + c) * Ns + n] = make_float2(re, im);
+}
+
+// ---- adjoint ----------------------------------------------------------------
+
+__global__ void k_chirp_sum(const float2* __restrict__ g, int V, int C, int Ns,
+                            float2* __restrict__ gs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V * Ns) return;
+  const int v = i / Ns, n = i - v * Ns;
+  float re = 0.f, im = 0.f;
+  for (int c = 0; c < C; ++c) {
+    const float2 x = g[((size_t)v * C + c) * Ns + n];
+    re += x.x;
+    im += x.y;
+  }
+  gs[i] = make_float2(re, im);
+}
+
+// One thread per (path, antenna): Eq. 12 gives dL/dA = sum_n Re(conj(g_n) e_n),
+// Eq. 11 gives dL/dtau = 2 pi A sum_n (f_c + mu t_n) Re(conj(g_n) j e_n); the
+// phasor e_n runs by rotation and is re-anchored from the split phase every 32
+// samples.  Output per metre of path: dL/dL = dL/dtau / c.
+__global__ void __launch_bounds__(256) k_synth_bwd(const float4* __restrict__ prep, int64_t cap,
+                                                   const int32_t* __restrict__ d_P, int Ns,
+                                                   const float2* __restrict__ gs, float inv_lambda,
+                                                   float b_over_cns, float* __restrict__ glen,
+                                                   float* __restrict__ gamp) {
+  extern __shared__ float2 sg[];
+  const int v = blockIdx.y;
+  for (int n = threadIdx.x; n < Ns; n += blockDim.x) sg[n] = gs[(size_t)v * Ns + n];
+  __syncthreads();
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= *d_P) return;
+  const float4 r = prep[(size_t)v * cap + p];
+  float ss, cs;
+  sincospif(2.f * (r.y + r.z), &ss, &cs);
+  float sa = 0.f, s0 = 0.f, s1 = 0.f;
+  for (int nb = 0; nb < Ns; nb += 32) {
+    const float fn = (float)nb;
+    float x = fn * r.y;
+    x -= rintf(x);
+    x = fmaf(fn, r.z, x) + r.x;
+    x -= rintf(x);
+    float s, c;
+    __sincosf(kTwoPiF * x, &s, &c);
+    float t0 = 0.f, t1 = 0.f;
+#pragma unroll 8
+    for (int m = 0; m < 32; ++m) {
+      const float2 g = sg[nb + m];
+      sa = fmaf(g.x, c, fmaf(g.y, s, sa));
+      const float im = fmaf(g.y, c, -g.x * s);
+      t0 += im;
+      t1 = fmaf((float)m, im, t1);
+      const float nc = fmaf(c, cs, -s * ss);
+      const float ns = fmaf(c, ss, s * cs);
+      c = nc;
+      s = ns;
+    }
+    s0 += t0;
+    s1 += fmaf(fn, t0, t1);
+  }
+  gamp[(size_t)v * cap + p] = sa;
+  glen[(size_t)v * cap + p] = kTwoPiF * r.w * fmaf(inv_lambda, s0, b_over_cns * s1);
+}
+
+int g_sms = 0;
+
+int sm_count() {
+  if (g_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_sms <= 0)
+      g_sms = 152;
+  }
+  return g_sms;
+}
+
+// Grid: V * Q CTAs, Q chosen to fill every SM at full occupancy, capped by the
+// number of path chunks.
+void grid_shape(int V, int Ns, int64_t cap, int* Q) {
+  const int T = threads_for(Ns);
+  int per_sm = 2048 / T;
+  if (per_sm > 32) per_sm = 32;
+  int64_t q = ((int64_t)sm_count() * per_sm + V - 1) / V;
+  const int64_t chunks = (cap + kChunk - 1) / kChunk;
+  if (q > chunks) q = chunks;
+  if (q < 1) q = 1;
+  *Q = (int)q;
+}
+
+size_t ws_layout(const sbr_radar_cfg* radar, int64_t cap, int* Q) {
+  const int V = radar->n_tx * radar->n_rx, Ns = radar->n_samples;
+  grid_shape(V, Ns, cap, Q);
+  Carver c(nullptr);
+  c.take<float2>((size_t)V * (*Q) * Ns);  // per-CTA partial sums
+  c.take<float2>((size_t)V * Ns);         // chirp-summed upstream gradient
+  return c.bytes();
+}
+
+}  // namespace
+}  // namespace sbr
+
+using namespace sbr;
+
+extern "C" size_t sbr_synth_ws_bytes(const sbr_radar_cfg* radar, int64_t path_cap) {
+  if (!radar || radar->n_tx < 1 || radar->n_rx < 1 || radar->n_samples < 1) return 0;
+  int Q;
+  return ws_layout(radar, path_cap, &Q);
+}
+
+namespace {
+struct SynthWs {
+  float2* partial;
+  float2* gsum;
+  int Q;
+};
+
+sbr_status bind_ws(const sbr_radar_cfg* radar, int64_t cap, void* ws, size_t bytes, SynthWs* w,
+                   const char* who) {
+  int Q;
+  const size_t need = ws_layout(radar, cap, &Q);
+  SBR_ARG(ws && aligned256(ws), "%s: workspace NULL or not 256-byte aligned", who);
+  if (bytes < need) {
+    set_error("%s: workspace of %zu bytes, %zu needed", who, bytes, need);
+    return SBR_ERR_OOM;
+  }
+  const int V = radar->n_tx * radar->n_rx, Ns = radar->n_samples;
+  Carver c(ws);
+  w->partial = c.take<float2>((size_t)V * Q * Ns);
+  w->gsum = c.take<float2>((size_t)V * Ns);
+  w->Q = Q;
+  return SBR_OK;
+}
+
+template <int M>
+void launch_fwd(sbr_phase_mode mode, const sbr_paths* p, const sbr_radar_cfg* r, const SynthWs& w,
+                cudaStream_t st) {
+  const int V = p->n_virt, Ns = r->n_samples, T = Ns / M;
+  const int grid = V * w.Q;
+  const float4* prep = reinterpret_cast<const float4*>(p->prep);
+  if (mode == SBR_PHASE_SPLIT) {
+    k_synth_split<M><<<grid, T, 0, st>>>(prep, p->path_cap, p->count, V, w.Q, Ns, w.partial);
+  } else if (mode == SBR_PHASE_FP64) {
+    k_synth_fp64<M><<<grid, T, 0, st>>>(prep, p->tau64, p->path_cap, p->count, V, w.Q, Ns, r->f0,
+                                        r->bandwidth / Ns, w.partial);
+  } else {
+    const double mu = r->bandwidth / r->chirp_time, dt = r->chirp_time / Ns;
+    k_synth_naive<M><<<grid, T, 0, st>>>(prep, p->tau64, p->path_cap, p->count, V, w.Q, Ns,
+                                         (float)r->f0, (float)mu, (float)dt, w.partial);
+  }
+}
+}  // namespace
+
+extern "C" sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg* radar,
+                                     sbr_phase_mode mode, float* d_cube, void* d_ws,
+                                     size_t ws_bytes, sbr_stream stream) {
+  SBR_ARG(paths && d_cube, "sbr_synthesize: NULL paths or cube");
+  sbr_status rs = check_radar(radar, "sbr_synthesize");
+  if (rs != SBR_OK) return rs;
+  SBR_ARG(paths->n_virt == radar->n_tx * radar->n_rx, "sbr_synthesize: paths have V=%d, radar %d",
+          paths->n_virt, radar->n_tx * radar->n_rx);
+  SBR_ARG(mode == SBR_PHASE_SPLIT || mode == SBR_PHASE_FP64 || mode == SBR_PHASE_NAIVE,
+          "sbr_synthesize: unknown phase mode %d", (int)mode);
+  SynthWs w;
+  rs = bind_ws(radar, paths->path_cap, d_ws, ws_bytes, &w, "sbr_synthesize");
+  if (rs != SBR_OK) return rs;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int Ns = radar->n_samples, T = threads_for(Ns), M = Ns / T;
+  switch (M) {
+    case 1: launch_fwd<1>(mode, paths, radar, w, st); break;
+    case 2: launch_fwd<2>(mode, paths, radar, w, st); break;
+    case 4: launch_fwd<4>(mode, paths, radar, w, st); break;
+    case 8: launch_fwd<8>(mode, paths, radar, w, st); break;
+    case 16: launch_fwd<16>(mode, paths, radar, w, st); break;
+    default: set_error("sbr_synthesize: no kernel for %d samples per thread", M); return SBR_ERR_UNSUPPORTED;
+  }
+  SBR_CUDA(cudaGetLastError());
+  const int V = paths->n_virt;
+  k_reduce<<<(V * Ns + 255) / 256, 256, 0, st>>>(w.partial, V, w.Q, Ns, radar->n_chirps,
+                                                  reinterpret_cast<float2*>(d_cube));
+  SBR_CUDA(cudaGetLastError());
+  return SBR_OK;
+}
+
+extern "C" sbr_status sbr_synthesize_bwd(const sbr_paths* paths, const sbr_radar_cfg* radar,
+                                         const float* d_gcube, float* d_glen, float* d_gamp,
+                                         void* d_ws, size_t ws_bytes, sbr_stream stream) {
+  SBR_ARG(paths && d_gcube && d_glen && d_gamp, "sbr_synthesize_bwd: NULL argument");
+  sbr_status rs = check_radar(radar, "sbr_synthesize_bwd");
+  if (rs != SBR_OK) return rs;
+  SBR_ARG(paths->n_virt == radar->n_tx * radar->n_rx, "sbr_synthesize_bwd: V mismatch");
+  SynthWs w;
+  rs = bind_ws(radar, paths->path_cap, d_ws, ws_bytes, &w, "sbr_synthesize_bwd");
+  if (rs != SBR_OK) return rs;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int V = paths->n_virt, Ns = radar->n_samples, C = radar->n_chirps;
+  k_chirp_sum<<<(V * Ns + 255) / 256, 256, 0, st>>>(reinterpret_cast<const float2*>(d_gcube), V, C,
+                                                     Ns, w.gsum);
+  const int64_t cap = paths->path_cap;
+  if (cap > 0) {
+    dim3 grid((unsigned)((cap + 255) / 256), (unsigned)V);
+    const double lam_inv = radar->f0 / kC;
+    const double bcn = radar->bandwidth / (kC * Ns);
+    k_synth_bwd<<<grid, 256, Ns * sizeof(float2), st>>>(
+        reinterpret_cast<const float4*>(paths->prep), cap, paths->count, Ns, w.gsum,
+        (float)lam_inv, (float)bcn, d_glen, d_gamp);
+  }
+  SBR_CUDA(cudaGetLastError());
+  return SBR_OK;
+}

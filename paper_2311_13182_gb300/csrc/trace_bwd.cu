@@ -1,0 +1,216 @@
+// Adjoint of the trace and path preparation (Section 3.3, Eq. 13 chain rule;
+// the continuous-integrand derivative of Eq. 4-5).
+//
+// With the triangle sequence of every ray held fixed (visibility changes are
+// the discontinuous part that Eq. 6-7 reparameterises; not included), each hit
+// is a smooth function of the vertices:
+//   h_k = o_k + t_k d_k,  t_k = N_k.(a_k - o_k) / (N_k.d_k),  N_k = (b_k - a_k) x (c_k - a_k)
+//   d_{k+1} = d_k - 2 (d_k.n_k) n_k,  n_k = N_k / |N_k|,  o_{k+1} = h_k
+// and each path (k, t, r) has length L_in + L_out and strength
+//   A = omega (-1)^(k-1) |d_k.n_k| / (4 pi L_in L_out),
+//   L_in = |h_1 - Tx_t| + sum_{j=2..k} |h_j - h_{j-1}|,  L_out = |Rx_r - h_k|.
+// One thread per ray accumulates the adjoints of its path lengths and
+// strengths onto the hit points and |d.n| terms, then sweeps the bounces in
+// reverse, and adds the per-corner vertex gradients with atomics.
+#include <math.h>
+
+#include "scene.cuh"
+
+namespace sbr {
+namespace {
+
+constexpr int kMaxK = 8;
+
+struct GridF {
+  float o[3], ax[3], ua[3], va[3];
+  double th;
+  int G;
+};
+
+struct RadarF {
+  float tx[SBR_MAX_TX][3];
+  float rx[SBR_MAX_RX][3];
+  int ntx, nrx;
+};
+
+__device__ inline float3 ld3(const float* v, int i) { return f3(v[3 * i], v[3 * i + 1], v[3 * i + 2]); }
+__device__ inline float len3(float3 a) { return sqrtf(dot(a, a)); }
+__device__ inline void add3(float3& a, float3 b) { a = a + b; }
+
+__device__ inline void scatter(float* g, int vi, float3 d) {
+  atomicAdd(&g[3 * vi], d.x);
+  atomicAdd(&g[3 * vi + 1], d.y);
+  atomicAdd(&g[3 * vi + 2], d.z);
+}
+
+__global__ void __launch_bounds__(128) k_trace_bwd(
+    const float* __restrict__ verts, int nv, const int32_t* __restrict__ faces, GridF g, RadarF rd,
+    const int32_t* __restrict__ ray_ids, int n_rays, int K, const sbr_hit* __restrict__ hits,
+    const double4* __restrict__ hit_pos, const int32_t* __restrict__ first,
+    const float4* __restrict__ prep, int64_t cap, const float* __restrict__ glen,
+    const float* __restrict__ gamp, float* __restrict__ gverts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_rays) return;
+  const int p0 = first[i], m = first[i + 1] - p0;
+  if (m <= 0) return;
+  // launch direction (FP64 grid formula, then FP32)
+  const int rid = ray_ids ? ray_ids[i] : i;
+  const int row = rid / g.G, col = rid - row * g.G;
+  const double a0 = g.th * (2.0 * (col + 0.5) / g.G - 1.0);
+  const double b0 = g.th * (2.0 * (row + 0.5) / g.G - 1.0);
+  double wx = g.ax[0] + g.ua[0] * a0 + g.va[0] * b0, wy = g.ax[1] + g.ua[1] * a0 + g.va[1] * b0,
+         wz = g.ax[2] + g.ua[2] * a0 + g.va[2] * b0;
+  const double wl = 1.0 / sqrt(wx * wx + wy * wy + wz * wz);
+  float3 d[kMaxK], h[kMaxK], nh[kMaxK], N[kMaxK], A[kMaxK];
+  float nlen[kMaxK], t[kMaxK], cdn[kMaxK];
+  int fv[kMaxK][3];
+  d[0] = f3((float)(wx * wl), (float)(wy * wl), (float)(wz * wl));
+  for (int k = 0; k < m; ++k) {
+    const size_t sl = (size_t)i * K + k;
+    const int id = hits[sl].tri;
+    t[k] = hits[sl].t;
+    const double4 hp = hit_pos[sl];
+    h[k] = f3((float)hp.x, (float)hp.y, (float)hp.z);
+    for (int c = 0; c < 3; ++c) {
+      const int q = faces[3 * id + c];
+      fv[k][c] = (q >= 0 && q < nv) ? q : 0;  // invalid faces were reported by the scene build
+    }
+    const float3 va = ld3(verts, fv[k][0]), vb = ld3(verts, fv[k][1]), vc = ld3(verts, fv[k][2]);
+    A[k] = va;
+    N[k] = cross(vb - va, vc - va);
+    nlen[k] = len3(N[k]);
+    nh[k] = N[k] * (1.f / nlen[k]);
+    cdn[k] = dot(d[k], nh[k]);
+    if (k + 1 < m) d[k + 1] = d[k] - nh[k] * (2.f * cdn[k]);
+  }
+  // adjoints of hit points and of |d.n| from every path of this ray
+  float3 hb[kMaxK];
+  float cb[kMaxK];
+  for (int k = 0; k < m; ++k) {
+    hb[k] = f3(0.f, 0.f, 0.f);
+    cb[k] = 0.f;
+  }
+  float segb[kMaxK];  // adjoint of |h_j - h_{j-1}|
+  for (int k = 0; k < m; ++k) segb[k] = 0.f;
+  float interior = 0.f;
+  for (int k = 0; k < m; ++k) {
+    if (k > 0) interior += len3(h[k] - h[k - 1]);
+    const int64_t p = p0 + k;
+    float lin_sum_b = 0.f;  // sum over antennas of dL/dL_in (for the interior segments)
+    for (int tt = 0; tt < rd.ntx; ++tt) {
+      const float3 et = h[0] - f3(rd.tx[tt][0], rd.tx[tt][1], rd.tx[tt][2]);
+      const float l1 = len3(et);
+      const float lin = l1 + interior;
+      float linb = 0.f;
+      for (int rr = 0; rr < rd.nrx; ++rr) {
+        const int v = tt * rd.nrx + rr;
+        const float3 er = h[k] - f3(rd.rx[rr][0], rd.rx[rr][1], rd.rx[rr][2]);
+        const float lout = len3(er);
+        const float gl = glen[(size_t)v * cap + p], ga = gamp[(size_t)v * cap + p];
+        const float amp = prep[(size_t)v * cap + p].w;
+        const float ab = ga * amp;
+        linb += gl - ab / lin;
+        const float loutb = gl - ab / lout;
+        add3(hb[k], er * (loutb / lout));
+        // A is linear in |d.n|: dA/d|d.n| = A / |d.n|
+        const float ac = fabsf(cdn[k]);
+        if (ac > 0.f) cb[k] += ab / ac;
+      }
+      add3(hb[0], et * (linb / l1));
+      lin_sum_b += linb;
+    }
+    for (int j = 1; j <= k; ++j) segb[j] += lin_sum_b;
+  }
+  for (int j = 1; j < m; ++j) {
+    const float3 e = h[j] - h[j - 1];
+    const float3 u = e * (segb[j] / len3(e));
+    add3(hb[j], u);
+    hb[j - 1] = hb[j - 1] - u;
+  }
+  // reverse sweep over bounces
+  float3 db_next = f3(0.f, 0.f, 0.f);  // adjoint of d_{k+1}
+  float3 ob_next = f3(0.f, 0.f, 0.f);  // adjoint of o_{k+1} = h_k
+  for (int k = m - 1; k >= 0; --k) {
+    float3 db = f3(0.f, 0.f, 0.f), nb = f3(0.f, 0.f, 0.f);
+    // |d.n|
+    const float cbar = cb[k] * (cdn[k] >= 0.f ? 1.f : -1.f);
+    float cdb = cbar;
+    // reflection d_{k+1} = d_k - 2 c n
+    if (k + 1 < m) {
+      add3(db, db_next);
+      cdb += -2.f * dot(nh[k], db_next);
+      add3(nb, db_next * (-2.f * cdn[k]));
+    }
+    add3(db, nh[k] * cdb);
+    add3(nb, d[k] * cdb);
+    // h_k = o_k + t d_k
+    const float3 H = hb[k] + ob_next;
+    float3 ob = H;
+    const float tb = dot(H, d[k]);
+    add3(db, H * t[k]);
+    // t = N.(a - o) / (N.d)
+    const float den = dot(N[k], d[k]);
+    float3 Nb = (A[k] - h[k]) * (tb / den);
+    float3 ab = N[k] * (tb / den);
+    ob = ob - N[k] * (tb / den);
+    db = db - N[k] * (tb * t[k] / den);
+    // n = N / |N|
+    add3(Nb, (nb - nh[k] * dot(nb, nh[k])) * (1.f / nlen[k]));
+    // N = (b - a) x (c - a)
+    const float3 vb = ld3(verts, fv[k][1]), vc = ld3(verts, fv[k][2]);
+    const float3 e1 = vb - A[k], e2 = vc - A[k];
+    const float3 e1b = cross(e2, Nb), e2b = cross(Nb, e1);
+    ab = ab - e1b - e2b;
+    scatter(gverts, fv[k][0], ab);
+    scatter(gverts, fv[k][1], e1b);
+    scatter(gverts, fv[k][2], e2b);
+    db_next = db;
+    ob_next = ob;
+  }
+}
+
+}  // namespace
+}  // namespace sbr
+
+using namespace sbr;
+
+extern "C" sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts, const sbr_radar_cfg* radar,
+                                    const sbr_ray_grid* grid, const int32_t* d_ray_ids,
+                                    const sbr_paths* paths, const float* d_glen, const float* d_gamp,
+                                    float* d_gverts, sbr_stream stream) {
+  SBR_ARG(scene && paths && d_verts && d_glen && d_gamp && d_gverts, "sbr_trace_bwd: NULL argument");
+  sbr_status rs = check_radar(radar, "sbr_trace_bwd");
+  if (rs != SBR_OK) return rs;
+  rs = check_grid(grid, "sbr_trace_bwd");
+  if (rs != SBR_OK) return rs;
+  SBR_ARG(paths->max_bounces <= kMaxK, "sbr_trace_bwd: max_bounces=%d above %d", paths->max_bounces, kMaxK);
+  SBR_ARG(paths->n_virt == radar->n_tx * radar->n_rx, "sbr_trace_bwd: V mismatch");
+  SBR_ARG(d_ray_ids || (int64_t)paths->n_rays == (int64_t)grid->G * grid->G,
+          "sbr_trace_bwd: paths cover %d rays; the grid has %lld (pass the forward's ray list)",
+          paths->n_rays, (long long)grid->G * grid->G);
+  if (paths->n_rays == 0) return SBR_OK;
+  GridF g;
+  for (int j = 0; j < 3; ++j) {
+    g.o[j] = (float)grid->origin[j];
+    g.ax[j] = (float)grid->axis[j];
+    g.ua[j] = (float)grid->u_axis[j];
+    g.va[j] = (float)grid->v_axis[j];
+  }
+  g.th = grid->tan_half;
+  g.G = grid->G;
+  RadarF rd;
+  for (int t = 0; t < SBR_MAX_TX; ++t)
+    for (int j = 0; j < 3; ++j) rd.tx[t][j] = (float)radar->tx[t][j];
+  for (int r = 0; r < SBR_MAX_RX; ++r)
+    for (int j = 0; j < 3; ++j) rd.rx[r][j] = (float)radar->rx[r][j];
+  rd.ntx = radar->n_tx;
+  rd.nrx = radar->n_rx;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int R = paths->n_rays;
+  k_trace_bwd<<<(R + 127) / 128, 128, 0, st>>>(
+      d_verts, scene->nv, scene->faces, g, rd, d_ray_ids, R, paths->max_bounces, paths->hits,
+      reinterpret_cast<const double4*>(paths->hit_pos), paths->ray_first,
+      reinterpret_cast<const float4*>(paths->prep), paths->path_cap, d_glen, d_gamp, d_gverts);
+  SBR_CUDA(cudaGetLastError());
+  return SBR_OK;
+}

@@ -1,0 +1,63 @@
+"""Gradient-based mesh reconstruction against a target radar point cloud (Section 3.4).
+
+One iteration (Eq. 14 objective, Eq. 15 update; Adam in place of plain SGD):
+  scene update -> trace -> synthesize -> point cloud            (forward, Eq. 8, Eq. 16's T)
+  loss = weighted squared Chamfer(points, target) + w_lap * uniform Laplacian
+  point-cloud adjoint -> synthesis adjoint (Eq. 11-12) -> trace adjoint (Eq. 13)
+  Adam step on the vertex positions
+Every step is a library kernel on one stream with no host synchronisation, so
+the whole iteration is captured once into a CUDA graph and replayed.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import sim
+from .autograd import Simulator
+
+
+class Reconstruction:
+    def __init__(self, verts0: np.ndarray, faces: np.ndarray, target: torch.Tensor, radar, grid, max_bounces,
+                 cfar, lr=1e-3, lap_weight=0.1, ray_ids=None, recompute=False, device="cuda"):
+        self.verts = torch.from_numpy(np.ascontiguousarray(verts0, np.float32)).to(device)
+        self.nv = self.verts.shape[0]
+        self.sim = Simulator(faces, self.nv, radar, grid, max_bounces, cfar, ray_ids=ray_ids,
+                             recompute=recompute, device=device)
+        self.adj = sim.Adjacency(faces, self.nv, device)
+        self.target = target.contiguous().float().to(device)
+        self.lr, self.lap_weight = lr, lap_weight
+        self.grad = torch.zeros_like(self.verts)
+        self.m = torch.zeros_like(self.verts)
+        self.v = torch.zeros_like(self.verts)
+        self.step_count = torch.zeros(1, dtype=torch.int32, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.gpoints = torch.zeros((cfar.k_max, 4), dtype=torch.float32, device=device)
+        self.graph = None
+
+    def _iteration(self):
+        pts, n = self.sim.forward(self.verts)
+        sim.chamfer(pts, n, self.target, loss=self.loss, gpred=self.gpoints)
+        self.grad.zero_()
+        sim.laplacian(self.verts, self.adj, self.lap_weight, self.loss, self.grad)
+        self.sim.backward(self.verts, self.gpoints, self.grad)
+        sim.adam_step(self.verts, self.grad, self.m, self.v, self.step_count, lr=self.lr)
+
+    def step(self):
+        """One eager iteration (the first call also builds the scene)."""
+        self._iteration()
+
+    def capture(self):
+        """Capture one iteration into a CUDA graph (after at least one eager step)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self._iteration()  # warm the stream-local allocator state before capture
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._iteration()
+
+    def replay(self, n: int = 1):
+        for _ in range(n):
+            self.graph.replay()

@@ -1,0 +1,314 @@
+"""Torch-facing wrappers of the libsbr C ABI (device memory and streams only).
+
+Every function here marshals arguments and calls one ``sbr_*`` entry point;
+all arithmetic of the simulator runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+PHASE_SPLIT, PHASE_FP64, PHASE_NAIVE = L.PHASE_SPLIT, L.PHASE_FP64, L.PHASE_NAIVE
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need_cuda(t: torch.Tensor, dtype, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA {dtype} tensor")
+
+
+def radar_struct(radar) -> L.RadarCfg:
+    r = L.RadarCfg()
+    r.f0, r.bandwidth, r.chirp_time, r.chirp_rep = radar.f0, radar.bandwidth, radar.chirp_time, radar.chirp_rep
+    r.n_samples, r.n_chirps = radar.n_samples, radar.n_chirps
+    r.n_tx, r.n_rx = radar.n_tx, radar.n_rx
+    if radar.n_tx > L.MAX_TX or radar.n_rx > L.MAX_RX:
+        raise ValueError("too many antennas for the C ABI")
+    for t in range(radar.n_tx):
+        for j in range(3):
+            r.tx[t][j] = float(radar.tx[t][j])
+    for q in range(radar.n_rx):
+        for j in range(3):
+            r.rx[q][j] = float(radar.rx[q][j])
+    return r
+
+
+def grid_struct(grid) -> L.RayGrid:
+    g = L.RayGrid()
+    g.G = grid.G
+    for j in range(3):
+        g.origin[j] = float(grid.origin[j])
+        g.axis[j] = float(grid.axis[j])
+        g.u_axis[j] = float(grid.u_axis[j])
+        g.v_axis[j] = float(grid.v_axis[j])
+    g.tan_half = float(grid.tan_half)
+    return g
+
+
+def cfar_struct(cfg) -> L.CfarCfg:
+    c = L.CfarCfg()
+    c.n_theta, c.guard, c.train, c.k_max = cfg.n_theta, cfg.guard, cfg.train, cfg.k_max
+    c.alpha, c.floor_rel, c.beta, c.w_min = cfg.alpha, cfg.floor_rel, cfg.beta, cfg.w_min
+    return c
+
+
+def _region(mem: torch.Tensor, ptr: int, dtype, shape):
+    """Typed view of a sub-region of ``mem`` starting at device address ``ptr``."""
+    off = ptr - mem.data_ptr()
+    n = int(np.prod(shape)) * torch.empty((), dtype=dtype).element_size()
+    return mem[off:off + n].view(dtype).view(*shape)
+
+
+class Scene:
+    """Triangle mesh + LBVH resident in device memory (sbr_scene_create)."""
+
+    def __init__(self, verts: torch.Tensor, faces: torch.Tensor, stream=None):
+        _need_cuda(verts, torch.float32, "verts")
+        _need_cuda(faces, torch.int32, "faces")
+        self.nv, self.nt = int(verts.shape[0]), int(faces.shape[0])
+        nbytes = int(L.load().sbr_scene_bytes(self.nt))
+        self.mem = torch.empty(nbytes, dtype=torch.uint8, device=verts.device)
+        h = ctypes.c_void_p()
+        L.call("sbr_scene_create", _vp(verts), self.nv, _vp(faces), self.nt, _vp(self.mem), nbytes,
+               _stream(stream), ctypes.byref(h))
+        self.handle = h
+        self.device = verts.device
+
+    @staticmethod
+    def bytes_for(nt: int) -> int:
+        return int(L.load().sbr_scene_bytes(nt))
+
+    def update(self, verts: torch.Tensor, stream=None):
+        _need_cuda(verts, torch.float32, "verts")
+        L.call("sbr_scene_update", self.handle, _vp(verts), _stream(stream))
+
+    def check(self, stream=None):
+        L.call("sbr_scene_check", self.handle, _stream(stream))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and L._LIB is not None:
+            L._LIB.sbr_scene_destroy(h)
+            self.handle = None
+
+
+class PathBuffers:
+    """Caller-owned path records of one trace (sbr_paths_bind)."""
+
+    def __init__(self, n_rays: int, max_bounces: int, n_virt: int, device="cuda"):
+        nbytes = int(L.load().sbr_paths_bytes(n_rays, max_bounces, n_virt))
+        if nbytes == 0:
+            raise ValueError("invalid path buffer sizes")
+        self.mem = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.s = L.Paths()
+        L.call("sbr_paths_bind", _vp(self.mem), nbytes, n_rays, max_bounces, n_virt, ctypes.byref(self.s))
+        self.R, self.K, self.V, self.cap = n_rays, max_bounces, n_virt, int(self.s.path_cap)
+
+    @staticmethod
+    def bytes_for(n_rays, max_bounces, n_virt) -> int:
+        return int(L.load().sbr_paths_bytes(n_rays, max_bounces, n_virt))
+
+    def hits(self):
+        raw = _region(self.mem, self.s.hits, torch.int32, (self.R, self.K, 4))
+        return raw[..., 0], raw[..., 1:].view(torch.float32)
+
+    def hit_pos(self):
+        return _region(self.mem, self.s.hit_pos, torch.float64, (self.R, self.K, 4))
+
+    def ray_weight(self):
+        return _region(self.mem, self.s.ray_weight, torch.float32, (self.R,))
+
+    def ray_first(self):
+        return _region(self.mem, self.s.ray_first, torch.int32, (self.R + 1,))
+
+    def path_ray(self):
+        return _region(self.mem, self.s.path_ray, torch.int32, (max(self.cap, 1),))
+
+    def prep(self):
+        return _region(self.mem, self.s.prep, torch.float32, (self.V, max(self.cap, 1), 4))
+
+    def tau64(self):
+        return _region(self.mem, self.s.tau64, torch.float64, (self.V, max(self.cap, 1)))
+
+    def count_tensor(self):
+        return _region(self.mem, self.s.count, torch.int32, (1,))
+
+    def count(self) -> int:
+        return int(self.count_tensor().item())
+
+
+def trace(scene: Scene, radar, grid, max_bounces: int, ray_ids: torch.Tensor | None = None,
+          out: PathBuffers | None = None, stream=None) -> PathBuffers:
+    """sbr_trace: nearest-hit specular trace of the grid (or of ``ray_ids``) + path prep."""
+    n = int(ray_ids.shape[0]) if ray_ids is not None else grid.G * grid.G
+    if ray_ids is not None:
+        _need_cuda(ray_ids, torch.int32, "ray_ids")
+    V = radar.n_tx * radar.n_rx
+    if out is None:
+        out = PathBuffers(n, max_bounces, V, device=scene.device)
+    r, g = radar_struct(radar), grid_struct(grid)
+    L.call("sbr_trace", scene.handle, ctypes.byref(r), ctypes.byref(g), _vp(ray_ids),
+           n if ray_ids is not None else -1, max_bounces, ctypes.byref(out.s), _stream(stream))
+    return out
+
+
+def synth_ws_bytes(radar, path_cap: int) -> int:
+    return int(L.load().sbr_synth_ws_bytes(ctypes.byref(radar_struct(radar)), path_cap))
+
+
+def synthesize(paths: PathBuffers, radar, mode: int = PHASE_SPLIT, out: torch.Tensor | None = None,
+               ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """sbr_synthesize: IF cube [V, C, N_s, 2] float32 (re, im) of Eq. 8."""
+    r = radar_struct(radar)
+    V, C, Ns = radar.n_virt, radar.n_chirps, radar.n_samples
+    if out is None:
+        out = torch.empty((V, C, Ns, 2), dtype=torch.float32, device=paths.mem.device)
+    nb = synth_ws_bytes(radar, paths.cap)
+    if ws is None or ws.numel() < nb:
+        ws = torch.empty(nb, dtype=torch.uint8, device=paths.mem.device)
+    L.call("sbr_synthesize", ctypes.byref(paths.s), ctypes.byref(r), int(mode), _vp(out), _vp(ws), nb,
+           _stream(stream))
+    return out
+
+
+def synthesize_bwd(paths: PathBuffers, radar, gcube: torch.Tensor, ws: torch.Tensor | None = None,
+                   stream=None):
+    """sbr_synthesize_bwd: (dL/d path length, dL/dA), each [V, path_cap] float32."""
+    _need_cuda(gcube, torch.float32, "gcube")
+    r = radar_struct(radar)
+    glen = torch.empty((paths.V, max(paths.cap, 1)), dtype=torch.float32, device=gcube.device)
+    gamp = torch.empty_like(glen)
+    nb = synth_ws_bytes(radar, paths.cap)
+    if ws is None or ws.numel() < nb:
+        ws = torch.empty(nb, dtype=torch.uint8, device=gcube.device)
+    L.call("sbr_synthesize_bwd", ctypes.byref(paths.s), ctypes.byref(r), _vp(gcube), _vp(glen), _vp(gamp),
+           _vp(ws), nb, _stream(stream))
+    return glen, gamp
+
+
+class PcState:
+    """Saved state + scratch of one point-cloud evaluation (sbr_pc_bind)."""
+
+    def __init__(self, radar, cfar, device="cuda"):
+        self.r, self.c = radar_struct(radar), cfar_struct(cfar)
+        nbytes = int(L.load().sbr_pc_bytes(ctypes.byref(self.r), ctypes.byref(self.c)))
+        if nbytes == 0:
+            raise ValueError(f"unsupported point-cloud configuration: {L.last_error()}")
+        self.mem = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.s = L.PcState()
+        L.call("sbr_pc_bind", _vp(self.mem), nbytes, ctypes.byref(self.r), ctypes.byref(self.c),
+               ctypes.byref(self.s))
+        self.k_max = cfar.k_max
+        self.shape = (radar.n_virt, radar.n_chirps, radar.n_samples)
+        self.A = cfar.n_theta
+
+    def n_points_tensor(self):
+        return _region(self.mem, self.s.n_points, torch.int32, (1,))
+
+    def n_points(self) -> int:
+        return int(self.n_points_tensor().item())
+
+    def power(self):
+        return _region(self.mem, self.s.power, torch.float32, (self.A, self.shape[2]))
+
+    def spectrum(self):
+        return _region(self.mem, self.s.spec, torch.float32, (*self.shape, 2))
+
+    def peak_cells(self):
+        return _region(self.mem, self.s.peak_cell, torch.int32, (self.k_max,))
+
+
+def pointcloud(cube: torch.Tensor, radar, cfar, state: PcState | None = None, out: torch.Tensor | None = None,
+               stream=None):
+    """sbr_pointcloud: points [k_max, 4] (x, y, z, w) and the state holding the count."""
+    _need_cuda(cube, torch.float32, "cube")
+    if state is None:
+        state = PcState(radar, cfar, device=cube.device)
+    if out is None:
+        out = torch.empty((cfar.k_max, 4), dtype=torch.float32, device=cube.device)
+    L.call("sbr_pointcloud", _vp(cube), ctypes.byref(state.r), ctypes.byref(state.c), _vp(out),
+           ctypes.byref(state.s), _stream(stream))
+    return out, state
+
+
+def pointcloud_bwd(state: PcState, gpoints: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """sbr_pointcloud_bwd: dL/dcube [V, C, N_s, 2] from dL/dpoints [k_max, 4]."""
+    _need_cuda(gpoints, torch.float32, "gpoints")
+    if out is None:
+        out = torch.empty((*state.shape, 2), dtype=torch.float32, device=gpoints.device)
+    L.call("sbr_pointcloud_bwd", ctypes.byref(state.r), ctypes.byref(state.c), ctypes.byref(state.s),
+           _vp(gpoints), _vp(out), _stream(stream))
+    return out
+
+
+def trace_bwd(scene: Scene, verts: torch.Tensor, radar, grid, paths: PathBuffers, glen: torch.Tensor,
+              gamp: torch.Tensor, ray_ids: torch.Tensor | None = None, gverts: torch.Tensor | None = None,
+              stream=None):
+    """sbr_trace_bwd: adds dL/dverts [nv, 3] from per-path (dL/dlength, dL/dA)."""
+    _need_cuda(verts, torch.float32, "verts")
+    if gverts is None:
+        gverts = torch.zeros_like(verts)
+    r, g = radar_struct(radar), grid_struct(grid)
+    L.call("sbr_trace_bwd", scene.handle, _vp(verts), ctypes.byref(r), ctypes.byref(g), _vp(ray_ids),
+           ctypes.byref(paths.s), _vp(glen), _vp(gamp), _vp(gverts), _stream(stream))
+    return gverts
+
+
+def chamfer(pred: torch.Tensor, n_pred: torch.Tensor, target: torch.Tensor, loss: torch.Tensor | None = None,
+            gpred: torch.Tensor | None = None, stream=None):
+    """sbr_chamfer: weighted squared Chamfer loss [1] and dL/dpred [cap, 4]."""
+    _need_cuda(pred, torch.float32, "pred")
+    _need_cuda(target, torch.float32, "target")
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=pred.device)
+    if gpred is None:
+        gpred = torch.empty_like(pred)
+    L.call("sbr_chamfer", _vp(pred), _vp(n_pred), int(pred.shape[0]), _vp(target), int(target.shape[0]),
+           _vp(loss), _vp(gpred), _stream(stream))
+    return loss, gpred
+
+
+class Adjacency:
+    """CSR vertex adjacency of a mesh topology, resident on the device."""
+
+    def __init__(self, faces: np.ndarray, nv: int, device="cuda"):
+        f = np.ascontiguousarray(faces, dtype=np.int32)
+        n = ctypes.c_int32()
+        off = np.zeros(nv + 1, np.int32)
+        L.call("sbr_mesh_adjacency", f.ctypes.data_as(ctypes.c_void_p), f.shape[0], nv,
+               off.ctypes.data_as(ctypes.c_void_p), None, 0, ctypes.byref(n))
+        adj = np.zeros(max(n.value, 1), np.int32)
+        L.call("sbr_mesh_adjacency", f.ctypes.data_as(ctypes.c_void_p), f.shape[0], nv,
+               off.ctypes.data_as(ctypes.c_void_p), adj.ctypes.data_as(ctypes.c_void_p), adj.shape[0],
+               ctypes.byref(n))
+        self.nv = nv
+        self.off = torch.from_numpy(off).to(device)
+        self.adj = torch.from_numpy(adj).to(device)
+        nb = int(L.load().sbr_laplacian_ws_bytes(nv))
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def laplacian(verts: torch.Tensor, adj: Adjacency, weight: float, loss: torch.Tensor, gverts: torch.Tensor,
+              stream=None):
+    """sbr_laplacian: adds weight * uniform-Laplacian term to loss and its gradient to gverts."""
+    L.call("sbr_laplacian", _vp(verts), adj.nv, _vp(adj.off), _vp(adj.adj), float(weight), _vp(loss),
+           _vp(gverts), _vp(adj.ws), int(adj.ws.numel()), _stream(stream))
+
+
+def adam_step(params: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: torch.Tensor,
+              lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """sbr_adam_step: in-place Adam update; ``step`` is a device int32 counter it increments."""
+    L.call("sbr_adam_step", _vp(params), _vp(grad), _vp(m), _vp(v), params.numel(), _vp(step), float(lr),
+           float(beta1), float(beta2), float(eps), _stream(stream))

@@ -321,3 +321,25 @@ def request_mesh(req: dict):
         s = max(1, int(round(math.log(max(req["n_tris"], 20) / 20.0, 4))))
         v, f = perturbed_icosphere(req["seed"], min(s, 7), 0.25, (0.0, 0.0, dist))
     return v, f
+
+
+@dataclasses.dataclass
+class CfarParams:
+    """Point-extraction parameters (soft CA-CFAR over range, 3x3 peaks, top-k).
+
+    Defaults: 64 angle bins, guard 2 / train 8 range cells, 12 dB CFAR scale,
+    floor 40 dB below the map maximum, sigmoid temperature 0.5 (natural-log
+    power units), minimum weight 0.01, at most 2000 points."""
+
+    n_theta: int = 64
+    guard: int = 2
+    train: int = 8
+    alpha_db: float = 12.0
+    floor_rel: float = 1e-4
+    beta: float = 0.5
+    w_min: float = 0.01
+    k_max: int = 2000
+
+    @property
+    def alpha(self) -> float:
+        return 10.0 ** (self.alpha_db / 10.0)

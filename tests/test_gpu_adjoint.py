@@ -1,0 +1,149 @@
+"""Trace adjoint and the end-to-end reconstruction gradient against FP64 central finite
+differences of the oracle with the discrete structure (triangle sequences, peak cells,
+nearest-neighbour pairs) held at the oracle's own unperturbed values.
+Relative error |g - g_fd| / max(|g_fd|, 1e-3 max|g_fd|) <= 1e-3."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import pointcloud as opc
+from sbr_inputs import (C_LIGHT, CfarParams, Workload, icosphere, radar_single_tx, ray_grid_for_sphere,
+                        sphere_scene, superquadric)
+from tests._util import gpu_trace
+
+pytestmark = pytest.mark.gpu
+H = 1e-6  # m
+
+
+def weights(ray, k, v):
+    """Deterministic upstream gradients per (ray, bounce, antenna) for both sides."""
+    return np.sin(1.3 * ray + 0.7 * k + 2.1 * v), np.cos(0.9 * ray - 1.1 * k + 0.5 * v) * 1e4
+
+
+def oracle_L(verts, wl, tr_ref, gl, ga):
+    pa = oracle.paths(oracle.trace_frozen(verts, wl.faces, tr_ref, wl.grid), wl.radar)
+    return float((gl * pa["tau"] * C_LIGHT).sum() + (ga * pa["amp"]).sum())
+
+
+def rel_err(g, fd):
+    return np.abs(g - fd) / np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max())
+
+
+def check_trace_adjoint(sbr, wl, ids=None, n_vert_checks=12):
+    tr = oracle.trace(wl.verts, wl.faces, wl.grid, wl.max_bounces, ray_ids=ids)
+    scene, paths = gpu_trace(sbr, wl, ray_ids=ids)
+    P = paths.count()
+    ray_g = paths.path_ray().cpu().numpy()[:P]
+    first = paths.ray_first().cpu().numpy()
+    k_g = np.arange(P) - first[ray_g]
+    V = wl.radar.n_virt
+    gl = np.zeros((V, paths.cap), np.float32)
+    ga = np.zeros((V, paths.cap), np.float32)
+    for v in range(V):
+        gl[v, :P], ga[v, :P] = weights(ray_g, k_g, v)
+    vt = torch.from_numpy(wl.verts).cuda()
+    ids_t = None if ids is None else torch.from_numpy(ids).cuda()
+    g = sbr.trace_bwd(scene, vt, wl.radar, wl.grid, paths, torch.from_numpy(gl).cuda(),
+                      torch.from_numpy(ga).cuda(), ray_ids=ids_t).cpu().numpy().astype(np.float64)
+    pa = oracle.paths(tr, wl.radar)
+    glo = np.stack([weights(pa["ray"], pa["bounce"], v)[0] for v in range(V)])
+    gao = np.stack([weights(pa["ray"], pa["bounce"], v)[1] for v in range(V)])
+    # the GPU trace must have the same triangle sequences (checked elsewhere); require it here
+    assert (paths.hits()[0].cpu().numpy() == tr["tri"]).all()
+    v64 = wl.verts.astype(np.float64)
+    used = np.unique(wl.faces[tr["tri"][tr["tri"] >= 0]])
+    rng = np.random.default_rng(3)
+    for vi in rng.choice(used, size=min(n_vert_checks, used.size), replace=False):
+        for ax in range(3):
+            vp, vm = v64.copy(), v64.copy()
+            vp[vi, ax] += H
+            vm[vi, ax] -= H
+            fd = (oracle_L(vp, wl, tr, glo, gao) - oracle_L(vm, wl, tr, glo, gao)) / (2 * H)
+            scale = max(abs(fd), 1e-3 * np.abs(g).max())
+            assert abs(g[vi, ax] - fd) <= 1e-3 * scale, (vi, ax, g[vi, ax], fd)
+    # a random direction over all vertices
+    D = rng.normal(size=v64.shape)
+    fd = (oracle_L(v64 + H * D, wl, tr, glo, gao) - oracle_L(v64 - H * D, wl, tr, glo, gao)) / (2 * H)
+    assert abs((g * D).sum() - fd) <= 1e-3 * abs(fd)
+
+
+def test_trace_adjoint_sphere(sbr):
+    check_trace_adjoint(sbr, sphere_scene(G=48))
+
+
+def test_trace_adjoint_corner_three_bounces(sbr):
+    from tests.test_oracle_pins import axis_grid, corner_reflector
+    C = np.array([0.25, 0.125, 2.0])
+    v, f = corner_reflector(C, 0.75)
+    wl = Workload("corner", v, f, radar_single_tx(), axis_grid(24, 0.12, axis=C), 3, {})
+    check_trace_adjoint(sbr, wl, n_vert_checks=12)
+
+
+def recon_setup(n_rays_side=64):
+    """Reconstruction workload: superquadric target (20,000 tris) seen by the 1 Tx / 4 Rx radar,
+    icosphere template (2562 vertices) at the target's centre."""
+    sv, sf, params = superquadric(seed=5)
+    c = np.array(params["center"])
+    radar = radar_single_tx(256, 1)
+    grid = ray_grid_for_sphere(c, 0.6, n_rays_side)
+    tv, tf = icosphere(4, 0.2, c)
+    return sv, sf, tv, tf, radar, grid
+
+
+def test_reconstruction_gradient_fd(sbr):
+    """End-to-end dLoss/dverts (Chamfer + 0.1 Laplacian) vs FP64 FD on 26 seeded vertices."""
+    from paper_2311_13182_gb300.autograd import Simulator
+    sv, sf, tv, tf, radar, grid = recon_setup()
+    cfg = CfarParams()
+    K = 2
+    # target: the oracle's point cloud of the superquadric
+    twl = Workload("target", sv, sf, radar, grid, K, {})
+    tcube, _, _ = oracle.simulate_cube(twl)
+    target = opc.pointcloud(tcube, radar, cfg)["points"]
+    # oracle structure at the template
+    wl = Workload("tmpl", tv, tf, radar, grid, K, {})
+    tr = oracle.trace(tv, tf, grid, K)
+    pa = oracle.paths(tr, radar)
+    cube = oracle.synthesize(pa["tau"], pa["amp"], radar)
+    pc = opc.pointcloud(cube, radar, cfg)
+    a, k = pc["a"], pc["k"]
+    P = pc["points"]
+    nn_pq = opc._nn(P, target)[0]
+    nn_qp = opc._nn(target, P)[0]
+
+    def loss(v):
+        trf = oracle.trace_frozen(v, tf, tr, grid)
+        p = oracle.paths(trf, radar)
+        c = oracle.synthesize(p["tau"], p["amp"], radar)
+        _, _, Pw = opc.power_map(c, radar, cfg)
+        pts = opc.points_at(Pw, radar, cfg, a, k)
+        return opc.chamfer_loss(pts, target, nn_pq, nn_qp) + 0.1 * opc.laplacian(v, tf)
+
+    # GPU gradient
+    simr = Simulator(tf, tv.shape[0], radar, grid, K, cfg)
+    vt = torch.from_numpy(tv).cuda()
+    pts, n = simr.forward(vt)
+    tgt = torch.from_numpy(target.astype(np.float32)).cuda()
+    l_gpu, gpts = sbr.chamfer(pts, n, tgt)
+    g = torch.zeros_like(vt)
+    adj = sbr.Adjacency(tf, tv.shape[0])
+    sbr.laplacian(vt, adj, 0.1, l_gpu, g)
+    simr.backward(vt, gpts, g)
+    g = g.cpu().numpy().astype(np.float64)
+    n = int(n.item())
+    assert sorted(simr.state.peak_cells().cpu().numpy()[:n].tolist()) == sorted((a * 256 + k).tolist())
+    v64 = tv.astype(np.float64)
+    assert abs(float(l_gpu.item()) - loss(v64)) <= 1e-3 * abs(loss(v64))
+    rng = np.random.default_rng(26)
+    seen = np.unique(tf[tr["tri"][tr["tri"] >= 0]])
+    chosen = rng.choice(seen, size=min(26, seen.size), replace=False)
+    fd = np.zeros((len(chosen), 3))
+    for i, vi in enumerate(chosen):
+        for ax in range(3):
+            vp, vm = v64.copy(), v64.copy()
+            vp[vi, ax] += H
+            vm[vi, ax] -= H
+            fd[i, ax] = (loss(vp) - loss(vm)) / (2 * H)
+    err = rel_err(g[chosen], fd)
+    assert (err <= 1e-3).all(), err.max()

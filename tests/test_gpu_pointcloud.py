@@ -1,0 +1,108 @@
+"""GPU point cloud parity (Chamfer <= 1 mm against the FP64 oracle's chain) and its adjoint
+against FP64 central differences with the peak set held fixed."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import pointcloud as opc
+from sbr_inputs import CfarParams, ray_subset, sphere_scene, superquadric_scene
+from tests._util import cube_complex, gpu_trace, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+CHAMFER_TOL = 1e-3  # m
+
+
+def to_cube_t(cube):
+    return torch.from_numpy(np.stack([cube.real, cube.imag], -1).astype(np.float32)).cuda().contiguous()
+
+
+def gpu_points(sbr, cube_t, radar, cfg):
+    pts, st = sbr.pointcloud(cube_t, radar, cfg)
+    n = st.n_points()
+    return pts.cpu().numpy()[:n].astype(np.float64), st, n
+
+
+@pytest.mark.parametrize("scene", ["sphere", "superquadric"])
+def test_pointcloud_from_oracle_cube(sbr, scene):
+    """Same IF cube into both chains: power map, peak cells and points agree."""
+    if scene == "sphere":
+        wl, ids = sphere_scene(), None
+    else:
+        wl = superquadric_scene(seed=3, G=1024)
+        ids = ray_subset(5, wl.grid.n_rays, wl.grid.n_rays // 64)
+    cube, _, _ = oracle.simulate_cube(wl, ids)
+    cfg = CfarParams()
+    ref = opc.pointcloud(cube, wl.radar, cfg)
+    pts, st, n = gpu_points(sbr, to_cube_t(cube), wl.radar, cfg)
+    assert rel_l2(st.power().double().cpu().numpy(), ref["Pw"]) < 1e-5
+    assert n > 0 and abs(n - ref["points"].shape[0]) <= max(2, n // 50)
+    assert opc.chamfer_parity(pts, ref["points"]) <= CHAMFER_TOL
+    # strong detections: identical cells
+    strong = ref["points"][:, 3] > 0.5
+    cells_ref = set((ref["a"][strong] * wl.radar.n_samples + ref["k"][strong]).tolist())
+    cells_gpu = set(st.peak_cells().cpu().numpy()[:n].tolist())
+    assert cells_ref <= cells_gpu
+    # rows past the count are zero
+    assert (sbr.pointcloud(to_cube_t(cube), wl.radar, cfg, state=st)[0][n:] == 0).all()
+
+
+def test_end_to_end_sphere_chamfer(sbr):
+    wl = sphere_scene()
+    cube, _, _ = oracle.simulate_cube(wl)
+    ref = opc.pointcloud(cube, wl.radar)
+    _, paths = gpu_trace(sbr, wl)
+    gcube = sbr.synthesize(paths, wl.radar)
+    pts, st, n = gpu_points(sbr, gcube, wl.radar, CfarParams())
+    assert opc.chamfer_parity(pts, ref["points"]) <= CHAMFER_TOL
+
+
+def test_end_to_end_superquadric_subset_chamfer(sbr):
+    wl = superquadric_scene(seed=4, G=1024)
+    ids = ray_subset(9, wl.grid.n_rays, wl.grid.n_rays // 64)
+    cube, _, _ = oracle.simulate_cube(wl, ids)
+    ref = opc.pointcloud(cube, wl.radar)
+    _, paths = gpu_trace(sbr, wl, ray_ids=ids)
+    pts, _, n = gpu_points(sbr, sbr.synthesize(paths, wl.radar), wl.radar, CfarParams())
+    assert opc.chamfer_parity(pts, ref["points"]) <= CHAMFER_TOL
+
+
+def test_empty_cube_no_points(sbr):
+    wl = sphere_scene()
+    z = torch.zeros((4, 1, 256, 2), device="cuda")
+    pts, st = sbr.pointcloud(z, wl.radar, CfarParams())
+    assert st.n_points() == 0 and (pts == 0).all()
+
+
+def test_pointcloud_adjoint_directional_fd(sbr):
+    """dL/dcube from sbr_pointcloud_bwd vs FP64 central differences of the oracle chain with
+    its own peak cells held fixed; L = sum_i g_i . point_i."""
+    wl = sphere_scene()
+    cube, _, _ = oracle.simulate_cube(wl)
+    cfg = CfarParams()
+    ref = opc.pointcloud(cube, wl.radar, cfg)
+    a, k = ref["a"], ref["k"]
+    pts, st, n = gpu_points(sbr, to_cube_t(cube), wl.radar, cfg)
+    cells_gpu = st.peak_cells().cpu().numpy()[:n]
+    assert sorted(cells_gpu.tolist()) == sorted((a * 256 + k).tolist())
+    rng = np.random.default_rng(21)
+    g_by_cell = {int(c): rng.normal(size=4) for c in sorted(cells_gpu.tolist())}
+    g_gpu = np.zeros((cfg.k_max, 4), np.float32)
+    for i, c in enumerate(cells_gpu):
+        g_gpu[i] = g_by_cell[int(c)]
+    g_ref = np.array([g_by_cell[int(c)] for c in (a * 256 + k)])
+    gcube = sbr.pointcloud_bwd(st, torch.from_numpy(g_gpu).cuda())
+    gc = cube_complex(gcube)
+
+    def L(c):
+        _, _, Pw = opc.power_map(c, wl.radar, cfg)
+        return float((opc.points_at(Pw, wl.radar, cfg, a, k) * g_ref).sum())
+
+    scale = np.abs(cube).max()
+    for trial in range(3):
+        D = rng.normal(size=cube.shape) + 1j * rng.normal(size=cube.shape)
+        h = 1e-6 * scale
+        fd = (L(cube + h * D) - L(cube - h * D)) / (2 * h)
+        an = float((gc.real * D.real + gc.imag * D.imag).sum())
+        assert abs(an - fd) <= 1e-3 * abs(fd), (trial, an, fd)
