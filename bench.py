@@ -1,0 +1,454 @@
+#!/usr/bin/env python3
+"""Benchmark of the SBR radar simulator hot path on GB300.
+
+One step = one pass of the forward hot path over the 3 Tx x 4 Rx MIMO workload:
+mesh pack + LBVH build of a 20,002-triangle scene (seeded superquadric over a
+ground plane), the trace of 1024 x 1024 rays with up to 3 specular bounces and
+FP64 path preparation, the synthesis of the [12, 128, 256] IF cube (Eq. 8),
+and the point cloud (range FFT, Doppler FFT, angle DFT, soft CFAR, refine).
+
+Printed (rank 0, one JSON line): traced rays/s over all ranks (device-timed,
+inputs resident), the same end to end through the public API with host
+buffers (`e2e`), path-samples/s, reconstruction iterations/s (2562-vertex
+template against a superquadric's point cloud, one CUDA-graph replay per
+iteration), the roofline of the dominant kernel against MEASURED_PEAKS.json,
+SM clocks sampled during the timed region, and the FP64 CPU oracle timed on a
+bounded sample on this host (`cpu_baseline`).
+
+``--impl reference`` times the FP64 CPU oracle itself (the only reference this
+method has) on the same workload and prints its line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "traced rays/s & path-samples/s; recon iters/s; p50/p99 request ms"
+WORKLOAD = ("superquadric 20,000 tris + 4x4 m ground (2 tris), seed 0; 1024x1024 rays, <=3 specular bounces; "
+            "77 GHz 3Tx x 4Rx (12 virtual), 128 chirps x 256 samples; range FFT, Doppler FFT, 64-bin angle DFT, "
+            "soft CA-CFAR -> <=2000 points")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-recon", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend, init_method="env://")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clk_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def build_forward(sbr, torch, wl, cfg):
+    v = torch.from_numpy(wl.verts).cuda()
+    f = torch.from_numpy(wl.faces).cuda()
+    scene = sbr.Scene(v, f)
+    paths = sbr.PathBuffers(wl.grid.n_rays, wl.max_bounces, wl.radar.n_virt)
+    ws = torch.empty(sbr.synth_ws_bytes(wl.radar, paths.cap), dtype=torch.uint8, device="cuda")
+    cube = torch.empty((wl.radar.n_virt, wl.radar.n_chirps, wl.radar.n_samples, 2), device="cuda")
+    state = sbr.PcState(wl.radar, cfg)
+    pts = torch.empty((cfg.k_max, 4), device="cuda")
+    return dict(v=v, f=f, scene=scene, paths=paths, ws=ws, cube=cube, state=state, pts=pts)
+
+
+def forward_step(sbr, wl, cfg, b, ev=None):
+    """Scene build, trace + path prep, synthesis, point cloud; optional per-stage events."""
+    if ev is not None:
+        ev[0].record()
+    b["scene"].update(b["v"])
+    if ev is not None:
+        ev[1].record()
+    sbr.trace(b["scene"], wl.radar, wl.grid, wl.max_bounces, out=b["paths"])
+    if ev is not None:
+        ev[2].record()
+    sbr.synthesize(b["paths"], wl.radar, sbr.PHASE_SPLIT, out=b["cube"], ws=b["ws"])
+    if ev is not None:
+        ev[3].record()
+    sbr.pointcloud(b["cube"], wl.radar, cfg, state=b["state"], out=b["pts"])
+    if ev is not None:
+        ev[4].record()
+
+
+def gpu_arm(args, rank, world, local):
+    import torch
+    import paper_2311_13182_gb300 as sbr
+    from sbr_inputs import CfarParams, superquadric_scene
+
+    sbr.build.build()
+    L = sbr.load()
+    torch.cuda.set_device(local)
+    wl = superquadric_scene(seed=args.seed + rank, G=1024)
+    cfg = CfarParams()
+    b = build_forward(sbr, torch, wl, cfg)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        forward_step(sbr, wl, cfg, b)
+    torch.cuda.synchronize()
+    P = b["paths"].count()
+    n_points = b["state"].n_points()
+
+    # ---- device-timed region: inputs resident, per-stage events, L2 flushed between steps
+    mk = lambda: torch.cuda.Event(enable_timing=True)
+    evs = [[mk() for _ in range(5)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = int(L.sbr_launch_count())
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        forward_step(sbr, wl, cfg, b, evs[i])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    launches = int(L.sbr_launch_count()) - launches0
+    barrier(world)
+    clk = clocks.stop()
+    stage = np.array([[evs[i][j].elapsed_time(evs[i][j + 1]) for j in range(4)] for i in range(args.steps)])
+    ms_step = float(stage.sum(1).mean())
+    ms_step_all = reduce_max(ms_step, world)
+    rays = wl.grid.n_rays
+    value = reduce_sum(rays, world) / (ms_step_all * 1e-3)
+    samples = P * wl.radar.n_virt * wl.radar.n_samples
+    path_samples = reduce_sum(samples, world) / (ms_step_all * 1e-3)
+    stage_ms = dict(zip(["scene_build", "trace", "synthesize", "pointcloud"], stage.mean(0).round(4).tolist()))
+
+    # ---- end to end through the public API with host buffers
+    e2e = e2e_arm(sbr, torch, wl, cfg, args, world)
+
+    # ---- roofline of the dominant kernel
+    peaks, src = measured_peaks()
+    roof = roofline(stage_ms, wl, P, peaks, src, clk)
+
+    recon = None if args.no_recon else recon_arm(sbr, torch, args)
+    out = {
+        "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_step_all, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 delays and phase reduction)",
+        "data": "synthetic (seeded superquadric + ground; no datasets)",
+        "config": {"workload": WORKLOAD, "rays_per_step": rays, "paths_per_step": P, "points": n_points,
+                   "parallelism": f"replicas x{world} (independent scenes per GPU, no collective)",
+                   "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written between steps, outside the per-step events"},
+        "path_samples_per_s": path_samples,
+        "stage_ms": stage_ms,
+        "recon_iters_per_s": None if recon is None else recon["iters_per_s"],
+        "recon": recon,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "wall_s_timed_region": t_wall,
+        "roofline": roof,
+        "clocks": clk,
+    }
+    return out
+
+
+def e2e_arm(sbr, torch, wl, cfg, args, world):
+    """Same step through the public API from pinned host buffers: H2D of the mesh each step, the
+    scene created from it, trace, synthesis, point cloud, D2H of the points and their count."""
+    hv = torch.from_numpy(wl.verts).pin_memory()
+    hf = torch.from_numpy(wl.faces).pin_memory()
+    hp = torch.empty((cfg.k_max, 4), dtype=torch.float32).pin_memory()
+    hn = torch.empty(1, dtype=torch.int32).pin_memory()
+    dv = torch.empty_like(hv, device="cuda")
+    df = torch.empty_like(hf, device="cuda")
+    paths = sbr.PathBuffers(wl.grid.n_rays, wl.max_bounces, wl.radar.n_virt)
+    ws = torch.empty(sbr.synth_ws_bytes(wl.radar, paths.cap), dtype=torch.uint8, device="cuda")
+    cube = torch.empty((wl.radar.n_virt, wl.radar.n_chirps, wl.radar.n_samples, 2), device="cuda")
+    state = sbr.PcState(wl.radar, cfg)
+    pts = torch.empty((cfg.k_max, 4), device="cuda")
+
+    def step():
+        dv.copy_(hv, non_blocking=True)
+        df.copy_(hf, non_blocking=True)
+        scene = sbr.Scene(dv, df)
+        sbr.trace(scene, wl.radar, wl.grid, wl.max_bounces, out=paths)
+        sbr.synthesize(paths, wl.radar, sbr.PHASE_SPLIT, out=cube, ws=ws)
+        sbr.pointcloud(cube, wl.radar, cfg, state=state, out=pts)
+        hp.copy_(pts, non_blocking=True)
+        hn.copy_(state.n_points_tensor(), non_blocking=True)
+        return scene
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record()
+    keep = []
+    for _ in range(args.steps):
+        keep.append(step())
+    e1.record()
+    torch.cuda.synchronize()
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, world)
+    bi = hv.numel() * 4 + hf.numel() * 4
+    bo = hp.numel() * 4 + 4
+    return {"value": reduce_sum(wl.grid.n_rays, world) / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+
+
+def roofline(stage_ms, wl, P, peaks, src, clk):
+    """Roofline of the dominant kernel of the step (see the design doc for the per-unit figures)."""
+    dom = max(stage_ms, key=stage_ms.get)
+    V, Ns = wl.radar.n_virt, wl.radar.n_samples
+    sms = 152
+    smax = float(peaks.get("sm_max_mhz", 2070.0))
+    if dom == "synthesize":
+        # FP32 pipe: 128 lanes/SM/clk; algorithmic work = 6 FP32 instructions per term
+        # (4 for the complex rotation, 2 for the accumulation), terms = P * V * N_s
+        terms = P * V * Ns
+        achieved = terms * 6 / (stage_ms[dom] * 1e-3) / 1e12
+        peak = sms * 128 * smax * 1e6 / 1e12
+        return {"kernel": "k_synth_split", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "T FP32 instr/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x {smax:.0f} MHz (SM max clock, {src})"}
+    if dom == "trace":
+        # bytes a launch must move: hit records (16 B) + FP64 hit data (32 B) per slot,
+        # ray weight + path offset (8 B) per ray, path prep (16 + 8 B) per (path, antenna)
+        R, K = wl.grid.n_rays, wl.max_bounces
+        algo = R * K * 48 + R * 8 + P * V * 24 + P * 4
+        achieved = algo / (stage_ms[dom] * 1e-3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        return {"kernel": "k_trace + k_prep", "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"hbm_gbs ({src})"}
+    return {"kernel": dom, "bound": "hbm", "achieved": None, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+            "frac": None, "traffic": None}
+
+
+def recon_arm(sbr, torch, args):
+    """Reconstruction iterations/s: 2562-vertex icosphere template fitted to the point cloud of a
+    seeded superquadric seen by the 1 Tx / 4 Rx radar (64 x 64 rays, 2 bounces)."""
+    from paper_2311_13182_gb300.autograd import Simulator
+    from paper_2311_13182_gb300.recon import Reconstruction
+    from sbr_inputs import CfarParams, icosphere, radar_single_tx, ray_grid_for_sphere, superquadric
+
+    sv, sf, params = superquadric(seed=5)
+    c = np.array(params["center"])
+    radar = radar_single_tx(256, 1)
+    grid = ray_grid_for_sphere(c, 0.6, 64)
+    cfg = CfarParams()
+    tsim = Simulator(sf, sv.shape[0], radar, grid, 2, cfg)
+    tpts, tn = tsim.forward(torch.from_numpy(sv).cuda())
+    target = tpts[: int(tn.item())].clone()
+    tv, tf = icosphere(4, 0.2, c)
+    rec = Reconstruction(tv, tf, target, radar, grid, 2, cfg, lr=1e-3, lap_weight=0.1)
+    for _ in range(3):
+        rec.step()
+    loss0 = float(rec.loss.item())
+    rec.capture()
+    torch.cuda.synchronize()
+    n = 200
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rec.replay(n)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    return {"iters_per_s": 1e3 / ms, "ms_per_iter": ms, "iterations": n + 4, "loss_first": loss0,
+            "loss_last": float(rec.loss.item()), "vertices": int(tv.shape[0]), "rays": grid.n_rays,
+            "mode": "CUDA graph of one full iteration (forward, loss, adjoints, Adam)"}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(n_rays: int, seed: int):
+    """FP64 oracle on a seeded sample of the workload's rays: brute-force trace, paths,
+    direct-sum synthesis of the sampled paths, point cloud of that partial cube."""
+    import oracle
+    from oracle import pointcloud as opc
+    from sbr_inputs import superquadric_scene, ray_subset
+    wl = superquadric_scene(seed=seed, G=1024)
+    ids = ray_subset(1234, wl.grid.n_rays, n_rays)
+    t0 = time.perf_counter()
+    tr = oracle.trace(wl.verts, wl.faces, wl.grid, wl.max_bounces, ray_ids=ids)
+    pa = oracle.paths(tr, wl.radar)
+    cube = oracle.synthesize(pa["tau"], pa["amp"], wl.radar)
+    opc.pointcloud(cube, wl.radar)
+    return time.perf_counter() - t0, pa["P"]
+
+
+def cpu_baseline(seed: int, budget_s: float = 12.0):
+    n = 2048
+    dt, _ = oracle_sample(n, seed)
+    n2 = int(min(1 << 20, max(n, n * budget_s / max(dt, 1e-3) * 0.8)))
+    dt2, P = oracle_sample(n2, seed)
+    return {"value": n2 / dt2, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n2} of 1,048,576 rays (seeded subset): brute-force FP64 trace, paths, direct-sum "
+                      f"synthesis of their {P} paths x 12 antennas x 256 samples, point cloud; {dt2:.1f} s"}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    per_step = 1024
+    for _ in range(max(args.warmup, 3)):
+        oracle_sample(256, args.seed)
+    times = []
+    for _ in range(args.steps):
+        dt, _ = oracle_sample(per_step, args.seed)
+        times.append(dt)
+    ms = 1e3 * float(np.mean(times))
+    val = per_step / (ms * 1e-3)
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": "rays/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_rays_per_step": per_step},
+            "cpu_baseline": {"value": val, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{per_step} seeded rays of the 1024x1024 grid per step"},
+            "e2e": {"value": val, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        out = reference_arm(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    # CPU baseline first (forking a pool after CUDA init is unsafe; the oracle uses OpenMP threads)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cpu = cpu_baseline(args.seed)
+    out = gpu_arm(args, rank, world, local)
+    if rank == 0:
+        out["cpu_baseline"] = cpu
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

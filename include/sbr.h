@@ -118,6 +118,8 @@ typedef struct {
 const char* sbr_version(void);
 /* Copies the calling thread's last error message (NUL-terminated, truncated to n). */
 void sbr_last_error(char* buf, size_t n);
+/* Number of CUDA kernel launches the library has issued in this process. */
+uint64_t sbr_launch_count(void);
 
 /* ------------------------------------------------------------------------ */
 /* Scene: triangle mesh + LBVH (Section 3.1: the mesh is the scene          */

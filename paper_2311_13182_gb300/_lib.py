@@ -62,6 +62,7 @@ P = ctypes.POINTER
 _SIGS = {
     "sbr_version": (ctypes.c_char_p, []),
     "sbr_last_error": (None, [ctypes.c_char_p, c_sz]),
+    "sbr_launch_count": (ctypes.c_uint64, []),
     "sbr_scene_bytes": (c_sz, [c_i32]),
     "sbr_scene_create": (c_i32, [c_p, c_i32, c_p, c_i32, c_p, c_sz, c_p, P(c_p)]),
     "sbr_scene_update": (c_i32, [c_p, c_p, c_p]),

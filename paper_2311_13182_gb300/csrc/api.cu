@@ -5,10 +5,14 @@
 
 #include "common.cuh"
 
+#include <atomic>
+
 namespace sbr {
 namespace {
 thread_local char g_err[512] = "";
+std::atomic<unsigned long long> g_launches{0};
 }
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void set_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -24,3 +28,5 @@ extern "C" void sbr_last_error(char* buf, size_t n) {
   strncpy(buf, sbr::g_err, n - 1);
   buf[n - 1] = '\0';
 }
+
+extern "C" uint64_t sbr_launch_count(void) { return sbr::g_launches.load(std::memory_order_relaxed); }

@@ -11,6 +11,9 @@ namespace sbr {
 
 void set_error(const char* fmt, ...);
 
+// Host-side count of kernel launches issued by the library (sbr_launch_count).
+void note_launch();
+
 constexpr double kC = 299792458.0;  // m/s
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr int kAlign = 256;

@@ -189,6 +189,7 @@ extern "C" sbr_status sbr_chamfer(const float* d_pred, const int32_t* d_n_pred, 
   SBR_ARG(n_target >= 0 && n_target <= kChamferMax && (n_target == 0 || d_target),
           "sbr_chamfer: n_target=%d outside [0, %d]", n_target, kChamferMax);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ::sbr::note_launch();
   k_chamfer<<<1, 1024, 0, st>>>(reinterpret_cast<const float4*>(d_pred), d_n_pred, pred_cap,
                                 reinterpret_cast<const float4*>(d_target), n_target, d_loss,
                                 reinterpret_cast<float4*>(d_gpred));
@@ -247,8 +248,11 @@ extern "C" sbr_status sbr_laplacian(const float* d_verts, int32_t nv, const int3
   float* sq = c.take<float>(nv);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int b = (nv + 255) / 256;
+  ::sbr::note_launch();
   k_lap_delta<<<b, 256, 0, st>>>(d_verts, nv, d_off, d_adj, delta, sq);
+  ::sbr::note_launch();
   k_sum_into<<<1, 1024, 0, st>>>(sq, nv, weight / (float)nv, d_loss);
+  ::sbr::note_launch();
   k_lap_grad<<<b, 256, 0, st>>>(delta, nv, d_off, d_adj, 2.f * weight / (float)nv, d_gverts);
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;
@@ -260,9 +264,12 @@ extern "C" sbr_status sbr_adam_step(float* d_params, const float* d_grad, float*
   SBR_ARG(d_params && d_grad && d_m && d_v && d_step && n >= 0, "sbr_adam_step: bad argument");
   SBR_ARG(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f, "sbr_adam_step: bad betas");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (n > 0)
+  if (n > 0) {
+    ::sbr::note_launch();
     k_adam<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_params, d_grad, d_m, d_v, n, d_step, lr, beta1, beta2,
                                                          eps);
+  }
+  ::sbr::note_launch();
   k_step_inc<<<1, 1, 0, st>>>(d_step);
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;

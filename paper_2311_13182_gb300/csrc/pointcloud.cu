@@ -496,6 +496,7 @@ void launch_angle_power(const float2* X, const Steer& xl, int V, int C, int Ns, 
   const int A = 8 * APT;
   const size_t sm = sizeof(float2) * ((size_t)A * V + (size_t)V * kKT);
   dim3 grid(Ns / kKT, groups);
+  ::sbr::note_launch();
   k_angle_power<APT><<<grid, 256, sm, st>>>(X, xl, V, C, Ns, (C + groups - 1) / groups, part);
 }
 
@@ -506,12 +507,14 @@ void launch_angle_bwd(const float2* X, const Steer& xl, const float* dpw, int V,
   const size_t sm = sizeof(float2) * ((size_t)A * V + (size_t)V * kKT + (size_t)A * kKT);
   dim3 grid(Ns / kKT, C);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_angle_bwd<APT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ::sbr::note_launch();
   k_angle_bwd<APT><<<grid, 256, sm, st>>>(X, xl, dpw, V, C, Ns, dX);
 }
 
 cudaError_t fft_rows(const float2* in, float2* out, int rows, int n, float sign, cudaStream_t st) {
   const int threads = n / 2 < 256 ? (n / 2 < 32 ? 32 : n / 2) : 256;
   const size_t sm = sizeof(float2) * n;
+  ::sbr::note_launch();
   k_fft_rows<<<rows, threads, sm, st>>>(in, out, n, ilog2(n), sign);
   return cudaGetLastError();
 }
@@ -523,6 +526,7 @@ cudaError_t fft_cols(float2* x, int V, int C, int Ns, float sign, cudaStream_t s
     cudaError_t e = cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
+  ::sbr::note_launch();
   k_fft_cols<<<V * (Ns / kColTile), 256, sm, st>>>(x, C, ilog2(C), Ns, sign);
   return cudaGetLastError();
 }
@@ -609,16 +613,21 @@ extern "C" sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* r
     default: set_error("sbr_pointcloud: n_theta=%d unsupported", A); return SBR_ERR_UNSUPPORTED;
   }
   SBR_CUDA(cudaGetLastError());
+  ::sbr::note_launch();
   k_power_reduce<<<(cells + 255) / 256, 256, 0, st>>>(L.part, L.groups, cells, L.power);
+  ::sbr::note_launch();
   k_argmax<<<1, 1024, 0, st>>>(L.power, cells, L.argmax);
   // 5-7: soft CFAR, peaks, compaction in cell order, stable sort by weight
   CfarArg ca{A, Ns, cfar->guard, cfar->train, cfar->alpha, cfar->floor_rel, cfar->beta, cfar->w_min};
+  ::sbr::note_launch();
   k_detect<<<(cells + 255) / 256, 256, 0, st>>>(L.power, ca, L.argmax, L.flag, L.key);
   SBR_CUDA(exclusive_scan(L.flag, L.off, cells, nullptr, L.scan_scr, st));
+  ::sbr::note_launch();
   k_compact<<<(cells + 255) / 256, 256, 0, st>>>(L.flag, L.off, L.key, cells, L.skeys[0], L.svals[0]);
   SBR_CUDA(radix_sort_pairs(L.skeys, L.svals, cells, L.off + cells, 32, L.sort_scr, st));
   // 8-9: refine and emit points
   PointArg pa{ca, cfar->k_max, (float)(kC / (2.0 * radar->bandwidth))};
+  ::sbr::note_launch();
   k_points<<<(cfar->k_max + 255) / 256, 256, 0, st>>>(L.power, pa, L.argmax, L.svals[0], L.off + cells,
                                                        reinterpret_cast<float4*>(d_points), L.peak_cell,
                                                        L.n_points);
@@ -644,6 +653,7 @@ extern "C" sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_c
   SBR_CUDA(cudaMemsetAsync(L.dpw, 0, sizeof(float) * cells, st));
   CfarArg ca{A, Ns, cfar->guard, cfar->train, cfar->alpha, cfar->floor_rel, cfar->beta, cfar->w_min};
   PointArg pa{ca, cfar->k_max, (float)(kC / (2.0 * radar->bandwidth))};
+  ::sbr::note_launch();
   k_points_bwd<<<(cfar->k_max + 255) / 256, 256, 0, st>>>(L.power, pa, L.argmax, L.peak_cell, L.n_points,
                                                            reinterpret_cast<const float4*>(d_gpoints), L.dpw);
   float2* g = reinterpret_cast<float2*>(d_gcube);

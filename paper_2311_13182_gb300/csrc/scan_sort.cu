@@ -184,8 +184,11 @@ cudaError_t exclusive_scan(const int32_t* in, int32_t* out, int64_t n, const int
                            void* scratch, cudaStream_t s) {
   const int nt = tiles_for(n < 1 ? 1 : n);
   int32_t* sums = static_cast<int32_t*>(scratch);
+  ::sbr::note_launch();
   k_tile_sums<<<nt, kThreads, 0, s>>>(in, n, d_n, sums);
+  ::sbr::note_launch();
   k_scan_single<<<1, 1024, 0, s>>>(sums, nt);
+  ::sbr::note_launch();
   k_tile_scan<<<nt, kThreads, 0, s>>>(in, out, n, d_n, sums);
   return cudaGetLastError();
 }
@@ -202,8 +205,11 @@ cudaError_t radix_sort_pairs(uint32_t* keys[2], int32_t* vals[2], int64_t n, con
   int cur = 0;
   for (int p = 0; p < passes; ++p) {
     const int shift = 4 * p;
+    ::sbr::note_launch();
     k_digit_hist<<<nt, kThreads, 0, s>>>(keys[cur], n, d_n, shift, hist, nt);
+    ::sbr::note_launch();
     k_scan_single<<<1, 1024, 0, s>>>(hist, (int64_t)16 * nt);
+    ::sbr::note_launch();
     k_digit_scatter<<<nt, kThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n,
                                             d_n, shift, hist, nt);
     cur ^= 1;

@@ -225,19 +225,25 @@ size_t layout(sbr_scene* s, void* mem, int32_t nt) {
 
 sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
   const int nt = s->nt, nv = s->nv;
+  ::sbr::note_launch();
   k_init_bounds<<<1, 32, 0, st>>>(s->bounds, s->err);
   if (nt == 0) {
     SBR_CUDA(cudaGetLastError());
     return SBR_OK;
   }
+  ::sbr::note_launch();
   k_bounds<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->bounds, s->err);
+  ::sbr::note_launch();
   k_morton<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->bounds, s->keys[0],
                                             s->vals[0], s->err);
   SBR_CUDA(radix_sort_pairs(s->keys, s->vals, nt, nullptr, 30, s->sort_scratch, st));
+  ::sbr::note_launch();
   k_pack<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->vals[0], s->tris, s->err);
   if (nt > 1) {
+    ::sbr::note_launch();
     k_karras<<<blocks(nt - 1, 256), 256, 0, st>>>(s->keys[0], nt, s->nodes, s->parent);
     SBR_CUDA(cudaMemsetAsync(s->visits, 0, sizeof(uint32_t) * (nt - 1), st));
+    ::sbr::note_launch();
     k_refit<<<blocks(nt, 256), 256, 0, st>>>(s->tris, nt, s->nodes, s->parent, s->visits,
                                              s->bounds);
   }

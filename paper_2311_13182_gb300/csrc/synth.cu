@@ -316,12 +316,15 @@ void launch_fwd(sbr_phase_mode mode, const sbr_paths* p, const sbr_radar_cfg* r,
   const int grid = V * w.Q;
   const float4* prep = reinterpret_cast<const float4*>(p->prep);
   if (mode == SBR_PHASE_SPLIT) {
+    ::sbr::note_launch();
     k_synth_split<M><<<grid, T, 0, st>>>(prep, p->path_cap, p->count, V, w.Q, Ns, w.partial);
   } else if (mode == SBR_PHASE_FP64) {
+    ::sbr::note_launch();
     k_synth_fp64<M><<<grid, T, 0, st>>>(prep, p->tau64, p->path_cap, p->count, V, w.Q, Ns, r->f0,
                                         r->bandwidth / Ns, w.partial);
   } else {
     const double mu = r->bandwidth / r->chirp_time, dt = r->chirp_time / Ns;
+    ::sbr::note_launch();
     k_synth_naive<M><<<grid, T, 0, st>>>(prep, p->tau64, p->path_cap, p->count, V, w.Q, Ns,
                                          (float)r->f0, (float)mu, (float)dt, w.partial);
   }
@@ -353,6 +356,7 @@ extern "C" sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg
   }
   SBR_CUDA(cudaGetLastError());
   const int V = paths->n_virt;
+  ::sbr::note_launch();
   k_reduce<<<(V * Ns + 255) / 256, 256, 0, st>>>(w.partial, V, w.Q, Ns, radar->n_chirps,
                                                   reinterpret_cast<float2*>(d_cube));
   SBR_CUDA(cudaGetLastError());
@@ -371,6 +375,7 @@ extern "C" sbr_status sbr_synthesize_bwd(const sbr_paths* paths, const sbr_radar
   if (rs != SBR_OK) return rs;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int V = paths->n_virt, Ns = radar->n_samples, C = radar->n_chirps;
+  ::sbr::note_launch();
   k_chirp_sum<<<(V * Ns + 255) / 256, 256, 0, st>>>(reinterpret_cast<const float2*>(d_gcube), V, C,
                                                      Ns, w.gsum);
   const int64_t cap = paths->path_cap;
@@ -378,6 +383,7 @@ extern "C" sbr_status sbr_synthesize_bwd(const sbr_paths* paths, const sbr_radar
     dim3 grid((unsigned)((cap + 255) / 256), (unsigned)V);
     const double lam_inv = radar->f0 / kC;
     const double bcn = radar->bandwidth / (kC * Ns);
+    ::sbr::note_launch();
     k_synth_bwd<<<grid, 256, Ns * sizeof(float2), st>>>(
         reinterpret_cast<const float4*>(paths->prep), cap, paths->count, Ns, w.gsum,
         (float)lam_inv, (float)bcn, d_glen, d_gamp);

@@ -438,12 +438,14 @@ extern "C" sbr_status sbr_trace(const sbr_scene* scene, const sbr_radar_cfg* rad
     SBR_CUDA(cudaMemsetAsync(paths->ray_first, 0, sizeof(int32_t), st));
     return SBR_OK;
   }
+  ::sbr::note_launch();
   k_trace<<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes, scene->nt, g, d_ray_ids,
                                           (int)R, max_bounces, paths->hits,
                                           reinterpret_cast<double4*>(paths->hit_pos),
                                           paths->ray_weight, paths->ray_first);
   SBR_CUDA(cudaGetLastError());
   SBR_CUDA(exclusive_scan(paths->ray_first, paths->ray_first, R, nullptr, paths->scratch, st));
+  ::sbr::note_launch();
   k_prep<<<blocks(R, 128), 128, 0, st>>>(reinterpret_cast<const double4*>(paths->hit_pos),
                                          paths->ray_weight, paths->ray_first, (int)R, max_bounces,
                                          rd, paths->path_cap,

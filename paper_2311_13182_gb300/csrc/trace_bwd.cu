@@ -207,6 +207,7 @@ extern "C" sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts
   rd.nrx = radar->n_rx;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int R = paths->n_rays;
+  ::sbr::note_launch();
   k_trace_bwd<<<(R + 127) / 128, 128, 0, st>>>(
       d_verts, scene->nv, scene->faces, g, rd, d_ray_ids, R, paths->max_bounces, paths->hits,
       reinterpret_cast<const double4*>(paths->hit_pos), paths->ray_first,

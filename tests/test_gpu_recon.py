@@ -18,25 +18,32 @@ def target_points(sv, sf, radar, grid):
 
 
 def test_recon_graph_matches_eager_and_descends(sbr):
+    """A replay of the captured iteration computes what an eager iteration computes from the
+    same state (gradients agree up to float-atomic ordering), and the loss decreases."""
     from paper_2311_13182_gb300.recon import Reconstruction
     sv, sf, tv, tf, radar, grid = recon_setup()
     tgt = target_points(sv, sf, radar, grid)
     a = Reconstruction(tv, tf, tgt, radar, grid, 2, CfarParams(), lr=1e-3)
     b = Reconstruction(tv, tf, tgt, radar, grid, 2, CfarParams(), lr=1e-3)
-    losses = []
+    a.step()
+    loss0 = float(a.loss.item())
+    b.step()
+    b.capture()
     for _ in range(3):
         a.step()
-        b.step()
-        losses.append(float(a.loss.item()))
-    b.capture()          # runs one warm-up iteration; capture itself only records
+    for x, y in ((b.verts, a.verts), (b.m, a.m), (b.v, a.v), (b.step_count, a.step_count)):
+        x.copy_(y)
+    b.replay()
     a.step()
-    for _ in range(20):
-        b.replay()
-        a.step()
     torch.cuda.synchronize()
-    assert int(a.step_count.item()) == int(b.step_count.item()) == 24
-    np.testing.assert_allclose(b.verts.cpu().numpy(), a.verts.cpu().numpy(), atol=2e-5)
-    assert float(a.loss.item()) < losses[0]
+    ga, gb = a.grad.cpu().numpy(), b.grad.cpu().numpy()
+    np.testing.assert_allclose(gb, ga, rtol=1e-3, atol=1e-5 * np.abs(ga).max())
+    assert abs(float(b.loss.item()) - float(a.loss.item())) <= 1e-5 * abs(float(a.loss.item()))
+    assert int(a.step_count.item()) == int(b.step_count.item()) == 5
+    for _ in range(30):
+        b.replay()
+    torch.cuda.synchronize()
+    assert float(b.loss.item()) < loss0
 
 
 def test_recompute_paths_same_gradient(sbr):
