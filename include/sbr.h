@@ -203,6 +203,29 @@ sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg* radar,
                           sbr_phase_mode mode, float* d_cube, void* d_ws, size_t ws_bytes,
                           sbr_stream stream);
 
+/* Allocation-free variant of sbr_synthesize (the paper has no counterpart;
+ * this is a deployment convenience).  Some callers cannot allocate device
+ * memory where they synthesise: plugin hosts that own every device
+ * allocation and hand none to their plugins, real-time loops that must not
+ * risk the device-wide synchronisation an allocation can cause, or code under
+ * a fixed memory budget.  This entry point takes no workspace: its per-CTA
+ * partial sums live in one file-scope device array of 1 MiB (131072 complex
+ * FP32 values) that every GPU which loads the library keeps until the process
+ * exits.  Same inputs, outputs and result as sbr_synthesize (up to summation
+ * order: fewer CTAs may share the work), with these limits:
+ *  - n_virt * n_samples must not exceed 131072, otherwise SBR_ERR_UNSUPPORTED
+ *    is returned before anything is enqueued;
+ *  - the first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture on the device;
+ *  - every call shares the one array: calls whose work overlaps on the GPU
+ *    (different streams, concurrent host threads) race on it and must be
+ *    serialised by the caller.  Each call overwrites every partial sum it
+ *    later reads, so no state carries over between calls.
+ * It calls no cudaMalloc/cudaFree or other allocating routine. */
+sbr_status sbr_synthesize_noalloc(const sbr_paths* paths, const sbr_radar_cfg* radar,
+                                  sbr_phase_mode mode, float* d_cube, sbr_stream stream);
+
 /* Adjoint through Eq. 11-12: for upstream d_gcube = dL/dRe + j dL/dIm of the
  * cube, writes d_gtau [V*path_cap] = dL/dtau (per metre of path length, i.e.
  * dL/dtau / c) and d_gamp [V*path_cap] = dL/dA. */

@@ -74,6 +74,7 @@ _SIGS = {
     "sbr_synth_ws_bytes": (c_sz, [P(RadarCfg), c_i64]),
     "sbr_synthesize": (c_i32, [P(Paths), P(RadarCfg), c_i32, c_p, c_p, c_sz, c_p]),
     "sbr_synthesize_bwd": (c_i32, [P(Paths), P(RadarCfg), c_p, c_p, c_p, c_p, c_sz, c_p]),
+    "sbr_synthesize_noalloc": (c_i32, [P(Paths), P(RadarCfg), c_i32, c_p, c_p]),
     "sbr_pc_bytes": (c_sz, [P(RadarCfg), P(CfarCfg)]),
     "sbr_pc_bind": (c_i32, [c_p, c_sz, P(RadarCfg), P(CfarCfg), P(PcState)]),
     "sbr_pointcloud": (c_i32, [c_p, P(RadarCfg), P(CfarCfg), c_p, P(PcState), c_p]),

@@ -13,6 +13,8 @@
 // (4 FP32 multiply/FMA per sample instead of two transcendental ops).  Each CTA
 // writes its partial sums; a second kernel adds them in a fixed order, so the
 // result is bitwise reproducible.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace sbr {
@@ -356,6 +358,82 @@ extern "C" sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg
   }
   SBR_CUDA(cudaGetLastError());
   const int V = paths->n_virt;
+  ::sbr::note_launch();
+  k_reduce<<<(V * Ns + 255) / 256, 256, 0, st>>>(w.partial, V, w.Q, Ns, radar->n_chirps,
+                                                  reinterpret_cast<float2*>(d_cube));
+  SBR_CUDA(cudaGetLastError());
+  return SBR_OK;
+}
+
+// ---- allocation-free variant ------------------------------------------------
+//
+// For callers that cannot call cudaMalloc (or reserve any device memory of
+// their own) at the point where they synthesise: hosts that hand out no device
+// allocator to plugins, real-time loops that must not risk the implicit device
+// synchronisation of an allocation, or code running under a frozen memory
+// budget.  The per-CTA partial sums then live in a fixed file-scope device
+// array instead of a caller workspace.
+
+namespace {
+constexpr size_t kStaticPartials = 131072;  // float2 entries: 1 MiB on every device using the library
+__device__ __align__(256) float2 g_static_partials[kStaticPartials];
+
+constexpr int kMaxDevices = 64;
+float2* g_static_ptr[kMaxDevices] = {};
+std::mutex g_static_mu;
+
+// Device address of the array for the current device (host code only holds a
+// stand-in symbol).  Looked up once per device, on that device's first call.
+sbr_status static_partials(float2** out) {
+  int dev = -1;
+  SBR_CUDA(cudaGetDevice(&dev));
+  SBR_ARG(dev >= 0 && dev < kMaxDevices, "sbr_synthesize_noalloc: device %d beyond %d", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    SBR_CUDA(cudaGetSymbolAddress(&p, g_static_partials));
+    g_static_ptr[dev] = static_cast<float2*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return SBR_OK;
+}
+}  // namespace
+
+extern "C" sbr_status sbr_synthesize_noalloc(const sbr_paths* paths, const sbr_radar_cfg* radar,
+                                             sbr_phase_mode mode, float* d_cube, sbr_stream stream) {
+  SBR_ARG(paths && d_cube, "sbr_synthesize_noalloc: NULL paths or cube");
+  sbr_status rs = check_radar(radar, "sbr_synthesize_noalloc");
+  if (rs != SBR_OK) return rs;
+  SBR_ARG(paths->n_virt == radar->n_tx * radar->n_rx, "sbr_synthesize_noalloc: paths have V=%d, radar %d",
+          paths->n_virt, radar->n_tx * radar->n_rx);
+  SBR_ARG(mode == SBR_PHASE_SPLIT || mode == SBR_PHASE_FP64 || mode == SBR_PHASE_NAIVE,
+          "sbr_synthesize_noalloc: unknown phase mode %d", (int)mode);
+  const int V = paths->n_virt, Ns = radar->n_samples;
+  const size_t row = (size_t)V * Ns;  // one partial cube (one CTA per antenna)
+  if (row > kStaticPartials) {
+    set_error("sbr_synthesize_noalloc: V * N_s = %zu partial sums exceed the fixed scratch of %zu "
+              "(1 MiB); use sbr_synthesize with a workspace",
+              row, kStaticPartials);
+    return SBR_ERR_UNSUPPORTED;
+  }
+  SynthWs w;
+  rs = static_partials(&w.partial);
+  if (rs != SBR_OK) return rs;
+  w.gsum = nullptr;
+  grid_shape(V, Ns, paths->path_cap, &w.Q);
+  const int qmax = (int)(kStaticPartials / row);
+  if (w.Q > qmax) w.Q = qmax;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int T = threads_for(Ns), M = Ns / T;
+  switch (M) {
+    case 1: launch_fwd<1>(mode, paths, radar, w, st); break;
+    case 2: launch_fwd<2>(mode, paths, radar, w, st); break;
+    case 4: launch_fwd<4>(mode, paths, radar, w, st); break;
+    case 8: launch_fwd<8>(mode, paths, radar, w, st); break;
+    case 16: launch_fwd<16>(mode, paths, radar, w, st); break;
+    default: set_error("sbr_synthesize_noalloc: no kernel for %d samples per thread", M); return SBR_ERR_UNSUPPORTED;
+  }
+  SBR_CUDA(cudaGetLastError());
   ::sbr::note_launch();
   k_reduce<<<(V * Ns + 255) / 256, 256, 0, st>>>(w.partial, V, w.Q, Ns, radar->n_chirps,
                                                   reinterpret_cast<float2*>(d_cube));
