@@ -161,12 +161,14 @@ typedef struct {
   int32_t n_rays, max_bounces, n_virt, _pad;
   int64_t path_cap;   /* = n_rays * max_bounces */
   sbr_hit* hits;      /* [R*K] nearest hits */
-  double* hit_pos;    /* [R*K*4] FP64 hit point xyz and |d_k . n_k| */
+  float* hit_pos;     /* [R*K*8] hit point as float-float pairs: x = [0] + [1],
+                         y = [2] + [3], z = [4] + [5] (about 48 bits); [6] = |d_k . n_k| */
   float* ray_weight;  /* [R] solid-angle weight omega */
   int32_t* ray_first; /* [R+1] first path of each ray (exclusive scan); [R] = P */
   int32_t* path_ray;  /* [path_cap] ray of path p */
   float* prep;        /* [V*path_cap*4] {phi0, delta_hi, delta_lo, A} per (v, p) */
-  double* tau64;      /* [V*path_cap] FP64 delay per (v, p) */
+  float* path_len;    /* [V*path_cap*2] path length L_in + L_out [m] per (v, p) as a
+                         float-float pair (hi, lo); tau = L / c */
   int32_t* count;     /* [1] P (device) */
   void* scratch;      /* scan scratch */
 } sbr_paths;
@@ -198,7 +200,8 @@ size_t sbr_synth_ws_bytes(const sbr_radar_cfg* radar, int64_t path_cap);
 /* d_cube [V][C][N_s] complex64 (interleaved re, im) =
  *   sum_p A_{p,v} exp(j 2 pi (f_c tau_{p,v} + mu tau_{p,v} t_n)),
  * broadcast over the C chirps of a static scene.  Deterministic: partial sums
- * per CTA are reduced in a fixed order.  SBR_PHASE_FP64 needs paths->tau64. */
+ * per CTA are reduced in a fixed order.  SBR_PHASE_FP64 forms each sample's phase
+ * in FP64 from paths->path_len; SBR_PHASE_NAIVE rounds the delay to FP32. */
 sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg* radar,
                           sbr_phase_mode mode, float* d_cube, void* d_ws, size_t ws_bytes,
                           sbr_stream stream);

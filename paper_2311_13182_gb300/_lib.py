@@ -48,7 +48,7 @@ class CfarCfg(ctypes.Structure):
 class Paths(ctypes.Structure):
     _fields_ = [("n_rays", c_i32), ("max_bounces", c_i32), ("n_virt", c_i32), ("_pad", c_i32),
                 ("path_cap", c_i64), ("hits", c_p), ("hit_pos", c_p), ("ray_weight", c_p),
-                ("ray_first", c_p), ("path_ray", c_p), ("prep", c_p), ("tau64", c_p), ("count", c_p),
+                ("ray_first", c_p), ("path_ray", c_p), ("prep", c_p), ("path_len", c_p), ("count", c_p),
                 ("scratch", c_p)]
 
 

@@ -24,8 +24,6 @@
 namespace sbr {
 namespace {
 
-constexpr float kCf = 299792458.0f;
-
 __device__ inline float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }

@@ -174,6 +174,177 @@ __global__ void k_digit_scatter(const uint32_t* __restrict__ kin, const int32_t*
 
 inline int tiles_for(int64_t n) { return (int)((n + kTile - 1) / kTile); }
 
+// ---- single-CTA variants for small inputs -----------------------------------
+//
+// Below kSmall elements a whole sort or scan runs in one CTA (one launch
+// instead of three per pass): 1024 threads sweep the array in rounds of
+// 1024 x kItems, keeping per-digit running offsets across rounds so the
+// scatter stays stable.
+
+constexpr int kSmall = 32768;  // packed 16-bit digit counts stay below 2^16
+constexpr int kSmallThreads = 1024;
+constexpr int kBitonicMax = 2048;  // keys sorted in shared memory by one bitonic network
+
+__global__ void __launch_bounds__(kSmallThreads) k_scan_small(const int32_t* __restrict__ in,
+                                                              int32_t* __restrict__ out, int64_t cap,
+                                                              const int32_t* d_n) {
+  __shared__ uint32_t wt[32];
+  const int64_t n = clamp_n(cap, d_n);
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < n; base += (int64_t)kSmallThreads * kItems) {
+    const int64_t b = base + (int64_t)threadIdx.x * kItems;
+    int32_t v[kItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      v[i] = b + i < n ? in[b + i] : 0;
+      s += (uint32_t)v[i];
+    }
+    uint32_t tot;
+    uint32_t run = carry + block_exclusive(s, &tot, wt);
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      if (b + i < n) out[b + i] = (int32_t)run;
+      run += (uint32_t)v[i];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) out[n] = (int32_t)carry;
+}
+
+__global__ void __launch_bounds__(kSmallThreads) k_sort_small(uint32_t* k0, int32_t* v0, uint32_t* k1,
+                                                              int32_t* v1, int64_t cap, const int32_t* d_n,
+                                                              int passes) {
+  __shared__ uint32_t wt[32];
+  __shared__ uint32_t hist[16];
+  __shared__ uint32_t carry[16];
+  __shared__ unsigned long long bsort[kBitonicMax];
+  const int64_t n = clamp_n(cap, d_n);
+  if (n <= kBitonicMax) {
+    // few live keys: bitonic sort of (key, value) pairs in shared memory; the
+    // values are distinct and already ascending in input order for equal keys
+    // (cell order), so the lexicographic order equals the stable radix order
+    int N = 1;
+    while (N < n) N <<= 1;
+    for (int i = threadIdx.x; i < N; i += kSmallThreads)
+      bsort[i] = i < n ? ((unsigned long long)k0[i] << 32) | (uint32_t)v0[i] : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= N; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < N; i += kSmallThreads) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const unsigned long long a = bsort[i], b = bsort[ixj];
+            if ((a > b) == ((i & k) == 0)) {
+              bsort[i] = b;
+              bsort[ixj] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int i = threadIdx.x; i < n; i += kSmallThreads) {
+      k0[i] = (uint32_t)(bsort[i] >> 32);
+      v0[i] = (int32_t)(uint32_t)bsort[i];
+    }
+    return;
+  }
+  uint32_t* kin = k0;
+  int32_t* vin = v0;
+  uint32_t* kout = k1;
+  int32_t* vout = v1;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 4 * p;
+    {
+      // digit totals: packed 16-bit per-thread counts, reduced across the CTA
+      // (no shared-memory atomics: 16 counters hit by every thread serialise)
+      uint32_t cnt[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) cnt[j] = 0;
+      for (int64_t base = 0; base < n; base += (int64_t)kSmallThreads * kItems) {
+        const int64_t b = base + (int64_t)threadIdx.x * kItems;
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+          if (b + i >= n) break;
+          const int d = (int)((kin[b + i] >> shift) & 15u);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if ((d >> 1) == j) cnt[j] += 1u << (16 * (d & 1));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint32_t tot;
+        block_exclusive(cnt[j], &tot, wt);
+        if (threadIdx.x == 0) {
+          hist[2 * j] = tot & 0xffffu;
+          hist[2 * j + 1] = tot >> 16;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t s = 0;
+      for (int d = 0; d < 16; ++d) {
+        carry[d] = s;  // running start of each digit's output range
+        s += hist[d];
+      }
+    }
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += (int64_t)kSmallThreads * kItems) {
+      const int64_t b = base + (int64_t)threadIdx.x * kItems;
+      uint32_t key[kItems];
+      int32_t val[kItems];
+      int dig[kItems];
+      uint32_t cnt[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) cnt[j] = 0;
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        const bool ok = b + i < n;
+        key[i] = ok ? kin[b + i] : 0u;
+        val[i] = ok ? vin[b + i] : 0;
+        dig[i] = ok ? (int)((key[i] >> shift) & 15u) : -1;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (ok && (dig[i] >> 1) == j) cnt[j] += 1u << (16 * (dig[i] & 1));
+      }
+      uint32_t pre[8], tot[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) pre[j] = block_exclusive(cnt[j], &tot[j], wt);
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        if (dig[i] < 0) continue;
+        const int d = dig[i];
+        uint32_t q = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if ((d >> 1) == j) q = pre[j];
+        const int64_t pos = (int64_t)carry[d] + ((q >> (16 * (d & 1))) & 0xffffu);
+        kout[pos] = key[i];
+        vout[pos] = val[i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if ((d >> 1) == j) pre[j] += 1u << (16 * (d & 1));
+      }
+      __syncthreads();  // every thread has read carry[] for this round
+      if (threadIdx.x < 16) {
+        const int d = threadIdx.x;
+        carry[d] += (tot[d >> 1] >> (16 * (d & 1))) & 0xffffu;
+      }
+      __syncthreads();
+    }
+    uint32_t* tk = kin;
+    kin = kout;
+    kout = tk;
+    int32_t* tv = vin;
+    vin = vout;
+    vout = tv;
+    __syncthreads();  // the pass's writes are visible to the whole CTA
+  }
+}
+
 }  // namespace
 
 size_t scan_scratch_bytes(int64_t capacity) {
@@ -182,6 +353,11 @@ size_t scan_scratch_bytes(int64_t capacity) {
 
 cudaError_t exclusive_scan(const int32_t* in, int32_t* out, int64_t n, const int32_t* d_n,
                            void* scratch, cudaStream_t s) {
+  if (n <= kSmall) {
+    ::sbr::note_launch();
+    k_scan_small<<<1, kSmallThreads, 0, s>>>(in, out, n, d_n);
+    return cudaGetLastError();
+  }
   const int nt = tiles_for(n < 1 ? 1 : n);
   int32_t* sums = static_cast<int32_t*>(scratch);
   ::sbr::note_launch();
@@ -199,9 +375,17 @@ size_t sort_scratch_bytes(int64_t capacity) {
 
 cudaError_t radix_sort_pairs(uint32_t* keys[2], int32_t* vals[2], int64_t n, const int32_t* d_n,
                              int bits, void* scratch, cudaStream_t s) {
+  const int passes = (bits + 3) / 4;
+  // one CTA wins when few keys are live: a device-side count (usually far below
+  // the capacity, e.g. detected peaks) or a small host count; a 20k-key sort
+  // is faster spread over many CTAs
+  if (passes % 2 == 0 && ((d_n && n <= kSmall) || n <= 4096)) {
+    ::sbr::note_launch();
+    k_sort_small<<<1, kSmallThreads, 0, s>>>(keys[0], vals[0], keys[1], vals[1], n, d_n, passes);
+    return cudaGetLastError();
+  }
   const int nt = tiles_for(n < 1 ? 1 : n);
   int32_t* hist = static_cast<int32_t*>(scratch);
-  const int passes = (bits + 3) / 4;
   int cur = 0;
   for (int p = 0; p < passes; ++p) {
     const int shift = 4 * p;

@@ -20,23 +20,37 @@
 namespace sbr {
 namespace {
 
-constexpr int kChunk = 256;
+constexpr int kChunk = 512;  // paths staged per chunk (16 KB of shared memory per CTA)
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
+// threads per CTA: N_s / 8 samples each (N_s <= 2048), clamped to [32, 256]
 inline int threads_for(int Ns) {
-  int t = Ns / 4;
+  int t = Ns / 8;
   return t < 32 ? 32 : (t > 256 ? 256 : t);
 }
 
+// Samples after the anchor follow the two-term recurrence of a sampled
+// sinusoid, e_{m+1} = 2 cos(w) e_m - e_{m-1} (w = 2 pi delta), one FMA per
+// component per sample; its rounding error grows at most linearly in the
+// number of steps (|sin(m w) / sin(w)| <= m), so M <= 16 keeps it near 1e-6.
+// A CTA has kSplitThreads threads in G = kSplitThreads / (N_s / M) sample
+// groups; every group covers all N_s samples and takes every G-th path of each
+// staged chunk, and the groups' sums are added through shared memory at the
+// end.  (One group per CTA would cap residency at 32 CTAs x 32 threads.)
+constexpr int kSplitThreads = 256;
+
 template <int M>
-__global__ void __launch_bounds__(256) k_synth_split(const float4* __restrict__ prep, int64_t cap,
-                                                     const int32_t* __restrict__ d_P, int V, int Q,
-                                                     int Ns, float2* __restrict__ partial) {
+__global__ void __launch_bounds__(kSplitThreads) k_synth_split(const float4* __restrict__ prep, int64_t cap,
+                                                               const int32_t* __restrict__ d_P, int V,
+                                                               int Q, int Ns, float2* __restrict__ partial) {
   __shared__ float4 sp[kChunk];
-  __shared__ float2 sstep[kChunk];
+  __shared__ float4 sstep[kChunk];  // cos w, sin w, 2 cos w
+  extern __shared__ float2 red[];   // [M][kSplitThreads] when G > 1
+  const int T = Ns / M, G = kSplitThreads / T;
+  const int g = threadIdx.x / T, lane = threadIdx.x - g * T;
   const int v = blockIdx.x % V, q = blockIdx.x / V;
   const int64_t P = *d_P;
-  const int n0 = threadIdx.x * M;
+  const int n0 = lane * M;
   const float fn0 = (float)n0;
   float accr[M], acci[M];
 #pragma unroll
@@ -50,31 +64,57 @@ __global__ void __launch_bounds__(256) k_synth_split(const float4* __restrict__ 
       sp[j] = r;
       float s, c;
       sincospif(2.f * (r.y + r.z), &s, &c);
-      sstep[j] = make_float2(c, s);
+      sstep[j] = make_float4(c, s, 2.f * c, 0.f);
     }
     __syncthreads();
 #pragma unroll 2
-    for (int j = 0; j < cnt; ++j) {
+    for (int j = g; j < cnt; j += G) {
       const float4 r = sp[j];
-      const float2 st = sstep[j];
+      const float4 st = sstep[j];
       float x = fn0 * r.y;  // exact: delta_hi is a multiple of 2^-12 and n0 < 4096
       x -= rintf(x);
       x = fmaf(fn0, r.z, x) + r.x;
       x -= rintf(x);
       float s, c;
       __sincosf(kTwoPiF * x, &s, &c);
-      float er = r.w * c, ei = r.w * s;
+      float pr = r.w * c, pi = r.w * s;  // e_0
+      accr[0] += pr;
+      acci[0] += pi;
+      if (M > 1) {
+        float er = fmaf(pr, st.x, -pi * st.y);  // e_1 = e_0 e^{jw}
+        float ei = fmaf(pr, st.y, pi * st.x);
 #pragma unroll
-      for (int m = 0; m < M; ++m) {
-        accr[m] += er;
-        acci[m] += ei;
-        if (m + 1 < M) {
-          const float nr = fmaf(er, st.x, -ei * st.y);
-          const float ni = fmaf(er, st.y, ei * st.x);
-          er = nr;
-          ei = ni;
+        for (int m = 1; m < M; ++m) {
+          accr[m] += er;
+          acci[m] += ei;
+          if (m + 1 < M) {
+            const float nr = fmaf(st.z, er, -pr);
+            const float ni = fmaf(st.z, ei, -pi);
+            pr = er;
+            pi = ei;
+            er = nr;
+            ei = ni;
+          }
         }
       }
+    }
+  }
+  if (G > 1) {  // add the groups' sums (fixed order: deterministic)
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < M; ++m) red[m * kSplitThreads + threadIdx.x] = make_float2(accr[m], acci[m]);
+    __syncthreads();
+    if (g != 0) return;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      float sr = 0.f, si = 0.f;
+      for (int gg = 0; gg < G; ++gg) {
+        const float2 x = red[m * kSplitThreads + gg * T + lane];
+        sr += x.x;
+        si += x.y;
+      }
+      accr[m] = sr;
+      acci[m] = si;
     }
   }
   float2* out = partial + (size_t)blockIdx.x * Ns + n0;
@@ -85,7 +125,7 @@ __global__ void __launch_bounds__(256) k_synth_split(const float4* __restrict__ 
 // Per-sample phase in FP64: x = f_c tau + (B / N_s) tau n, reduced mod 1.
 template <int M>
 __global__ void __launch_bounds__(256) k_synth_fp64(const float4* __restrict__ prep,
-                                                    const double* __restrict__ tau64, int64_t cap,
+                                                    const float2* __restrict__ plen, int64_t cap,
                                                     const int32_t* __restrict__ d_P, int V, int Q,
                                                     int Ns, double f0, double b_over_ns,
                                                     float2* __restrict__ partial) {
@@ -101,7 +141,8 @@ __global__ void __launch_bounds__(256) k_synth_fp64(const float4* __restrict__ p
     const int cnt = (int)min((int64_t)kChunk, P - c0);
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-      const double t = tau64[(size_t)v * cap + c0 + j];
+      const float2 L = plen[(size_t)v * cap + c0 + j];
+      const double t = ((double)L.x + (double)L.y) * (1.0 / kC);
       const double x0 = f0 * t;
       const double d = b_over_ns * t;
       sx[j] = make_double2(x0 - rint(x0), d - rint(d));
@@ -130,7 +171,7 @@ __global__ void __launch_bounds__(256) k_synth_fp64(const float4* __restrict__ p
 // Everything in FP32: tau, f_c tau and mu tau t_n (no split, no FP64).
 template <int M>
 __global__ void __launch_bounds__(256) k_synth_naive(const float4* __restrict__ prep,
-                                                     const double* __restrict__ tau64, int64_t cap,
+                                                     const float2* __restrict__ plen, int64_t cap,
                                                      const int32_t* __restrict__ d_P, int V, int Q,
                                                      int Ns, float f0, float mu, float dt,
                                                      float2* __restrict__ partial) {
@@ -145,7 +186,7 @@ __global__ void __launch_bounds__(256) k_synth_naive(const float4* __restrict__ 
     const int cnt = (int)min((int64_t)kChunk, P - c0);
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += blockDim.x)
-      sx[j] = make_float2((float)tau64[(size_t)v * cap + c0 + j], prep[(size_t)v * cap + c0 + j].w);
+      sx[j] = make_float2(plen[(size_t)v * cap + c0 + j].x * (float)(1.0 / kC), prep[(size_t)v * cap + c0 + j].w);
     __syncthreads();
     for (int j = 0; j < cnt; ++j) {
       const float t = sx[j].x, a = sx[j].y;
@@ -256,10 +297,32 @@ int sm_count() {
 
 // Grid: V * Q CTAs, Q chosen to fill every SM at full occupancy, capped by the
 // number of path chunks.
+// dynamic shared memory of the split kernel: the groups' reduction buffer
+inline size_t split_smem(int Ns) {
+  const int T = threads_for(Ns), M = Ns / T;
+  return kSplitThreads / T > 1 ? sizeof(float2) * M * kSplitThreads : 0;
+}
+
+// resident CTAs of the split kernel per SM (registers and shared memory decide)
+int split_per_sm(int Ns) {
+  static int cache[17] = {};
+  const int T = threads_for(Ns), M = Ns / T;
+  if (M > 16 || cache[M]) return M > 16 ? 1 : cache[M];
+  int n = 0;
+  const size_t sm = split_smem(Ns);
+  switch (M) {
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_synth_split<1>, kSplitThreads, sm); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_synth_split<2>, kSplitThreads, sm); break;
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_synth_split<4>, kSplitThreads, sm); break;
+    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_synth_split<8>, kSplitThreads, sm); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_synth_split<16>, kSplitThreads, sm); break;
+  }
+  cache[M] = n > 0 ? n : 1;
+  return cache[M];
+}
+
 void grid_shape(int V, int Ns, int64_t cap, int* Q) {
-  const int T = threads_for(Ns);
-  int per_sm = 2048 / T;
-  if (per_sm > 32) per_sm = 32;
+  const int per_sm = split_per_sm(Ns);
   int64_t q = ((int64_t)sm_count() * per_sm + V - 1) / V;
   const int64_t chunks = (cap + kChunk - 1) / kChunk;
   if (q > chunks) q = chunks;
@@ -319,15 +382,16 @@ void launch_fwd(sbr_phase_mode mode, const sbr_paths* p, const sbr_radar_cfg* r,
   const float4* prep = reinterpret_cast<const float4*>(p->prep);
   if (mode == SBR_PHASE_SPLIT) {
     ::sbr::note_launch();
-    k_synth_split<M><<<grid, T, 0, st>>>(prep, p->path_cap, p->count, V, w.Q, Ns, w.partial);
+    k_synth_split<M><<<grid, kSplitThreads, split_smem(Ns), st>>>(prep, p->path_cap, p->count, V, w.Q, Ns,
+                                                                   w.partial);
   } else if (mode == SBR_PHASE_FP64) {
     ::sbr::note_launch();
-    k_synth_fp64<M><<<grid, T, 0, st>>>(prep, p->tau64, p->path_cap, p->count, V, w.Q, Ns, r->f0,
+    k_synth_fp64<M><<<grid, T, 0, st>>>(prep, reinterpret_cast<const float2*>(p->path_len), p->path_cap, p->count, V, w.Q, Ns, r->f0,
                                         r->bandwidth / Ns, w.partial);
   } else {
     const double mu = r->bandwidth / r->chirp_time, dt = r->chirp_time / Ns;
     ::sbr::note_launch();
-    k_synth_naive<M><<<grid, T, 0, st>>>(prep, p->tau64, p->path_cap, p->count, V, w.Q, Ns,
+    k_synth_naive<M><<<grid, T, 0, st>>>(prep, reinterpret_cast<const float2*>(p->path_len), p->path_cap, p->count, V, w.Q, Ns,
                                          (float)r->f0, (float)mu, (float)dt, w.partial);
   }
 }

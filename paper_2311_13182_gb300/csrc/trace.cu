@@ -1,131 +1,143 @@
 // Ray tracing with specular bounces (Section 3.2.1, Eq. 2-3) and path preparation.
 //
-// One thread per ray.  Each bounce runs a stack traversal of the LBVH in FP32
-// (64-B nodes fetched as four float4, triangles as three float4) with the
-// Moller-Trumbore (1997) test.  Every FP32 decision carries a forward error
-// bound: a triangle is accepted or rejected in FP32 only when the bound says
-// FP64 arithmetic on the FP64 ray would decide the same; otherwise the test is
-// repeated in FP64.  Nearest-hit ordering is decided the same way (interval
-// overlap -> FP64 t, exact ties -> lower triangle index).  The hit of each bounce
-// is then refined in FP64 and the FP64 ray is reflected, so the chosen triangle
-// sequence is that of an FP64 brute-force search for every ray not within
-// rounding distance of an edge.
+// One thread per ray.  The ray is carried in float-float (ff.cuh): its FP32 hi
+// parts drive a stack traversal of the LBVH (64-B nodes as four float4 loads,
+// triangles as three float4 loads) with the Moller-Trumbore (1997) test.  Every
+// FP32 decision carries a forward error bound: a triangle is accepted or
+// rejected in FP32 only when the bound says exact arithmetic on the exact ray
+// would decide the same; otherwise the test is repeated in float-float
+// (signs of float-float numerators, ~1e-14 relative).  Nearest-hit ordering is
+// decided the same way (interval overlap -> float-float t, exact ties -> lower
+// triangle index).  The chosen hit of each bounce is then
+// refined in float-float (plane intersection of the exact triangle) and the ray
+// is reflected in float-float, so the triangle sequence is that of an FP64
+// brute-force search for every ray not within rounding distance of an edge,
+// without the FP64 pipe (a small fraction of the FP32 rate on GB300) on the
+// per-ray path.
 //
-// Path preparation (FP64, O(paths x antennas)): per hit k and virtual antenna
-// (t, r): L_in = |h_1 - Tx_t| + sum_{j=2..k} |h_j - h_{j-1}|, L_out = |Rx_r - h_k|,
-// tau = (L_in + L_out)/c, phi0 = frac(f_c tau), delta = frac(B tau / N_s) split
-// into delta_hi (a multiple of 2^-12, so n * delta_hi is exact in FP32 for
-// n < 4096) and delta_lo, and A = omega (-1)^(k-1) |d_k . n_k| / (4 pi L_in L_out).
+// Path preparation (float-float, O(paths x antennas)): per hit k and virtual
+// antenna (t, r): L_in = |h_1 - Tx_t| + sum_{j=2..k} |h_j - h_{j-1}|,
+// L_out = |Rx_r - h_k|, L = L_in + L_out, tau = L / c; phi0 = frac(f_c tau),
+// delta = frac(B tau / N_s) split into delta_hi (a multiple of 2^-12, so
+// n * delta_hi is exact in FP32 for n < 4096) and delta_lo; and
+// A = omega (-1)^(k-1) |d_k . n_k| / (4 pi L_in L_out).
 #include <math.h>
 
+#include "ff.cuh"
 #include "scene.cuh"
 
 namespace sbr {
 namespace {
 
 struct GridArg {
-  double o[3], ax[3], ua[3], va[3];
-  double th;
+  ff o[3], ax[3], ua[3], va[3];
+  ff th;
+  float cell;  // 2 tan_half / G
   int G;
 };
 
 struct RadarArg {
-  double tx[SBR_MAX_TX][3];
-  double rx[SBR_MAX_RX][3];
-  double f0, b_over_ns;
+  ff tx[SBR_MAX_TX][3];
+  ff rx[SBR_MAX_RX][3];
+  ff k0;  // f_c / c         [cycles per metre]
+  ff kb;  // B / (c N_s)     [cycles per sample per metre]
   int ntx, nrx;
 };
 
 constexpr float kTmin = 1e-9f;
-constexpr double kTmin64 = 1e-9;
 constexpr float kErr = 1.0f / 262144.0f;  // 2^-18 = 64 ulp(1): scale of the FP32 error bounds
 
-__device__ inline void grid_ray(const GridArg& g, int rid, d3& o, d3& d, float& omega) {
+__device__ inline ff3 ff3_arr(const ff* a) { return ff3{a[0], a[1], a[2]}; }
+
+__device__ inline void grid_ray(const GridArg& g, int rid, ff3& o, ff3& d, float& omega) {
   const int row = rid / g.G, col = rid - row * g.G;
-  const double a = g.th * (2.0 * (col + 0.5) / g.G - 1.0);
-  const double b = g.th * (2.0 * (row + 0.5) / g.G - 1.0);
-  d3 w = mk3(g.ax[0], g.ax[1], g.ax[2]) + (mk3(g.ua[0], g.ua[1], g.ua[2]) * a +
-                                            mk3(g.va[0], g.va[1], g.va[2]) * b);
-  const double len = sqrt(dot(w, w));
-  d = w * (1.0 / len);
-  o = mk3(g.o[0], g.o[1], g.o[2]);
-  const double cell = 2.0 * g.th / g.G;
-  omega = (float)(cell * cell / (len * len * len));
+  // a = tan_half (2 (col + 1/2) / G - 1) = tan_half (2 col + 1 - G) / G
+  const ff fG = ff_of((float)g.G);
+  const ff a = ff_mul(g.th, ff_div(ff_of((float)(2 * col + 1 - g.G)), fG));
+  const ff b = ff_mul(g.th, ff_div(ff_of((float)(2 * row + 1 - g.G)), fG));
+  const ff3 w = ff3_add(ff3_arr(g.ax), ff3_add(ff3_scale(ff3_arr(g.ua), a), ff3_scale(ff3_arr(g.va), b)));
+  const ff inv = ff_rsqrt(ff3_dot(w, w));
+  d = ff3_scale(w, inv);
+  o = ff3_arr(g.o);
+  omega = g.cell * g.cell * inv.hi * inv.hi * inv.hi;
 }
 
-__device__ inline d3 tri_vert(const float4* __restrict__ tris, int slot, int c) {
-  float4 v = __ldg(&tris[3 * slot + c]);
-  return mk3(v.x, v.y, v.z);
+__device__ inline float3 tri_vert(const float4* __restrict__ tris, int slot, int c) {
+  const float4 v = __ldg(&tris[3 * slot + c]);
+  return f3(v.x, v.y, v.z);
 }
 
-// FP64 Moller-Trumbore, two-sided; the rule the brute-force definition uses.
-__device__ inline bool mt64(d3 o, d3 d, d3 a, d3 b, d3 c, double& t, double& u, double& v) {
-  d3 e1 = b - a, e2 = c - a;
-  d3 p = cross(d, e2);
-  double det = dot(e1, p);
-  if (fabs(det) < 1e-12) return false;
-  double inv = 1.0 / det;
-  d3 s = o - a;
-  u = dot(s, p) * inv;
-  if (u < 0.0 || u > 1.0) return false;
-  d3 q = cross(s, e1);
-  v = dot(d, q) * inv;
-  if (v < 0.0 || u + v > 1.0) return false;
-  t = dot(e2, q) * inv;
-  return t > kTmin64;
-}
+__device__ inline bool ff_less(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 
 struct Best {
   int id, slot;
-  float lo, hi;  // interval containing the FP64 distance
+  float lo, hi;  // interval containing the exact distance
   bool exact;
-  double t64;
+  ff t;          // float-float distance when exact
 };
 
 struct Ray {
-  float3 o, d, idir;
-  d3 o64, d64;
+  ff3 o, d;       // float-float ray
+  float3 of, df;  // FP32 (hi parts)
+  float3 idir;
   int skip;
 };
 
-__device__ inline bool exact_t(const float4* __restrict__ tris, const Ray& r, int slot, double& t) {
-  double u, v;
-  return mt64(r.o64, r.d64, tri_vert(tris, slot, 0), tri_vert(tris, slot, 1), tri_vert(tris, slot, 2),
-              t, u, v);
+// Moller-Trumbore in float-float on the float-float ray: the same two-sided
+// rule as the FP64 definition (|det| < 1e-12 misses; 0 <= u, v; u + v <= 1;
+// t > 1e-9), decided on signs of float-float numerators (about 1e-14 relative),
+// which agree with FP64 except within rounding distance of an edge or tie.
+__device__ inline bool exact_t(const float4* __restrict__ tris, const Ray& r, int slot, ff& t) {
+  const float3 a = tri_vert(tris, slot, 0), b = tri_vert(tris, slot, 1), c = tri_vert(tris, slot, 2);
+  const ff3 e1 = ff3_diff(b, a), e2 = ff3_diff(c, a);
+  const ff3 p = ff3_cross(r.d, e2);
+  const ff det = ff3_dot(e1, p);
+  if (fabsf(det.hi) < 1e-12f) return false;
+  const float sg = det.hi > 0.f ? 1.f : -1.f;
+  const ff adet = ff{det.hi * sg, det.lo * sg};
+  const ff3 s = ff3_sub(r.o, ff3_of(a));
+  ff un = ff3_dot(s, p);
+  un = ff{un.hi * sg, un.lo * sg};
+  if (un.hi < 0.f || ff_sub(adet, un).hi < 0.f) return false;        // u < 0 or u > 1
+  const ff3 q = ff3_cross(s, e1);
+  ff vn = ff3_dot(r.d, q);
+  vn = ff{vn.hi * sg, vn.lo * sg};
+  if (vn.hi < 0.f || ff_sub(adet, ff_add(un, vn)).hi < 0.f) return false;  // v < 0 or u + v > 1
+  t = ff_div(ff3_dot(e2, q), det);
+  return ff_sub(t, ff_of(kTmin)).hi > 0.f;
 }
 
-__device__ inline void take_exact(Best& b, int id, int slot, double t) {
+__device__ inline void take_exact(Best& b, int id, int slot, ff t) {
   b.id = id;
   b.slot = slot;
   b.exact = true;
-  b.t64 = t;
-  float tf = (float)t;
-  b.lo = tf - fabsf(tf) * 2.4e-7f;
-  b.hi = tf + fabsf(tf) * 2.4e-7f;
+  b.t = t;
+  b.lo = t.hi - fabsf(t.hi) * 2.4e-7f;
+  b.hi = t.hi + fabsf(t.hi) * 2.4e-7f;
 }
 
-// Offer a candidate whose FP64 distance lies in [lo, hi] (exact: t64 known).
+// Offer a candidate whose exact distance lies in [lo, hi] (exact: t known).
 __device__ inline void consider(Best& b, const float4* __restrict__ tris, const Ray& r, int id,
-                                int slot, float lo, float hi, bool exact, double t64) {
+                                int slot, float lo, float hi, bool exact, ff t) {
   if (b.id < 0 || hi < b.lo) {
-    if (exact) take_exact(b, id, slot, t64);
+    if (exact) take_exact(b, id, slot, t);
     else {
       b.id = id; b.slot = slot; b.lo = lo; b.hi = hi; b.exact = false;
     }
     return;
   }
   if (lo > b.hi) return;
-  // overlapping intervals: order in FP64, ties to the lower triangle index
-  if (!exact && !exact_t(tris, r, slot, t64)) return;
+  // overlapping intervals: order in float-float, ties to the lower triangle index
+  if (!exact && !exact_t(tris, r, slot, t)) return;
   if (!b.exact) {
-    double tb;
+    ff tb;
     if (!exact_t(tris, r, b.slot, tb)) {  // cannot happen with valid bounds; keep the new one
-      take_exact(b, id, slot, t64);
+      take_exact(b, id, slot, t);
       return;
     }
     take_exact(b, b.id, b.slot, tb);
   }
-  if (t64 < b.t64 || (t64 == b.t64 && id < b.id)) take_exact(b, id, slot, t64);
+  if (ff_less(t, b.t) || (t.hi == b.t.hi && t.lo == b.t.lo && id < b.id)) take_exact(b, id, slot, t);
 }
 
 __device__ inline void test_tri(Best& b, const float4* __restrict__ tris, const Ray& r, int slot) {
@@ -137,13 +149,13 @@ __device__ inline void test_tri(Best& b, const float4* __restrict__ tris, const 
   const float3 v0 = f3(A.x, A.y, A.z);
   const float3 e1 = f3(B.x, B.y, B.z) - v0;
   const float3 e2 = f3(C.x, C.y, C.z) - v0;
-  const float3 p = cross(r.d, e2);
+  const float3 p = cross(r.df, e2);
   const float det = dot(e1, p);
-  const float3 s = r.o - v0;
+  const float3 s = r.of - v0;
   const float3 q = cross(s, e1);
-  const float un = dot(s, p), vn = dot(r.d, q), tn = dot(e2, q);
-  // forward error bounds of the FP32 values against FP64 arithmetic on the FP64 ray
-  const float m1 = l1(e1), m2 = l1(e2), ms = l1(r.o) + l1(v0);
+  const float un = dot(s, p), vn = dot(r.df, q), tn = dot(e2, q);
+  // forward error bounds of the FP32 values against FP64 arithmetic on the exact ray
+  const float m1 = l1(e1), m2 = l1(e2), ms = l1(r.of) + l1(v0);
   const float edet = kErr * m1 * m2;
   const float eu = kErr * ms * m2, ev = kErr * ms * m1, et = kErr * ms * m1 * m2;
   const float adet = fabsf(det);
@@ -162,15 +174,13 @@ __device__ inline void test_tri(Best& b, const float4* __restrict__ tris, const 
     if (hi <= kTmin) return;                      // behind the origin in FP64 too
     if (b.id >= 0 && lo > b.hi) return;           // farther than the current hit
     if (su > eu && sv > ev && sw > ew && lo > kTmin) {
-      consider(b, tris, r, id, slot, lo, hi, false, 0.0);
+      consider(b, tris, r, id, slot, lo, hi, false, ff_of(0.f));
       return;
     }
   }
-  double t;
-  if (exact_t(tris, r, slot, t)) {
-    const float tf = (float)t;
-    consider(b, tris, r, id, slot, tf - fabsf(tf) * 2.4e-7f, tf + fabsf(tf) * 2.4e-7f, true, t);
-  }
+  ff t;
+  if (exact_t(tris, r, slot, t))
+    consider(b, tris, r, id, slot, t.hi - fabsf(t.hi) * 2.4e-7f, t.hi + fabsf(t.hi) * 2.4e-7f, true, t);
 }
 
 __device__ inline void slab(const float3& o, const float3& idir, float lox, float hix, float loy,
@@ -190,7 +200,7 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node* __restrict_
   b.slot = -1;
   b.lo = b.hi = INFINITY;
   b.exact = false;
-  b.t64 = 0.0;
+  b.t = ff_of(0.f);
   if (nt <= 0) return b;
   int stack[64];
   int sp = 0;
@@ -204,8 +214,8 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node* __restrict_
       const float4 z = __ldg(&nodes[node].lrz);
       const int4 ch = __ldg(&nodes[node].child);
       float ln, lf, rn, rf;
-      slab(r.o, r.idir, a.x, a.y, a.z, a.w, z.x, z.y, ln, lf);
-      slab(r.o, r.idir, c.x, c.y, c.z, c.w, z.z, z.w, rn, rf);
+      slab(r.of, r.idir, a.x, a.y, a.z, a.w, z.x, z.y, ln, lf);
+      slab(r.of, r.idir, c.x, c.y, c.z, c.w, z.z, z.w, rn, rf);
       const float lim = b.hi;
       const bool hl = ln <= lf && lf >= 0.f && ln <= lim;
       const bool hr = rn <= rf && rf >= 0.f && rn <= lim;
@@ -227,17 +237,30 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node* __restrict_
 }
 
 __device__ inline void set_f32(Ray& r) {
-  r.o = f3((float)r.o64.x, (float)r.o64.y, (float)r.o64.z);
-  r.d = f3((float)r.d64.x, (float)r.d64.y, (float)r.d64.z);
+  r.of = ff3_hi(r.o);
+  r.df = ff3_hi(r.d);
   auto inv = [](float x) { return 1.0f / (fabsf(x) < 1e-20f ? copysignf(1e-20f, x) : x); };
-  r.idir = f3(inv(r.d.x), inv(r.d.y), inv(r.d.z));
+  r.idir = f3(inv(r.df.x), inv(r.df.y), inv(r.df.z));
 }
 
-__global__ void __launch_bounds__(128) k_trace(const float4* __restrict__ tris,
+// barycentrics of the hit (reported, not used downstream), FP32
+__device__ inline void bary(const Ray& r, float3 a, float3 b, float3 c, float& u, float& v) {
+  const float3 e1 = b - a, e2 = c - a, p = cross(r.df, e2);
+  const float inv = 1.f / dot(e1, p);
+  const float3 s = r.of - a;
+  u = dot(s, p) * inv;
+  v = dot(r.df, cross(s, e1)) * inv;
+}
+
+#ifndef SBR_TRACE_MIN_BLOCKS
+#define SBR_TRACE_MIN_BLOCKS 6  // resident 128-thread CTAs per SM the register budget targets
+#endif
+
+__global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float4* __restrict__ tris,
                                                const Node* __restrict__ nodes, int nt, GridArg g,
                                                const int32_t* __restrict__ ray_ids, int n_rays,
                                                int K, sbr_hit* __restrict__ hits,
-                                               double4* __restrict__ hit_pos,
+                                               float4* __restrict__ hit_pos,
                                                float* __restrict__ ray_w,
                                                int32_t* __restrict__ nvalid) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -245,7 +268,7 @@ __global__ void __launch_bounds__(128) k_trace(const float4* __restrict__ tris,
   const int rid = ray_ids ? ray_ids[i] : i;
   Ray r;
   float omega;
-  grid_ray(g, rid, r.o64, r.d64, omega);
+  grid_ray(g, rid, r.o, r.d, omega);
   r.skip = -1;
   set_f32(r);
   ray_w[i] = omega;
@@ -255,28 +278,32 @@ __global__ void __launch_bounds__(128) k_trace(const float4* __restrict__ tris,
     Best b = nearest(tris, nodes, nt, r);
     if (b.id < 0) {
       for (int kk = k; kk < K; ++kk) {
-        hits[(size_t)i * K + kk] = sbr_hit{-1, 0.f, 0.f, 0.f};
-        hit_pos[(size_t)i * K + kk] = make_double4(0.0, 0.0, 0.0, 0.0);
+        const size_t s2 = (size_t)i * K + kk;
+        hits[s2] = sbr_hit{-1, 0.f, 0.f, 0.f};
+        hit_pos[2 * s2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        hit_pos[2 * s2 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       break;
     }
-    const d3 a = tri_vert(tris, b.slot, 0), bb = tri_vert(tris, b.slot, 1),
-             c = tri_vert(tris, b.slot, 2);
-    double t, u, v;
-    if (!mt64(r.o64, r.d64, a, bb, c, t, u, v)) {
-      // unreachable with valid bounds: fall back to the plane intersection
-      d3 n0 = cross(bb - a, c - a);
-      t = dot(n0, a - r.o64) / dot(n0, r.d64);
-      u = v = 0.0;
-    }
-    const d3 h = r.o64 + r.d64 * t;
-    d3 n = cross(bb - a, c - a);
-    n = n * (1.0 / sqrt(dot(n, n)));
-    const double dn = dot(r.d64, n);
-    hits[sl] = sbr_hit{b.id, (float)t, (float)u, (float)v};
-    hit_pos[sl] = make_double4(h.x, h.y, h.z, fabs(dn));
-    r.d64 = r.d64 - n * (2.0 * dn);
-    r.o64 = h;
+    const float4 A = __ldg(&tris[3 * b.slot]), B = __ldg(&tris[3 * b.slot + 1]),
+                 C = __ldg(&tris[3 * b.slot + 2]);
+    const float3 a = f3(A.x, A.y, A.z), bb = f3(B.x, B.y, B.z), c = f3(C.x, C.y, C.z);
+    // float-float refine: plane of the exact triangle, t = N.(a - o) / (N.d)
+    const ff3 N = ff3_cross(ff3_diff(bb, a), ff3_diff(c, a));
+    const ff den = ff3_dot(N, r.d);
+    const ff t = ff_div(ff3_dot(N, ff3_sub(ff3_of(a), r.o)), den);
+    const ff3 h = ff3_add(r.o, ff3_scale(r.d, t));
+    const ff nn = ff3_dot(N, N);
+    const float cosv = fabsf(den.hi) * rsqrtf(nn.hi);
+    float u, v;
+    bary(r, a, bb, c, u, v);
+    hits[sl] = sbr_hit{b.id, t.hi, u, v};
+    hit_pos[2 * sl] = make_float4(h.x.hi, h.x.lo, h.y.hi, h.y.lo);
+    hit_pos[2 * sl + 1] = make_float4(h.z.hi, h.z.lo, cosv, 0.f);
+    // specular reflection d' = d - 2 (d.N) / (N.N) N, next origin = hit point
+    const ff f = ff_div(ff_mulf(den, 2.f), nn);
+    r.d = ff3_sub(r.d, ff3_scale(N, f));
+    r.o = h;
     r.skip = b.id;
     set_f32(r);
     ++nh;
@@ -284,45 +311,56 @@ __global__ void __launch_bounds__(128) k_trace(const float4* __restrict__ tris,
   nvalid[i] = nh;
 }
 
-__device__ inline double dist(d3 a, d3 b) {
-  d3 e = a - b;
-  return sqrt(dot(e, e));
+__device__ inline ff3 ld_hit(const float4* __restrict__ hp, size_t sl, float& cosv) {
+  const float4 p = hp[2 * sl], q = hp[2 * sl + 1];
+  cosv = q.z;
+  return ff3{ff{p.x, p.y}, ff{p.z, p.w}, ff{q.x, q.y}};
 }
 
-__global__ void k_prep(const double4* __restrict__ hit_pos, const float* __restrict__ ray_w,
+// frac(x) of a float-float value, about [-1/2, 1/2], as a float-float pair
+__device__ inline ff ff_frac(ff x) {
+  const float n = rintf(x.hi);
+  return fast_two_sum(x.hi - n, x.lo);  // x.hi - n is exact
+}
+
+__global__ void k_prep(const float4* __restrict__ hit_pos, const float* __restrict__ ray_w,
                        const int32_t* __restrict__ first, int n_rays, int K, RadarArg rd,
-                       int64_t cap, float4* __restrict__ prep, double* __restrict__ tau64,
+                       int64_t cap, float4* __restrict__ prep, float2* __restrict__ plen,
                        int32_t* __restrict__ path_ray) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_rays) return;
   const int p0 = first[i], nh = first[i + 1] - p0;
+  if (nh <= 0) return;
   const float omega = ray_w[i];
-  double interior = 0.0;
-  d3 h1 = mk3(0, 0, 0), hp = mk3(0, 0, 0);
+  float c0;
+  const ff3 h1 = ld_hit(hit_pos, (size_t)i * K, c0);
+  ff lin0[SBR_MAX_TX];
+  for (int t = 0; t < rd.ntx; ++t) lin0[t] = ff3_len(ff3_sub(h1, ff3_arr(rd.tx[t])));
+  ff interior = ff_of(0.f);
+  ff3 hp = h1;
   for (int k = 0; k < nh; ++k) {
-    const double4 hk = hit_pos[(size_t)i * K + k];
-    const d3 h = mk3(hk.x, hk.y, hk.z);
-    if (k == 0) h1 = h;
-    else interior += dist(h, hp);
+    float cosv = c0;
+    const ff3 h = k == 0 ? h1 : ld_hit(hit_pos, (size_t)i * K + k, cosv);
+    if (k > 0) interior = ff_add(interior, ff3_len(ff3_sub(h, hp)));
     hp = h;
     const int64_t p = p0 + k;
     path_ray[p] = i;
-    const double sign = (k & 1) ? -1.0 : 1.0;
-    double lout[SBR_MAX_RX];
-    for (int rr = 0; rr < rd.nrx; ++rr) lout[rr] = dist(mk3(rd.rx[rr][0], rd.rx[rr][1], rd.rx[rr][2]), h);
-    for (int t = 0; t < rd.ntx; ++t) {
-      const double lin = dist(h1, mk3(rd.tx[t][0], rd.tx[t][1], rd.tx[t][2])) + interior;
-      for (int rr = 0; rr < rd.nrx; ++rr) {
+    const float sign = (k & 1) ? -1.f : 1.f;
+    const float wa = omega * sign * cosv * (float)(0.25 / M_PI);
+    for (int rr = 0; rr < rd.nrx; ++rr) {
+      const ff lout = ff3_len(ff3_sub(ff3_arr(rd.rx[rr]), h));
+      for (int t = 0; t < rd.ntx; ++t) {
         const int v = t * rd.nrx + rr;
-        const double tau = (lin + lout[rr]) / kC;
-        const double x0 = rd.f0 * tau;
-        const double phi0 = x0 - rint(x0);
-        double dl = rd.b_over_ns * tau;
-        dl -= rint(dl);
-        const double dhi = rint(dl * 4096.0) * (1.0 / 4096.0);
-        const float amp = (float)(omega * sign * hk.w / (4.0 * M_PI * lin * lout[rr]));
-        prep[(size_t)v * cap + p] = make_float4((float)phi0, (float)dhi, (float)(dl - dhi), amp);
-        tau64[(size_t)v * cap + p] = tau;
+        const ff lin = ff_add(lin0[t], interior);
+        const ff L = ff_add(lin, lout);
+        const ff x0 = ff_frac(ff_mul(L, rd.k0));
+        float phi0 = x0.hi + x0.lo;
+        phi0 -= rintf(phi0);
+        const ff dl = ff_frac(ff_mul(L, rd.kb));
+        const float dhi = rintf(dl.hi * 4096.f) * (1.f / 4096.f);
+        const float dlo = (dl.hi - dhi) + dl.lo;  // dl.hi - dhi is exact
+        prep[(size_t)v * cap + p] = make_float4(phi0, dhi, dlo, wa / (lin.hi * lout.hi));
+        plen[(size_t)v * cap + p] = make_float2(L.hi, L.lo);
       }
     }
   }
@@ -339,12 +377,12 @@ size_t paths_layout(sbr_paths* p, void* mem, int32_t R, int32_t K, int32_t V) {
   p->n_virt = V;
   p->path_cap = cap;
   p->hits = c.take<sbr_hit>(capc);
-  p->hit_pos = c.take<double>(4 * capc);
+  p->hit_pos = c.take<float>(8 * capc);
   p->ray_weight = c.take<float>(R > 0 ? R : 1);
   p->ray_first = c.take<int32_t>((int64_t)R + 1);
   p->path_ray = c.take<int32_t>(capc);
   p->prep = c.take<float>(4 * (int64_t)V * capc);
-  p->tau64 = c.take<double>((int64_t)V * capc);
+  p->path_len = c.take<float>(2 * (int64_t)V * capc);
   p->scratch = c.take<char>(scan_scratch_bytes(R > 0 ? R : 1));
   p->count = p->ray_first ? p->ray_first + R : nullptr;
   return c.bytes();
@@ -418,20 +456,21 @@ extern "C" sbr_status sbr_trace(const sbr_scene* scene, const sbr_radar_cfg* rad
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   GridArg g;
   for (int j = 0; j < 3; ++j) {
-    g.o[j] = grid->origin[j];
-    g.ax[j] = grid->axis[j];
-    g.ua[j] = grid->u_axis[j];
-    g.va[j] = grid->v_axis[j];
+    g.o[j] = ff_from_double(grid->origin[j]);
+    g.ax[j] = ff_from_double(grid->axis[j]);
+    g.ua[j] = ff_from_double(grid->u_axis[j]);
+    g.va[j] = ff_from_double(grid->v_axis[j]);
   }
-  g.th = grid->tan_half;
+  g.th = ff_from_double(grid->tan_half);
+  g.cell = (float)(2.0 * grid->tan_half / grid->G);
   g.G = grid->G;
   RadarArg rd;
   for (int t = 0; t < SBR_MAX_TX; ++t)
-    for (int j = 0; j < 3; ++j) rd.tx[t][j] = radar->tx[t][j];
+    for (int j = 0; j < 3; ++j) rd.tx[t][j] = ff_from_double(radar->tx[t][j]);
   for (int r = 0; r < SBR_MAX_RX; ++r)
-    for (int j = 0; j < 3; ++j) rd.rx[r][j] = radar->rx[r][j];
-  rd.f0 = radar->f0;
-  rd.b_over_ns = radar->bandwidth / radar->n_samples;
+    for (int j = 0; j < 3; ++j) rd.rx[r][j] = ff_from_double(radar->rx[r][j]);
+  rd.k0 = ff_from_double(radar->f0 / kC);
+  rd.kb = ff_from_double(radar->bandwidth / (kC * radar->n_samples));
   rd.ntx = radar->n_tx;
   rd.nrx = radar->n_rx;
   if (R == 0) {
@@ -441,16 +480,16 @@ extern "C" sbr_status sbr_trace(const sbr_scene* scene, const sbr_radar_cfg* rad
   ::sbr::note_launch();
   k_trace<<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes, scene->nt, g, d_ray_ids,
                                           (int)R, max_bounces, paths->hits,
-                                          reinterpret_cast<double4*>(paths->hit_pos),
+                                          reinterpret_cast<float4*>(paths->hit_pos),
                                           paths->ray_weight, paths->ray_first);
   SBR_CUDA(cudaGetLastError());
   SBR_CUDA(exclusive_scan(paths->ray_first, paths->ray_first, R, nullptr, paths->scratch, st));
   ::sbr::note_launch();
-  k_prep<<<blocks(R, 128), 128, 0, st>>>(reinterpret_cast<const double4*>(paths->hit_pos),
+  k_prep<<<blocks(R, 128), 128, 0, st>>>(reinterpret_cast<const float4*>(paths->hit_pos),
                                          paths->ray_weight, paths->ray_first, (int)R, max_bounces,
                                          rd, paths->path_cap,
-                                         reinterpret_cast<float4*>(paths->prep), paths->tau64,
-                                         paths->path_ray);
+                                         reinterpret_cast<float4*>(paths->prep),
+                                         reinterpret_cast<float2*>(paths->path_len), paths->path_ray);
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;
 }

@@ -46,7 +46,7 @@ __device__ inline void scatter(float* g, int vi, float3 d) {
 __global__ void __launch_bounds__(128) k_trace_bwd(
     const float* __restrict__ verts, int nv, const int32_t* __restrict__ faces, GridF g, RadarF rd,
     const int32_t* __restrict__ ray_ids, int n_rays, int K, const sbr_hit* __restrict__ hits,
-    const double4* __restrict__ hit_pos, const int32_t* __restrict__ first,
+    const float4* __restrict__ hit_pos, const int32_t* __restrict__ first,
     const float4* __restrict__ prep, int64_t cap, const float* __restrict__ glen,
     const float* __restrict__ gamp, float* __restrict__ gverts) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(128) k_trace_bwd(
     const size_t sl = (size_t)i * K + k;
     const int id = hits[sl].tri;
     t[k] = hits[sl].t;
-    const double4 hp = hit_pos[sl];
-    h[k] = f3((float)hp.x, (float)hp.y, (float)hp.z);
+    const float4 hp = hit_pos[2 * sl], hq = hit_pos[2 * sl + 1];  // float-float pairs: hi parts
+    h[k] = f3(hp.x, hp.z, hq.x);
     for (int c = 0; c < 3; ++c) {
       const int q = faces[3 * id + c];
       fv[k][c] = (q >= 0 && q < nv) ? q : 0;  // invalid faces were reported by the scene build
@@ -210,7 +210,7 @@ extern "C" sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts
   ::sbr::note_launch();
   k_trace_bwd<<<(R + 127) / 128, 128, 0, st>>>(
       d_verts, scene->nv, scene->faces, g, rd, d_ray_ids, R, paths->max_bounces, paths->hits,
-      reinterpret_cast<const double4*>(paths->hit_pos), paths->ray_first,
+      reinterpret_cast<const float4*>(paths->hit_pos), paths->ray_first,
       reinterpret_cast<const float4*>(paths->prep), paths->path_cap, d_glen, d_gamp, d_gverts);
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;

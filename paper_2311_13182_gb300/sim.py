@@ -125,7 +125,13 @@ class PathBuffers:
         return raw[..., 0], raw[..., 1:].view(torch.float32)
 
     def hit_pos(self):
-        return _region(self.mem, self.s.hit_pos, torch.float64, (self.R, self.K, 4))
+        """Raw hit records [R, K, 8]: float-float x, y, z pairs and |d.n| (see sbr.h)."""
+        return _region(self.mem, self.s.hit_pos, torch.float32, (self.R, self.K, 8))
+
+    def hit_points(self):
+        """Hit points [R, K, 3] in float64 (hi + lo of the stored float-float pairs)."""
+        raw = self.hit_pos().double()
+        return raw[..., 0:6:2] + raw[..., 1:6:2]
 
     def ray_weight(self):
         return _region(self.mem, self.s.ray_weight, torch.float32, (self.R,))
@@ -139,8 +145,10 @@ class PathBuffers:
     def prep(self):
         return _region(self.mem, self.s.prep, torch.float32, (self.V, max(self.cap, 1), 4))
 
-    def tau64(self):
-        return _region(self.mem, self.s.tau64, torch.float64, (self.V, max(self.cap, 1)))
+    def path_len(self):
+        """Path lengths L_in + L_out [V, path_cap] in float64 (hi + lo of the stored pairs)."""
+        raw = _region(self.mem, self.s.path_len, torch.float32, (self.V, max(self.cap, 1), 2)).double()
+        return raw[..., 0] + raw[..., 1]
 
     def count_tensor(self):
         return _region(self.mem, self.s.count, torch.int32, (1,))

@@ -17,14 +17,14 @@ def check_paths(wl, tr, paths):
     mism, n_ok, tri_gpu = compare_tri(tr, paths)
     assert mism == 0, f"{mism} of {n_ok} unflagged rays chose a different triangle"
     ok = tr["flag"] == 0
-    hp = paths.hit_pos().cpu().numpy()
+    hp = paths.hit_points().cpu().numpy()
     valid = (tr["tri"] >= 0) & ok[:, None]
-    np.testing.assert_allclose(hp[..., :3][valid], tr["hit"][valid], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(hp[valid], tr["hit"][valid], rtol=0, atol=1e-9)
     P = paths.count()
     assert P == int((tri_gpu >= 0).sum())
     pa = oracle.paths(tr, wl.radar)
     if P:
-        tau = paths.tau64().cpu().numpy()[:, :P]
+        tau = paths.path_len().cpu().numpy()[:, :P] / C_LIGHT
         amp = paths.prep().cpu().numpy()[:, :P, 3]
         ray_gpu = paths.path_ray().cpu().numpy()[:P]
         # compare paths of unflagged rays, matched by (ray, bounce) order (both ray-major)
