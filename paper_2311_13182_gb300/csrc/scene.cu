@@ -102,7 +102,15 @@ __global__ void k_morton(const float* __restrict__ verts, int nv, const int32_t*
   uint32_t ix = (uint32_t)fminf(fmaxf(qx * 1024.f, 0.f), 1023.f);
   uint32_t iy = (uint32_t)fminf(fmaxf(qy * 1024.f, 0.f), 1023.f);
   uint32_t iz = (uint32_t)fminf(fmaxf(qz * 1024.f, 0.f), 1023.f);
-  keys[f] = (spread10(ix) << 2) | (spread10(iy) << 1) | spread10(iz);
+  // Triangles spanning more than 1/32 of the centroid box (a ground plane under
+  // an object) get key bit 30, so the radix tree puts them in their own subtree
+  // at the root instead of inflating the boxes of their Morton neighbours.
+  const float side = fmaxf(fmaxf(fmaxf(fabsf(a.x - b.x), fabsf(b.x - c.x)), fabsf(c.x - a.x)),
+                           fmaxf(fmaxf(fmaxf(fabsf(a.y - b.y), fabsf(b.y - c.y)), fabsf(c.y - a.y)),
+                                 fmaxf(fmaxf(fabsf(a.z - b.z), fabsf(b.z - c.z)), fabsf(c.z - a.z))));
+  const float extent = fmaxf(fmaxf(ext.x, ext.y), ext.z);
+  const uint32_t big = (extent > 0.f && side * 32.f > extent) ? (1u << 30) : 0u;
+  keys[f] = big | (spread10(ix) << 2) | (spread10(iy) << 1) | spread10(iz);
   vals[f] = f;
 }
 
@@ -236,7 +244,7 @@ sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
   ::sbr::note_launch();
   k_morton<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->bounds, s->keys[0],
                                             s->vals[0], s->err);
-  SBR_CUDA(radix_sort_pairs(s->keys, s->vals, nt, nullptr, 30, s->sort_scratch, st));
+  SBR_CUDA(radix_sort_pairs(s->keys, s->vals, nt, nullptr, 31, s->sort_scratch, st));
   ::sbr::note_launch();
   k_pack<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->vals[0], s->tris, s->err);
   if (nt > 1) {

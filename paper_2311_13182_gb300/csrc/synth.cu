@@ -23,10 +23,10 @@ namespace {
 constexpr int kChunk = 512;  // paths staged per chunk (16 KB of shared memory per CTA)
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
-// threads per CTA: N_s / 8 samples each (N_s <= 2048), clamped to [32, 256]
+// threads per sample group: N_s / 16 (16 samples each), at least 16, at most 256
 inline int threads_for(int Ns) {
-  int t = Ns / 8;
-  return t < 32 ? 32 : (t > 256 ? 256 : t);
+  int t = Ns / 16;
+  return t < 16 ? 16 : (t > 256 ? 256 : t);
 }
 
 // Samples after the anchor follow the two-term recurrence of a sampled
@@ -52,9 +52,11 @@ __global__ void __launch_bounds__(kSplitThreads) k_synth_split(const float4* __r
   const int64_t P = *d_P;
   const int n0 = lane * M;
   const float fn0 = (float)n0;
-  float accr[M], acci[M];
+  // (re, im) pairs advance with packed FP32x2 instructions: one FADD2 per
+  // accumulated sample and one FFMA2 per recurrence step
+  float2 acc[M];
 #pragma unroll
-  for (int m = 0; m < M; ++m) accr[m] = acci[m] = 0.f;
+  for (int m = 0; m < M; ++m) acc[m] = make_float2(0.f, 0.f);
   const float4* pv = prep + (size_t)v * cap;
   for (int64_t c0 = (int64_t)q * kChunk; c0 < P; c0 += (int64_t)Q * kChunk) {
     const int cnt = (int)min((int64_t)kChunk, P - c0);
@@ -77,23 +79,20 @@ __global__ void __launch_bounds__(kSplitThreads) k_synth_split(const float4* __r
       x -= rintf(x);
       float s, c;
       __sincosf(kTwoPiF * x, &s, &c);
-      float pr = r.w * c, pi = r.w * s;  // e_0
-      accr[0] += pr;
-      acci[0] += pi;
+      float2 ep = __fmul2_rn(make_float2(r.w, r.w), make_float2(c, s));  // e_0
+      acc[0] = __fadd2_rn(acc[0], ep);
       if (M > 1) {
-        float er = fmaf(pr, st.x, -pi * st.y);  // e_1 = e_0 e^{jw}
-        float ei = fmaf(pr, st.y, pi * st.x);
+        // e_1 = e_0 e^{jw}
+        float2 e = __ffma2_rn(make_float2(-ep.y, ep.y), make_float2(st.y, st.x),
+                              __fmul2_rn(make_float2(ep.x, ep.x), make_float2(st.x, st.y)));
+        const float2 c2 = make_float2(st.z, st.z);
 #pragma unroll
         for (int m = 1; m < M; ++m) {
-          accr[m] += er;
-          acci[m] += ei;
+          acc[m] = __fadd2_rn(acc[m], e);
           if (m + 1 < M) {
-            const float nr = fmaf(st.z, er, -pr);
-            const float ni = fmaf(st.z, ei, -pi);
-            pr = er;
-            pi = ei;
-            er = nr;
-            ei = ni;
+            const float2 en = __ffma2_rn(c2, e, make_float2(-ep.x, -ep.y));
+            ep = e;
+            e = en;
           }
         }
       }
@@ -102,24 +101,19 @@ __global__ void __launch_bounds__(kSplitThreads) k_synth_split(const float4* __r
   if (G > 1) {  // add the groups' sums (fixed order: deterministic)
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < M; ++m) red[m * kSplitThreads + threadIdx.x] = make_float2(accr[m], acci[m]);
+    for (int m = 0; m < M; ++m) red[m * kSplitThreads + threadIdx.x] = acc[m];
     __syncthreads();
     if (g != 0) return;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      float sr = 0.f, si = 0.f;
-      for (int gg = 0; gg < G; ++gg) {
-        const float2 x = red[m * kSplitThreads + gg * T + lane];
-        sr += x.x;
-        si += x.y;
-      }
-      accr[m] = sr;
-      acci[m] = si;
+      float2 sum = make_float2(0.f, 0.f);
+      for (int gg = 0; gg < G; ++gg) sum = __fadd2_rn(sum, red[m * kSplitThreads + gg * T + lane]);
+      acc[m] = sum;
     }
   }
   float2* out = partial + (size_t)blockIdx.x * Ns + n0;
 #pragma unroll
-  for (int m = 0; m < M; ++m) out[m] = make_float2(accr[m], acci[m]);
+  for (int m = 0; m < M; ++m) out[m] = acc[m];
 }
 
 // Per-sample phase in FP64: x = f_c tau + (B / N_s) tau n, reduced mod 1.

@@ -31,7 +31,8 @@ namespace {
 
 struct GridArg {
   ff o[3], ax[3], ua[3], va[3];
-  ff th;
+  ff start;    // -tan_half + tan_half / G: the first cell centre
+  ff step;     // 2 tan_half / G: the cell pitch
   float cell;  // 2 tan_half / G
   int G;
 };
@@ -49,17 +50,27 @@ constexpr float kErr = 1.0f / 262144.0f;  // 2^-18 = 64 ulp(1): scale of the FP3
 
 __device__ inline ff3 ff3_arr(const ff* a) { return ff3{a[0], a[1], a[2]}; }
 
-__device__ inline void grid_ray(const GridArg& g, int rid, ff3& o, ff3& d, float& omega) {
+// Launch direction of grid ray rid in float-float: cell centre
+// a = tan_half (2 (col + 1/2) / G - 1) = start + col * step, likewise b with row,
+// direction = normalize(axis + a u + b v).
+__device__ inline ff3 grid_dir_ff(const GridArg& g, int rid) {
   const int row = rid / g.G, col = rid - row * g.G;
-  // a = tan_half (2 (col + 1/2) / G - 1) = tan_half (2 col + 1 - G) / G
-  const ff fG = ff_of((float)g.G);
-  const ff a = ff_mul(g.th, ff_div(ff_of((float)(2 * col + 1 - g.G)), fG));
-  const ff b = ff_mul(g.th, ff_div(ff_of((float)(2 * row + 1 - g.G)), fG));
+  const ff a = ff_add(g.start, ff_mulf(g.step, (float)col));
+  const ff b = ff_add(g.start, ff_mulf(g.step, (float)row));
   const ff3 w = ff3_add(ff3_arr(g.ax), ff3_add(ff3_scale(ff3_arr(g.ua), a), ff3_scale(ff3_arr(g.va), b)));
-  const ff inv = ff_rsqrt(ff3_dot(w, w));
-  d = ff3_scale(w, inv);
-  o = ff3_arr(g.o);
-  omega = g.cell * g.cell * inv.hi * inv.hi * inv.hi;
+  return ff3_scale(w, ff_rsqrt(ff3_dot(w, w)));
+}
+
+// The same direction in FP32 (a few ulp; the traversal's error bounds allow
+// 64) and the ray's solid-angle weight cell^2 cos^3.
+__device__ inline float3 grid_dir_f32(const GridArg& g, int rid, float& omega) {
+  const int row = rid / g.G, col = rid - row * g.G;
+  const float a = fmaf(g.step.hi, (float)col, g.start.hi), b = fmaf(g.step.hi, (float)row, g.start.hi);
+  const float3 w = f3(g.ax[0].hi + a * g.ua[0].hi + b * g.va[0].hi, g.ax[1].hi + a * g.ua[1].hi + b * g.va[1].hi,
+                      g.ax[2].hi + a * g.ua[2].hi + b * g.va[2].hi);
+  const float inv = rsqrtf(dot(w, w));
+  omega = g.cell * g.cell * inv * inv * inv;
+  return w * inv;
 }
 
 __device__ inline float3 tri_vert(const float4* __restrict__ tris, int slot, int c) {
@@ -77,17 +88,28 @@ struct Best {
 };
 
 struct Ray {
-  ff3 o, d;       // float-float ray
-  float3 of, df;  // FP32 (hi parts)
+  ff3 o, d;       // float-float ray (d valid once has_ff)
+  float3 of, df;  // FP32 ray driving the traversal
   float3 idir;
   int skip;
+  bool has_ff;        // primary rays build d in float-float only when needed
+  int rid;
+  const GridArg* g;
 };
+
+__device__ inline void ensure_ff(Ray& r) {
+  if (!r.has_ff) {
+    r.d = grid_dir_ff(*r.g, r.rid);
+    r.has_ff = true;
+  }
+}
 
 // Moller-Trumbore in float-float on the float-float ray: the same two-sided
 // rule as the FP64 definition (|det| < 1e-12 misses; 0 <= u, v; u + v <= 1;
 // t > 1e-9), decided on signs of float-float numerators (about 1e-14 relative),
 // which agree with FP64 except within rounding distance of an edge or tie.
-__device__ inline bool exact_t(const float4* __restrict__ tris, const Ray& r, int slot, ff& t) {
+__device__ inline bool exact_t(const float4* __restrict__ tris, Ray& r, int slot, ff& t) {
+  ensure_ff(r);
   const float3 a = tri_vert(tris, slot, 0), b = tri_vert(tris, slot, 1), c = tri_vert(tris, slot, 2);
   const ff3 e1 = ff3_diff(b, a), e2 = ff3_diff(c, a);
   const ff3 p = ff3_cross(r.d, e2);
@@ -117,7 +139,7 @@ __device__ inline void take_exact(Best& b, int id, int slot, ff t) {
 }
 
 // Offer a candidate whose exact distance lies in [lo, hi] (exact: t known).
-__device__ inline void consider(Best& b, const float4* __restrict__ tris, const Ray& r, int id,
+__device__ inline void consider(Best& b, const float4* __restrict__ tris, Ray& r, int id,
                                 int slot, float lo, float hi, bool exact, ff t) {
   if (b.id < 0 || hi < b.lo) {
     if (exact) take_exact(b, id, slot, t);
@@ -140,7 +162,7 @@ __device__ inline void consider(Best& b, const float4* __restrict__ tris, const 
   if (ff_less(t, b.t) || (t.hi == b.t.hi && t.lo == b.t.lo && id < b.id)) take_exact(b, id, slot, t);
 }
 
-__device__ inline void test_tri(Best& b, const float4* __restrict__ tris, const Ray& r, int slot) {
+__device__ inline void test_tri(Best& b, const float4* __restrict__ tris, Ray& r, int slot) {
   const float4 A = __ldg(&tris[3 * slot]);
   const int id = __float_as_int(A.w);
   if (id == r.skip) return;
@@ -194,7 +216,7 @@ __device__ inline void slab(const float3& o, const float3& idir, float lox, floa
 }
 
 __device__ Best nearest(const float4* __restrict__ tris, const Node* __restrict__ nodes, int nt,
-                        const Ray& r) {
+                        Ray& r) {
   Best b;
   b.id = -1;
   b.slot = -1;
@@ -236,11 +258,15 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node* __restrict_
   return b;
 }
 
+__device__ inline void set_idir(Ray& r) {
+  auto inv = [](float x) { return 1.0f / (fabsf(x) < 1e-20f ? copysignf(1e-20f, x) : x); };
+  r.idir = f3(inv(r.df.x), inv(r.df.y), inv(r.df.z));
+}
+
 __device__ inline void set_f32(Ray& r) {
   r.of = ff3_hi(r.o);
   r.df = ff3_hi(r.d);
-  auto inv = [](float x) { return 1.0f / (fabsf(x) < 1e-20f ? copysignf(1e-20f, x) : x); };
-  r.idir = f3(inv(r.df.x), inv(r.df.y), inv(r.df.z));
+  set_idir(r);
 }
 
 // barycentrics of the hit (reported, not used downstream), FP32
@@ -268,9 +294,14 @@ __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float
   const int rid = ray_ids ? ray_ids[i] : i;
   Ray r;
   float omega;
-  grid_ray(g, rid, r.o, r.d, omega);
+  r.g = &g;
+  r.rid = rid;
+  r.has_ff = false;
+  r.o = ff3_arr(g.o);
+  r.of = ff3_hi(r.o);
+  r.df = grid_dir_f32(g, rid, omega);
   r.skip = -1;
-  set_f32(r);
+  set_idir(r);
   ray_w[i] = omega;
   int nh = 0;
   for (int k = 0; k < K; ++k) {
@@ -289,6 +320,7 @@ __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float
                  C = __ldg(&tris[3 * b.slot + 2]);
     const float3 a = f3(A.x, A.y, A.z), bb = f3(B.x, B.y, B.z), c = f3(C.x, C.y, C.z);
     // float-float refine: plane of the exact triangle, t = N.(a - o) / (N.d)
+    ensure_ff(r);
     const ff3 N = ff3_cross(ff3_diff(bb, a), ff3_diff(c, a));
     const ff den = ff3_dot(N, r.d);
     const ff t = ff_div(ff3_dot(N, ff3_sub(ff3_of(a), r.o)), den);
@@ -461,7 +493,8 @@ extern "C" sbr_status sbr_trace(const sbr_scene* scene, const sbr_radar_cfg* rad
     g.ua[j] = ff_from_double(grid->u_axis[j]);
     g.va[j] = ff_from_double(grid->v_axis[j]);
   }
-  g.th = ff_from_double(grid->tan_half);
+  g.start = ff_from_double(-grid->tan_half + grid->tan_half / grid->G);
+  g.step = ff_from_double(2.0 * grid->tan_half / grid->G);
   g.cell = (float)(2.0 * grid->tan_half / grid->G);
   g.G = grid->G;
   RadarArg rd;
