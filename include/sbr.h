@@ -52,7 +52,8 @@ typedef enum {
   SBR_ERR_OOM = 2,         /* caller-provided region smaller than *_bytes() */
   SBR_ERR_TIMEOUT = 3,     /* a bounded device wait gave up (status word) */
   SBR_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has the name) */
-  SBR_ERR_UNSUPPORTED = 5  /* configuration outside the compiled kernels' range */
+  SBR_ERR_UNSUPPORTED = 5, /* configuration outside the compiled kernels' range */
+  SBR_ERR_CANCELLED = 6    /* serving: the request was cancelled before admission */
 } sbr_status;
 
 #define SBR_MAX_TX 16
@@ -317,6 +318,90 @@ sbr_status sbr_laplacian(const float* d_verts, int32_t nv, const int32_t* d_off,
  * increments it, so a captured CUDA graph of the loop stays correct. */
 sbr_status sbr_adam_step(float* d_params, const float* d_grad, float* d_m, float* d_v, int64_t n,
                          int32_t* d_step, float lr, float beta1, float beta2, float eps, sbr_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Serving (the deployment form of the simulator; the paper has no serving   */
+/* layer): continuous batching of forward-simulation and reconstruction     */
+/* requests of uneven mesh and ray budgets on one GPU.                      */
+/* ------------------------------------------------------------------------ */
+
+/* Offset allocator over a byte range (first fit, 256-byte granules, adjacent
+ * free blocks merged).  Host bookkeeping only: it never touches device memory;
+ * the server places every request's device buffers with it. */
+typedef struct sbr_arena sbr_arena;
+sbr_arena* sbr_arena_create(size_t bytes);
+int64_t sbr_arena_alloc(sbr_arena* a, size_t bytes);   /* offset, or -1 when no block fits */
+void sbr_arena_free(sbr_arena* a, int64_t offset, size_t bytes);
+size_t sbr_arena_used(const sbr_arena* a);
+size_t sbr_arena_peak(const sbr_arena* a);
+size_t sbr_arena_largest_free(const sbr_arena* a);
+void sbr_arena_destroy(sbr_arena* a);
+
+typedef enum { SBR_REQ_FORWARD = 0, SBR_REQ_RECON = 1 } sbr_request_kind;
+
+/* A request.  Host arrays are copied at submission; out_* must stay valid
+ * until the request's completion is returned by sbr_server_poll. */
+typedef struct {
+  int32_t kind;         /* sbr_request_kind */
+  int32_t max_bounces;
+  uint64_t mesh_id;     /* caller identity of (verts, faces); equal ids = equal meshes; 0 = not cached */
+  const float* verts;   /* host [nv][3] */
+  const int32_t* faces; /* host [nt][3] */
+  int32_t nv, nt;
+  sbr_ray_grid grid;
+  /* reconstruction: iterations of forward + loss + adjoints + Adam from verts */
+  int32_t iterations;
+  int32_t n_target;
+  const float* target;  /* host [n_target][4] target points (x, y, z, w) */
+  float lr, lap_weight;
+  /* results */
+  float* out_points;    /* host [k_max][4] point cloud (recon: of the last iteration) */
+  float* out_verts;     /* host [nv][3] final vertices of a reconstruction, or NULL */
+} sbr_request;
+
+typedef struct {
+  int64_t ticket;
+  int32_t status;       /* sbr_status of this request */
+  int32_t n_points;
+  int32_t scene_cached; /* 1: a resident BVH was reused (no build) */
+  int32_t cube_cached;  /* 1: a resident IF cube was reused (no trace, no synthesis) */
+  float loss;           /* reconstruction: loss of the last iteration */
+  float gpu_ms;         /* device time from admission to completion (CUDA events) */
+  double t_submit_us, t_admit_us, t_done_us; /* host clock, microseconds since sbr_server_create */
+  uint64_t footprint;   /* device bytes the request held while running */
+} sbr_completion;
+
+typedef struct {
+  uint64_t arena_bytes, used_bytes, peak_bytes, cached_bytes;
+  int32_t waiting, running, cached_scenes, cached_cubes;
+  int64_t submitted, completed, cache_hits;
+} sbr_server_stats;
+
+typedef struct sbr_server sbr_server;
+
+/* Device bytes a request holds while it runs (its admission footprint),
+ * excluding a resident scene or cube it may reuse. */
+size_t sbr_server_request_bytes(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const sbr_request* req);
+/* d_arena / arena_bytes: the caller's device memory the server may use (the
+ * HBM budget).  n_slots requests run concurrently, each on its own stream. */
+sbr_status sbr_server_create(void* d_arena, size_t arena_bytes, int32_t n_slots, const sbr_radar_cfg* radar,
+                             const sbr_cfar_cfg* cfar, sbr_server** out);
+/* Queues a request (FIFO).  SBR_ERR_OOM when its footprint exceeds the whole
+ * arena, SBR_ERR_INVALID_ARG for malformed sizes; nothing runs until polled. */
+sbr_status sbr_server_submit(sbr_server* s, const sbr_request* req, int64_t* ticket);
+/* Cancels a request that has not been admitted (its completion then reports
+ * SBR_ERR_CANCELLED); SBR_ERR_INVALID_ARG for unknown or admitted tickets. */
+sbr_status sbr_server_cancel(sbr_server* s, int64_t ticket);
+/* One turn of the loop: collects requests whose device work has finished
+ * (their memory and slots return to the pool), admits waiting requests while a
+ * slot is free and their footprint fits (evicting least-recently-used
+ * resident scenes and cubes when needed; a request may overtake at most 8
+ * larger ones ahead of it), enqueues their work, and copies up to cap
+ * completions into out. */
+sbr_status sbr_server_poll(sbr_server* s, sbr_completion* out, int32_t cap, int32_t* n_out);
+sbr_status sbr_server_get_stats(const sbr_server* s, sbr_server_stats* out);
+/* Waits for the device work of every running request, then frees the host state. */
+void sbr_server_destroy(sbr_server* s);
 
 #ifdef __cplusplus
 }

@@ -58,8 +58,42 @@ class PcState(ctypes.Structure):
                 ("n_points", c_p), ("argmax", c_p), ("scratch", c_p)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("kind", c_i32), ("max_bounces", c_i32), ("mesh_id", ctypes.c_uint64), ("verts", c_p),
+                ("faces", c_p), ("nv", c_i32), ("nt", c_i32), ("grid", RayGrid), ("iterations", c_i32),
+                ("n_target", c_i32), ("target", c_p), ("lr", c_f32), ("lap_weight", c_f32), ("out_points", c_p),
+                ("out_verts", c_p)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("ticket", c_i64), ("status", c_i32), ("n_points", c_i32), ("scene_cached", c_i32),
+                ("cube_cached", c_i32), ("loss", c_f32), ("gpu_ms", c_f32), ("t_submit_us", c_f64),
+                ("t_admit_us", c_f64), ("t_done_us", c_f64), ("footprint", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("arena_bytes", ctypes.c_uint64), ("used_bytes", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
+                ("cached_bytes", ctypes.c_uint64), ("waiting", c_i32), ("running", c_i32),
+                ("cached_scenes", c_i32), ("cached_cubes", c_i32), ("submitted", c_i64), ("completed", c_i64),
+                ("cache_hits", c_i64)]
+
+
 P = ctypes.POINTER
 _SIGS = {
+    "sbr_server_request_bytes": (c_sz, [P(RadarCfg), P(CfarCfg), P(Request)]),
+    "sbr_server_create": (c_i32, [c_p, c_sz, c_i32, P(RadarCfg), P(CfarCfg), P(c_p)]),
+    "sbr_server_submit": (c_i32, [c_p, P(Request), P(c_i64)]),
+    "sbr_server_cancel": (c_i32, [c_p, c_i64]),
+    "sbr_server_poll": (c_i32, [c_p, P(Completion), c_i32, P(c_i32)]),
+    "sbr_server_get_stats": (c_i32, [c_p, P(ServerStats)]),
+    "sbr_server_destroy": (None, [c_p]),
+    "sbr_arena_create": (c_p, [c_sz]),
+    "sbr_arena_alloc": (c_i64, [c_p, c_sz]),
+    "sbr_arena_free": (None, [c_p, c_i64, c_sz]),
+    "sbr_arena_used": (c_sz, [c_p]),
+    "sbr_arena_peak": (c_sz, [c_p]),
+    "sbr_arena_largest_free": (c_sz, [c_p]),
+    "sbr_arena_destroy": (None, [c_p]),
     "sbr_version": (ctypes.c_char_p, []),
     "sbr_last_error": (None, [ctypes.c_char_p, c_sz]),
     "sbr_launch_count": (ctypes.c_uint64, []),

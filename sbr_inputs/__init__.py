@@ -343,3 +343,25 @@ class CfarParams:
     @property
     def alpha(self) -> float:
         return 10.0 ** (self.alpha_db / 10.0)
+
+
+def serving_workload(seed: int, n: int = 512, pool: int = 64, nt_range=(1_000, 200_000),
+                     rays_range=(65_536, 4_194_304), recon_iterations: int = 50):
+    """Seeded request stream over a pool of meshes (so BVHs can be reused).
+
+    Pool mesh j: superquadric or perturbed icosphere (50/50) with a log-uniform
+    triangle budget in ``nt_range`` at 1-3 m.  Request i: a pool mesh, a
+    log-uniform ray budget in ``rays_range`` (rounded to G x G), and a kind:
+    half forward-only, half ``recon_iterations``-iteration reconstructions."""
+    rng = np.random.default_rng(seed)
+    meshes = []
+    for j in range(pool):
+        nt = int(math.exp(rng.uniform(math.log(nt_range[0]), math.log(nt_range[1]))))
+        kind = "superquadric" if rng.random() < 0.5 else "icosphere"
+        meshes.append(dict(id=j + 1, n_tris=nt, mesh=kind, seed=int(rng.integers(0, 2**31 - 1))))
+    reqs = []
+    for i in range(n):
+        nr = math.exp(rng.uniform(math.log(rays_range[0]), math.log(rays_range[1])))
+        reqs.append(dict(id=i, mesh=int(rng.integers(0, pool)), G=max(8, int(round(math.sqrt(nr)))),
+                         kind="forward" if rng.random() < 0.5 else "recon", iterations=recon_iterations))
+    return meshes, reqs
