@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recon", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
 
@@ -240,11 +242,14 @@ def gpu_arm(args, rank, world, local):
     # ---- end to end through the public API with host buffers
     e2e = e2e_arm(sbr, torch, wl, cfg, args, world)
 
-    # ---- roofline of the dominant kernel
+    # ---- rooflines (work counters from one counting trace, outside the timed region)
+    from paper_2311_13182_gb300 import sim as _sim
+    counts = _sim.trace_counts(b["scene"], wl.radar, wl.grid, wl.max_bounces, out=b["paths"])
     peaks, src = measured_peaks()
-    roof = roofline(stage_ms, wl, P, peaks, src, clk)
+    roof, roofs = rooflines(stage_ms, wl, P, counts, peaks, src)
 
     recon = None if args.no_recon else recon_arm(sbr, torch, args)
+    serve = None if args.no_serve else serve_arm(sbr, torch, args)
     out = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_step_all, "higher_is_better": True,
@@ -257,10 +262,12 @@ def gpu_arm(args, rank, world, local):
         "stage_ms": stage_ms,
         "recon_iters_per_s": None if recon is None else recon["iters_per_s"],
         "recon": recon,
+        "serving": serve,
         "e2e": e2e,
         "gpu_launches": launches,
         "wall_s_timed_region": t_wall,
         "roofline": roof,
+        "rooflines": roofs,
         "clocks": clk,
     }
     return out
@@ -311,33 +318,38 @@ def e2e_arm(sbr, torch, wl, cfg, args, world):
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
 
-def roofline(stage_ms, wl, P, peaks, src, clk):
-    """Roofline of the dominant kernel of the step (see the design doc for the per-unit figures)."""
-    dom = max(stage_ms, key=stage_ms.get)
+def rooflines(stage_ms, wl, P, counts, peaks, src):
+    """Rooflines of the step's two large kernels; per-unit figures in the design doc.
+
+    trace (sbr_trace = k_trace + scan + k_prep, timed together): bytes a launch moves
+      BVH nodes fetched x 64 B + triangles tested x 48 B (counted by sbr_trace_counts)
+      + hit records 16 B + float-float hit data 32 B per ray-bounce slot + 8 B per ray
+      + per (path, antenna) the 16-B synthesis record and 8-B path length + 4 B per path,
+      against the measured HBM copy bandwidth (the working set is L2-resident, so this is
+      the bytes-served rate; `traffic` is the DRAM part, from ncu).
+    synthesis (k_synth_split + k_reduce): 6 FP32 flops per (path, antenna, sample) term
+      (2 adds accumulating the phasor, 2 FMAs advancing the two-term recurrence), against
+      152 SMs x 128 FP32 lanes x 2 flops x SM max clock."""
     V, Ns = wl.radar.n_virt, wl.radar.n_samples
-    sms = 152
+    R, K = wl.grid.n_rays, wl.max_bounces
     smax = float(peaks.get("sm_max_mhz", 2070.0))
-    if dom == "synthesize":
-        # FP32 pipe: 128 lanes/SM/clk; algorithmic work = 6 FP32 instructions per term
-        # (4 for the complex rotation, 2 for the accumulation), terms = P * V * N_s
-        terms = P * V * Ns
-        achieved = terms * 6 / (stage_ms[dom] * 1e-3) / 1e12
-        peak = sms * 128 * smax * 1e6 / 1e12
-        return {"kernel": "k_synth_split", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "T FP32 instr/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x {smax:.0f} MHz (SM max clock, {src})"}
-    if dom == "trace":
-        # bytes a launch must move: hit records (16 B) + FP64 hit data (32 B) per slot,
-        # ray weight + path offset (8 B) per ray, path prep (16 + 8 B) per (path, antenna)
-        R, K = wl.grid.n_rays, wl.max_bounces
-        algo = R * K * 48 + R * 8 + P * V * 24 + P * 4
-        achieved = algo / (stage_ms[dom] * 1e-3) / 1e9
-        peak = float(peaks["hbm_gbs"])
-        return {"kernel": "k_trace + k_prep", "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"hbm_gbs ({src})"}
-    return {"kernel": dom, "bound": "hbm", "achieved": None, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-            "frac": None, "traffic": None}
+    nodes, tris, trav = counts
+    tb = nodes * 64 + tris * 48 + R * K * 48 + R * 8 + P * V * 24 + P * 4
+    t_ach = tb / (stage_ms["trace"] * 1e-3) / 1e9
+    hbm = float(peaks["hbm_gbs"])
+    trace = {"kernel": "k_trace (+ scan, k_prep)", "bound": "hbm", "achieved": t_ach, "peak": hbm, "unit": "GB/s",
+             "frac": t_ach / hbm, "traffic": None, "bytes_per_launch": tb,
+             "units": {"rays": R, "traversals": trav, "nodes": nodes, "triangles": tris, "paths": P},
+             "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({src}, burst copy)"}
+    terms = P * V * Ns
+    s_ach = terms * 6 / (stage_ms["synthesize"] * 1e-3) / 1e12
+    fp32 = 152 * 128 * 2 * smax * 1e6 / 1e12
+    synth = {"kernel": "k_synth_split (+ k_reduce)", "bound": "alu", "achieved": s_ach, "peak": fp32,
+             "unit": "TFLOP/s (FP32)", "frac": s_ach / fp32, "traffic": None, "terms_per_launch": terms,
+             "terms_per_s": terms / (stage_ms["synthesize"] * 1e-3),
+             "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {smax:.0f} MHz (SM max clock of MEASURED_PEAKS.json)"}
+    dom = trace if stage_ms["trace"] >= stage_ms["synthesize"] else synth
+    return dom, [trace, synth]
 
 
 def recon_arm(sbr, torch, args):
@@ -374,6 +386,60 @@ def recon_arm(sbr, torch, args):
             "mode": "CUDA graph of one full iteration (forward, loss, adjoints, Adam)"}
 
 
+def serve_arm(sbr, torch, args):
+    """Serving: a seeded Poisson stream of requests over a pool of 64 meshes (superquadrics and
+    perturbed icospheres, 1k-200k triangles log-uniform), ray budgets 64k-4M (log-uniform),
+    half forward-only and half 50-iteration reconstructions, 1 Tx / 4 Rx radar, 2 bounces.
+    First the same requests run one at a time through the plain simulator (synchronous, no
+    caches); the stream rate is then 0.8 x that single-stream capacity.  Latency = completion
+    time - arrival time of each request."""
+    from paper_2311_13182_gb300 import serving as S
+    from sbr_inputs import CfarParams, radar_single_tx, serving_workload
+    radar, cfg = radar_single_tx(256, 1), CfarParams()
+    meshes, reqs = serving_workload(args.seed + 7, n=args.serve_requests, pool=64)
+    items = S.build_items(meshes, reqs, radar, cfg)
+    rays = [it["grid"].G ** 2 * (it["iterations"] if it["kind"] == S.RECON else 1) for it in items]
+    seq = S.run_sequential(items, radar, cfg)
+    capacity = len(items) / (sum(seq) * 1e-3)
+    rate = 0.8 * capacity
+    free, _ = torch.cuda.mem_get_info()
+    arena = int(min(64 << 30, 0.5 * free))
+    srv = S.Server(radar, cfg, arena, n_slots=16)
+    done, wall, tickets = S.run_stream(srv, items, rate, seed=args.seed + 11)
+    stats = srv.stats()
+    srv.close()
+    ok = [d for d in done if d["status"] == 0]
+    lat = [(d["t_done_us"] - d["t_submit_us"]) * 1e-3 for d in ok]
+    # one at a time under the same arrivals: a single FIFO server with the measured service times
+    arrivals = np.cumsum(np.random.default_rng(args.seed + 11).exponential(1.0 / rate, size=len(items))) * 1e3
+    t_free, seq_lat = 0.0, []
+    for a, st in zip(arrivals, seq):
+        start = max(a, t_free)
+        t_free = start + st
+        seq_lat.append(t_free - a)
+    # capacity of the served system: every request submitted at once
+    srv = S.Server(radar, cfg, arena, n_slots=16)
+    t0 = time.perf_counter()
+    for it in items:
+        srv.submit(**it)
+    sat = srv.drain(600)
+    sat_wall = time.perf_counter() - t0
+    srv.close()
+    out = {"requests": len(items), "completed_ok": len(ok), "rate_hz": rate,
+           "rate_rule": "0.8 x one-at-a-time capacity", "capacity_one_at_a_time_hz": capacity,
+           "paced": {"wall_s": wall, **S.percentiles(lat)},
+           "one_at_a_time_same_arrivals": S.percentiles(seq_lat),
+           "saturated": {"rays_per_s": sum(rays) / sat_wall, "wall_s": sat_wall,
+                         "completed_ok": sum(1 for d in sat if d["status"] == 0)},
+           "one_at_a_time": {"rays_per_s": sum(rays) / (sum(seq) * 1e-3), "wall_s": sum(seq) * 1e-3,
+                             "service_p50_ms": float(np.percentile(seq, 50)),
+                             "service_p99_ms": float(np.percentile(seq, 99))},
+           "cache_hits": stats["cache_hits"], "peak_bytes": stats["peak_bytes"], "arena_bytes": arena,
+           "slots": 16, "recon_iterations": 50, "rays_counted": "rays per forward pass x passes"}
+    out["p50_ms"], out["p99_ms"] = out["paced"]["p50_ms"], out["paced"]["p99_ms"]
+    return out
+
+
 # ----------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ----------------------------------------------------------------------------
@@ -394,10 +460,10 @@ def oracle_sample(n_rays: int, seed: int):
     return time.perf_counter() - t0, pa["P"]
 
 
-def cpu_baseline(seed: int, budget_s: float = 12.0):
+def cpu_baseline(seed: int, budget_s: float = 20.0):
     n = 2048
     dt, _ = oracle_sample(n, seed)
-    n2 = int(min(1 << 20, max(n, n * budget_s / max(dt, 1e-3) * 0.8)))
+    n2 = int(min(1 << 20, max(n, n * budget_s / max(dt, 1e-3))))
     dt2, P = oracle_sample(n2, seed)
     return {"value": n2 / dt2, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{n2} of 1,048,576 rays (seeded subset): brute-force FP64 trace, paths, direct-sum "

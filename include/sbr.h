@@ -191,6 +191,16 @@ sbr_status sbr_trace(const sbr_scene* scene, const sbr_radar_cfg* radar,
                      const sbr_ray_grid* grid, const int32_t* d_ray_ids, int32_t n_ids,
                      int32_t max_bounces, const sbr_paths* paths, sbr_stream stream);
 
+/* sbr_trace plus work counters for roofline accounting: d_counts[0] = BVH
+ * nodes fetched (64 B each), [1] = triangles tested (48 B each), [2] = ray
+ * traversals (one per bounce attempted), [3] = 0.  d_counts (device, 4 x
+ * uint64) is zeroed by the call.  Same results as sbr_trace; slower (the
+ * counting kernel variant), so not for timed runs. */
+sbr_status sbr_trace_counts(const sbr_scene* scene, const sbr_radar_cfg* radar,
+                            const sbr_ray_grid* grid, const int32_t* d_ray_ids, int32_t n_ids,
+                            int32_t max_bounces, const sbr_paths* paths, uint64_t* d_counts,
+                            sbr_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* Synthesis (Section 3.2.2, Eq. 8)                                         */
 /* ------------------------------------------------------------------------ */

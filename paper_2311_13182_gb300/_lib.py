@@ -105,6 +105,7 @@ _SIGS = {
     "sbr_paths_bytes": (c_sz, [c_i32, c_i32, c_i32]),
     "sbr_paths_bind": (c_i32, [c_p, c_sz, c_i32, c_i32, c_i32, P(Paths)]),
     "sbr_trace": (c_i32, [c_p, P(RadarCfg), P(RayGrid), c_p, c_i32, c_i32, P(Paths), c_p]),
+    "sbr_trace_counts": (c_i32, [c_p, P(RadarCfg), P(RayGrid), c_p, c_i32, c_i32, P(Paths), c_p, c_p]),
     "sbr_synth_ws_bytes": (c_sz, [P(RadarCfg), c_i64]),
     "sbr_synthesize": (c_i32, [P(Paths), P(RadarCfg), c_i32, c_p, c_p, c_sz, c_p]),
     "sbr_synthesize_bwd": (c_i32, [P(Paths), P(RadarCfg), c_p, c_p, c_p, c_p, c_sz, c_p]),

@@ -215,8 +215,10 @@ __device__ inline void slab(const float3& o, const float3& idir, float lox, floa
   tf = tf * 1.0000005f + 1e-30f;
 }
 
+// kCount: also count the nodes and triangles fetched (the roofline's bytes)
+template <bool kCount>
 __device__ Best nearest(const float4* __restrict__ tris, const Node* __restrict__ nodes, int nt,
-                        Ray& r) {
+                        Ray& r, int& n_nodes, int& n_tris) {
   Best b;
   b.id = -1;
   b.slot = -1;
@@ -231,6 +233,7 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node* __restrict_
   // against a corrupted hierarchy turning into an endless loop
   for (int guard = 2 * nt + 64; guard > 0; --guard) {
     if (node >= 0) {
+      if (kCount) ++n_nodes;
       const float4 a = __ldg(&nodes[node].lxy);
       const float4 c = __ldg(&nodes[node].rxy);
       const float4 z = __ldg(&nodes[node].lrz);
@@ -250,6 +253,7 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node* __restrict_
       if (hl) { node = ch.x; continue; }
       if (hr) { node = ch.y; continue; }
     } else {
+      if (kCount) ++n_tris;
       test_tri(b, tris, r, ~node);
     }
     if (sp == 0) break;
@@ -282,15 +286,24 @@ __device__ inline void bary(const Ray& r, float3 a, float3 b, float3 c, float& u
 #define SBR_TRACE_MIN_BLOCKS 6  // resident 128-thread CTAs per SM the register budget targets
 #endif
 
+template <bool kCount>
 __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float4* __restrict__ tris,
                                                const Node* __restrict__ nodes, int nt, GridArg g,
                                                const int32_t* __restrict__ ray_ids, int n_rays,
                                                int K, sbr_hit* __restrict__ hits,
                                                float4* __restrict__ hit_pos,
                                                float* __restrict__ ray_w,
-                                               int32_t* __restrict__ nvalid) {
+                                               int32_t* __restrict__ nvalid,
+                                               unsigned long long* __restrict__ counts) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_rays) return;
+  int n_nodes = 0, n_tris = 0, n_trav = 0;
+  if (kCount) {
+    // whole warps stay to the reduction below; idle lanes count nothing
+    if (i - (int)(threadIdx.x & 31) >= n_rays) return;
+  } else if (i >= n_rays) {
+    return;
+  }
+  if (i < n_rays) {
   const int rid = ray_ids ? ray_ids[i] : i;
   Ray r;
   float omega;
@@ -306,7 +319,8 @@ __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float
   int nh = 0;
   for (int k = 0; k < K; ++k) {
     const size_t sl = (size_t)i * K + k;
-    Best b = nearest(tris, nodes, nt, r);
+    if (kCount) ++n_trav;
+    Best b = nearest<kCount>(tris, nodes, nt, r, n_nodes, n_tris);
     if (b.id < 0) {
       for (int kk = k; kk < K; ++kk) {
         const size_t s2 = (size_t)i * K + kk;
@@ -341,6 +355,19 @@ __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float
     ++nh;
   }
   nvalid[i] = nh;
+  }
+  if (kCount) {
+    for (int o = 16; o; o >>= 1) {
+      n_nodes += __shfl_xor_sync(0xffffffffu, n_nodes, o);
+      n_tris += __shfl_xor_sync(0xffffffffu, n_tris, o);
+      n_trav += __shfl_xor_sync(0xffffffffu, n_trav, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&counts[0], (unsigned long long)n_nodes);
+      atomicAdd(&counts[1], (unsigned long long)n_tris);
+      atomicAdd(&counts[2], (unsigned long long)n_trav);
+    }
+  }
 }
 
 __device__ inline ff3 ld_hit(const float4* __restrict__ hp, size_t sl, float& cosv) {
@@ -470,9 +497,28 @@ sbr_status check_grid(const sbr_ray_grid* g, const char* who) {
 }
 }  // namespace sbr
 
+static sbr_status trace_impl(const sbr_scene* scene, const sbr_radar_cfg* radar, const sbr_ray_grid* grid,
+                             const int32_t* d_ray_ids, int32_t n_ids, int32_t max_bounces,
+                             const sbr_paths* paths, sbr_stream stream, unsigned long long* d_counts);
+
 extern "C" sbr_status sbr_trace(const sbr_scene* scene, const sbr_radar_cfg* radar,
                                 const sbr_ray_grid* grid, const int32_t* d_ray_ids, int32_t n_ids,
                                 int32_t max_bounces, const sbr_paths* paths, sbr_stream stream) {
+  return trace_impl(scene, radar, grid, d_ray_ids, n_ids, max_bounces, paths, stream, nullptr);
+}
+
+extern "C" sbr_status sbr_trace_counts(const sbr_scene* scene, const sbr_radar_cfg* radar,
+                                       const sbr_ray_grid* grid, const int32_t* d_ray_ids, int32_t n_ids,
+                                       int32_t max_bounces, const sbr_paths* paths, uint64_t* d_counts,
+                                       sbr_stream stream) {
+  SBR_ARG(d_counts, "sbr_trace_counts: d_counts is NULL");
+  return trace_impl(scene, radar, grid, d_ray_ids, n_ids, max_bounces, paths, stream,
+                    reinterpret_cast<unsigned long long*>(d_counts));
+}
+
+static sbr_status trace_impl(const sbr_scene* scene, const sbr_radar_cfg* radar, const sbr_ray_grid* grid,
+                             const int32_t* d_ray_ids, int32_t n_ids, int32_t max_bounces,
+                             const sbr_paths* paths, sbr_stream stream, unsigned long long* d_counts) {
   SBR_ARG(scene && paths, "sbr_trace: NULL scene or paths");
   sbr_status rs = check_radar(radar, "sbr_trace");
   if (rs != SBR_OK) return rs;
@@ -511,10 +557,16 @@ extern "C" sbr_status sbr_trace(const sbr_scene* scene, const sbr_radar_cfg* rad
     return SBR_OK;
   }
   ::sbr::note_launch();
-  k_trace<<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes, scene->nt, g, d_ray_ids,
-                                          (int)R, max_bounces, paths->hits,
-                                          reinterpret_cast<float4*>(paths->hit_pos),
-                                          paths->ray_weight, paths->ray_first);
+  if (d_counts) {
+    SBR_CUDA(cudaMemsetAsync(d_counts, 0, 4 * sizeof(unsigned long long), st));
+    k_trace<true><<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes, scene->nt, g, d_ray_ids, (int)R,
+                                                  max_bounces, paths->hits, reinterpret_cast<float4*>(paths->hit_pos),
+                                                  paths->ray_weight, paths->ray_first, d_counts);
+  } else {
+    k_trace<false><<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes, scene->nt, g, d_ray_ids, (int)R,
+                                                   max_bounces, paths->hits, reinterpret_cast<float4*>(paths->hit_pos),
+                                                   paths->ray_weight, paths->ray_first, nullptr);
+  }
   SBR_CUDA(cudaGetLastError());
   SBR_CUDA(exclusive_scan(paths->ray_first, paths->ray_first, R, nullptr, paths->scratch, st));
   ::sbr::note_launch();

@@ -172,6 +172,17 @@ def trace(scene: Scene, radar, grid, max_bounces: int, ray_ids: torch.Tensor | N
     return out
 
 
+def trace_counts(scene: Scene, radar, grid, max_bounces: int, out: PathBuffers, ray_ids=None, stream=None):
+    """sbr_trace_counts: the trace of ``trace`` plus (nodes fetched, triangles tested, traversals)."""
+    counts = torch.zeros(4, dtype=torch.int64, device=scene.device)
+    r, g = radar_struct(radar), grid_struct(grid)
+    n = int(ray_ids.shape[0]) if ray_ids is not None else -1
+    L.call("sbr_trace_counts", scene.handle, ctypes.byref(r), ctypes.byref(g), _vp(ray_ids), n, max_bounces,
+           ctypes.byref(out.s), _vp(counts), _stream(stream))
+    c = counts.cpu().tolist()
+    return c[0], c[1], c[2]
+
+
 def synth_ws_bytes(radar, path_cap: int) -> int:
     return int(L.load().sbr_synth_ws_bytes(ctypes.byref(radar_struct(radar)), path_cap))
 

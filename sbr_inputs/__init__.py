@@ -319,7 +319,7 @@ def request_mesh(req: dict):
         v, f, _ = superquadric(req["seed"], n_lon=m, n_rings=m, center=(0.0, 0.0, dist))
     else:
         s = max(1, int(round(math.log(max(req["n_tris"], 20) / 20.0, 4))))
-        v, f = perturbed_icosphere(req["seed"], min(s, 7), 0.25, (0.0, 0.0, dist))
+        v, f = perturbed_icosphere(req["seed"], min(s, 6), 0.25, (0.0, 0.0, dist))
     return v, f
 
 
