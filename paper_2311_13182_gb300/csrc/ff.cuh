@@ -49,12 +49,14 @@ __device__ inline ff two_prod(float a, float b) {
   return ff{p, fmaf(a, b, -p)};
 }
 
+// Sum with an error of a few units of 2^-44 relative to |a| + |b| (the
+// "sloppy" double-double addition of Hida, Li & Bailey): exact sum of the hi
+// parts, low parts added in FP32.  Under cancellation the result keeps that
+// absolute accuracy, which is all the geometry here needs (~1e-13 of the
+// operands' magnitude).
 __device__ inline ff ff_add(ff a, ff b) {
   ff s = two_sum(a.hi, b.hi);
-  const ff t = two_sum(a.lo, b.lo);
-  s.lo += t.hi;
-  s = fast_two_sum(s.hi, s.lo);
-  s.lo += t.lo;
+  s.lo += a.lo + b.lo;
   return fast_two_sum(s.hi, s.lo);
 }
 

@@ -11,6 +11,8 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <cuda/atomic>
+
 #include "scene.cuh"
 
 namespace sbr {
@@ -197,9 +199,10 @@ __global__ void k_refit(const float4* __restrict__ tris, int n, Node* nodes,
   const float pad = ldexpf(1.f + unord(bounds[6]), -18);
   int node = parent[n - 1 + l];
   for (int depth = 0; node >= 0 && depth < 128; ++depth) {  // tree depth <= 62 (30 + 32 key bits)
-    __threadfence();
-    if (atomicAdd(&visits[node], 1u) == 0u) return;  // sibling subtree not done yet
-    __threadfence();
+    // acquire-release counter: the first arrival's child boxes (written before its
+    // own increment) are visible to the second, which builds this node
+    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> arrivals(visits[node]);
+    if (arrivals.fetch_add(1u, cuda::memory_order_acq_rel) == 0u) return;  // sibling subtree not done yet
     int4 ch = __ldcg(&nodes[node].child);
     Box bl = ch.x < 0 ? tri_box(tris, ~ch.x, pad) : node_box(nodes, ch.x);
     Box br = ch.y < 0 ? tri_box(tris, ~ch.y, pad) : node_box(nodes, ch.y);

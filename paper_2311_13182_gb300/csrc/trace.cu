@@ -88,7 +88,10 @@ struct Best {
 };
 
 struct Ray {
-  ff3 o, d;       // float-float ray (d valid once has_ff)
+  // float-float ray (d valid once has_ff)
+  ff3& o;
+  ff3& d;
+  __device__ Ray(ff3& o_, ff3& d_) : o(o_), d(d_) {}
   float3 of, df;  // FP32 ray driving the traversal
   float3 idir;
   int skip;
@@ -189,10 +192,11 @@ __device__ inline void test_tri(Best& b, const float4* __restrict__ tris, Ray& r
     const float ew = edet + eu + ev + kErr * adet;
     if (su < -eu || sv < -ev || sw < -ew) return;  // outside in FP64 as well
     const float nlo = st - et, nhi = st + et;
-    float lo = nlo / (nlo >= 0.f ? adet + edet : adet - edet);
-    float hi = nhi / (nhi >= 0.f ? adet - edet : adet + edet);
-    lo -= fabsf(lo) * 2.4e-7f;
-    hi += fabsf(hi) * 2.4e-7f;
+    // approximate quotients (<= 2 ulp); the 6e-7 relative pad keeps the interval valid
+    float lo = __fdividef(nlo, nlo >= 0.f ? adet + edet : adet - edet);
+    float hi = __fdividef(nhi, nhi >= 0.f ? adet - edet : adet + edet);
+    lo -= fabsf(lo) * 6e-7f;
+    hi += fabsf(hi) * 6e-7f;
     if (hi <= kTmin) return;                      // behind the origin in FP64 too
     if (b.id >= 0 && lo > b.hi) return;           // farther than the current hit
     if (su > eu && sv > ev && sw > ew && lo > kTmin) {
@@ -305,7 +309,8 @@ __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float
   }
   if (i < n_rays) {
   const int rid = ray_ids ? ray_ids[i] : i;
-  Ray r;
+  ff3 ray_o, ray_d;
+  Ray r(ray_o, ray_d);
   float omega;
   r.g = &g;
   r.rid = rid;
