@@ -46,11 +46,29 @@ cudaError_t exclusive_scan(const int32_t* in, int32_t* out, int64_t n, const int
                            void* scratch, cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
-// keys (4-bit digits).  Ping-pongs between the two buffers; the sorted result
-// ends in keys[0]/vals[0].  n from host, or from *d_n (n = capacity).
+// keys.  Ping-pongs between the two buffers; the sorted result ends in
+// keys[0]/vals[0].  n from host, or from *d_n (n = capacity).  Up to
+// kSortOneCta keys sort in one CTA with 8-bit digits; d_hist, when not NULL,
+// then holds the caller's counts of every digit place (place p's 256 counts at
+// [256p, 256p + 256), for the live keys), which spares the CTA its counting
+// sweep.  Larger inputs take the multi-CTA path (4-bit digits) and ignore it.
+constexpr int64_t kSortOneCta = 65536;
 size_t sort_scratch_bytes(int64_t capacity);
 cudaError_t radix_sort_pairs(uint32_t* keys[2], int32_t* vals[2], int64_t n, const int32_t* d_n,
-                             int bits, void* scratch, cudaStream_t s);
+                             int bits, void* scratch, cudaStream_t s, const uint32_t* d_hist = nullptr);
+
+// Lanes of the calling warp (all 32 active) whose 8-bit value d equals this
+// lane's, restricted to lanes with ok set: one ballot per bit.
+__device__ inline uint32_t warp_peers8(uint32_t d, bool ok) {
+  uint32_t m = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const uint32_t bit = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? bal : ~bal;
+  }
+  return m;
+}
 
 // Argument validation shared by the entry points (trace.cu).
 sbr_status check_radar(const sbr_radar_cfg* r, const char* who);

@@ -24,12 +24,13 @@ __device__ inline int32_t ord(float f) {
 }
 __device__ inline float unord(int32_t i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
 
-__global__ void k_init_bounds(int32_t* b, int32_t* err) {
+__global__ void k_init_bounds(int32_t* b, int32_t* err, uint32_t* hist) {
   if (threadIdx.x < 3) b[threadIdx.x] = 0x7fffffff;           // min x, y, z
   else if (threadIdx.x < 6) b[threadIdx.x] = (int32_t)0x80000000;  // max x, y, z
   else if (threadIdx.x == 6) b[6] = 0;                        // max |coord| (ordered, >= 0)
   else if (threadIdx.x == 7) b[7] = 0;
   if (threadIdx.x == 0) *err = 0;
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) hist[i] = 0u;
 }
 
 __device__ inline int face_vert(const int32_t* faces, int f, int c, int nv, int32_t* err) {
@@ -86,34 +87,53 @@ __device__ inline uint32_t spread10(uint32_t v) {
   return v;
 }
 
-__global__ void k_morton(const float* __restrict__ verts, int nv, const int32_t* __restrict__ faces,
-                         int nt, const int32_t* __restrict__ bounds, uint32_t* keys, int32_t* vals,
-                         int32_t* err) {
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nt) return;
-  float3 a = vload(verts, face_vert(faces, f, 0, nv, err));
-  float3 b = vload(verts, face_vert(faces, f, 1, nv, err));
-  float3 c = vload(verts, face_vert(faces, f, 2, nv, err));
-  float3 m = (a + b + c) * (1.f / 3.f);
-  float3 lo = f3(unord(bounds[0]), unord(bounds[1]), unord(bounds[2]));
-  float3 hi = f3(unord(bounds[3]), unord(bounds[4]), unord(bounds[5]));
-  float3 ext = hi - lo;
-  float qx = ext.x > 0.f ? (m.x - lo.x) / ext.x : 0.f;
-  float qy = ext.y > 0.f ? (m.y - lo.y) / ext.y : 0.f;
-  float qz = ext.z > 0.f ? (m.z - lo.z) / ext.z : 0.f;
-  uint32_t ix = (uint32_t)fminf(fmaxf(qx * 1024.f, 0.f), 1023.f);
-  uint32_t iy = (uint32_t)fminf(fmaxf(qy * 1024.f, 0.f), 1023.f);
-  uint32_t iz = (uint32_t)fminf(fmaxf(qz * 1024.f, 0.f), 1023.f);
-  // Triangles spanning more than 1/32 of the centroid box (a ground plane under
-  // an object) get key bit 30, so the radix tree puts them in their own subtree
-  // at the root instead of inflating the boxes of their Morton neighbours.
-  const float side = fmaxf(fmaxf(fmaxf(fabsf(a.x - b.x), fabsf(b.x - c.x)), fabsf(c.x - a.x)),
-                           fmaxf(fmaxf(fmaxf(fabsf(a.y - b.y), fabsf(b.y - c.y)), fabsf(c.y - a.y)),
-                                 fmaxf(fmaxf(fabsf(a.z - b.z), fabsf(b.z - c.z)), fabsf(c.z - a.z))));
-  const float extent = fmaxf(fmaxf(ext.x, ext.y), ext.z);
-  const uint32_t big = (extent > 0.f && side * 32.f > extent) ? (1u << 30) : 0u;
-  keys[f] = big | (spread10(ix) << 2) | (spread10(iy) << 1) | spread10(iz);
-  vals[f] = f;
+// Morton keys, and the counts of their four 8-bit digit places for the sort.
+__global__ void __launch_bounds__(256) k_morton(const float* __restrict__ verts, int nv,
+                                                const int32_t* __restrict__ faces, int nt,
+                                                const int32_t* __restrict__ bounds, uint32_t* keys,
+                                                int32_t* vals, uint32_t* hist, int32_t* err) {
+  __shared__ uint32_t h[4 * 256];
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = f < nt;
+  uint32_t key = 0u;
+  if (ok) {
+    float3 a = vload(verts, face_vert(faces, f, 0, nv, err));
+    float3 b = vload(verts, face_vert(faces, f, 1, nv, err));
+    float3 c = vload(verts, face_vert(faces, f, 2, nv, err));
+    float3 m = (a + b + c) * (1.f / 3.f);
+    float3 lo = f3(unord(bounds[0]), unord(bounds[1]), unord(bounds[2]));
+    float3 hi = f3(unord(bounds[3]), unord(bounds[4]), unord(bounds[5]));
+    float3 ext = hi - lo;
+    float qx = ext.x > 0.f ? (m.x - lo.x) / ext.x : 0.f;
+    float qy = ext.y > 0.f ? (m.y - lo.y) / ext.y : 0.f;
+    float qz = ext.z > 0.f ? (m.z - lo.z) / ext.z : 0.f;
+    uint32_t ix = (uint32_t)fminf(fmaxf(qx * 1024.f, 0.f), 1023.f);
+    uint32_t iy = (uint32_t)fminf(fmaxf(qy * 1024.f, 0.f), 1023.f);
+    uint32_t iz = (uint32_t)fminf(fmaxf(qz * 1024.f, 0.f), 1023.f);
+    // Triangles spanning more than 1/32 of the centroid box (a ground plane under
+    // an object) get key bit 30, so the radix tree puts them in their own subtree
+    // at the root instead of inflating the boxes of their Morton neighbours.
+    const float side = fmaxf(fmaxf(fmaxf(fabsf(a.x - b.x), fabsf(b.x - c.x)), fabsf(c.x - a.x)),
+                             fmaxf(fmaxf(fmaxf(fabsf(a.y - b.y), fabsf(b.y - c.y)), fabsf(c.y - a.y)),
+                                   fmaxf(fmaxf(fabsf(a.z - b.z), fabsf(b.z - c.z)), fabsf(c.z - a.z))));
+    const float extent = fmaxf(fmaxf(ext.x, ext.y), ext.z);
+    const uint32_t big = (extent > 0.f && side * 32.f > extent) ? (1u << 30) : 0u;
+    key = big | (spread10(ix) << 2) | (spread10(iy) << 1) | spread10(iz);
+    keys[f] = key;
+    vals[f] = f;
+  }
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {  // warp-aggregated counts
+    const uint32_t d = (key >> (8 * p)) & 255u;
+    const uint32_t peers = warp_peers8(d, ok);
+    if (ok && lane == __ffs(peers) - 1) atomicAdd(&h[256 * p + d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
 __global__ void k_pack(const float* __restrict__ verts, int nv, const int32_t* __restrict__ faces,
@@ -130,37 +150,48 @@ __global__ void k_pack(const float* __restrict__ verts, int nv, const int32_t* _
   tris[3 * i + 2] = make_float4(c.x, c.y, c.z, 0.f);
 }
 
-// Length of the common prefix of sorted keys i and j (index bits break ties).
-__device__ inline int prefix(const uint32_t* __restrict__ k, int n, int i, int j) {
+// Length of the common prefix of sorted keys i and j (index bits break ties);
+// key(j) reads sorted key j.
+template <class KeyAt>
+__device__ inline int prefix(const KeyAt& key, uint32_t ki, int n, int i, int j) {
   if (j < 0 || j >= n) return -1;
-  uint32_t a = k[i], b = k[j];
-  if (a != b) return __clz(a ^ b);
+  const uint32_t b = key(j);
+  if (ki != b) return __clz(ki ^ b);
   return 32 + __clz((uint32_t)(i ^ j));
+}
+
+// Children and leaf range [lo, hi] of internal node i of the radix tree.
+template <class KeyAt>
+__device__ inline void karras_node(const KeyAt& key, int n, int i, int* left, int* right, int* lo, int* hi) {
+  const uint32_t ki = key(i);
+  // direction of the range covered by node i
+  int d = (prefix(key, ki, n, i, i + 1) - prefix(key, ki, n, i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = prefix(key, ki, n, i, i - d);
+  int lmax = 2;
+  while (prefix(key, ki, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (prefix(key, ki, n, i, i + (l + t) * d) > dmin) l += t;
+  int j = i + l * d;
+  int dnode = prefix(key, ki, n, i, j);
+  // split: last index sharing more than dnode bits with i
+  int s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (prefix(key, ki, n, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int g = i + s * d + (d < 0 ? -1 : 0);
+  *lo = min(i, j);
+  *hi = max(i, j);
+  *left = (*lo == g) ? ~g : g;
+  *right = (*hi == g + 1) ? ~(g + 1) : g + 1;
 }
 
 __global__ void k_karras(const uint32_t* __restrict__ keys, int n, Node* nodes, int32_t* parent) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
-  // direction of the range covered by node i
-  int d = (prefix(keys, n, i, i + 1) - prefix(keys, n, i, i - 1)) >= 0 ? 1 : -1;
-  int dmin = prefix(keys, n, i, i - d);
-  int lmax = 2;
-  while (prefix(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
-  int l = 0;
-  for (int t = lmax >> 1; t >= 1; t >>= 1)
-    if (prefix(keys, n, i, i + (l + t) * d) > dmin) l += t;
-  int j = i + l * d;
-  int dnode = prefix(keys, n, i, j);
-  // split: last index sharing more than dnode bits with i
-  int s = 0, t = l;
-  do {
-    t = (t + 1) >> 1;
-    if (prefix(keys, n, i, i + (s + t) * d) > dnode) s += t;
-  } while (t > 1);
-  int g = i + s * d + (d < 0 ? -1 : 0);
-  int lo = min(i, j), hi = max(i, j);
-  int left = (lo == g) ? ~g : g;
-  int right = (hi == g + 1) ? ~(g + 1) : g + 1;
+  int left, right, lo, hi;
+  karras_node([&](int j) { return __ldg(&keys[j]); }, n, i, &left, &right, &lo, &hi);
   nodes[i].child = make_int4(left, right, 0, 0);
   parent[left >= 0 ? left : (n - 1 + ~left)] = i;
   parent[right >= 0 ? right : (n - 1 + ~right)] = i;
@@ -213,6 +244,298 @@ __global__ void k_refit(const float4* __restrict__ tris, int n, Node* nodes,
   }
 }
 
+// ---- fused build for meshes of up to kTiledMax triangles ---------------------
+//
+// Every internal node's index lies inside its leaf range [lo, hi] (a property of
+// the Karras tree), so with leaves and node indices cut into tiles of kBuildTile
+// a node whose range stays inside one tile ("local") has its whole subtree in
+// that tile.  k_build_tree runs one CTA per tile: it packs the tile's triangles
+// in sorted order, computes the tile's tree nodes and refits the local ones with
+// shared-memory arrival counters.  The last CTA to finish then refits the rest
+// ("crossing" nodes, whose range spans a tile boundary).  Crossing nodes all
+// contain the two leaves on either side of some boundary, so they are the
+// ancestors of at most tiles-1 lowest common ancestors: at most 64 per boundary,
+// as the tree depth is bounded by the 63 prefix bits of key and index.
+
+constexpr int kBuildTile = 1024;
+constexpr int kTiledMax = 65536;
+// Sorted keys staged in shared memory for the tree searches: all of them up to
+// kKeyWindow, else a window around the tile (a local node's searches stay
+// within twice its range of it; the rest read global memory).
+constexpr int kKeyWindow = 40960;
+
+// exclusive scan of one value per thread over a CTA of whole warps
+__device__ inline uint32_t block_exclusive_u32(uint32_t v, uint32_t* total, uint32_t* warp_tot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t q = lane < nw ? warp_tot[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, q, o);
+      if (lane >= o) q += y;
+    }
+    if (lane < nw) warp_tot[lane] = q;
+  }
+  __syncthreads();
+  const uint32_t r = (w ? warp_tot[w - 1] : 0u) + x - v;
+  *total = warp_tot[nw - 1];
+  __syncthreads();
+  return r;
+}
+
+struct SBox {
+  float lx, ly, lz, hx, hy, hz;
+};
+__device__ inline SBox sbox(const Box& b) { return SBox{b.lo.x, b.lo.y, b.lo.z, b.hi.x, b.hi.y, b.hi.z}; }
+__device__ inline Box unsbox(const SBox& b) {
+  Box r;
+  r.lo = f3(b.lx, b.ly, b.lz);
+  r.hi = f3(b.hx, b.hy, b.hz);
+  return r;
+}
+__device__ inline Box box_union(const Box& a, const Box& b) {
+  Box r;
+  r.lo = f3(fminf(a.lo.x, b.lo.x), fminf(a.lo.y, b.lo.y), fminf(a.lo.z, b.lo.z));
+  r.hi = f3(fmaxf(a.hi.x, b.hi.x), fmaxf(a.hi.y, b.hi.y), fmaxf(a.hi.z, b.hi.z));
+  return r;
+}
+__device__ inline void write_node(Node* nodes, int i, const Box& l, const Box& r) {
+  nodes[i].lxy = make_float4(l.lo.x, l.hi.x, l.lo.y, l.hi.y);
+  nodes[i].rxy = make_float4(r.lo.x, r.hi.x, r.lo.y, r.hi.y);
+  nodes[i].lrz = make_float4(l.lo.z, l.hi.z, r.lo.z, r.hi.z);
+}
+__device__ inline float refit_pad(const int32_t* bounds) {
+  // conservative pad: covers the FP32 ray's deviation from its exact source and
+  // slab-test rounding for rays within the scene's coordinate range
+  return ldexpf(1.f + unord(bounds[6]), -18);
+}
+
+__device__ inline Box tri_box_cg(const float4* tris, int slot, float pad) {  // written in this kernel
+  const float4 a = __ldcg(&tris[3 * slot]), b = __ldcg(&tris[3 * slot + 1]), c = __ldcg(&tris[3 * slot + 2]);
+  Box r;
+  r.lo = f3(fminf(fminf(a.x, b.x), c.x) - pad, fminf(fminf(a.y, b.y), c.y) - pad,
+            fminf(fminf(a.z, b.z), c.z) - pad);
+  r.hi = f3(fmaxf(fmaxf(a.x, b.x), c.x) + pad, fmaxf(fmaxf(a.y, b.y), c.y) + pad,
+            fmaxf(fmaxf(a.z, b.z), c.z) + pad);
+  return r;
+}
+
+// Shared memory of the crossing-node refit for a mesh of n triangles.
+inline int top_slots(int n) {
+  const int tiles = (n + kBuildTile - 1) / kBuildTile;
+  int m = 64 * (tiles - 1);
+  return m < n - 1 ? m : n - 1;
+}
+inline size_t top_smem(int n) {
+  const int words = (n - 1 + 31) / 32;
+  const int slots = top_slots(n) > 0 ? top_slots(n) : 1;
+  return (size_t)words * 8 + (size_t)slots * (sizeof(SBox) + 4 + 4 + 4 + 4);
+}
+inline size_t tree_smem(int n) {
+  const size_t keys = (size_t)(n < kKeyWindow ? n : kKeyWindow) * sizeof(uint32_t);
+  const size_t top = top_smem(n);
+  return keys > top ? keys : top;
+}
+
+// Refit of the crossing nodes by one CTA of 1024 threads (the build's last).
+__device__ void refit_crossing(int n, const float4* tris, float pad, Node* nodes, const int32_t* parent,
+                               const uint32_t* crossing, int slots, int32_t* err, unsigned char* smem) {
+  const int words = (n - 1 + 31) / 32;
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_wpre = s_mask + words;  // crossing nodes before each mask word
+  SBox* s_box = reinterpret_cast<SBox*>(s_wpre + words);
+  int32_t* s_id = reinterpret_cast<int32_t*>(s_box + slots);
+  int32_t* s_pslot = s_id + slots;
+  int32_t* s_kids = s_pslot + slots;  // left slot (low 16 bits) and right slot, 0xffff = not crossing
+  uint32_t* s_arr = reinterpret_cast<uint32_t*>(s_kids + slots);
+  __shared__ uint32_t wt[32];
+  __shared__ uint32_t s_total;
+  const int t = threadIdx.x;
+  // slot of each crossing node = its rank in index order
+  uint32_t cnt = 0;
+  for (int j = 0; j < 2; ++j) {  // words 2t, 2t+1 (words <= 2048)
+    const int wd = 2 * t + j;
+    const uint32_t v = wd < words ? __ldcg(&crossing[wd]) : 0u;
+    if (wd < words) s_mask[wd] = v;
+    cnt += __popc(v);
+  }
+  uint32_t tot;
+  uint32_t pre = block_exclusive_u32(cnt, &tot, wt);
+  for (int j = 0; j < 2; ++j) {
+    const int wd = 2 * t + j;
+    if (wd < words) {
+      s_wpre[wd] = pre;
+      pre += __popc(s_mask[wd]);
+    }
+  }
+  if (t == 0) s_total = tot;
+  __syncthreads();
+  const int m = (int)s_total;
+  if (m > slots) {  // cannot happen for a radix tree (bound in the comment above)
+    if (t == 0) atomicOr(err, 2);
+    return;
+  }
+  if (m == 0) return;
+  auto slot_of = [&](int id) -> int {  // -1 if node id is local
+    const uint32_t wv = s_mask[id >> 5], bit = 1u << (id & 31);
+    return (wv & bit) ? (int)(s_wpre[id >> 5] + __popc(wv & (bit - 1u))) : -1;
+  };
+  // slot -> node id, then one thread per crossing node (they cluster near tile
+  // boundaries, so a thread per mask word would serialise them)
+  for (int wd = t; wd < words; wd += 1024) {
+    uint32_t v = s_mask[wd];
+    int s = (int)s_wpre[wd];
+    while (v) {
+      s_id[s++] = 32 * wd + __ffs(v) - 1;
+      v &= v - 1u;
+    }
+  }
+  __syncthreads();
+  // setup: parent slots, crossing children, the other children's boxes
+  for (int s = t; s < m; s += 1024) {
+    const int id = s_id[s];
+    const int pid = __ldcg(&parent[id]);
+    const int4 ch = __ldcg(&nodes[id].child);
+    s_pslot[s] = pid >= 0 ? slot_of(pid) : -1;
+    s_arr[s] = 0u;
+    const int ls = ch.x >= 0 ? slot_of(ch.x) : -1, rs = ch.y >= 0 ? slot_of(ch.y) : -1;
+    s_kids[s] = (int32_t)(((uint32_t)rs << 16) | ((uint32_t)ls & 0xffffu));
+    if (ls < 0 && rs < 0) {  // both children built already: build this node now
+      const Box bl = ch.x < 0 ? tri_box_cg(tris, ~ch.x, pad) : node_box(nodes, ch.x);
+      const Box br = ch.y < 0 ? tri_box_cg(tris, ~ch.y, pad) : node_box(nodes, ch.y);
+      write_node(nodes, id, bl, br);
+      s_box[s] = sbox(box_union(bl, br));
+    } else if (ls < 0) {
+      s_box[s] = sbox(ch.x < 0 ? tri_box_cg(tris, ~ch.x, pad) : node_box(nodes, ch.x));
+    } else if (rs < 0) {
+      s_box[s] = sbox(ch.y < 0 ? tri_box_cg(tris, ~ch.y, pad) : node_box(nodes, ch.y));
+    }
+  }
+  __syncthreads();
+  // climb from the nodes built in setup; the last child to arrive builds the parent
+  for (int s0 = t; s0 < m; s0 += 1024) {
+    if (s_kids[s0] != -1) continue;  // has a crossing child: built by a climb
+    int s = s0;
+    for (int depth = 0; depth < 128; ++depth) {
+      const int ps = s_pslot[s];
+      if (ps < 0) break;  // root
+      const int kids = s_kids[ps];
+      const int ls = (int16_t)(kids & 0xffff), rs = kids >> 16;
+      const uint32_t need = (ls >= 0) + (rs >= 0);
+      __threadfence_block();
+      if (atomicAdd(&s_arr[ps], 1u) + 1u < need) break;  // other crossing child not done yet
+      __threadfence_block();
+      const Box bl = unsbox(s_box[ls >= 0 ? ls : ps]);
+      const Box br = unsbox(s_box[rs >= 0 ? rs : ps]);
+      write_node(nodes, s_id[ps], bl, br);
+      s_box[ps] = sbox(box_union(bl, br));
+      s = ps;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBuildTile) k_build_tree(const float* __restrict__ verts, int nv,
+                                                           const int32_t* __restrict__ faces,
+                                                           const uint32_t* __restrict__ keys,
+                                                           const int32_t* __restrict__ order, int n,
+                                                           float4* tris, const int32_t* __restrict__ bounds,
+                                                           Node* nodes, int32_t* parent, uint32_t* crossing,
+                                                           uint32_t* done, int slots, int32_t* err) {
+  __shared__ int32_t s_par_leaf[kBuildTile];  // in-tile parent of leaf c0+t, else -1
+  __shared__ int32_t s_par_node[kBuildTile];  // in-tile local parent of node c0+t, else -1
+  __shared__ int2 s_child[kBuildTile];
+  __shared__ uint32_t s_arr[kBuildTile];
+  __shared__ SBox s_box[kBuildTile];  // box of local node c0+t once built
+  __shared__ bool s_last;
+  extern __shared__ __align__(16) unsigned char tree_sm[];  // key window, then the crossing refit
+  uint32_t* s_keys = reinterpret_cast<uint32_t*>(tree_sm);
+  const int t = threadIdx.x, c0 = blockIdx.x * kBuildTile, i = c0 + t;
+  const int wlen = min(n, kKeyWindow);
+  const int wlo = min(max(c0 + kBuildTile / 2 - kKeyWindow / 2, 0), n - wlen);
+  for (int j = t; j < wlen; j += kBuildTile) s_keys[j] = keys[wlo + j];
+  s_par_leaf[t] = -1;
+  s_par_node[t] = -1;
+  s_arr[t] = 0u;
+  const float pad = refit_pad(bounds);
+  // this tile's triangles in sorted order, and the leaf's box
+  Box b{};
+  if (i < n) {
+    const int f = order[i];
+    const float3 p0 = vload(verts, face_vert(faces, f, 0, nv, err));
+    const float3 p1 = vload(verts, face_vert(faces, f, 1, nv, err));
+    const float3 p2 = vload(verts, face_vert(faces, f, 2, nv, err));
+    tris[3 * i + 0] = make_float4(p0.x, p0.y, p0.z, __int_as_float(f));
+    tris[3 * i + 1] = make_float4(p1.x, p1.y, p1.z, 0.f);
+    tris[3 * i + 2] = make_float4(p2.x, p2.y, p2.z, 0.f);
+    b.lo = f3(fminf(fminf(p0.x, p1.x), p2.x) - pad, fminf(fminf(p0.y, p1.y), p2.y) - pad,
+              fminf(fminf(p0.z, p1.z), p2.z) - pad);
+    b.hi = f3(fmaxf(fmaxf(p0.x, p1.x), p2.x) + pad, fmaxf(fmaxf(p0.y, p1.y), p2.y) + pad,
+              fmaxf(fmaxf(p0.z, p1.z), p2.z) + pad);
+  }
+  __syncthreads();
+  bool cross = false;
+  if (i < n - 1) {
+    int left, right, lo, hi;
+    karras_node(
+        [&](int j) {
+          const unsigned r = (unsigned)(j - wlo);
+          return r < (unsigned)wlen ? s_keys[r] : __ldg(&keys[j]);
+        },
+        n, i, &left, &right, &lo, &hi);
+    nodes[i].child = make_int4(left, right, 0, 0);
+    parent[left >= 0 ? left : (n - 1 + ~left)] = i;
+    parent[right >= 0 ? right : (n - 1 + ~right)] = i;
+    s_child[t] = make_int2(left, right);
+    cross = (lo / kBuildTile) != (hi / kBuildTile);
+    if (!cross) {  // local: both children are in this tile
+      if (left < 0) s_par_leaf[~left - c0] = i;
+      else s_par_node[left - c0] = i;
+      if (right < 0) s_par_leaf[~right - c0] = i;
+      else s_par_node[right - c0] = i;
+    }
+  }
+  if (i == 0) parent[0] = -1;
+  const uint32_t mword = __ballot_sync(0xffffffffu, cross);
+  if ((t & 31) == 0 && i < n - 1) crossing[i >> 5] = mword;
+  __syncthreads();
+  // local refit: climb from the leaves; the second child to arrive builds the parent
+  int me = ~i;  // child code of the subtree this thread holds
+  int p = i < n ? s_par_leaf[t] : -1;
+  while (p >= 0) {
+    const int lp = p - c0;
+    if (me >= 0) s_box[me - c0] = sbox(b);  // leaf boxes are re-read by the sibling
+    __threadfence_block();
+    if (atomicAdd(&s_arr[lp], 1u) == 0u) break;  // sibling subtree not done yet
+    __threadfence_block();
+    const int2 ch = s_child[lp];
+    const bool is_left = ch.x == me;
+    const int sib = is_left ? ch.y : ch.x;
+    const Box sb = sib < 0 ? tri_box_cg(tris, ~sib, pad) : unsbox(s_box[sib - c0]);
+    if (is_left) write_node(nodes, p, b, sb);
+    else write_node(nodes, p, sb, b);
+    b = box_union(b, sb);
+    me = p;
+    p = s_par_node[lp];
+  }
+  // the last CTA to finish refits the crossing nodes
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  refit_crossing(n, tris, pad, nodes, parent, crossing, slots, err, tree_sm);
+  if (t == 0) *done = 0u;  // ready for the next build
+}
+
 inline int blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 size_t layout(sbr_scene* s, void* mem, int32_t nt) {
@@ -230,6 +553,8 @@ size_t layout(sbr_scene* s, void* mem, int32_t nt) {
   s->faces = c.take<int32_t>(3 * n);
   s->bounds = c.take<int32_t>(8);
   s->err = c.take<int32_t>(1);
+  s->hist = c.take<uint32_t>(4 * 256);
+  s->done = c.take<uint32_t>(1);
   s->sort_scratch = c.take<char>(sort_scratch_bytes(n));
   return c.bytes();
 }
@@ -237,7 +562,7 @@ size_t layout(sbr_scene* s, void* mem, int32_t nt) {
 sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
   const int nt = s->nt, nv = s->nv;
   ::sbr::note_launch();
-  k_init_bounds<<<1, 32, 0, st>>>(s->bounds, s->err);
+  k_init_bounds<<<1, 256, 0, st>>>(s->bounds, s->err, s->hist);
   if (nt == 0) {
     SBR_CUDA(cudaGetLastError());
     return SBR_OK;
@@ -246,11 +571,18 @@ sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
   k_bounds<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->bounds, s->err);
   ::sbr::note_launch();
   k_morton<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->bounds, s->keys[0],
-                                            s->vals[0], s->err);
-  SBR_CUDA(radix_sort_pairs(s->keys, s->vals, nt, nullptr, 31, s->sort_scratch, st));
-  ::sbr::note_launch();
-  k_pack<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->vals[0], s->tris, s->err);
-  if (nt > 1) {
+                                            s->vals[0], s->hist, s->err);
+  SBR_CUDA(radix_sort_pairs(s->keys, s->vals, nt, nullptr, 31, s->sort_scratch, st, s->hist));
+  if (nt > 1 && nt <= kTiledMax) {
+    ::sbr::note_launch();
+    k_build_tree<<<blocks(nt, kBuildTile), kBuildTile, tree_smem(nt), st>>>(
+        verts, nv, s->faces, s->keys[0], s->vals[0], nt, s->tris, s->bounds, s->nodes, s->parent, s->visits,
+        s->done, top_slots(nt), s->err);
+  } else {
+    ::sbr::note_launch();
+    k_pack<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->vals[0], s->tris, s->err);
+  }
+  if (nt > kTiledMax) {
     ::sbr::note_launch();
     k_karras<<<blocks(nt - 1, 256), 256, 0, st>>>(s->keys[0], nt, s->nodes, s->parent);
     SBR_CUDA(cudaMemsetAsync(s->visits, 0, sizeof(uint32_t) * (nt - 1), st));
@@ -294,6 +626,16 @@ extern "C" sbr_status sbr_scene_create(const float* d_verts, int32_t nv, const i
   s->nv = nv;
   s->nt = nt;
   s->bytes = layout(s, d_mem, nt);
+  if (nt > 1 && nt <= kTiledMax) {  // dynamic shared memory above the default 48 KB
+    cudaError_t e = cudaFuncSetAttribute(k_build_tree, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tree_smem(kTiledMax));
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->done, 0, sizeof(uint32_t), reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+      set_error("sbr_scene_create: shared-memory attribute: %s", cudaGetErrorString(e));
+      free(s);
+      return SBR_ERR_CUDA;
+    }
+  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (nt > 0) {
     cudaError_t e = cudaMemcpyAsync(s->faces, d_faces, sizeof(int32_t) * 3 * (size_t)nt,
@@ -325,7 +667,11 @@ extern "C" sbr_status sbr_scene_check(const sbr_scene* scene, sbr_stream stream)
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   SBR_CUDA(cudaMemcpyAsync(&err, scene->err, sizeof(err), cudaMemcpyDeviceToHost, st));
   SBR_CUDA(cudaStreamSynchronize(st));
-  SBR_ARG(err == 0, "sbr_scene: face index outside [0, nv) (error word %d)", err);
+  SBR_ARG((err & 1) == 0, "sbr_scene: face index outside [0, nv) (error word %d)", err);
+  if (err) {
+    set_error("sbr_scene: tree build failed (error word %d)", err);
+    return SBR_ERR_CUDA;
+  }
   return SBR_OK;
 }
 

@@ -22,12 +22,14 @@ struct sbr_scene {
   float4* tris;        // [nt*3] sorted: (v0, original id bits), (v1, 0), (v2, 0)
   sbr::Node* nodes;    // [max(nt-1, 1)]
   int32_t* parent;     // [2nt-1]: internal 0..nt-2, leaves nt-1..2nt-2
-  uint32_t* visits;    // [max(nt-1,1)] refit arrival counters
+  uint32_t* visits;    // [max(nt-1,1)] refit arrival counters, or the crossing-node mask
   uint32_t* keys[2];   // [nt] Morton codes (sort ping-pong)
   int32_t* vals[2];    // [nt] triangle ids (sort ping-pong)
   int32_t* faces;      // [nt*3] copy of the topology
   int32_t* bounds;     // [8] centroid box as ordered ints + pad
   int32_t* err;        // [1] device error word (bit 0: face index out of range)
+  uint32_t* hist;      // [4*256] Morton key digit counts (8-bit places) for the sort
+  uint32_t* done;      // [1] CTAs of the fused tree build that have finished
   void* sort_scratch;
   size_t bytes;
 };

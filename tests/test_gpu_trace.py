@@ -104,3 +104,28 @@ def test_bad_face_index_reported(sbr):
     scene = sbr.Scene(v, f)
     with pytest.raises(sbr.SbrError):
         scene.check()
+
+
+@pytest.mark.parametrize("nt", [2, 1023, 1024, 1025, 2049, 5000])
+def test_tree_tile_boundaries(sbr, nt):
+    """Meshes whose triangle counts sit on and around the 1024-leaf tiles of the fused tree
+    build: the first nt faces of a 20,480-face sphere (open, so rays also reach its inside)."""
+    c = (0.05, -0.02, 1.3)
+    v, f = icosphere(5, 0.25, c)
+    wl = Workload("tiles", v, np.ascontiguousarray(f[:nt]), radar_single_tx(), ray_grid_for_sphere(c, 0.25, 40), 2,
+                  {})
+    tr = oracle.trace(wl.verts, wl.faces, wl.grid, 2)
+    _, paths = gpu_trace(sbr, wl)
+    check_paths(wl, tr, paths)
+
+
+def test_large_mesh_multi_cta_build(sbr):
+    """81,920 triangles: above the fused build's limit, so the Morton sort runs over many CTAs
+    and the tree is refitted by global arrival counters."""
+    c = (0.0, 0.03, 1.1)
+    v, f = icosphere(6, 0.25, c)
+    assert len(f) > 65536
+    wl = Workload("large", v, f, radar_single_tx(), ray_grid_for_sphere(c, 0.25, 32), 2, {})
+    tr = oracle.trace(wl.verts, wl.faces, wl.grid, 2)
+    _, paths = gpu_trace(sbr, wl)
+    check_paths(wl, tr, paths)
