@@ -87,6 +87,29 @@ __device__ inline uint32_t spread10(uint32_t v) {
   return v;
 }
 
+// 30-bit Morton code of the centroid in the centroid box (bounds, ordered ints).
+// Triangles spanning more than 1/32 of that box (a ground plane under an object)
+// get key bit 30, so the radix tree puts them in their own subtree at the root
+// instead of inflating the boxes of their Morton neighbours.
+__device__ inline uint32_t morton_key(float3 a, float3 b, float3 c, const int32_t* bounds) {
+  const float3 m = (a + b + c) * (1.f / 3.f);
+  const float3 lo = f3(unord(__ldcg(&bounds[0])), unord(__ldcg(&bounds[1])), unord(__ldcg(&bounds[2])));
+  const float3 hi = f3(unord(__ldcg(&bounds[3])), unord(__ldcg(&bounds[4])), unord(__ldcg(&bounds[5])));
+  const float3 ext = hi - lo;
+  const float qx = ext.x > 0.f ? (m.x - lo.x) / ext.x : 0.f;
+  const float qy = ext.y > 0.f ? (m.y - lo.y) / ext.y : 0.f;
+  const float qz = ext.z > 0.f ? (m.z - lo.z) / ext.z : 0.f;
+  const uint32_t ix = (uint32_t)fminf(fmaxf(qx * 1024.f, 0.f), 1023.f);
+  const uint32_t iy = (uint32_t)fminf(fmaxf(qy * 1024.f, 0.f), 1023.f);
+  const uint32_t iz = (uint32_t)fminf(fmaxf(qz * 1024.f, 0.f), 1023.f);
+  const float side = fmaxf(fmaxf(fmaxf(fabsf(a.x - b.x), fabsf(b.x - c.x)), fabsf(c.x - a.x)),
+                           fmaxf(fmaxf(fmaxf(fabsf(a.y - b.y), fabsf(b.y - c.y)), fabsf(c.y - a.y)),
+                                 fmaxf(fmaxf(fabsf(a.z - b.z), fabsf(b.z - c.z)), fabsf(c.z - a.z))));
+  const float extent = fmaxf(fmaxf(ext.x, ext.y), ext.z);
+  const uint32_t big = (extent > 0.f && side * 32.f > extent) ? (1u << 30) : 0u;
+  return big | (spread10(ix) << 2) | (spread10(iy) << 1) | spread10(iz);
+}
+
 // Morton keys, and the counts of their four 8-bit digit places for the sort.
 __global__ void __launch_bounds__(256) k_morton(const float* __restrict__ verts, int nv,
                                                 const int32_t* __restrict__ faces, int nt,
@@ -99,28 +122,10 @@ __global__ void __launch_bounds__(256) k_morton(const float* __restrict__ verts,
   const bool ok = f < nt;
   uint32_t key = 0u;
   if (ok) {
-    float3 a = vload(verts, face_vert(faces, f, 0, nv, err));
-    float3 b = vload(verts, face_vert(faces, f, 1, nv, err));
-    float3 c = vload(verts, face_vert(faces, f, 2, nv, err));
-    float3 m = (a + b + c) * (1.f / 3.f);
-    float3 lo = f3(unord(bounds[0]), unord(bounds[1]), unord(bounds[2]));
-    float3 hi = f3(unord(bounds[3]), unord(bounds[4]), unord(bounds[5]));
-    float3 ext = hi - lo;
-    float qx = ext.x > 0.f ? (m.x - lo.x) / ext.x : 0.f;
-    float qy = ext.y > 0.f ? (m.y - lo.y) / ext.y : 0.f;
-    float qz = ext.z > 0.f ? (m.z - lo.z) / ext.z : 0.f;
-    uint32_t ix = (uint32_t)fminf(fmaxf(qx * 1024.f, 0.f), 1023.f);
-    uint32_t iy = (uint32_t)fminf(fmaxf(qy * 1024.f, 0.f), 1023.f);
-    uint32_t iz = (uint32_t)fminf(fmaxf(qz * 1024.f, 0.f), 1023.f);
-    // Triangles spanning more than 1/32 of the centroid box (a ground plane under
-    // an object) get key bit 30, so the radix tree puts them in their own subtree
-    // at the root instead of inflating the boxes of their Morton neighbours.
-    const float side = fmaxf(fmaxf(fmaxf(fabsf(a.x - b.x), fabsf(b.x - c.x)), fabsf(c.x - a.x)),
-                             fmaxf(fmaxf(fmaxf(fabsf(a.y - b.y), fabsf(b.y - c.y)), fabsf(c.y - a.y)),
-                                   fmaxf(fmaxf(fabsf(a.z - b.z), fabsf(b.z - c.z)), fabsf(c.z - a.z))));
-    const float extent = fmaxf(fmaxf(ext.x, ext.y), ext.z);
-    const uint32_t big = (extent > 0.f && side * 32.f > extent) ? (1u << 30) : 0u;
-    key = big | (spread10(ix) << 2) | (spread10(iy) << 1) | spread10(iz);
+    const float3 a = vload(verts, face_vert(faces, f, 0, nv, err));
+    const float3 b = vload(verts, face_vert(faces, f, 1, nv, err));
+    const float3 c = vload(verts, face_vert(faces, f, 2, nv, err));
+    key = morton_key(a, b, c, bounds);
     keys[f] = key;
     vals[f] = f;
   }
@@ -249,13 +254,14 @@ __global__ void k_refit(const float4* __restrict__ tris, int n, Node* nodes,
 // Every internal node's index lies inside its leaf range [lo, hi] (a property of
 // the Karras tree), so with leaves and node indices cut into tiles of kBuildTile
 // a node whose range stays inside one tile ("local") has its whole subtree in
-// that tile.  k_build_tree runs one CTA per tile: it packs the tile's triangles
-// in sorted order, computes the tile's tree nodes and refits the local ones with
-// shared-memory arrival counters.  The last CTA to finish then refits the rest
-// ("crossing" nodes, whose range spans a tile boundary).  Crossing nodes all
-// contain the two leaves on either side of some boundary, so they are the
-// ancestors of at most tiles-1 lowest common ancestors: at most 64 per boundary,
-// as the tree depth is bounded by the 63 prefix bits of key and index.
+// that tile.  The tree phase of k_build_scene runs one CTA per tile: it packs
+// the tile's triangles in sorted order, computes the tile's tree nodes and
+// refits the local ones with shared-memory arrival counters.  The last CTA to
+// finish then refits the rest ("crossing" nodes, whose range spans a tile
+// boundary).  Crossing nodes all contain the two leaves on either side of some
+// boundary, so they are the ancestors of at most tiles-1 lowest common
+// ancestors: at most 64 per boundary, as the tree depth is bounded by the 63
+// prefix bits of key and index.
 
 constexpr int kBuildTile = 1024;
 constexpr int kTiledMax = 65536;
@@ -442,43 +448,281 @@ __device__ void refit_crossing(int n, const float4* tris, float pad, Node* nodes
   }
 }
 
-__global__ void __launch_bounds__(kBuildTile) k_build_tree(const float* __restrict__ verts, int nv,
-                                                           const int32_t* __restrict__ faces,
-                                                           const uint32_t* __restrict__ keys,
-                                                           const int32_t* __restrict__ order, int n,
-                                                           float4* tris, const int32_t* __restrict__ bounds,
-                                                           Node* nodes, int32_t* parent, uint32_t* crossing,
-                                                           uint32_t* done, int slots, int32_t* err) {
+// ---- the whole build as one cooperative kernel -------------------------------
+//
+// One CTA of 1024 threads per tile of 1024 triangles, all resident at once
+// (cooperative launch), with grid-wide barriers between the phases: centroid
+// bounds; Morton keys and their digit counts; four stable passes of an 8-bit
+// LSD radix sort (each CTA ranks its tile by digit, publishes the tile's digit
+// counts, and after a barrier scatters with the counts of the tiles before it);
+// then the tiled tree build above.  Data written by other CTAs is read through
+// L2 (ld.cg), never through the non-coherent L1 path.
+
+constexpr int kBarrierSpins = 1 << 22;  // ~0.3 s of polling before a barrier gives up
+constexpr int kSortStride = 257;        // padded per-warp row of 256 digit counters
+
+struct BuildBufs {
+  uint32_t* keys[2];
+  int32_t* vals[2];
+  float4* tris;
+  Node* nodes;
+  int32_t* parent;
+  uint32_t* crossing;
+  int32_t* bounds;    // [8] ordered ints: centroid min xyz, max xyz, max |coord|
+  uint32_t* hist;     // [4*256] digit counts of all keys
+  uint32_t* tile_hist;  // [tiles*256] digit counts per tile (current pass)
+  uint32_t* bar;      // [2] grid barrier: arrivals, generation
+  uint32_t* done;     // [1] CTAs finished with the tree
+  int32_t* err;
+};
+
+// Grid-wide barrier for a cooperative launch.  Waits are bounded: on timeout the
+// error word gets bit 2 and false is returned (the caller then exits).
+__device__ bool grid_sync(uint32_t* bar, uint32_t nblocks, int32_t* err) {
+  __shared__ int s_ok;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> cnt(bar[0]), gen(bar[1]);
+    const uint32_t g = gen.load(cuda::memory_order_acquire);
+    int ok = 1;
+    if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == nblocks - 1u) {
+      cnt.store(0u, cuda::memory_order_relaxed);
+      gen.store(g + 1u, cuda::memory_order_release);
+    } else {
+      for (int it = 0; gen.load(cuda::memory_order_acquire) == g; ++it) {
+        if (it >= kBarrierSpins) {
+          atomicOr(err, 4);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// exclusive scan of 256 counts held in shared memory, by one warp (8 per lane)
+__device__ inline void warp_scan256(const uint32_t* in, uint32_t* out) {
+  const int lane = threadIdx.x & 31;
+  uint32_t c[8], sum = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    c[j] = in[8 * lane + j];
+    sum += c[j];
+  }
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  uint32_t r = x - sum;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    out[8 * lane + j] = r;
+    r += c[j];
+  }
+}
+
+// Dynamic shared memory: the sort's counters and staging, later reused for the
+// key window and the crossing-node refit.
+constexpr size_t kSortSmem = (size_t)(32 * kSortStride + 4 * 256 + 3 * 256 + 2 * kBuildTile) * 4;
+inline size_t build_smem(int n) {
+  const size_t t = tree_smem(n);
+  return t > kSortSmem ? t : kSortSmem;
+}
+
+__global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restrict__ verts, int nv,
+                                                            const int32_t* __restrict__ faces, int n,
+                                                            BuildBufs B, int slots) {
   __shared__ int32_t s_par_leaf[kBuildTile];  // in-tile parent of leaf c0+t, else -1
   __shared__ int32_t s_par_node[kBuildTile];  // in-tile local parent of node c0+t, else -1
   __shared__ int2 s_child[kBuildTile];
   __shared__ uint32_t s_arr[kBuildTile];
   __shared__ SBox s_box[kBuildTile];  // box of local node c0+t once built
+  __shared__ int32_t s_red[32][8];
   __shared__ bool s_last;
-  extern __shared__ __align__(16) unsigned char tree_sm[];  // key window, then the crossing refit
-  uint32_t* s_keys = reinterpret_cast<uint32_t*>(tree_sm);
-  const int t = threadIdx.x, c0 = blockIdx.x * kBuildTile, i = c0 + t;
+  extern __shared__ __align__(16) unsigned char build_sm[];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, c0 = blockIdx.x * kBuildTile, i = c0 + t;
+  const uint32_t nb = gridDim.x;
+  const bool live = i < n;
+
+  // 1. centroid box and largest coordinate (ordered-int atomics, one set per CTA)
+  float3 a = f3(0.f, 0.f, 0.f), b = a, c = a;
+  if (live) {
+    a = vload(verts, face_vert(faces, i, 0, nv, B.err));
+    b = vload(verts, face_vert(faces, i, 1, nv, B.err));
+    c = vload(verts, face_vert(faces, i, 2, nv, B.err));
+  }
+  {
+    const float3 m = (a + b + c) * (1.f / 3.f);
+    int32_t v[7] = {ord(m.x), ord(m.y), ord(m.z), ord(m.x), ord(m.y), ord(m.z),
+                    ord(fmaxf(fmaxf(l1(a), l1(b)), l1(c)))};
+    if (!live) {
+      v[0] = v[1] = v[2] = 0x7fffffff;
+      v[3] = v[4] = v[5] = (int32_t)0x80000000;
+      v[6] = 0;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[k] = min(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+#pragma unroll
+      for (int k = 3; k < 7; ++k) v[k] = max(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 7; ++k) s_red[w][k] = v[k];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v[k] = s_red[lane][k];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] = min(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+#pragma unroll
+        for (int k = 3; k < 7; ++k) v[k] = max(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+      }
+      int32_t mine = v[0];
+#pragma unroll
+      for (int k = 1; k < 7; ++k)
+        if (lane == k) mine = v[k];
+      if (lane < 3) atomicMin(&B.bounds[lane], mine);
+      else if (lane < 7) atomicMax(&B.bounds[lane], mine);
+    }
+  }
+  if (!grid_sync(B.bar, nb, B.err)) return;
+
+  // 2. Morton keys and the digit counts of all four places
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(build_sm);  // [32][kSortStride]
+  uint32_t* goff = cnt + 32 * kSortStride;                 // [4][256] start of each digit, whole array
+  uint32_t* tot = goff + 4 * 256;                          // [256] tile's digit counts
+  uint32_t* lstart = tot + 256;                            // [256] digit start within the tile
+  uint32_t* gbase = lstart + 256;                          // [256] output position of the tile's digit d, minus lstart
+  uint32_t* stage_k = gbase + 256;                         // [1024] tile grouped by digit
+  int32_t* stage_v = reinterpret_cast<int32_t*>(stage_k + kBuildTile);
+  uint32_t key = live ? morton_key(a, b, c, B.bounds) : 0u;
+  int32_t val = i;
+  goff[t] = 0u;  // 1024 threads: the CTA's own counts first
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const uint32_t d = (key >> (8 * p)) & 255u;
+    const uint32_t peers = warp_peers8(d, live);
+    if (live && lane == __ffs(peers) - 1) atomicAdd(&goff[256 * p + d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  if (goff[t]) atomicAdd(&B.hist[t], goff[t]);
+  if (!grid_sync(B.bar, nb, B.err)) return;
+  if (w < 4) {  // warp p: start of each digit of place p in the sorted array
+    uint32_t c8[8], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      c8[j] = __ldcg(&B.hist[256 * w + 8 * lane + j]);
+      sum += c8[j];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    uint32_t r = x - sum;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      goff[256 * w + 8 * lane + j] = r;
+      r += c8[j];
+    }
+  }
+
+  // 3. four stable passes; pass p moves keys[p & 1] to keys[(p + 1) & 1]
+  const uint32_t lt = (1u << lane) - 1u;
+  const int rn = min(n - c0, kBuildTile);
+  uint32_t* row = cnt + w * kSortStride;
+#pragma unroll 1
+  for (int p = 0; p < 4; ++p) {
+    const int shift = 8 * p;
+    if (p > 0) {
+      key = live ? __ldcg(&((p & 1) ? B.keys[1] : B.keys[0])[i]) : 0u;
+      val = live ? __ldcg(&((p & 1) ? B.vals[1] : B.vals[0])[i]) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) row[lane + 32 * j] = 0u;
+    __syncwarp();
+    const uint32_t d = (key >> shift) & 255u;
+    const uint32_t peers = warp_peers8(d, live);
+    const uint32_t rank = __popc(peers & lt);
+    if (live && lane == __ffs(peers) - 1) row[d] = __popc(peers);
+    __syncthreads();
+    // per digit: exclusive scan over the warps (warp w: digits w, w+32, ...)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int dd = w + 32 * j;
+      const uint32_t cv = cnt[lane * kSortStride + dd];
+      uint32_t x = cv;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      cnt[lane * kSortStride + dd] = x - cv;
+      if (lane == 31) tot[dd] = x;
+    }
+    __syncthreads();
+    if (t < 256) B.tile_hist[(size_t)blockIdx.x * 256 + t] = tot[t];
+    if (w == 0) warp_scan256(tot, lstart);
+    __syncthreads();
+    if (live) {
+      const uint32_t q = lstart[d] + row[d] + rank;
+      stage_k[q] = key;
+      stage_v[q] = val;
+    }
+    if (!grid_sync(B.bar, nb, B.err)) return;
+    if (t < 256) {  // digit t's output start for this tile: whole-array start + earlier tiles
+      uint32_t pre = 0;
+      for (uint32_t c2 = 0; c2 < blockIdx.x; ++c2) pre += __ldcg(&B.tile_hist[(size_t)c2 * 256 + t]);
+      gbase[t] = goff[256 * p + t] + pre - lstart[t];
+    }
+    __syncthreads();
+    if (t < rn) {
+      const uint32_t k2 = stage_k[t];
+      const uint32_t pos = gbase[(k2 >> shift) & 255u] + (uint32_t)t;
+      if (pos < (uint32_t)n) {  // always true when the counts match the keys
+        ((p & 1) ? B.keys[0] : B.keys[1])[pos] = k2;
+        ((p & 1) ? B.vals[0] : B.vals[1])[pos] = stage_v[t];
+      }
+    }
+    if (!grid_sync(B.bar, nb, B.err)) return;
+  }
+
+  // 4. tree: this tile's triangles in sorted order, its nodes, the local refit
+  const uint32_t* keys = B.keys[0];
+  uint32_t* s_keys = reinterpret_cast<uint32_t*>(build_sm);
   const int wlen = min(n, kKeyWindow);
   const int wlo = min(max(c0 + kBuildTile / 2 - kKeyWindow / 2, 0), n - wlen);
-  for (int j = t; j < wlen; j += kBuildTile) s_keys[j] = keys[wlo + j];
+  for (int j = t; j < wlen; j += kBuildTile) s_keys[j] = __ldcg(&keys[wlo + j]);
   s_par_leaf[t] = -1;
   s_par_node[t] = -1;
   s_arr[t] = 0u;
-  const float pad = refit_pad(bounds);
-  // this tile's triangles in sorted order, and the leaf's box
-  Box b{};
-  if (i < n) {
-    const int f = order[i];
-    const float3 p0 = vload(verts, face_vert(faces, f, 0, nv, err));
-    const float3 p1 = vload(verts, face_vert(faces, f, 1, nv, err));
-    const float3 p2 = vload(verts, face_vert(faces, f, 2, nv, err));
-    tris[3 * i + 0] = make_float4(p0.x, p0.y, p0.z, __int_as_float(f));
-    tris[3 * i + 1] = make_float4(p1.x, p1.y, p1.z, 0.f);
-    tris[3 * i + 2] = make_float4(p2.x, p2.y, p2.z, 0.f);
-    b.lo = f3(fminf(fminf(p0.x, p1.x), p2.x) - pad, fminf(fminf(p0.y, p1.y), p2.y) - pad,
-              fminf(fminf(p0.z, p1.z), p2.z) - pad);
-    b.hi = f3(fmaxf(fmaxf(p0.x, p1.x), p2.x) + pad, fmaxf(fmaxf(p0.y, p1.y), p2.y) + pad,
-              fmaxf(fmaxf(p0.z, p1.z), p2.z) + pad);
+  const float pad = ldexpf(1.f + unord(__ldcg(&B.bounds[6])), -18);  // as refit_pad
+  Box bx{};
+  if (live) {
+    const int f = __ldcg(&B.vals[0][i]);
+    const float3 p0 = vload(verts, face_vert(faces, f, 0, nv, B.err));
+    const float3 p1 = vload(verts, face_vert(faces, f, 1, nv, B.err));
+    const float3 p2 = vload(verts, face_vert(faces, f, 2, nv, B.err));
+    B.tris[3 * i + 0] = make_float4(p0.x, p0.y, p0.z, __int_as_float(f));
+    B.tris[3 * i + 1] = make_float4(p1.x, p1.y, p1.z, 0.f);
+    B.tris[3 * i + 2] = make_float4(p2.x, p2.y, p2.z, 0.f);
+    bx.lo = f3(fminf(fminf(p0.x, p1.x), p2.x) - pad, fminf(fminf(p0.y, p1.y), p2.y) - pad,
+               fminf(fminf(p0.z, p1.z), p2.z) - pad);
+    bx.hi = f3(fmaxf(fmaxf(p0.x, p1.x), p2.x) + pad, fmaxf(fmaxf(p0.y, p1.y), p2.y) + pad,
+               fmaxf(fmaxf(p0.z, p1.z), p2.z) + pad);
   }
   __syncthreads();
   bool cross = false;
@@ -487,12 +731,12 @@ __global__ void __launch_bounds__(kBuildTile) k_build_tree(const float* __restri
     karras_node(
         [&](int j) {
           const unsigned r = (unsigned)(j - wlo);
-          return r < (unsigned)wlen ? s_keys[r] : __ldg(&keys[j]);
+          return r < (unsigned)wlen ? s_keys[r] : __ldcg(&keys[j]);
         },
         n, i, &left, &right, &lo, &hi);
-    nodes[i].child = make_int4(left, right, 0, 0);
-    parent[left >= 0 ? left : (n - 1 + ~left)] = i;
-    parent[right >= 0 ? right : (n - 1 + ~right)] = i;
+    B.nodes[i].child = make_int4(left, right, 0, 0);
+    B.parent[left >= 0 ? left : (n - 1 + ~left)] = i;
+    B.parent[right >= 0 ? right : (n - 1 + ~right)] = i;
     s_child[t] = make_int2(left, right);
     cross = (lo / kBuildTile) != (hi / kBuildTile);
     if (!cross) {  // local: both children are in this tile
@@ -502,38 +746,43 @@ __global__ void __launch_bounds__(kBuildTile) k_build_tree(const float* __restri
       else s_par_node[right - c0] = i;
     }
   }
-  if (i == 0) parent[0] = -1;
+  if (i == 0) B.parent[0] = -1;
   const uint32_t mword = __ballot_sync(0xffffffffu, cross);
-  if ((t & 31) == 0 && i < n - 1) crossing[i >> 5] = mword;
+  if (lane == 0 && i < n - 1) B.crossing[i >> 5] = mword;
   __syncthreads();
-  // local refit: climb from the leaves; the second child to arrive builds the parent
   int me = ~i;  // child code of the subtree this thread holds
-  int p = i < n ? s_par_leaf[t] : -1;
-  while (p >= 0) {
-    const int lp = p - c0;
-    if (me >= 0) s_box[me - c0] = sbox(b);  // leaf boxes are re-read by the sibling
+  int pn = live ? s_par_leaf[t] : -1;
+  while (pn >= 0) {
+    const int lp = pn - c0;
+    if (me >= 0) s_box[me - c0] = sbox(bx);  // leaf boxes are re-read by the sibling
     __threadfence_block();
     if (atomicAdd(&s_arr[lp], 1u) == 0u) break;  // sibling subtree not done yet
     __threadfence_block();
     const int2 ch = s_child[lp];
     const bool is_left = ch.x == me;
     const int sib = is_left ? ch.y : ch.x;
-    const Box sb = sib < 0 ? tri_box_cg(tris, ~sib, pad) : unsbox(s_box[sib - c0]);
-    if (is_left) write_node(nodes, p, b, sb);
-    else write_node(nodes, p, sb, b);
-    b = box_union(b, sb);
-    me = p;
-    p = s_par_node[lp];
+    const Box sb = sib < 0 ? tri_box_cg(B.tris, ~sib, pad) : unsbox(s_box[sib - c0]);
+    if (is_left) write_node(B.nodes, pn, bx, sb);
+    else write_node(B.nodes, pn, sb, bx);
+    bx = box_union(bx, sb);
+    me = pn;
+    pn = s_par_node[lp];
   }
-  // the last CTA to finish refits the crossing nodes
+
+  // 5. the last CTA refits the crossing nodes and resets the counters
   __threadfence();
   __syncthreads();
-  if (t == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  if (t == 0) s_last = atomicAdd(B.done, 1u) == nb - 1u;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  refit_crossing(n, tris, pad, nodes, parent, crossing, slots, err, tree_sm);
-  if (t == 0) *done = 0u;  // ready for the next build
+  refit_crossing(n, B.tris, pad, B.nodes, B.parent, B.crossing, slots, B.err, build_sm);
+  __syncthreads();
+  if (t < 3) B.bounds[t] = 0x7fffffff;
+  else if (t < 6) B.bounds[t] = (int32_t)0x80000000;
+  else if (t < 8) B.bounds[t] = 0;
+  B.hist[t] = 0u;
+  if (t == 0) *B.done = 0u;
 }
 
 inline int blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -555,12 +804,25 @@ size_t layout(sbr_scene* s, void* mem, int32_t nt) {
   s->err = c.take<int32_t>(1);
   s->hist = c.take<uint32_t>(4 * 256);
   s->done = c.take<uint32_t>(1);
+  s->bar = c.take<uint32_t>(2);
+  s->tile_hist = c.take<uint32_t>((size_t)256 * ((n + kBuildTile - 1) / kBuildTile));
   s->sort_scratch = c.take<char>(sort_scratch_bytes(n));
   return c.bytes();
 }
 
 sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
   const int nt = s->nt, nv = s->nv;
+  if (s->coop) {  // one cooperative launch; it leaves its counters reset for the next build
+    BuildBufs B{{s->keys[0], s->keys[1]}, {s->vals[0], s->vals[1]}, s->tris, s->nodes, s->parent, s->visits,
+                s->bounds, s->hist, s->tile_hist, s->bar, s->done, s->err};
+    int slots = top_slots(nt), n = nt, nvv = nv;
+    const int32_t* faces = s->faces;
+    void* args[] = {(void*)&verts, (void*)&nvv, (void*)&faces, (void*)&n, (void*)&B, (void*)&slots};
+    ::sbr::note_launch();
+    SBR_CUDA(cudaLaunchCooperativeKernel((const void*)k_build_scene, dim3(blocks(nt, kBuildTile)),
+                                         dim3(kBuildTile), args, build_smem(nt), st));
+    return SBR_OK;
+  }
   ::sbr::note_launch();
   k_init_bounds<<<1, 256, 0, st>>>(s->bounds, s->err, s->hist);
   if (nt == 0) {
@@ -573,16 +835,9 @@ sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
   k_morton<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->bounds, s->keys[0],
                                             s->vals[0], s->hist, s->err);
   SBR_CUDA(radix_sort_pairs(s->keys, s->vals, nt, nullptr, 31, s->sort_scratch, st, s->hist));
-  if (nt > 1 && nt <= kTiledMax) {
-    ::sbr::note_launch();
-    k_build_tree<<<blocks(nt, kBuildTile), kBuildTile, tree_smem(nt), st>>>(
-        verts, nv, s->faces, s->keys[0], s->vals[0], nt, s->tris, s->bounds, s->nodes, s->parent, s->visits,
-        s->done, top_slots(nt), s->err);
-  } else {
-    ::sbr::note_launch();
-    k_pack<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->vals[0], s->tris, s->err);
-  }
-  if (nt > kTiledMax) {
+  ::sbr::note_launch();
+  k_pack<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->vals[0], s->tris, s->err);
+  if (nt > 1) {
     ::sbr::note_launch();
     k_karras<<<blocks(nt - 1, 256), 256, 0, st>>>(s->keys[0], nt, s->nodes, s->parent);
     SBR_CUDA(cudaMemsetAsync(s->visits, 0, sizeof(uint32_t) * (nt - 1), st));
@@ -626,12 +881,37 @@ extern "C" sbr_status sbr_scene_create(const float* d_verts, int32_t nv, const i
   s->nv = nv;
   s->nt = nt;
   s->bytes = layout(s, d_mem, nt);
-  if (nt > 1 && nt <= kTiledMax) {  // dynamic shared memory above the default 48 KB
-    cudaError_t e = cudaFuncSetAttribute(k_build_tree, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tree_smem(kTiledMax));
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->done, 0, sizeof(uint32_t), reinterpret_cast<cudaStream_t>(stream));
+  {
+    // The cooperative build needs every tile's CTA resident at once (1024
+    // threads and up to ~224 KB of shared memory each); otherwise the
+    // multi-kernel build runs.
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (nt >= 2 && nt <= kTiledMax) {
+      int dev = 0, sms = 0, coop = 0, per_sm = 0;
+      e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_build_scene, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)build_smem(kTiledMax));  // the largest any scene asks
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_scene, kBuildTile, build_smem(nt));
+      s->coop = e == cudaSuccess && coop && (int64_t)per_sm * sms >= blocks(nt, kBuildTile);
+      if (e != cudaSuccess) (void)cudaGetLastError();  // not fatal: the multi-kernel build runs
+      e = cudaSuccess;
+    }
+    // counters of the cooperative build start cleared; bounds start empty
+    e = cudaMemsetAsync(s->err, 0, sizeof(int32_t), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->bar, 0, 2 * sizeof(uint32_t), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->done, 0, sizeof(uint32_t), cs);
+    if (e == cudaSuccess) {
+      ::sbr::note_launch();
+      k_init_bounds<<<1, 256, 0, cs>>>(s->bounds, s->err, s->hist);
+      e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
-      set_error("sbr_scene_create: shared-memory attribute: %s", cudaGetErrorString(e));
+      set_error("sbr_scene_create: %s", cudaGetErrorString(e));
       free(s);
       return SBR_ERR_CUDA;
     }

@@ -29,7 +29,10 @@ struct sbr_scene {
   int32_t* bounds;     // [8] centroid box as ordered ints + pad
   int32_t* err;        // [1] device error word (bit 0: face index out of range)
   uint32_t* hist;      // [4*256] Morton key digit counts (8-bit places) for the sort
-  uint32_t* done;      // [1] CTAs of the fused tree build that have finished
+  uint32_t* done;      // [1] CTAs of the cooperative build that have finished the tree
+  uint32_t* bar;       // [2] grid barrier of the cooperative build: arrivals, generation
+  uint32_t* tile_hist; // [tiles*256] per-tile digit counts of the cooperative sort
+  int coop;            // build with one cooperative launch (all tiles resident at once)
   void* sort_scratch;
   size_t bytes;
 };
