@@ -480,8 +480,7 @@ struct BuildBufs {
 // error word gets bit 2 and false is returned (the caller then exits).
 __device__ bool grid_sync(uint32_t* bar, uint32_t nblocks, int32_t* err) {
   __shared__ int s_ok;
-  __threadfence();
-  __syncthreads();
+  __syncthreads();  // the CTA's writes happen before thread 0's release (cumulative)
   if (threadIdx.x == 0) {
     cuda::atomic_ref<uint32_t, cuda::thread_scope_device> cnt(bar[0]), gen(bar[1]);
     const uint32_t g = gen.load(cuda::memory_order_acquire);
@@ -496,7 +495,7 @@ __device__ bool grid_sync(uint32_t* bar, uint32_t nblocks, int32_t* err) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        if (it > 256) __nanosleep(64);  // poll tightly at first, then back off
       }
     }
     s_ok = ok;
@@ -705,7 +704,24 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
   uint32_t* s_keys = reinterpret_cast<uint32_t*>(build_sm);
   const int wlen = min(n, kKeyWindow);
   const int wlo = min(max(c0 + kBuildTile / 2 - kKeyWindow / 2, 0), n - wlen);
-  for (int j = t; j < wlen; j += kBuildTile) s_keys[j] = __ldcg(&keys[wlo + j]);
+  {
+    // window copy with every load in flight before the stores (a plain loop
+    // would wait out one L2 round trip per element it moves)
+    constexpr int kU = 8;
+    for (int base = 0; base < wlen; base += kU * kBuildTile) {
+      uint32_t tmp[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int j = base + u * kBuildTile + t;
+        tmp[u] = j < wlen ? __ldcg(&keys[wlo + j]) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int j = base + u * kBuildTile + t;
+        if (j < wlen) s_keys[j] = tmp[u];
+      }
+    }
+  }
   s_par_leaf[t] = -1;
   s_par_node[t] = -1;
   s_arr[t] = 0u;
