@@ -801,6 +801,78 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
   if (t == 0) *B.done = 0u;
 }
 
+// ---- 4-wide collapse ---------------------------------------------------------
+
+__device__ inline float half_area(const Box& b) {
+  const float dx = b.hi.x - b.lo.x, dy = b.hi.y - b.lo.y, dz = b.hi.z - b.lo.z;
+  return dx * dy + dy * dz + dz * dx;
+}
+__device__ inline void node_children(const Node* nodes, int i, Box& l, Box& r, int& cl, int& cr) {
+  const float4 a = __ldg(&nodes[i].lxy), b = __ldg(&nodes[i].rxy), z = __ldg(&nodes[i].lrz);
+  const int4 ch = __ldg(&nodes[i].child);
+  l.lo = f3(a.x, a.z, z.x);
+  l.hi = f3(a.y, a.w, z.y);
+  r.lo = f3(b.x, b.z, z.z);
+  r.hi = f3(b.y, b.w, z.w);
+  cl = ch.x;
+  cr = ch.y;
+}
+
+// Entry i of the 4-wide tree: binary node i's grandchildren, then greedy
+// expansion of the largest internal slot while fewer than four slots are used.
+__global__ void k_collapse4(const Node* __restrict__ nodes, int n, Node4* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  Box bx[4];
+  int id[4];
+  int cnt = 0;
+  {
+    Box l, r;
+    int cl, cr;
+    node_children(nodes, i, l, r, cl, cr);
+    bx[0] = l;
+    id[0] = cl;
+    bx[1] = r;
+    id[1] = cr;
+    cnt = 2;
+  }
+  for (int it = 0; it < 3 && cnt < 4; ++it) {
+    int best = -1;
+    float area = -1.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < cnt && id[k] >= 0 && half_area(bx[k]) > area) {
+        area = half_area(bx[k]);
+        best = k;
+      }
+    if (best < 0) break;
+    Box l, r;
+    int cl, cr;
+    node_children(nodes, id[best], l, r, cl, cr);
+    bx[best] = l;
+    id[best] = cl;
+    bx[cnt] = r;  // cnt < 4
+    id[cnt] = cr;
+    ++cnt;
+  }
+  Node4 o;
+  float* f = reinterpret_cast<float*>(&o);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool used = k < cnt;
+    f[0 * 4 + k] = used ? bx[k].lo.x : 0.f;
+    f[1 * 4 + k] = used ? bx[k].hi.x : 0.f;
+    f[2 * 4 + k] = used ? bx[k].lo.y : 0.f;
+    f[3 * 4 + k] = used ? bx[k].hi.y : 0.f;
+    f[4 * 4 + k] = used ? bx[k].lo.z : 0.f;
+    f[5 * 4 + k] = used ? bx[k].hi.z : 0.f;
+  }
+  o.child = make_int4(cnt > 0 ? id[0] : kEmpty, cnt > 1 ? id[1] : kEmpty, cnt > 2 ? id[2] : kEmpty,
+                      cnt > 3 ? id[3] : kEmpty);
+  o.pad = make_int4(cnt, 0, 0, 0);
+  out[i] = o;
+}
+
 inline int blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 size_t layout(sbr_scene* s, void* mem, int32_t nt) {
@@ -809,6 +881,7 @@ size_t layout(sbr_scene* s, void* mem, int32_t nt) {
   int64_t ni = n > 1 ? n - 1 : 1;
   s->tris = c.take<float4>(3 * n);
   s->nodes = c.take<Node>(ni);
+  s->nodes4 = c.take<Node4>(ni);
   s->parent = c.take<int32_t>(2 * n);
   s->visits = c.take<uint32_t>(ni);
   s->keys[0] = c.take<uint32_t>(n);
@@ -837,6 +910,9 @@ sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
     ::sbr::note_launch();
     SBR_CUDA(cudaLaunchCooperativeKernel((const void*)k_build_scene, dim3(blocks(nt, kBuildTile)),
                                          dim3(kBuildTile), args, build_smem(nt), st));
+    ::sbr::note_launch();
+    k_collapse4<<<blocks(nt - 1, 128), 128, 0, st>>>(s->nodes, nt, s->nodes4);
+    SBR_CUDA(cudaGetLastError());
     return SBR_OK;
   }
   ::sbr::note_launch();
@@ -860,6 +936,8 @@ sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
     ::sbr::note_launch();
     k_refit<<<blocks(nt, 256), 256, 0, st>>>(s->tris, nt, s->nodes, s->parent, s->visits,
                                              s->bounds);
+    ::sbr::note_launch();
+    k_collapse4<<<blocks(nt - 1, 128), 128, 0, st>>>(s->nodes, nt, s->nodes4);
   }
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;

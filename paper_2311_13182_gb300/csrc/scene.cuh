@@ -15,12 +15,25 @@ struct __align__(16) Node {
   int4 child;   // left, right, unused, unused
 };
 
+// 4-wide node for the traversal, collapsed from the binary tree: the entry of
+// binary node i holds i's grandchildren (a leaf child stands for itself), then
+// the largest internal slot is expanded while a slot is free.  child >= 0:
+// internal binary node (its own 4-wide entry); kEmpty: unused slot; otherwise a
+// leaf ~slot.  Boxes per axis as float4 over the four slots (112 of 128 bytes).
+constexpr int kEmpty = (int)0x80000000;
+struct __align__(128) Node4 {
+  float4 lox, hix, loy, hiy, loz, hiz;
+  int4 child;
+  int4 pad;
+};
+
 }  // namespace sbr
 
 struct sbr_scene {
   int32_t nv, nt;
   float4* tris;        // [nt*3] sorted: (v0, original id bits), (v1, 0), (v2, 0)
-  sbr::Node* nodes;    // [max(nt-1, 1)]
+  sbr::Node* nodes;    // [max(nt-1, 1)] binary tree
+  sbr::Node4* nodes4;  // [max(nt-1, 1)] 4-wide entries, indexed like the binary nodes
   int32_t* parent;     // [2nt-1]: internal 0..nt-2, leaves nt-1..2nt-2
   uint32_t* visits;    // [max(nt-1,1)] refit arrival counters, or the crossing-node mask
   uint32_t* keys[2];   // [nt] Morton codes (sort ping-pong)

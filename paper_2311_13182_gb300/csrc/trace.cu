@@ -219,9 +219,25 @@ __device__ inline void slab(const float3& o, const float3& idir, float lox, floa
   tf = tf * 1.0000005f + 1e-30f;
 }
 
-// kCount: also count the nodes and triangles fetched (the roofline's bytes)
+constexpr int kStack = 192;  // 3 pending siblings per 4-wide level, 64 binary levels at most
+
+// compare-exchange of (distance, child) pairs
+__device__ inline void cswap(float& da, int& ca, float& db, int& cb) {
+  if (db < da) {
+    const float td = da;
+    da = db;
+    db = td;
+    const int tc = ca;
+    ca = cb;
+    cb = tc;
+  }
+}
+
+// Nearest hit through the 4-wide tree: children whose padded boxes the ray
+// enters before the current hit's far bound are visited nearest first.
+// kCount: also count the nodes and triangles fetched (the roofline's bytes).
 template <bool kCount>
-__device__ Best nearest(const float4* __restrict__ tris, const Node* __restrict__ nodes, int nt,
+__device__ Best nearest(const float4* __restrict__ tris, const Node4* __restrict__ nodes, int nt,
                         Ray& r, int& n_nodes, int& n_tris) {
   Best b;
   b.id = -1;
@@ -230,7 +246,7 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node* __restrict_
   b.exact = false;
   b.t = ff_of(0.f);
   if (nt <= 0) return b;
-  int stack[64];
+  int stack[kStack];
   int sp = 0;
   int node = nt > 1 ? 0 : ~0;
   // a valid tree is visited at most once per node: the cap only guards
@@ -238,24 +254,34 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node* __restrict_
   for (int guard = 2 * nt + 64; guard > 0; --guard) {
     if (node >= 0) {
       if (kCount) ++n_nodes;
-      const float4 a = __ldg(&nodes[node].lxy);
-      const float4 c = __ldg(&nodes[node].rxy);
-      const float4 z = __ldg(&nodes[node].lrz);
-      const int4 ch = __ldg(&nodes[node].child);
-      float ln, lf, rn, rf;
-      slab(r.of, r.idir, a.x, a.y, a.z, a.w, z.x, z.y, ln, lf);
-      slab(r.of, r.idir, c.x, c.y, c.z, c.w, z.z, z.w, rn, rf);
+      const Node4* q = nodes + node;
+      const float4 lx = __ldg(&q->lox), hx = __ldg(&q->hix), ly = __ldg(&q->loy), hy = __ldg(&q->hiy),
+                   lz = __ldg(&q->loz), hz = __ldg(&q->hiz);
+      const int4 ch = __ldg(&q->child);
       const float lim = b.hi;
-      const bool hl = ln <= lf && lf >= 0.f && ln <= lim;
-      const bool hr = rn <= rf && rf >= 0.f && rn <= lim;
-      if (hl && hr) {
-        const bool lfirst = ln <= rn;
-        if (sp < 64) stack[sp++] = lfirst ? ch.y : ch.x;
-        node = lfirst ? ch.x : ch.y;
+      float d0, d1, d2, d3, tf;
+      int c0 = ch.x, c1 = ch.y, c2 = ch.z, c3 = ch.w;
+      slab(r.of, r.idir, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, d0, tf);
+      d0 = (c0 != kEmpty && d0 <= tf && tf >= 0.f && d0 <= lim) ? d0 : INFINITY;
+      slab(r.of, r.idir, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, d1, tf);
+      d1 = (c1 != kEmpty && d1 <= tf && tf >= 0.f && d1 <= lim) ? d1 : INFINITY;
+      slab(r.of, r.idir, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, d2, tf);
+      d2 = (c2 != kEmpty && d2 <= tf && tf >= 0.f && d2 <= lim) ? d2 : INFINITY;
+      slab(r.of, r.idir, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, d3, tf);
+      d3 = (c3 != kEmpty && d3 <= tf && tf >= 0.f && d3 <= lim) ? d3 : INFINITY;
+      // sort the four entry distances (misses are +inf and sink to the end)
+      cswap(d0, c0, d1, c1);
+      cswap(d2, c2, d3, c3);
+      cswap(d0, c0, d2, c2);
+      cswap(d1, c1, d3, c3);
+      cswap(d1, c1, d2, c2);
+      if (d0 < INFINITY) {
+        if (d3 < INFINITY && sp < kStack) stack[sp++] = c3;
+        if (d2 < INFINITY && sp < kStack) stack[sp++] = c2;
+        if (d1 < INFINITY && sp < kStack) stack[sp++] = c1;
+        node = c0;
         continue;
       }
-      if (hl) { node = ch.x; continue; }
-      if (hr) { node = ch.y; continue; }
     } else {
       if (kCount) ++n_tris;
       test_tri(b, tris, r, ~node);
@@ -292,7 +318,7 @@ __device__ inline void bary(const Ray& r, float3 a, float3 b, float3 c, float& u
 
 template <bool kCount>
 __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float4* __restrict__ tris,
-                                               const Node* __restrict__ nodes, int nt, GridArg g,
+                                               const Node4* __restrict__ nodes, int nt, GridArg g,
                                                const int32_t* __restrict__ ray_ids, int n_rays,
                                                int K, sbr_hit* __restrict__ hits,
                                                float4* __restrict__ hit_pos,
@@ -564,11 +590,11 @@ static sbr_status trace_impl(const sbr_scene* scene, const sbr_radar_cfg* radar,
   ::sbr::note_launch();
   if (d_counts) {
     SBR_CUDA(cudaMemsetAsync(d_counts, 0, 4 * sizeof(unsigned long long), st));
-    k_trace<true><<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes, scene->nt, g, d_ray_ids, (int)R,
+    k_trace<true><<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, d_ray_ids, (int)R,
                                                   max_bounces, paths->hits, reinterpret_cast<float4*>(paths->hit_pos),
                                                   paths->ray_weight, paths->ray_first, d_counts);
   } else {
-    k_trace<false><<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes, scene->nt, g, d_ray_ids, (int)R,
+    k_trace<false><<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, d_ray_ids, (int)R,
                                                    max_bounces, paths->hits, reinterpret_cast<float4*>(paths->hit_pos),
                                                    paths->ray_weight, paths->ray_first, nullptr);
   }
