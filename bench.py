@@ -4,7 +4,7 @@
 One step = one pass of the forward hot path over the 3 Tx x 4 Rx MIMO workload:
 mesh pack + LBVH build of a 20,002-triangle scene (seeded superquadric over a
 ground plane), the trace of 1024 x 1024 rays with up to 3 specular bounces and
-FP64 path preparation, the synthesis of the [12, 128, 256] IF cube (Eq. 8),
+float-float path preparation, the synthesis of the [12, 128, 256] IF cube (Eq. 8),
 and the point cloud (range FFT, Doppler FFT, angle DFT, soft CFAR, refine).
 
 Printed (rank 0, one JSON line): traced rays/s over all ranks (device-timed,
@@ -253,7 +253,7 @@ def gpu_arm(args, rank, world, local):
     out = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_step_all, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 delays and phase reduction)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (float-float ray refine, delays and phase reduction)",
         "data": "synthetic (seeded superquadric + ground; no datasets)",
         "config": {"workload": WORKLOAD, "rays_per_step": rays, "paths_per_step": P, "points": n_points,
                    "parallelism": f"replicas x{world} (independent scenes per GPU, no collective)",
@@ -322,7 +322,7 @@ def rooflines(stage_ms, wl, P, counts, peaks, src):
     """Rooflines of the step's two large kernels; per-unit figures in the design doc.
 
     trace (sbr_trace = k_trace + scan + k_prep, timed together): bytes a launch moves
-      BVH nodes fetched x 64 B + triangles tested x 48 B (counted by sbr_trace_counts)
+      4-wide BVH nodes fetched x 112 B + triangles tested x 48 B (counted by sbr_trace_counts)
       + hit records 16 B + float-float hit data 32 B per ray-bounce slot + 8 B per ray
       + per (path, antenna) the 16-B synthesis record and 8-B path length + 4 B per path,
       against the measured HBM copy bandwidth (the working set is L2-resident, so this is
@@ -334,7 +334,7 @@ def rooflines(stage_ms, wl, P, counts, peaks, src):
     R, K = wl.grid.n_rays, wl.max_bounces
     smax = float(peaks.get("sm_max_mhz", 2070.0))
     nodes, tris, trav = counts
-    tb = nodes * 64 + tris * 48 + R * K * 48 + R * 8 + P * V * 24 + P * 4
+    tb = nodes * 112 + tris * 48 + R * K * 48 + R * 8 + P * V * 24 + P * 4
     t_ach = tb / (stage_ms["trace"] * 1e-3) / 1e9
     hbm = float(peaks["hbm_gbs"])
     trace = {"kernel": "k_trace (+ scan, k_prep)", "bound": "hbm", "achieved": t_ach, "peak": hbm, "unit": "GB/s",

@@ -104,7 +104,7 @@ typedef struct {
 } sbr_cfar_cfg;
 
 typedef enum {
-  SBR_PHASE_SPLIT = 0, /* tau in FP64, phase anchors in hi/lo FP32, FP32 rotation */
+  SBR_PHASE_SPLIT = 0, /* tau in float-float, phase anchors in hi/lo FP32, FP32 rotation */
   SBR_PHASE_FP64 = 1,  /* per-sample carrier phase f_c tau + mu tau t_n in FP64 */
   SBR_PHASE_NAIVE = 2  /* tau, f_c tau and mu tau t_n all in FP32 */
 } sbr_phase_mode;
@@ -134,8 +134,13 @@ typedef struct sbr_scene sbr_scene; /* opaque host-side handle */
 size_t sbr_scene_bytes(int32_t nt);
 
 /* Packs the mesh and builds its LBVH (Morton codes of centroids, radix sort,
- * binary radix tree, bottom-up AABB refit) in d_mem.  d_verts [nv][3] float32,
- * d_faces [nt][3] int32 stay owned by the caller and are read, not kept.
+ * binary radix tree, bottom-up AABB refit, then the 4-wide tree the traversal
+ * walks) in d_mem; up to 65,536 triangles the build is one cooperative launch
+ * (all its CTAs resident; a device that cannot host them gets the multi-kernel
+ * build, same tree).  The paper (Section 3.2.1) names no acceleration
+ * structure: this one only speeds up the nearest-hit search of Eq. 2-3.
+ * d_verts [nv][3] float32, d_faces [nt][3] int32 stay owned by the caller and
+ * are read, not kept.
  * Face indices must lie in [0, nv): out-of-range faces make the build set an
  * error word that the next sbr_scene_check() reports; d_mem must hold
  * sbr_scene_bytes(nt) bytes.  *out is a host handle released by
@@ -146,7 +151,11 @@ sbr_status sbr_scene_create(const float* d_verts, int32_t nv, const int32_t* d_f
 /* Rebuilds the scene for new vertex positions of the same topology (the
  * per-iteration update of the reconstruction loop). */
 sbr_status sbr_scene_update(sbr_scene* scene, const float* d_verts, sbr_stream stream);
-/* Synchronises the stream and reports a device-side error word set by the build. */
+/* Synchronises the stream and reports a device-side error word set by the
+ * build: bit 0 (a face index outside [0, nv)) gives SBR_ERR_INVALID_ARG; bit 1
+ * (the crossing-node bound of the tiled refit exceeded, which a radix tree
+ * cannot do) and bit 2 (a grid barrier of the cooperative build gave up after
+ * its bounded wait) give SBR_ERR_CUDA, and the scene must be recreated. */
 sbr_status sbr_scene_check(const sbr_scene* scene, sbr_stream stream);
 void sbr_scene_destroy(sbr_scene* scene);
 
@@ -180,10 +189,12 @@ sbr_status sbr_paths_bind(void* d_mem, size_t bytes, int32_t n_rays, int32_t max
 
 /* Traces the grid's rays (all G*G when n_ids < 0; otherwise the n_ids ray
  * indices in d_ray_ids, each in [0, G*G), any order, n_ids = 0 allowed) through up to max_bounces specular interactions with
- * nearest-hit Moller-Trumbore tests (FP32 with a guarded FP64 fallback that
- * makes the chosen triangle that of an FP64 brute-force search), skipping the
- * previously hit triangle; refines every hit in FP64, and writes per path and
- * virtual antenna the FP64 delay tau = (|h_1 - Tx_t| + sum |h_j - h_{j-1}| +
+ * nearest-hit Moller-Trumbore tests (FP32 with a guarded float-float fallback,
+ * about 48 significant bits, that makes the chosen triangle that of an FP64
+ * brute-force search except within rounding distance of an edge or tie),
+ * skipping the previously hit triangle; refines every hit in float-float
+ * (Section 3.2.1, Eq. 2-3), and writes per path and virtual antenna the
+ * float-float delay tau = (|h_1 - Tx_t| + sum |h_j - h_{j-1}| +
  * |Rx_r - h_k|) / c, its phase terms frac(f_c tau), frac(mu tau T / N_s) split
  * hi/lo, and the strength A = omega (-1)^(k-1) |d_k . n_k| / (4 pi L_in L_out).
  * paths must come from sbr_paths_bind with n_rays = (n_ids < 0 ? G*G : n_ids). */
@@ -191,8 +202,8 @@ sbr_status sbr_trace(const sbr_scene* scene, const sbr_radar_cfg* radar,
                      const sbr_ray_grid* grid, const int32_t* d_ray_ids, int32_t n_ids,
                      int32_t max_bounces, const sbr_paths* paths, sbr_stream stream);
 
-/* sbr_trace plus work counters for roofline accounting: d_counts[0] = BVH
- * nodes fetched (64 B each), [1] = triangles tested (48 B each), [2] = ray
+/* sbr_trace plus work counters for roofline accounting: d_counts[0] = 4-wide
+ * BVH nodes fetched (112 B each), [1] = triangles tested (48 B each), [2] = ray
  * traversals (one per bounce attempted), [3] = 0.  d_counts (device, 4 x
  * uint64) is zeroed by the call.  Same results as sbr_trace; slower (the
  * counting kernel variant), so not for timed runs. */
