@@ -3,6 +3,19 @@
 // cube[v, c, n] = sum_p A_{p,v} exp(j 2 pi (f_c tau_{p,v} + mu tau_{p,v} t_n)),
 // t_n = n T / N_s, identical for every chirp c of a static scene.
 //
+// Tensor-core kernel (N_s = 256 or 512, the default for SBR_PHASE_SPLIT): with
+// n = 16 a + b (b < 16), Eq. 8 factorises per path into U_p[a] W_p[b] with
+// U_p[a] = A e^{j 2 pi (phi0 + 16 a delta)} and W_p[b] = e^{j 2 pi b delta}, so
+// each antenna's samples are the complex matrix product sum_p U_p W_p^T, a
+// GEMM whose contraction runs over the paths.  Written as a real GEMM with
+// rows (Re, Im) x a, columns b and two contraction entries (Re, Im) per path,
+// it goes to mma.sync m16n8k16 with every operand split into two fp16 halves
+// (hi + lo, three products hi.hi + hi.lo + lo.hi: ~21-bit products) and FP32
+// accumulation; amplitudes are scaled by a power of two per staged chunk so the
+// halves stay in fp16 range (the accumulators are rescaled exactly when the
+// scale drops).  Per (path, antenna) this generates 32 phasors instead of
+// N_s = 256, and the 256 x 2 complex multiply-adds run on the tensor pipe.
+//
 // Forward kernel (persistent, one virtual antenna per CTA): the CTA's threads
 // own M consecutive samples each and together cover all N_s samples, so the
 // sum over paths accumulates in registers with no cross-thread reduction.
@@ -13,6 +26,8 @@
 // (4 FP32 multiply/FMA per sample instead of two transcendental ops).  Each CTA
 // writes its partial sums; a second kernel adds them in a fixed order, so the
 // result is bitwise reproducible.
+#include <cuda_fp16.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -114,6 +129,194 @@ __global__ void __launch_bounds__(kSplitThreads) k_synth_split(const float4* __r
   float2* out = partial + (size_t)blockIdx.x * Ns + n0;
 #pragma unroll
   for (int m = 0; m < M; ++m) out[m] = acc[m];
+}
+
+// ---- tensor-core forward kernel ---------------------------------------------
+
+// fp16 pair (x0, x1) as hi + lo halves packed in f16x2 registers (lower index low)
+__device__ inline void split_h2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// c += a b for one m16n8k16 tile (fp16 operands, FP32 accumulators)
+__device__ inline void mma_f16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+constexpr int kMmaThreads = 256;
+
+// MT m16 tiles of a per (Re | Im) block: N_s = 256 MT.  Warp lane (g = lane / 4,
+// t = lane % 4) holds, for the 8-path group of one mma k-step, paths 2t and
+// 2t + 1 (contraction columns 2t, 2t + 1 for Re and 2t + 8, 2t + 9 for Im),
+// rows a = 16 m + g and 16 m + g + 8 of U, and columns b = g, g + 8 of W.
+template <int MT>
+__global__ void __launch_bounds__(kMmaThreads) k_synth_mma(const float4* __restrict__ prep, int64_t cap,
+                                                           const int32_t* __restrict__ d_P, int V, int Q,
+                                                           float2* __restrict__ partial) {
+  constexpr int Ns = 256 * MT, NU = 2 * MT;  // U values per (thread, path): a = g + 8 i
+  constexpr int kWarps = kMmaThreads / 32;
+  // staged records and steps; at the end the warps' sums ([warp][n][Re, Im])
+  constexpr int kRed = kWarps * 2 * Ns / 4, kSbuf = kRed > 2 * kChunk ? kRed : 2 * kChunk;
+  __shared__ float4 sbuf[kSbuf];
+  __shared__ uint32_t wmax[kWarps];
+  float4* sp = sbuf;
+  float4* sst = sbuf + kChunk;  // e^{j 2 pi 8 delta}, e^{j 2 pi 128 delta}
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int v = blockIdx.x % V, q = blockIdx.x / V;
+  const int64_t P = *d_P;
+  float acc[2][MT][2][4];  // [Re | Im][m tile][n tile][fragment]
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) acc[a][m][c][d] = 0.f;
+  int s_run = 126;  // the accumulators hold the sums times 2^s_run
+  const float4* pv = prep + (size_t)v * cap;
+  const float fa = 16.f * (float)g, fg = (float)g;
+  for (int64_t c0 = (int64_t)q * kChunk; c0 < P; c0 += (int64_t)Q * kChunk) {
+    const int cnt = (int)min((int64_t)kChunk, P - c0);
+    __syncthreads();
+    uint32_t m = 0;
+    for (int j = threadIdx.x; j < kChunk; j += blockDim.x) {
+      const float4 r = j < cnt ? pv[c0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+      sp[j] = r;
+      m = max(m, __float_as_uint(fabsf(r.w)));
+      float x8 = 8.f * r.y;  // exact: delta_hi is a multiple of 2^-12
+      x8 -= rintf(x8);
+      x8 = fmaf(8.f, r.z, x8);
+      float x128 = 128.f * r.y;  // exact
+      x128 -= rintf(x128);
+      x128 = fmaf(128.f, r.z, x128);
+      x128 -= rintf(x128);
+      float s8, c8, s128, c128;
+      __sincosf(kTwoPiF * x8, &s8, &c8);
+      __sincosf(kTwoPiF * x128, &s128, &c128);
+      sst[j] = make_float4(c8, s8, c128, s128);
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0) wmax[warp] = m;
+    __syncthreads();
+    m = wmax[0];
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w) m = max(m, wmax[w]);
+    if (m == 0u) continue;  // every amplitude of the chunk is zero
+    // the chunk's largest |A| lands in [2^14, 2^15): in fp16 range with room for the lo halves
+    const int s_c = 14 - ilogbf(__uint_as_float(m));
+    if (s_c < s_run) {
+      const float f = s_run > 125 ? 1.f : ldexpf(1.f, s_c - s_run);  // exact power of two
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int mm = 0; mm < MT; ++mm)
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int d = 0; d < 4; ++d) acc[a][mm][c][d] *= f;
+      s_run = s_c;
+    }
+    const float scale = ldexpf(1.f, s_run);
+    const int groups = (cnt + 7) >> 3;
+    for (int gr = warp; gr < groups; gr += kWarps) {
+      float ur[2][NU], ui[2][NU], wr[2][2], wi[2][2];  // [path 2t + h][a index | b = g, g + 8]
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 8 * gr + 2 * t + h;  // < kChunk; zero records beyond cnt add nothing
+        const float4 r = sp[j];
+        const float4 st = sst[j];
+        float x = fa * r.y;  // exact: 16 g < 128
+        x -= rintf(x);
+        x = fmaf(fa, r.z, x) + r.x;
+        x -= rintf(x);
+        float su, cu;
+        __sincosf(kTwoPiF * x, &su, &cu);
+        const float A = r.w * scale;
+        ur[h][0] = A * cu;
+        ui[h][0] = A * su;
+#pragma unroll
+        for (int i = 1; i < NU; ++i) {  // a + 8: n + 128
+          ur[h][i] = fmaf(ur[h][i - 1], st.z, -ui[h][i - 1] * st.w);
+          ui[h][i] = fmaf(ur[h][i - 1], st.w, ui[h][i - 1] * st.z);
+        }
+        float y = fg * r.y;  // exact
+        y -= rintf(y);
+        y = fmaf(fg, r.z, y);
+        y -= rintf(y);
+        float sw, cw;
+        __sincosf(kTwoPiF * y, &sw, &cw);
+        wr[h][0] = cw;
+        wi[h][0] = sw;
+        wr[h][1] = fmaf(cw, st.x, -sw * st.y);  // b + 8
+        wi[h][1] = fmaf(cw, st.y, sw * st.x);
+      }
+      uint32_t Bh[2][2], Bl[2][2];
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        split_h2(wr[0][nt], wr[1][nt], Bh[nt][0], Bl[nt][0]);
+        split_h2(wi[0][nt], wi[1][nt], Bh[nt][1], Bl[nt][1]);
+      }
+      constexpr uint32_t kNeg = 0x80008000u;
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        uint32_t urh[2], url[2], uih[2], uil[2];
+        split_h2(ur[0][2 * mt], ur[1][2 * mt], urh[0], url[0]);
+        split_h2(ur[0][2 * mt + 1], ur[1][2 * mt + 1], urh[1], url[1]);
+        split_h2(ui[0][2 * mt], ui[1][2 * mt], uih[0], uil[0]);
+        split_h2(ui[0][2 * mt + 1], ui[1][2 * mt + 1], uih[1], uil[1]);
+        // Re rows take (Re U, -Im U) against (Re W, Im W); Im rows take (Im U, Re U)
+        const uint32_t Ah_re[4] = {urh[0], urh[1], uih[0] ^ kNeg, uih[1] ^ kNeg};
+        const uint32_t Al_re[4] = {url[0], url[1], uil[0] ^ kNeg, uil[1] ^ kNeg};
+        const uint32_t Ah_im[4] = {uih[0], uih[1], urh[0], urh[1]};
+        const uint32_t Al_im[4] = {uil[0], uil[1], url[0], url[1]};
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const uint32_t bh[2] = {Bh[nt][0], Bh[nt][1]}, bl[2] = {Bl[nt][0], Bl[nt][1]};
+          mma_f16(acc[0][mt][nt], Ah_re, bh);
+          mma_f16(acc[0][mt][nt], Ah_re, bl);
+          mma_f16(acc[0][mt][nt], Al_re, bh);
+          mma_f16(acc[1][mt][nt], Ah_im, bh);
+          mma_f16(acc[1][mt][nt], Ah_im, bl);
+          mma_f16(acc[1][mt][nt], Al_im, bh);
+        }
+      }
+    }
+  }
+  // undo the scale, then add the warps' sums in a fixed order through shared memory
+  const float unscale = s_run > 125 ? 0.f : ldexpf(1.f, -s_run);
+  __syncthreads();
+  float* red = reinterpret_cast<float*>(sbuf);  // [warp][n][Re, Im]
+#pragma unroll
+  for (int part = 0; part < 2; ++part)
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int a = 16 * mt + g + ((e & 2) ? 8 : 0);
+          const int b = 8 * nt + 2 * t + (e & 1);
+          red[warp * 2 * Ns + 2 * (16 * a + b) + part] = acc[part][mt][nt][e] * unscale;
+        }
+  __syncthreads();
+  float2* out = partial + (size_t)blockIdx.x * Ns;
+  for (int n = threadIdx.x; n < Ns; n += blockDim.x) {
+    float re = 0.f, im = 0.f;
+    for (int w = 0; w < kWarps; ++w) {
+      re += red[w * 2 * Ns + 2 * n];
+      im += red[w * 2 * Ns + 2 * n + 1];
+    }
+    out[n] = make_float2(re, im);
+  }
 }
 
 // Per-sample phase in FP64: x = f_c tau + (B / N_s) tau n, reduced mod 1.
@@ -374,7 +577,11 @@ void launch_fwd(sbr_phase_mode mode, const sbr_paths* p, const sbr_radar_cfg* r,
   const int V = p->n_virt, Ns = r->n_samples, T = Ns / M;
   const int grid = V * w.Q;
   const float4* prep = reinterpret_cast<const float4*>(p->prep);
-  if (mode == SBR_PHASE_SPLIT) {
+  if (mode == SBR_PHASE_SPLIT && (Ns == 256 || Ns == 512)) {
+    ::sbr::note_launch();
+    if (Ns == 256) k_synth_mma<1><<<grid, kMmaThreads, 0, st>>>(prep, p->path_cap, p->count, V, w.Q, w.partial);
+    else k_synth_mma<2><<<grid, kMmaThreads, 0, st>>>(prep, p->path_cap, p->count, V, w.Q, w.partial);
+  } else if (mode == SBR_PHASE_SPLIT) {
     ::sbr::note_launch();
     k_synth_split<M><<<grid, kSplitThreads, split_smem(Ns), st>>>(prep, p->path_cap, p->count, V, w.Q, Ns,
                                                                    w.partial);

@@ -78,3 +78,26 @@ def test_synthesis_adjoint_matches_oracle(sbr):
     # GPU reports dL/d(path length) = dL/dtau / c
     np.testing.assert_allclose(glen * C_LIGHT, gt, rtol=0, atol=1e-3 * np.abs(gt).max())
     np.testing.assert_allclose(gamp, ga, rtol=0, atol=1e-4 * np.abs(ga).max())
+
+
+@pytest.mark.parametrize("ns", [256, 512])
+def test_tensor_core_sample_counts(sbr, ns):
+    """The split mode at 256 and 512 samples runs the fp16x3 tensor-core factorisation of
+    Eq. 8 (n = 16 a + b); both sit at the FP32 kernels' accuracy, far inside 1e-4."""
+    wl = sphere_scene(G=64, distance=2.0, n_samples=ns)
+    ref, _, _ = oracle_cube(wl)
+    _, paths = gpu_trace(sbr, wl)
+    cube = cube_complex(sbr.synthesize(paths, wl.radar, sbr.PHASE_SPLIT))
+    e_split = rel_l2(cube, ref)
+    e_fp64 = rel_l2(cube_complex(sbr.synthesize(paths, wl.radar, sbr.PHASE_FP64)), ref)
+    assert e_split <= 1e-5 and e_fp64 <= 1e-5, (e_split, e_fp64)
+
+
+def test_no_paths_gives_zero_cube(sbr):
+    wl = sphere_scene(G=8)
+    from sbr_inputs import Workload
+    far = Workload("miss", wl.verts + np.float32([50, 0, 0]), wl.faces, wl.radar, wl.grid, 2, {})
+    _, paths = gpu_trace(sbr, far)
+    assert paths.count() == 0
+    cube = sbr.synthesize(paths, far.radar)
+    assert torch.count_nonzero(cube).item() == 0
