@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--write-traffic", metavar="NCU_CSV",
+                    help="write profiles/traffic.json from an ncu --csv log of dram__bytes_read.sum and "
+                         "dram__bytes_write.sum for the step's kernels, then exit")
     return ap.parse_args()
 
 
@@ -318,6 +321,64 @@ def e2e_arm(sbr, torch, wl, cfg, args, world):
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
 
+# DRAM traffic per launch of each roofline stage, from one ncu capture (profiles/traffic.json);
+# used only while the library sources still hash to what was captured.
+TRAFFIC_STAGES = {
+    "trace": ("k_trace", "k_tile_sums", "k_scan_single", "k_tile_scan", "k_prep"),
+    "synthesize": ("k_synth_mma", "k_reduce"),
+}
+
+
+def sources_sha1() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha1()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2311_13182_gb300", "csrc", "*.cu*")))
+    for f in files + [os.path.join(ROOT, "include", "sbr.h")]:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode() + fh.read())
+    return h.hexdigest()
+
+
+def write_traffic(csv_path: str):
+    """Per-launch DRAM bytes of each stage from an ncu CSV (the timed steps' launches)."""
+    import csv
+    with open(csv_path) as fh:
+        rows = list(csv.reader(fh))
+    head = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
+    hdr = rows[head]
+    ki, mi, vi, ui = (hdr.index("Kernel Name"), hdr.index("Metric Name"), hdr.index("Metric Value"),
+                      hdr.index("Metric Unit"))
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    per_kernel = {}
+    for r in rows[head + 1:]:
+        if len(r) <= vi or r[mi] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        name = r[ki].split("(")[0].split("::")[-1].split("<")[0].replace("void ", "").strip()
+        per_kernel.setdefault(name, []).append(float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0))
+    stages = {}
+    for st, names in TRAFFIC_STAGES.items():
+        # two metrics per launch: sum them, average over the launches of the stage's first kernel
+        n = max(1, len(per_kernel.get(names[0], [])) // 2)
+        total = sum(sum(per_kernel.get(k, [])) for k in names)
+        stages[st] = {"bytes_per_launch": total / n, "launches": n, "kernels": list(names)}
+    out = {"sources_sha1": sources_sha1(), "stages": stages,
+           "from": os.path.basename(csv_path)}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(json.dumps(out))
+
+
+def measured_traffic() -> dict:
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return {}
+    return d.get("stages", {}) if d.get("sources_sha1") == sources_sha1() else {}
+
+
 def rooflines(stage_ms, wl, P, counts, peaks, src):
     """Rooflines of the step's two large kernels; per-unit figures in the design doc.
 
@@ -327,27 +388,33 @@ def rooflines(stage_ms, wl, P, counts, peaks, src):
       + per (path, antenna) the 16-B synthesis record and 8-B path length + 4 B per path,
       against the measured HBM copy bandwidth (the working set is L2-resident, so this is
       the bytes-served rate; `traffic` is the DRAM part, from ncu).
-    synthesis (k_synth_split + k_reduce): 6 FP32 flops per (path, antenna, sample) term
-      (2 adds accumulating the phasor, 2 FMAs advancing the two-term recurrence), against
-      152 SMs x 128 FP32 lanes x 2 flops x SM max clock."""
+    synthesis (k_synth_mma + k_reduce): the per-antenna complex GEMM sum_p U_p W_p^T with
+      N_s = 256 outputs per (path, antenna): 256 complex multiply-adds = 2048 real flops,
+      issued three times (fp16 hi.hi + hi.lo + lo.hi) = 6144 tensor flops per (path, antenna),
+      against the measured dense bf16 burst rate (fp16 runs at the same nominal rate)."""
     V, Ns = wl.radar.n_virt, wl.radar.n_samples
     R, K = wl.grid.n_rays, wl.max_bounces
-    smax = float(peaks.get("sm_max_mhz", 2070.0))
+    traffic = measured_traffic()
     nodes, tris, trav = counts
     tb = nodes * 112 + tris * 48 + R * K * 48 + R * 8 + P * V * 24 + P * 4
     t_ach = tb / (stage_ms["trace"] * 1e-3) / 1e9
     hbm = float(peaks["hbm_gbs"])
     trace = {"kernel": "k_trace (+ scan, k_prep)", "bound": "hbm", "achieved": t_ach, "peak": hbm, "unit": "GB/s",
-             "frac": t_ach / hbm, "traffic": None, "bytes_per_launch": tb,
+             "frac": t_ach / hbm, "traffic": traffic.get("trace", {}).get("bytes_per_launch"),
+             "bytes_per_launch": tb,
              "units": {"rays": R, "traversals": trav, "nodes": nodes, "triangles": tris, "paths": P},
              "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({src}, burst copy)"}
     terms = P * V * Ns
-    s_ach = terms * 6 / (stage_ms["synthesize"] * 1e-3) / 1e12
-    fp32 = 152 * 128 * 2 * smax * 1e6 / 1e12
-    synth = {"kernel": "k_synth_split (+ k_reduce)", "bound": "alu", "achieved": s_ach, "peak": fp32,
-             "unit": "TFLOP/s (FP32)", "frac": s_ach / fp32, "traffic": None, "terms_per_launch": terms,
+    flops = P * V * 6144 * (Ns // 256)
+    s_ach = flops / (stage_ms["synthesize"] * 1e-3) / 1e12
+    tc = float(peaks["bf16_tflops"])
+    synth = {"kernel": "k_synth_mma (+ k_reduce)", "bound": "tensor", "achieved": s_ach, "peak": tc,
+             "unit": "TFLOP/s (fp16 tensor)", "frac": s_ach / tc,
+             "traffic": traffic.get("synthesize", {}).get("bytes_per_launch"), "terms_per_launch": terms,
              "terms_per_s": terms / (stage_ms["synthesize"] * 1e-3),
-             "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {smax:.0f} MHz (SM max clock of MEASURED_PEAKS.json)"}
+             "note": "legacy mma.sync path (measured ceiling ~600 TFLOP/s for m16n8k16); operand generation "
+                     "on the FP32/MUFU pipes is the limiter",
+             "peak_source": f"bf16_tflops of MEASURED_PEAKS.json ({src}, burst; fp16 nominal ratio 1)"}
     dom = trace if stage_ms["trace"] >= stage_ms["synthesize"] else synth
     return dom, [trace, synth]
 
@@ -495,6 +562,9 @@ def reference_arm(args, rank, world):
 
 def main():
     args = parse()
+    if args.write_traffic:
+        write_traffic(args.write_traffic)
+        return
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         out = reference_arm(args, rank, world)
