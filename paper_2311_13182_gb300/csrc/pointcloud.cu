@@ -19,7 +19,9 @@
 // adjoint of a forward DFT).
 #include <math.h>
 
-#include "common.cuh"
+#include <atomic>
+
+#include "cta_sort.cuh"
 
 namespace sbr {
 namespace {
@@ -152,38 +154,28 @@ __global__ void __launch_bounds__(256) k_angle_power(const float2* __restrict__ 
   for (int i = 0; i < APT; ++i) part[((size_t)g * A + ag * APT + i) * Ns + k0 + kk] = acc[i];
 }
 
-__global__ void k_power_reduce(const float* __restrict__ part, int groups, int cells,
-                               float* __restrict__ Pw) {
+// Pw = fixed-order sum of the Doppler-group partials; also the argmax of Pw as
+// the largest key (Pw bits << 32 | ~cell): the lowest cell among equal maxima.
+// amax_key must be 0 on entry.
+__global__ void k_power_reduce(const float* __restrict__ part, int groups, int cells, float* __restrict__ Pw,
+                               unsigned long long* __restrict__ amax_key) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= cells) return;
-  float s = 0.f;
-  for (int g = 0; g < groups; ++g) s += part[(size_t)g * cells + i];
-  Pw[i] = s;
-}
-
-// argmax of Pw (lowest index among equal maxima) with one CTA.
-__global__ void k_argmax(const float* __restrict__ Pw, int cells, int32_t* __restrict__ out) {
-  __shared__ unsigned long long red[32];
-  unsigned long long best = 0ull;
-  for (int i = threadIdx.x; i < cells; i += blockDim.x) {
-    const unsigned long long key =
-        ((unsigned long long)__float_as_uint(fmaxf(Pw[i], 0.f)) << 32) | (0xffffffffu - (unsigned)i);
-    best = key > best ? key : best;
+  unsigned long long key = 0ull;
+  if (i < cells) {
+    float s = 0.f;
+    for (int g = 0; g < groups; ++g) s += part[(size_t)g * cells + i];
+    Pw[i] = s;
+    key = ((unsigned long long)__float_as_uint(fmaxf(s, 0.f)) << 32) | (0xffffffffu - (unsigned)i);
   }
   for (int o = 16; o; o >>= 1) {
-    const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
-    best = y > best ? y : best;
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
+    key = y > key ? y : key;
   }
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    best = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ull;
-    for (int o = 16; o; o >>= 1) {
-      const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
-      best = y > best ? y : best;
-    }
-    if (threadIdx.x == 0) *out = (int32_t)(0xffffffffu - (unsigned)(best & 0xffffffffull));
-  }
+  if ((threadIdx.x & 31) == 0 && key) atomicMax(amax_key, key);
+}
+
+__device__ inline int amax_cell(const unsigned long long* key) {
+  return (int)(0xffffffffu - (unsigned)(*key & 0xffffffffull));
 }
 
 struct CfarArg {
@@ -221,13 +213,12 @@ __device__ inline float soft_w(const float* __restrict__ Pw, const CfarArg& c, i
   return 1.f / (1.f + expf(-z));
 }
 
-__global__ void k_detect(const float* __restrict__ Pw, CfarArg c, const int32_t* __restrict__ amax,
-                         int32_t* __restrict__ flag, uint32_t* __restrict__ key) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= c.A * c.Ns) return;
+// Detection test of cell i: a 3x3 local maximum above the floor (equal values:
+// the lower cell wins) whose soft CFAR weight reaches w_min; returns the sort key
+// (w descending), or 0xffffffff.
+__device__ inline uint32_t detect_key(const float* __restrict__ Pw, const CfarArg& c, int i, float floor_v) {
   const int a = i / c.Ns, k = i - a * c.Ns;
   const float p = Pw[i];
-  const float floor_v = c.floor_rel * Pw[*amax];
   bool peak = p > floor_v;
   for (int da = -1; da <= 1 && peak; ++da)
     for (int dk = -1; dk <= 1; ++dk) {
@@ -241,14 +232,21 @@ __global__ void k_detect(const float* __restrict__ Pw, CfarArg c, const int32_t*
         break;
       }
     }
-  float w = 0.f;
-  if (peak) {
-    int cnt;
-    w = soft_w(Pw, c, a, k, floor_v, nullptr, nullptr, &cnt);
-  }
-  const bool keep = peak && w >= c.w_min;
-  flag[i] = keep ? 1 : 0;
-  key[i] = keep ? 0xffffffffu - __float_as_uint(w) : 0xffffffffu;
+  if (!peak) return 0xffffffffu;
+  int cnt;
+  const float w = soft_w(Pw, c, a, k, floor_v, nullptr, nullptr, &cnt);
+  return w >= c.w_min ? 0xffffffffu - __float_as_uint(w) : 0xffffffffu;
+}
+
+__global__ void k_detect(const float* __restrict__ Pw, CfarArg c, const unsigned long long* __restrict__ amax_key,
+                         int32_t* __restrict__ amax, int32_t* __restrict__ flag, uint32_t* __restrict__ key) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int am = amax_cell(amax_key);
+  if (i == 0) *amax = am;
+  if (i >= c.A * c.Ns) return;
+  const uint32_t kk = detect_key(Pw, c, i, c.floor_rel * Pw[am]);
+  flag[i] = kk != 0xffffffffu ? 1 : 0;
+  key[i] = kk;
 }
 
 __global__ void k_compact(const int32_t* __restrict__ flag, const int32_t* __restrict__ off,
@@ -258,6 +256,33 @@ __global__ void k_compact(const int32_t* __restrict__ flag, const int32_t* __res
   if (i >= cells || !flag[i]) return;
   ko[off[i]] = key[i];
   vo[off[i]] = i;
+}
+
+// exclusive scan of one value per thread over a CTA of whole warps
+__device__ inline uint32_t block_exclusive_sel(uint32_t v, uint32_t* total, uint32_t* warp_tot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t q = lane < nw ? warp_tot[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, q, o);
+      if (lane >= o) q += y;
+    }
+    if (lane < nw) warp_tot[lane] = q;
+  }
+  __syncthreads();
+  const uint32_t r = (w ? warp_tot[w - 1] : 0u) + x - v;
+  *total = warp_tot[nw - 1];
+  __syncthreads();
+  return r;
 }
 
 __device__ inline float refine(float lm, float l0, float lp, float* dm, float* d0, float* dp) {
@@ -280,6 +305,24 @@ struct PointArg {
   float range_bin;  // c / (2B)
 };
 
+// Point i of the cloud from detected cell `cell`: parabolic refine of ln Pw per
+// axis, then (r u, 0, r sqrt(1 - u^2)) with its soft weight.
+__device__ inline float4 emit_point(const float* __restrict__ Pw, const PointArg& pa, float floor_v, int cell) {
+  const CfarArg& c = pa.c;
+  const int a = cell / c.Ns, k = cell - a * c.Ns;
+  int cnt;
+  const float w = soft_w(Pw, c, a, k, floor_v, nullptr, nullptr, &cnt);
+  const float* row = Pw + (size_t)a * c.Ns;
+  const float l0 = lnp(row[k]);
+  float t0, t1, t2, dk = 0.f, da = 0.f;
+  if (k > 0 && k < c.Ns - 1) dk = refine(lnp(row[k - 1]), l0, lnp(row[k + 1]), &t0, &t1, &t2);
+  if (a > 0 && a < c.A - 1)
+    da = refine(lnp(Pw[(size_t)(a - 1) * c.Ns + k]), l0, lnp(Pw[(size_t)(a + 1) * c.Ns + k]), &t0, &t1, &t2);
+  const float r = ((float)k + dk) * pa.range_bin;
+  const float u = fminf(fmaxf(-1.f + 2.f * ((float)a + da) / (float)c.A, -1.f), 1.f);
+  return make_float4(r * u, 0.f, r * sqrtf(fmaxf(1.f - u * u, 0.f)), w);
+}
+
 __global__ void k_points(const float* __restrict__ Pw, PointArg pa, const int32_t* __restrict__ amax,
                          const int32_t* __restrict__ cand, const int32_t* __restrict__ n_cand,
                          float4* __restrict__ pts, int32_t* __restrict__ cell_out,
@@ -293,22 +336,63 @@ __global__ void k_points(const float* __restrict__ Pw, PointArg pa, const int32_
     cell_out[i] = -1;
     return;
   }
-  const CfarArg& c = pa.c;
   const int cell = cand[i];
-  const int a = cell / c.Ns, k = cell - a * c.Ns;
-  const float floor_v = c.floor_rel * Pw[*amax];
-  int cnt;
-  const float w = soft_w(Pw, c, a, k, floor_v, nullptr, nullptr, &cnt);
-  const float* row = Pw + (size_t)a * c.Ns;
-  const float l0 = lnp(row[k]);
-  float t0, t1, t2, dk = 0.f, da = 0.f;
-  if (k > 0 && k < c.Ns - 1) dk = refine(lnp(row[k - 1]), l0, lnp(row[k + 1]), &t0, &t1, &t2);
-  if (a > 0 && a < c.A - 1)
-    da = refine(lnp(Pw[(size_t)(a - 1) * c.Ns + k]), l0, lnp(Pw[(size_t)(a + 1) * c.Ns + k]), &t0, &t1, &t2);
-  const float r = ((float)k + dk) * pa.range_bin;
-  const float u = fminf(fmaxf(-1.f + 2.f * ((float)a + da) / (float)c.A, -1.f), 1.f);
-  pts[i] = make_float4(r * u, 0.f, r * sqrtf(fmaxf(1.f - u * u, 0.f)), w);
+  pts[i] = emit_point(Pw, pa, pa.c.floor_rel * Pw[*amax], cell);
   cell_out[i] = cell;
+}
+
+// Steps 5-9 in one CTA when the map has at most kSortOneCta cells:
+// detection and compaction in cell order (each thread owns a run of
+// consecutive cells; one block scan places them), the stable sort by weight,
+// and the points.  Same results as k_detect, scan, k_compact, the sort and
+// k_points, in one launch instead of five.
+constexpr int kSelThreads = 1024;
+__global__ void __launch_bounds__(kSelThreads) k_select(const float* __restrict__ Pw, PointArg pa,
+                                                        const unsigned long long* __restrict__ amax_key,
+                                                        int32_t* __restrict__ amax, uint32_t* __restrict__ key,
+                                                        uint32_t* k0, int32_t* v0, uint32_t* k1, int32_t* v1,
+                                                        float4* __restrict__ pts, int32_t* __restrict__ cell_out,
+                                                        int32_t* __restrict__ n_out) {
+  extern __shared__ __align__(16) uint32_t sel_sm[];  // cta::kSortSmemWords
+  __shared__ uint32_t wt[32];
+  const CfarArg& c = pa.c;
+  const int cells = c.A * c.Ns, t = threadIdx.x;
+  const int am = amax_cell(amax_key);
+  if (t == 0) *amax = am;
+  const float floor_v = c.floor_rel * Pw[am];
+  const int per = (cells + kSelThreads - 1) / kSelThreads;
+  const int c0 = t * per, c1 = min(c0 + per, cells);
+  uint32_t mine = 0;
+  for (int i = c0; i < c1; ++i) {
+    const uint32_t kk = detect_key(Pw, c, i, floor_v);
+    key[i] = kk;
+    mine += kk != 0xffffffffu;
+  }
+  uint32_t total;
+  uint32_t pos = block_exclusive_sel(mine, &total, wt);
+  for (int i = c0; i < c1; ++i) {  // own writes: visible to this thread
+    const uint32_t kk = key[i];
+    if (kk != 0xffffffffu) {
+      k0[pos] = kk;
+      v0[pos] = i;
+      ++pos;
+    }
+  }
+  __syncthreads();  // the compacted candidates are visible to the whole CTA
+  cta::sort_pairs(k0, v0, k1, v1, (int64_t)total, 32, nullptr, sel_sm);
+  __syncthreads();
+  const int n = min((int)total, pa.k_max);
+  if (t == 0) *n_out = n;
+  for (int i = t; i < pa.k_max; i += kSelThreads) {
+    if (i >= n) {
+      pts[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      cell_out[i] = -1;
+    } else {
+      const int cell = v0[i];
+      pts[i] = emit_point(Pw, pa, floor_v, cell);
+      cell_out[i] = cell;
+    }
+  }
 }
 
 // ---- adjoint ----------------------------------------------------------------
@@ -429,6 +513,7 @@ struct Layout {
   int32_t* peak_cell;
   int32_t* n_points;
   int32_t* argmax;
+  unsigned long long* amax_key;
   float* part;
   int32_t* flag;
   int32_t* off;
@@ -443,6 +528,18 @@ struct Layout {
 
 inline int dgroups(int C) { return C >= 8 ? C / 8 : 1; }
 
+// k_select's shared memory exceeds the 48 KB default: raise the limit once per device.
+cudaError_t select_attr() {
+  static std::atomic<uint64_t> done{0};  // bit per device ordinal below 64
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && ((done.load() >> dev) & 1u)) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cta::kSortSmemBytes);
+  if (e == cudaSuccess && dev < 64) done.fetch_or(1ull << dev);
+  return e;
+}
+
 size_t pc_layout(Layout* L, void* mem, const sbr_radar_cfg* r, const sbr_cfar_cfg* f) {
   Carver c(mem);
   const int V = r->n_tx * r->n_rx, C = r->n_chirps, Ns = r->n_samples, A = f->n_theta;
@@ -453,6 +550,7 @@ size_t pc_layout(Layout* L, void* mem, const sbr_radar_cfg* r, const sbr_cfar_cf
   L->peak_cell = c.take<int32_t>(f->k_max > 0 ? f->k_max : 1);
   L->n_points = c.take<int32_t>(1);
   L->argmax = c.take<int32_t>(1);
+  L->amax_key = c.take<unsigned long long>(1);
   L->part = c.take<float>((size_t)L->groups * cells);
   L->flag = c.take<int32_t>(cells);
   L->off = c.take<int32_t>(cells + 1);
@@ -611,20 +709,29 @@ extern "C" sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* r
     default: set_error("sbr_pointcloud: n_theta=%d unsupported", A); return SBR_ERR_UNSUPPORTED;
   }
   SBR_CUDA(cudaGetLastError());
+  SBR_CUDA(cudaMemsetAsync(L.amax_key, 0, sizeof(unsigned long long), st));
   ::sbr::note_launch();
-  k_power_reduce<<<(cells + 255) / 256, 256, 0, st>>>(L.part, L.groups, cells, L.power);
-  ::sbr::note_launch();
-  k_argmax<<<1, 1024, 0, st>>>(L.power, cells, L.argmax);
-  // 5-7: soft CFAR, peaks, compaction in cell order, stable sort by weight
+  k_power_reduce<<<(cells + 255) / 256, 256, 0, st>>>(L.part, L.groups, cells, L.power, L.amax_key);
+  // 5-9: soft CFAR, peaks, compaction in cell order, stable sort by weight, points
   CfarArg ca{A, Ns, cfar->guard, cfar->train, cfar->alpha, cfar->floor_rel, cfar->beta, cfar->w_min};
+  PointArg pa{ca, cfar->k_max, (float)(kC / (2.0 * radar->bandwidth))};
+  if (cells <= kSortOneCta) {
+    SBR_CUDA(select_attr());
+    ::sbr::note_launch();
+    k_select<<<1, kSelThreads, cta::kSortSmemBytes, st>>>(L.power, pa, L.amax_key, L.argmax, L.key, L.skeys[0],
+                                                           L.svals[0], L.skeys[1], L.svals[1],
+                                                           reinterpret_cast<float4*>(d_points), L.peak_cell,
+                                                           L.n_points);
+    SBR_CUDA(cudaGetLastError());
+    return SBR_OK;
+  }
   ::sbr::note_launch();
-  k_detect<<<(cells + 255) / 256, 256, 0, st>>>(L.power, ca, L.argmax, L.flag, L.key);
+  k_detect<<<(cells + 255) / 256, 256, 0, st>>>(L.power, ca, L.amax_key, L.argmax, L.flag, L.key);
   SBR_CUDA(exclusive_scan(L.flag, L.off, cells, nullptr, L.scan_scr, st));
   ::sbr::note_launch();
   k_compact<<<(cells + 255) / 256, 256, 0, st>>>(L.flag, L.off, L.key, cells, L.skeys[0], L.svals[0]);
   SBR_CUDA(radix_sort_pairs(L.skeys, L.svals, cells, L.off + cells, 32, L.sort_scr, st));
   // 8-9: refine and emit points
-  PointArg pa{ca, cfar->k_max, (float)(kC / (2.0 * radar->bandwidth))};
   ::sbr::note_launch();
   k_points<<<(cfar->k_max + 255) / 256, 256, 0, st>>>(L.power, pa, L.argmax, L.svals[0], L.off + cells,
                                                        reinterpret_cast<float4*>(d_points), L.peak_cell,
