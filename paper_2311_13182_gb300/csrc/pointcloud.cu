@@ -245,7 +245,7 @@ __global__ void k_detect(const float* __restrict__ Pw, CfarArg c, const unsigned
   if (i == 0) *amax = am;
   if (i >= c.A * c.Ns) return;
   const uint32_t kk = detect_key(Pw, c, i, c.floor_rel * Pw[am]);
-  flag[i] = kk != 0xffffffffu ? 1 : 0;
+  if (flag) flag[i] = kk != 0xffffffffu ? 1 : 0;
   key[i] = kk;
 }
 
@@ -341,15 +341,14 @@ __global__ void k_points(const float* __restrict__ Pw, PointArg pa, const int32_
   cell_out[i] = cell;
 }
 
-// Steps 5-9 in one CTA when the map has at most kSortOneCta cells:
-// detection and compaction in cell order (each thread owns a run of
-// consecutive cells; one block scan places them), the stable sort by weight,
-// and the points.  Same results as k_detect, scan, k_compact, the sort and
-// k_points, in one launch instead of five.
+// Steps 7-9 in one CTA when the map has at most kSortOneCta cells: compaction
+// of k_detect's keys in cell order (each thread owns a run of consecutive cells;
+// one block scan places them), the stable sort by weight, and the points.  Same
+// results as scan, k_compact, the sort and k_points, in one launch instead of four.
 constexpr int kSelThreads = 1024;
 __global__ void __launch_bounds__(kSelThreads) k_select(const float* __restrict__ Pw, PointArg pa,
                                                         const unsigned long long* __restrict__ amax_key,
-                                                        int32_t* __restrict__ amax, uint32_t* __restrict__ key,
+                                                        const uint32_t* __restrict__ key,
                                                         uint32_t* k0, int32_t* v0, uint32_t* k1, int32_t* v1,
                                                         float4* __restrict__ pts, int32_t* __restrict__ cell_out,
                                                         int32_t* __restrict__ n_out) {
@@ -357,20 +356,14 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const float* __restrict_
   __shared__ uint32_t wt[32];
   const CfarArg& c = pa.c;
   const int cells = c.A * c.Ns, t = threadIdx.x;
-  const int am = amax_cell(amax_key);
-  if (t == 0) *amax = am;
-  const float floor_v = c.floor_rel * Pw[am];
+  const float floor_v = c.floor_rel * Pw[amax_cell(amax_key)];
   const int per = (cells + kSelThreads - 1) / kSelThreads;
   const int c0 = t * per, c1 = min(c0 + per, cells);
   uint32_t mine = 0;
-  for (int i = c0; i < c1; ++i) {
-    const uint32_t kk = detect_key(Pw, c, i, floor_v);
-    key[i] = kk;
-    mine += kk != 0xffffffffu;
-  }
+  for (int i = c0; i < c1; ++i) mine += key[i] != 0xffffffffu;
   uint32_t total;
   uint32_t pos = block_exclusive_sel(mine, &total, wt);
-  for (int i = c0; i < c1; ++i) {  // own writes: visible to this thread
+  for (int i = c0; i < c1; ++i) {
     const uint32_t kk = key[i];
     if (kk != 0xffffffffu) {
       k0[pos] = kk;
@@ -718,7 +711,9 @@ extern "C" sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* r
   if (cells <= kSortOneCta) {
     SBR_CUDA(select_attr());
     ::sbr::note_launch();
-    k_select<<<1, kSelThreads, cta::kSortSmemBytes, st>>>(L.power, pa, L.amax_key, L.argmax, L.key, L.skeys[0],
+    k_detect<<<(cells + 255) / 256, 256, 0, st>>>(L.power, ca, L.amax_key, L.argmax, nullptr, L.key);
+    ::sbr::note_launch();
+    k_select<<<1, kSelThreads, cta::kSortSmemBytes, st>>>(L.power, pa, L.amax_key, L.key, L.skeys[0],
                                                            L.svals[0], L.skeys[1], L.svals[1],
                                                            reinterpret_cast<float4*>(d_points), L.peak_cell,
                                                            L.n_points);
