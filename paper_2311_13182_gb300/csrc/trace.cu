@@ -233,12 +233,74 @@ __device__ inline void cswap(float& da, int& ca, float& db, int& cb) {
   }
 }
 
+__device__ inline ff ff3_at(const ff3& v, int j) { return j == 0 ? v.x : (j == 1 ? v.y : v.z); }
+
+// Traversals that run past kStragglerSteps entries (rays grazing a surface
+// after a bounce: hundreds of node and triangle tests) would keep their whole
+// CTA resident long after the other lanes finished, and decide the launch's
+// length.  Such a ray is handed over, with everything needed to resume it, to
+// k_trace_coop, where the 32 lanes of a warp finish it together.
+constexpr int kStragglerSteps = 128;
+constexpr int kDumpStack = 64;
+constexpr int kDumpMax = 8192;
+struct __align__(16) RayDump {
+  int slot, rid, k, nh;
+  int skip, has_ff, node, sp;
+  float o[6], d[6];  // float-float origin and direction: (hi, lo) per axis
+  int bid, bslot, bexact, pad;
+  float blo, bhi, bt_hi, bt_lo;
+  int stack[kDumpStack];
+};
+
+// Where a lane hands its ray over, and the ray's output slot and bounce.
+struct DumpCtx {
+  RayDump* dumps;
+  unsigned int* n;
+  int slot, k, nh;
+};
+
+constexpr int kHanded = -2;  // Best::id of a ray handed over
+
+// Records a straggler's state; false when the hand-over area is full (the
+// lane then finishes the ray itself).  Out of line: it runs for few rays.
+__device__ __noinline__ bool hand_over(DumpCtx dc, ff3 o, ff3 d, int rid, int skip, bool has_ff, Best b, int node,
+                                       const int* stack, int sp) {
+  const unsigned di = atomicAdd(dc.n, 1u);
+  if (di >= (unsigned)kDumpMax) return false;
+  RayDump& D = dc.dumps[di];
+  D.slot = dc.slot;
+  D.rid = rid;
+  D.k = dc.k;
+  D.nh = dc.nh;
+  D.skip = skip;
+  D.has_ff = has_ff;
+  D.node = node;
+  D.sp = sp;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const ff oj = ff3_at(o, j), dj = ff3_at(d, j);
+    D.o[2 * j] = oj.hi;
+    D.o[2 * j + 1] = oj.lo;
+    D.d[2 * j] = has_ff ? dj.hi : 0.f;
+    D.d[2 * j + 1] = has_ff ? dj.lo : 0.f;
+  }
+  D.bid = b.id;
+  D.bslot = b.slot;
+  D.bexact = b.exact;
+  D.blo = b.lo;
+  D.bhi = b.hi;
+  D.bt_hi = b.t.hi;
+  D.bt_lo = b.t.lo;
+  for (int j = 0; j < sp; ++j) D.stack[j] = stack[j];
+  return true;
+}
+
 // Nearest hit through the 4-wide tree: children whose padded boxes the ray
 // enters before the current hit's far bound are visited nearest first.
 // kCount: also count the nodes and triangles fetched (the roofline's bytes).
 template <bool kCount>
 __device__ Best nearest(const float4* __restrict__ tris, const Node4* __restrict__ nodes, int nt,
-                        Ray& r, int& n_nodes, int& n_tris) {
+                        Ray& r, int& n_nodes, int& n_tris, const DumpCtx* dc) {
   Best b;
   b.id = -1;
   b.slot = -1;
@@ -251,7 +313,13 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node4* __restrict
   int node = nt > 1 ? 0 : ~0;
   // a valid tree is visited at most once per node: the cap only guards
   // against a corrupted hierarchy turning into an endless loop
+  const int hand_at = 2 * nt + 64 - kStragglerSteps;  // the guard's value after kStragglerSteps entries
   for (int guard = 2 * nt + 64; guard > 0; --guard) {
+    if (guard == hand_at && dc && sp <= kDumpStack &&
+        hand_over(*dc, r.o, r.d, r.rid, r.skip, r.has_ff, b, node, stack, sp)) {
+      b.id = kHanded;
+      return b;
+    }
     if (node >= 0) {
       if (kCount) ++n_nodes;
       const Node4* q = nodes + node;
@@ -292,6 +360,65 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node4* __restrict
   return b;
 }
 
+__device__ inline void init_best(Best& b) {
+  b.id = -1;
+  b.slot = -1;
+  b.lo = b.hi = INFINITY;
+  b.exact = false;
+  b.t = ff_of(0.f);
+}
+
+// Resumable traversal for k_trace_coop: the next entry (>= 0 internal node,
+// < 0 leaf ~slot) and the pending ones on `stack`.  Processes at most `budget`
+// entries and returns true once the traversal is complete.  ext_lim: a far
+// bound another lane holds for the same ray (pruning only).
+template <bool kCount>
+__device__ bool traverse(const float4* __restrict__ tris, const Node4* __restrict__ nodes, int nt, Ray& r,
+                         Best& b, int* stack, int& sp, int& node, int& steps, int budget, float ext_lim,
+                         int& n_nodes, int& n_tris) {
+  if (nt <= 0) return true;
+  const int guard = 2 * nt + 64;  // a valid tree is visited at most once per node
+  for (; budget > 0; --budget) {
+    if (++steps > guard) return true;
+    if (node >= 0) {
+      if (kCount) ++n_nodes;
+      const Node4* q = nodes + node;
+      const float4 lx = __ldg(&q->lox), hx = __ldg(&q->hix), ly = __ldg(&q->loy), hy = __ldg(&q->hiy),
+                   lz = __ldg(&q->loz), hz = __ldg(&q->hiz);
+      const int4 ch = __ldg(&q->child);
+      const float lim = fminf(b.hi, ext_lim);
+      float d0, d1, d2, d3, tf;
+      int c0 = ch.x, c1 = ch.y, c2 = ch.z, c3 = ch.w;
+      slab(r.of, r.idir, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, d0, tf);
+      d0 = (c0 != kEmpty && d0 <= tf && tf >= 0.f && d0 <= lim) ? d0 : INFINITY;
+      slab(r.of, r.idir, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, d1, tf);
+      d1 = (c1 != kEmpty && d1 <= tf && tf >= 0.f && d1 <= lim) ? d1 : INFINITY;
+      slab(r.of, r.idir, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, d2, tf);
+      d2 = (c2 != kEmpty && d2 <= tf && tf >= 0.f && d2 <= lim) ? d2 : INFINITY;
+      slab(r.of, r.idir, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, d3, tf);
+      d3 = (c3 != kEmpty && d3 <= tf && tf >= 0.f && d3 <= lim) ? d3 : INFINITY;
+      cswap(d0, c0, d1, c1);
+      cswap(d2, c2, d3, c3);
+      cswap(d0, c0, d2, c2);
+      cswap(d1, c1, d3, c3);
+      cswap(d1, c1, d2, c2);
+      if (d0 < INFINITY) {
+        if (d3 < INFINITY && sp < kStack) stack[sp++] = c3;
+        if (d2 < INFINITY && sp < kStack) stack[sp++] = c2;
+        if (d1 < INFINITY && sp < kStack) stack[sp++] = c1;
+        node = c0;
+        continue;
+      }
+    } else {
+      if (kCount) ++n_tris;
+      test_tri(b, tris, r, ~node);
+    }
+    if (sp == 0) return true;
+    node = stack[--sp];
+  }
+  return false;
+}
+
 __device__ inline void set_idir(Ray& r) {
   auto inv = [](float x) { return 1.0f / (fabsf(x) < 1e-20f ? copysignf(1e-20f, x) : x); };
   r.idir = f3(inv(r.df.x), inv(r.df.y), inv(r.df.z));
@@ -316,6 +443,45 @@ __device__ inline void bary(const Ray& r, float3 a, float3 b, float3 c, float& u
 #define SBR_TRACE_MIN_BLOCKS 6  // resident 128-thread CTAs per SM the register budget targets
 #endif
 
+// Records k..K-1 of a ray that found nothing at bounce k.
+__device__ inline void record_miss(sbr_hit* hits, float4* hit_pos, int slot, int k, int K) {
+  for (int kk = k; kk < K; ++kk) {
+    const size_t s2 = (size_t)slot * K + kk;
+    hits[s2] = sbr_hit{-1, 0.f, 0.f, 0.f};
+    hit_pos[2 * s2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    hit_pos[2 * s2 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// Hit record k (written when `write`) from the ray's nearest triangle, refined
+// in float-float on the plane of the exact triangle; the ray then continues
+// from the hit point along d' = d - 2 (d.N) / (N.N) N.
+__device__ inline void record_hit(const float4* __restrict__ tris, Ray& r, const Best& b, sbr_hit* hits,
+                                  float4* hit_pos, size_t sl, bool write) {
+  const float4 A = __ldg(&tris[3 * b.slot]), B = __ldg(&tris[3 * b.slot + 1]),
+               C = __ldg(&tris[3 * b.slot + 2]);
+  const float3 a = f3(A.x, A.y, A.z), bb = f3(B.x, B.y, B.z), c = f3(C.x, C.y, C.z);
+  ensure_ff(r);
+  const ff3 N = ff3_cross(ff3_diff(bb, a), ff3_diff(c, a));
+  const ff den = ff3_dot(N, r.d);
+  const ff t = ff_div(ff3_dot(N, ff3_sub(ff3_of(a), r.o)), den);
+  const ff3 h = ff3_add(r.o, ff3_scale(r.d, t));
+  const ff nn = ff3_dot(N, N);
+  if (write) {
+    const float cosv = fabsf(den.hi) * rsqrtf(nn.hi);
+    float u, v;
+    bary(r, a, bb, c, u, v);
+    hits[sl] = sbr_hit{b.id, t.hi, u, v};
+    hit_pos[2 * sl] = make_float4(h.x.hi, h.x.lo, h.y.hi, h.y.lo);
+    hit_pos[2 * sl + 1] = make_float4(h.z.hi, h.z.lo, cosv, 0.f);
+  }
+  const ff f = ff_div(ff_mulf(den, 2.f), nn);
+  r.d = ff3_sub(r.d, ff3_scale(N, f));
+  r.o = h;
+  r.skip = b.id;
+  set_f32(r);
+}
+
 template <bool kCount>
 __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float4* __restrict__ tris,
                                                const Node4* __restrict__ nodes, int nt, GridArg g,
@@ -324,6 +490,7 @@ __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float
                                                float4* __restrict__ hit_pos,
                                                float* __restrict__ ray_w,
                                                int32_t* __restrict__ nvalid,
+                                               RayDump* __restrict__ dumps, unsigned int* __restrict__ n_dumps,
                                                unsigned long long* __restrict__ counts) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   int n_nodes = 0, n_tris = 0, n_trav = 0;
@@ -348,10 +515,16 @@ __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float
   set_idir(r);
   ray_w[i] = omega;
   int nh = 0;
+  bool handed = false;
   for (int k = 0; k < K; ++k) {
     const size_t sl = (size_t)i * K + k;
     if (kCount) ++n_trav;
-    Best b = nearest<kCount>(tris, nodes, nt, r, n_nodes, n_tris);
+    const DumpCtx dc{dumps, n_dumps, i, k, nh};
+    Best b = nearest<kCount>(tris, nodes, nt, r, n_nodes, n_tris, &dc);
+    if (b.id == kHanded) {  // k_trace_coop writes the rest of this ray
+      handed = true;
+      break;
+    }
     if (b.id < 0) {
       for (int kk = k; kk < K; ++kk) {
         const size_t s2 = (size_t)i * K + kk;
@@ -385,7 +558,7 @@ __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float
     set_f32(r);
     ++nh;
   }
-  nvalid[i] = nh;
+  if (!handed) nvalid[i] = nh;
   }
   if (kCount) {
     for (int o = 16; o; o >>= 1) {
@@ -394,6 +567,176 @@ __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float
       n_trav += __shfl_xor_sync(0xffffffffu, n_trav, o);
     }
     if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&counts[0], (unsigned long long)n_nodes);
+      atomicAdd(&counts[1], (unsigned long long)n_tris);
+      atomicAdd(&counts[2], (unsigned long long)n_trav);
+    }
+  }
+}
+
+// ---- cooperative completion of straggler rays --------------------------------
+
+constexpr int kCoopList = 128;  // per-warp work list: < 32 entries expanded 4-wide at most
+
+__device__ inline float warp_min(float x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+// All 32 lanes finish one ray's nearest-hit search.  The pending entries
+// (list[0..cnt)) are first expanded breadth-first (an internal node is replaced
+// by the children the ray enters before the current far bound) until there are
+// at least 32, then dealt out to the lanes, which traverse their subtrees with
+// private stacks and share the nearest far bound between rounds.  The lanes'
+// candidates are merged by the rule every traversal applies (enclosing
+// intervals, then float-float distance, then the lower triangle index), which
+// orders candidates totally, so the result is that of one sequential traversal.
+template <bool kCount>
+__device__ Best coop_nearest(const float4* __restrict__ tris, const Node4* __restrict__ nodes, int nt, Ray& r,
+                             Best b, int* list, int cnt, int& n_nodes, int& n_tris) {
+  const int lane = threadIdx.x & 31;
+  for (int round = 0; round < 8 && cnt < 32; ++round) {
+    const int e = lane < cnt ? list[lane] : 0;
+    const bool expand = lane < cnt && e >= 0;
+    int kid[4] = {0, 0, 0, 0}, nk = 0;
+    if (lane < cnt && !expand) kid[nk++] = e;
+    if (expand) {
+      if (kCount) ++n_nodes;
+      const Node4* q = nodes + e;
+      const float4 lx = __ldg(&q->lox), hx = __ldg(&q->hix), ly = __ldg(&q->loy), hy = __ldg(&q->hiy),
+                   lz = __ldg(&q->loz), hz = __ldg(&q->hiz);
+      const int4 ch = __ldg(&q->child);
+      float tn, tf;
+      slab(r.of, r.idir, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, tn, tf);
+      if (ch.x != kEmpty && tn <= tf && tf >= 0.f && tn <= b.hi) kid[nk++] = ch.x;
+      slab(r.of, r.idir, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, tn, tf);
+      if (ch.y != kEmpty && tn <= tf && tf >= 0.f && tn <= b.hi) kid[nk++] = ch.y;
+      slab(r.of, r.idir, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, tn, tf);
+      if (ch.z != kEmpty && tn <= tf && tf >= 0.f && tn <= b.hi) kid[nk++] = ch.z;
+      slab(r.of, r.idir, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, tn, tf);
+      if (ch.w != kEmpty && tn <= tf && tf >= 0.f && tn <= b.hi) kid[nk++] = ch.w;
+    }
+    if (!__any_sync(0xffffffffu, expand)) break;  // only leaves left
+    int x = nk;  // inclusive scan of the entries each lane produces
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, x, 31);  // <= 4 x 31 < kCoopList
+    __syncwarp();  // every lane has read its entry
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < nk) list[x - nk + j] = kid[j];
+    __syncwarp();
+    cnt = total;
+  }
+  int stack[kStack];
+  int sp = 0, node = 0, steps = 0;
+  int mine[kCoopList / 32], nm = 0;
+  for (int j = lane; j < cnt; j += 32) mine[nm++] = list[j];
+  __syncwarp();  // the caller rewrites the list
+  for (int m = nm - 1; m >= 1; --m) stack[sp++] = mine[m];
+  bool done = nm == 0;
+  if (!done) node = mine[0];
+  float lim = warp_min(b.hi);
+  while (__any_sync(0xffffffffu, !done)) {
+    if (!done) done = traverse<kCount>(tris, nodes, nt, r, b, stack, sp, node, steps, 16, lim, n_nodes, n_tris);
+    lim = warp_min(b.hi);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const int id = __shfl_xor_sync(0xffffffffu, b.id, o);
+    const int slot = __shfl_xor_sync(0xffffffffu, b.slot, o);
+    const float lo = __shfl_xor_sync(0xffffffffu, b.lo, o);
+    const float hi = __shfl_xor_sync(0xffffffffu, b.hi, o);
+    const int ex = __shfl_xor_sync(0xffffffffu, (int)b.exact, o);
+    const float th = __shfl_xor_sync(0xffffffffu, b.t.hi, o);
+    const float tl = __shfl_xor_sync(0xffffffffu, b.t.lo, o);
+    if (id >= 0 && id != b.id) consider(b, tris, r, id, slot, lo, hi, ex != 0, ff{th, tl});
+  }
+  return b;
+}
+
+// One warp per handed-over ray: resumes its traversal, then makes its remaining
+// bounces with cooperative traversals from the root.
+template <bool kCount>
+__global__ void __launch_bounds__(128) k_trace_coop(const float4* __restrict__ tris,
+                                                    const Node4* __restrict__ nodes, int nt, GridArg g, int K,
+                                                    const RayDump* __restrict__ dumps,
+                                                    const unsigned int* __restrict__ n_dumps,
+                                                    unsigned int* __restrict__ work, sbr_hit* __restrict__ hits,
+                                                    float4* __restrict__ hit_pos, int32_t* __restrict__ nvalid,
+                                                    unsigned long long* __restrict__ counts) {
+  __shared__ int lists[4][kCoopList];
+  const int lane = threadIdx.x & 31;
+  int* list = lists[threadIdx.x >> 5];
+  int n_nodes = 0, n_tris = 0, n_trav = 0;
+  const unsigned n = min(*n_dumps, (unsigned)kDumpMax);
+  for (;;) {
+    unsigned idx = 0;
+    if (lane == 0) idx = atomicAdd(work, 1u);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    if (idx >= n) break;
+    const RayDump& D = dumps[idx];
+    ff3 ray_o, ray_d;
+    Ray r(ray_o, ray_d);
+    r.g = &g;
+    r.rid = D.rid;
+    r.skip = D.skip;
+    r.has_ff = D.has_ff != 0;
+    r.o = ff3{ff{D.o[0], D.o[1]}, ff{D.o[2], D.o[3]}, ff{D.o[4], D.o[5]}};
+    if (r.has_ff) {
+      r.d = ff3{ff{D.d[0], D.d[1]}, ff{D.d[2], D.d[3]}, ff{D.d[4], D.d[5]}};
+      set_f32(r);
+    } else {  // a primary ray: the same FP32 ray as in k_trace
+      float omega;
+      r.of = ff3_hi(r.o);
+      r.df = grid_dir_f32(g, r.rid, omega);
+      set_idir(r);
+    }
+    Best b;
+    b.id = D.bid;
+    b.slot = D.bslot;
+    b.exact = D.bexact != 0;
+    b.lo = D.blo;
+    b.hi = D.bhi;
+    b.t = ff{D.bt_hi, D.bt_lo};
+    int cnt = 1 + D.sp;
+    for (int j = lane; j < cnt; j += 32) list[j] = j == 0 ? D.node : D.stack[j - 1];
+    __syncwarp();
+    const int slot = D.slot;
+    int nh = D.nh, k = D.k;
+    for (;;) {
+      b = coop_nearest<kCount>(tris, nodes, nt, r, b, list, cnt, n_nodes, n_tris);
+      if (b.id < 0) {
+        if (lane == 0) {
+          record_miss(hits, hit_pos, slot, k, K);
+          nvalid[slot] = nh;
+        }
+        break;
+      }
+      record_hit(tris, r, b, hits, hit_pos, (size_t)slot * K + k, lane == 0);
+      ++nh;
+      if (++k == K) {
+        if (lane == 0) nvalid[slot] = nh;
+        break;
+      }
+      if (kCount && lane == 0) ++n_trav;
+      init_best(b);
+      if (lane == 0) list[0] = nt > 1 ? 0 : ~0;
+      cnt = 1;
+      __syncwarp();
+    }
+  }
+  if (kCount) {
+    for (int o = 16; o; o >>= 1) {
+      n_nodes += __shfl_xor_sync(0xffffffffu, n_nodes, o);
+      n_tris += __shfl_xor_sync(0xffffffffu, n_tris, o);
+      n_trav += __shfl_xor_sync(0xffffffffu, n_trav, o);
+    }
+    if (lane == 0) {
       atomicAdd(&counts[0], (unsigned long long)n_nodes);
       atomicAdd(&counts[1], (unsigned long long)n_tris);
       atomicAdd(&counts[2], (unsigned long long)n_trav);
@@ -458,6 +801,25 @@ __global__ void k_prep(const float4* __restrict__ hit_pos, const float* __restri
 
 inline int blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
+// After the scan's scratch in the paths region: the straggler hand-over's two
+// counters (handed over, claimed) and its records.
+constexpr size_t kCtrBytes = 256;
+inline size_t scan_part(int32_t R) { return (scan_scratch_bytes(R > 0 ? R : 1) + 255) / 256 * 256; }
+inline unsigned int* dump_counters(const sbr_paths* p) {
+  return reinterpret_cast<unsigned int*>(static_cast<char*>(p->scratch) + scan_part(p->n_rays));
+}
+inline RayDump* dump_records(const sbr_paths* p) {
+  return reinterpret_cast<RayDump*>(static_cast<char*>(p->scratch) + scan_part(p->n_rays) + kCtrBytes);
+}
+// warps of the straggler kernel: 16 per SM, each takes rays until none is left
+inline int coop_grid() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+    sms = 152;
+  return 4 * sms;
+}
+
 size_t paths_layout(sbr_paths* p, void* mem, int32_t R, int32_t K, int32_t V) {
   Carver c(mem);
   const int64_t cap = (int64_t)R * K;
@@ -473,7 +835,7 @@ size_t paths_layout(sbr_paths* p, void* mem, int32_t R, int32_t K, int32_t V) {
   p->path_ray = c.take<int32_t>(capc);
   p->prep = c.take<float>(4 * (int64_t)V * capc);
   p->path_len = c.take<float>(2 * (int64_t)V * capc);
-  p->scratch = c.take<char>(scan_scratch_bytes(R > 0 ? R : 1));
+  p->scratch = c.take<char>(scan_part(R) + kCtrBytes + sizeof(RayDump) * (size_t)kDumpMax);
   p->count = p->ray_first ? p->ray_first + R : nullptr;
   return c.bytes();
 }
@@ -587,16 +949,26 @@ static sbr_status trace_impl(const sbr_scene* scene, const sbr_radar_cfg* radar,
     SBR_CUDA(cudaMemsetAsync(paths->ray_first, 0, sizeof(int32_t), st));
     return SBR_OK;
   }
+  RayDump* dumps = dump_records(paths);
+  unsigned int* dctr = dump_counters(paths);
+  SBR_CUDA(cudaMemsetAsync(dctr, 0, 2 * sizeof(unsigned int), st));
+  float4* hp = reinterpret_cast<float4*>(paths->hit_pos);
   ::sbr::note_launch();
   if (d_counts) {
     SBR_CUDA(cudaMemsetAsync(d_counts, 0, 4 * sizeof(unsigned long long), st));
     k_trace<true><<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, d_ray_ids, (int)R,
-                                                  max_bounces, paths->hits, reinterpret_cast<float4*>(paths->hit_pos),
-                                                  paths->ray_weight, paths->ray_first, d_counts);
+                                                  max_bounces, paths->hits, hp, paths->ray_weight, paths->ray_first,
+                                                  dumps, dctr, d_counts);
+    ::sbr::note_launch();
+    k_trace_coop<true><<<coop_grid(), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, max_bounces, dumps,
+                                                    dctr, dctr + 1, paths->hits, hp, paths->ray_first, d_counts);
   } else {
     k_trace<false><<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, d_ray_ids, (int)R,
-                                                   max_bounces, paths->hits, reinterpret_cast<float4*>(paths->hit_pos),
-                                                   paths->ray_weight, paths->ray_first, nullptr);
+                                                   max_bounces, paths->hits, hp, paths->ray_weight,
+                                                   paths->ray_first, dumps, dctr, nullptr);
+    ::sbr::note_launch();
+    k_trace_coop<false><<<coop_grid(), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, max_bounces, dumps,
+                                                     dctr, dctr + 1, paths->hits, hp, paths->ray_first, nullptr);
   }
   SBR_CUDA(cudaGetLastError());
   SBR_CUDA(exclusive_scan(paths->ray_first, paths->ray_first, R, nullptr, paths->scratch, st));
