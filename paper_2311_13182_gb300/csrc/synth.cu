@@ -492,8 +492,8 @@ int sm_count() {
   return g_sms;
 }
 
-// Grid: V * Q CTAs, Q chosen to fill every SM at full occupancy, capped by the
-// number of path chunks.
+// Grid: V * Q CTAs, Q the largest that keeps every CTA resident at once (one
+// wave), capped by the number of path chunks.
 // dynamic shared memory of the split kernel: the groups' reduction buffer
 inline size_t split_smem(int Ns) {
   const int T = threads_for(Ns), M = Ns / T;
@@ -518,9 +518,27 @@ int split_per_sm(int Ns) {
   return cache[M];
 }
 
+// resident CTAs of the tensor-core kernel per SM (N_s = 256 or 512)
+int mma_per_sm(int Ns) {
+  static int cache[3] = {};
+  const int mt = Ns / 256;
+  if (cache[mt]) return cache[mt];
+  int n = 0;
+  if (mt == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_synth_mma<1>, kMmaThreads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_synth_mma<2>, kMmaThreads, 0);
+  cache[mt] = n > 0 ? n : 1;
+  return cache[mt];
+}
+
 void grid_shape(int V, int Ns, int64_t cap, int* Q) {
-  const int per_sm = split_per_sm(Ns);
-  int64_t q = ((int64_t)sm_count() * per_sm + V - 1) / V;
+  int per_sm = split_per_sm(Ns);
+  if (Ns == 256 || Ns == 512) {
+    const int m = mma_per_sm(Ns);
+    if (m < per_sm) per_sm = m;
+  }
+  // whole waves only: every CTA resident from the start (a CTA beyond the
+  // first wave would run alone after the others and double the launch)
+  int64_t q = ((int64_t)sm_count() * per_sm) / V;
   const int64_t chunks = (cap + kChunk - 1) / kChunk;
   if (q > chunks) q = chunks;
   if (q < 1) q = 1;
