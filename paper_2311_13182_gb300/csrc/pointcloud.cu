@@ -519,7 +519,7 @@ struct Layout {
   int groups;
 };
 
-inline int dgroups(int C) { return C >= 8 ? C / 8 : 1; }
+inline int dgroups(int C) { return C >= 2 ? C / 2 : 1; }  // 2 Doppler bins per CTA: enough CTAs to cover the SMs
 
 // k_select's shared memory exceeds the 48 KB default: raise the limit once per device.
 cudaError_t select_attr() {
