@@ -324,17 +324,23 @@ def e2e_arm(sbr, torch, wl, cfg, args, world):
 # DRAM traffic per launch of each roofline stage, from one ncu capture (profiles/traffic.json);
 # used only while the library sources still hash to what was captured.
 TRAFFIC_STAGES = {
-    "trace": ("k_trace", "k_tile_sums", "k_scan_single", "k_tile_scan", "k_prep"),
+    "trace": ("k_trace", "k_trace_coop", "k_tile_sums", "k_scan_single", "k_tile_scan", "k_prep"),
     "synthesize": ("k_synth_mma", "k_reduce"),
 }
 
 
-def sources_sha1() -> str:
-    import glob
+# the sources each stage's kernels are compiled from
+TRAFFIC_SOURCES = {
+    "trace": ("trace.cu", "scan_sort.cu", "cta_sort.cuh", "scene.cuh", "ff.cuh", "common.cuh"),
+    "synthesize": ("synth.cu", "common.cuh"),
+}
+
+
+def sources_sha1(stage: str) -> str:
     import hashlib
     h = hashlib.sha1()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_2311_13182_gb300", "csrc", "*.cu*")))
-    for f in files + [os.path.join(ROOT, "include", "sbr.h")]:
+    csrc = os.path.join(ROOT, "paper_2311_13182_gb300", "csrc")
+    for f in [os.path.join(csrc, n) for n in TRAFFIC_SOURCES[stage]] + [os.path.join(ROOT, "include", "sbr.h")]:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode() + fh.read())
     return h.hexdigest()
@@ -361,9 +367,9 @@ def write_traffic(csv_path: str):
         # two metrics per launch: sum them, average over the launches of the stage's first kernel
         n = max(1, len(per_kernel.get(names[0], [])) // 2)
         total = sum(sum(per_kernel.get(k, [])) for k in names)
-        stages[st] = {"bytes_per_launch": total / n, "launches": n, "kernels": list(names)}
-    out = {"sources_sha1": sources_sha1(), "stages": stages,
-           "from": os.path.basename(csv_path)}
+        stages[st] = {"bytes_per_launch": total / n, "launches": n, "kernels": list(names),
+                      "sources_sha1": sources_sha1(st)}
+    out = {"stages": stages, "from": os.path.basename(csv_path)}
     with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
         json.dump(out, fh, indent=1)
     print(json.dumps(out))
@@ -376,7 +382,8 @@ def measured_traffic() -> dict:
             d = json.load(fh)
     except (OSError, ValueError):
         return {}
-    return d.get("stages", {}) if d.get("sources_sha1") == sources_sha1() else {}
+    return {st: v for st, v in d.get("stages", {}).items()
+            if st in TRAFFIC_SOURCES and v.get("sources_sha1") == sources_sha1(st)}
 
 
 def rooflines(stage_ms, wl, P, counts, peaks, src):
@@ -399,7 +406,7 @@ def rooflines(stage_ms, wl, P, counts, peaks, src):
     tb = nodes * 112 + tris * 48 + R * K * 48 + R * 8 + P * V * 24 + P * 4
     t_ach = tb / (stage_ms["trace"] * 1e-3) / 1e9
     hbm = float(peaks["hbm_gbs"])
-    trace = {"kernel": "k_trace (+ scan, k_prep)", "bound": "hbm", "achieved": t_ach, "peak": hbm, "unit": "GB/s",
+    trace = {"kernel": "k_trace (+ k_trace_coop, scan, k_prep)", "bound": "hbm", "achieved": t_ach, "peak": hbm, "unit": "GB/s",
              "frac": t_ach / hbm, "traffic": traffic.get("trace", {}).get("bytes_per_launch"),
              "bytes_per_launch": tb,
              "units": {"rays": R, "traversals": trav, "nodes": nodes, "triangles": tris, "paths": P},
