@@ -403,6 +403,10 @@ __global__ void __launch_bounds__(256) k_synth_naive(const float4* __restrict__ 
   for (int m = 0; m < M; ++m) out[m] = make_float2(accr[m], acci[m]);
 }
 
+// One thread per (antenna, sample) and group of kRedChirps chirps: the Q per-CTA
+// partial sums added in a fixed order (bitwise reproducible), then written to
+// the group's chirps (a static scene: every chirp equal).
+constexpr int kRedChirps = 16;
 __global__ void k_reduce(const float2* __restrict__ partial, int V, int Q, int Ns, int C,
                          float2* __restrict__ cube) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,7 +418,12 @@ __global__ void k_reduce(const float2* __restrict__ partial, int V, int Q, int N
     re += x.x;
     im += x.y;
   }
-  for (int c = 0; c < C; ++c) cube[((size_t)v * C + c) * Ns + n] = make_float2(re, im);
+  const int c1 = min(C, (int)(blockIdx.y + 1) * kRedChirps);
+  for (int c = blockIdx.y * kRedChirps; c < c1; ++c) cube[((size_t)v * C + c) * Ns + n] = make_float2(re, im);
+}
+
+inline dim3 reduce_grid(int V, int Ns, int C) {
+  return dim3((V * Ns + 255) / 256, (C + kRedChirps - 1) / kRedChirps);
 }
 
 // ---- adjoint ----------------------------------------------------------------
@@ -642,7 +651,7 @@ extern "C" sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg
   SBR_CUDA(cudaGetLastError());
   const int V = paths->n_virt;
   ::sbr::note_launch();
-  k_reduce<<<(V * Ns + 255) / 256, 256, 0, st>>>(w.partial, V, w.Q, Ns, radar->n_chirps,
+  k_reduce<<<reduce_grid(V, Ns, radar->n_chirps), 256, 0, st>>>(w.partial, V, w.Q, Ns, radar->n_chirps,
                                                   reinterpret_cast<float2*>(d_cube));
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;
@@ -718,7 +727,7 @@ extern "C" sbr_status sbr_synthesize_noalloc(const sbr_paths* paths, const sbr_r
   }
   SBR_CUDA(cudaGetLastError());
   ::sbr::note_launch();
-  k_reduce<<<(V * Ns + 255) / 256, 256, 0, st>>>(w.partial, V, w.Q, Ns, radar->n_chirps,
+  k_reduce<<<reduce_grid(V, Ns, radar->n_chirps), 256, 0, st>>>(w.partial, V, w.Q, Ns, radar->n_chirps,
                                                   reinterpret_cast<float2*>(d_cube));
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;
