@@ -168,36 +168,6 @@ def measured_peaks():
 # GPU arm
 # ----------------------------------------------------------------------------
 
-def build_forward(sbr, torch, wl, cfg):
-    v = torch.from_numpy(wl.verts).cuda()
-    f = torch.from_numpy(wl.faces).cuda()
-    scene = sbr.Scene(v, f)
-    paths = sbr.PathBuffers(wl.grid.n_rays, wl.max_bounces, wl.radar.n_virt)
-    ws = torch.empty(sbr.synth_ws_bytes(wl.radar, paths.cap), dtype=torch.uint8, device="cuda")
-    cube = torch.empty((wl.radar.n_virt, wl.radar.n_chirps, wl.radar.n_samples, 2), device="cuda")
-    state = sbr.PcState(wl.radar, cfg)
-    pts = torch.empty((cfg.k_max, 4), device="cuda")
-    return dict(v=v, f=f, scene=scene, paths=paths, ws=ws, cube=cube, state=state, pts=pts)
-
-
-def forward_step(sbr, wl, cfg, b, ev=None):
-    """Scene build, trace + path prep, synthesis, point cloud; optional per-stage events."""
-    if ev is not None:
-        ev[0].record()
-    b["scene"].update(b["v"])
-    if ev is not None:
-        ev[1].record()
-    sbr.trace(b["scene"], wl.radar, wl.grid, wl.max_bounces, out=b["paths"])
-    if ev is not None:
-        ev[2].record()
-    sbr.synthesize(b["paths"], wl.radar, sbr.PHASE_SPLIT, out=b["cube"], ws=b["ws"])
-    if ev is not None:
-        ev[3].record()
-    sbr.pointcloud(b["cube"], wl.radar, cfg, state=b["state"], out=b["pts"])
-    if ev is not None:
-        ev[4].record()
-
-
 def gpu_arm(args, rank, world, local):
     import torch
     import paper_2311_13182_gb300 as sbr
@@ -208,33 +178,48 @@ def gpu_arm(args, rank, world, local):
     torch.cuda.set_device(local)
     wl = superquadric_scene(seed=args.seed + rank, G=1024)
     cfg = CfarParams()
-    b = build_forward(sbr, torch, wl, cfg)
+    # the step as one CUDA graph (sbr.Forward): capture, then replays
+    fw = sbr.Forward(torch.from_numpy(wl.verts).cuda(), torch.from_numpy(wl.faces).cuda(), wl.radar, wl.grid,
+                     wl.max_bounces, cfg)
+    b = {"scene": fw.scene, "paths": fw.paths, "state": fw.state}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    mk = lambda: torch.cuda.Event(enable_timing=True)
+    # per-stage breakdown: the same step as separate launches, events between the stages
+    evs = [[mk() for _ in range(5)] for _ in range(args.steps)]
+    for _ in range(3):
+        fw.run_eager()
+    launches0 = int(L.sbr_launch_count())
+    fw.run_eager()
+    per_step_launches = int(L.sbr_launch_count()) - launches0  # = the kernels in the graph
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        fw.run_eager(evs[i])
+    torch.cuda.synchronize()
+    stage = np.array([[evs[i][j].elapsed_time(evs[i][j + 1]) for j in range(4)] for i in range(args.steps)])
     for _ in range(max(args.warmup, 3)):
-        forward_step(sbr, wl, cfg, b)
+        fw.run()
     torch.cuda.synchronize()
     P = b["paths"].count()
     n_points = b["state"].n_points()
 
-    # ---- device-timed region: inputs resident, per-stage events, L2 flushed between steps
-    mk = lambda: torch.cuda.Event(enable_timing=True)
-    evs = [[mk() for _ in range(5)] for _ in range(args.steps)]
+    # ---- device-timed region: graph replays, inputs resident, L2 flushed between steps
+    ev = [(mk(), mk()) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     barrier(world)
     torch.cuda.synchronize()
-    launches0 = int(L.sbr_launch_count())
     t_wall = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(float(i))
-        forward_step(sbr, wl, cfg, b, evs[i])
+        ev[i][0].record()
+        fw.run()
+        ev[i][1].record()
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
-    launches = int(L.sbr_launch_count()) - launches0
+    launches = per_step_launches * args.steps
     barrier(world)
     clk = clocks.stop()
-    stage = np.array([[evs[i][j].elapsed_time(evs[i][j + 1]) for j in range(4)] for i in range(args.steps)])
-    ms_step = float(stage.sum(1).mean())
+    ms_step = float(np.mean([a.elapsed_time(e) for a, e in ev]))
     ms_step_all = reduce_max(ms_step, world)
     rays = wl.grid.n_rays
     value = reduce_sum(rays, world) / (ms_step_all * 1e-3)
@@ -260,7 +245,9 @@ def gpu_arm(args, rank, world, local):
         "data": "synthetic (seeded superquadric + ground; no datasets)",
         "config": {"workload": WORKLOAD, "rays_per_step": rays, "paths_per_step": P, "points": n_points,
                    "parallelism": f"replicas x{world} (independent scenes per GPU, no collective)",
-                   "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written between steps, outside the per-step events"},
+                   "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written between steps, outside the per-step events",
+                   "timing": "each step one CUDA-graph replay of the whole forward step (sbr.Forward); stage_ms "
+                             "from the same step as separate launches with events between the stages"},
         "path_samples_per_s": path_samples,
         "stage_ms": stage_ms,
         "recon_iters_per_s": None if recon is None else recon["iters_per_s"],

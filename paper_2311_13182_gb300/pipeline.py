@@ -1,0 +1,73 @@
+"""The forward simulation as one CUDA graph.
+
+A forward step (LBVH build of the current vertices, trace and path preparation
+(Section 3.2.1, Eq. 2-3), synthesis (Section 3.2.2, Eq. 8), point cloud (the map
+T of Section 3.4)) is about twenty-five kernel launches and memsets on fixed
+buffers.  ``Forward`` captures the sequence once and replays it, so a step costs
+one graph launch on the host and no gaps between dependent kernels on the GPU.
+New vertex positions of the same topology are written into ``verts`` between
+replays (``set_vertices``); everything else (radar, grid, bounce count, CFAR
+settings) is fixed at construction.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import sim
+
+
+class Forward:
+    def __init__(self, verts: torch.Tensor, faces: torch.Tensor, radar, grid, max_bounces: int, cfar,
+                 mode: int = sim.PHASE_SPLIT, graph: bool = True):
+        self.radar, self.grid, self.max_bounces, self.cfar, self.mode = radar, grid, max_bounces, cfar, mode
+        self.verts = verts.detach().clone().contiguous()
+        self.faces = faces.detach().contiguous()
+        self.scene = sim.Scene(self.verts, self.faces)
+        self.paths = sim.PathBuffers(grid.n_rays, max_bounces, radar.n_virt)
+        self.ws = torch.empty(sim.synth_ws_bytes(radar, self.paths.cap), dtype=torch.uint8, device=self.verts.device)
+        self.cube = torch.empty((radar.n_virt, radar.n_chirps, radar.n_samples, 2), device=self.verts.device)
+        self.state = sim.PcState(radar, cfar)
+        self.points = torch.empty((cfar.k_max, 4), device=self.verts.device)
+        self.graph = None
+        if graph:
+            # first calls outside the capture: they set per-device kernel attributes
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                for _ in range(2):
+                    self.run_eager()
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self.run_eager()
+            torch.cuda.synchronize()
+
+    def set_vertices(self, verts: torch.Tensor):
+        """New positions for the same topology (read by the next run)."""
+        self.verts.copy_(verts, non_blocking=True)
+
+    def run_eager(self, events=None):
+        """The step as separate launches; events[0..4] (optional) bracket its four stages."""
+        def mark(i):
+            if events is not None:
+                events[i].record()
+        mark(0)
+        self.scene.update(self.verts)
+        mark(1)
+        sim.trace(self.scene, self.radar, self.grid, self.max_bounces, out=self.paths)
+        mark(2)
+        sim.synthesize(self.paths, self.radar, self.mode, out=self.cube, ws=self.ws)
+        mark(3)
+        sim.pointcloud(self.cube, self.radar, self.cfar, state=self.state, out=self.points)
+        mark(4)
+
+    def run(self):
+        """One forward step: a graph replay (or the eager launches when built with graph=False)."""
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.run_eager()
+
+    def n_points(self) -> int:
+        return self.state.n_points()
