@@ -77,6 +77,23 @@ def test_superquadric_full_grid_sampled_rays(sbr):
     np.testing.assert_array_equal(sub.hits()[0].cpu().numpy(), tri_gpu)
 
 
+def test_superquadric_full_grid_every_ray(sbr):
+    """All 1,048,576 rays of the bench configuration against the oracle.  A few dozen of them
+    graze the surface after a bounce and run past the traversal's hand-over threshold, so
+    their search is finished by the cooperative (warp-per-ray) kernel: they must choose the
+    same triangles as every other ray."""
+    wl = superquadric_scene(seed=0, G=1024)
+    _, paths = gpu_trace(sbr, wl)
+    tr = oracle.trace(wl.verts, wl.faces, wl.grid, 3)
+    mism, n_ok, tri_gpu = compare_tri(tr, paths)
+    assert mism == 0, f"{mism} of {n_ok} unflagged rays chose a different triangle"
+    ok = tr["flag"] == 0
+    hp = paths.hit_points().cpu().numpy()
+    valid = (tr["tri"] >= 0) & ok[:, None]
+    np.testing.assert_allclose(hp[valid], tr["hit"][valid], rtol=0, atol=1e-9)
+    assert paths.count() == int((tri_gpu >= 0).sum())
+
+
 def test_empty_and_ragged_inputs(sbr):
     # a mesh the rays miss, a single triangle, a ray list of length 1 and 0
     wl = sphere_scene(G=8)
