@@ -756,28 +756,52 @@ __device__ inline ff ff_frac(ff x) {
   return fast_two_sum(x.hi - n, x.lo);  // x.hi - n is exact
 }
 
+// One (ray, bounce) path per lane: the hits of a warp's 32 rays are dealt out to
+// its lanes (a ray's hits are ragged, 0 to K, so one thread per ray would leave
+// most lanes idle); each lane recomputes its ray's Tx legs and interior length.
 __global__ void k_prep(const float4* __restrict__ hit_pos, const float* __restrict__ ray_w,
                        const int32_t* __restrict__ first, int n_rays, int K, RadarArg rd,
                        int64_t cap, float4* __restrict__ prep, float2* __restrict__ plen,
                        int32_t* __restrict__ path_ray) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_rays) return;
-  const int p0 = first[i], nh = first[i + 1] - p0;
-  if (nh <= 0) return;
-  const float omega = ray_w[i];
-  float c0;
-  const ff3 h1 = ld_hit(hit_pos, (size_t)i * K, c0);
-  ff lin0[SBR_MAX_TX];
-  for (int t = 0; t < rd.ntx; ++t) lin0[t] = ff3_len(ff3_sub(h1, ff3_arr(rd.tx[t])));
-  ff interior = ff_of(0.f);
-  ff3 hp = h1;
-  for (int k = 0; k < nh; ++k) {
-    float cosv = c0;
-    const ff3 h = k == 0 ? h1 : ld_hit(hit_pos, (size_t)i * K + k, cosv);
-    if (k > 0) interior = ff_add(interior, ff3_len(ff3_sub(h, hp)));
-    hp = h;
-    const int64_t p = p0 + k;
-    path_ray[p] = i;
+  const int lane = threadIdx.x & 31;
+  int p0 = 0, nh = 0;
+  if (i < n_rays) {
+    p0 = first[i];
+    nh = first[i + 1] - p0;
+  }
+  int x = nh;  // inclusive scan of the warp's hit counts
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  const int pre = x - nh, total = __shfl_sync(0xffffffffu, x, 31);
+  for (int base = 0; base < total; base += 32) {
+    const int j = base + lane;
+    int s = 0;  // owner: the last lane whose first item is <= j (it has hits)
+#pragma unroll
+    for (int step = 16; step; step >>= 1) {
+      const int pc = __shfl_sync(0xffffffffu, pre, (s + step) & 31);
+      if (s + step < 32 && pc <= j) s += step;
+    }
+    const int ps = __shfl_sync(0xffffffffu, pre, s), p0s = __shfl_sync(0xffffffffu, p0, s);
+    if (j >= total) continue;
+    const int k = j - ps, ri = i - lane + s;
+    const int64_t p = p0s + k;
+    const float omega = ray_w[ri];
+    float cosv;
+    const ff3 h1 = ld_hit(hit_pos, (size_t)ri * K, cosv);
+    ff lin0[SBR_MAX_TX];
+    for (int t = 0; t < rd.ntx; ++t) lin0[t] = ff3_len(ff3_sub(h1, ff3_arr(rd.tx[t])));
+    ff interior = ff_of(0.f);
+    ff3 h = h1;
+    for (int m = 1; m <= k; ++m) {  // same order of additions as a per-ray loop
+      const ff3 hm = ld_hit(hit_pos, (size_t)ri * K + m, cosv);
+      interior = ff_add(interior, ff3_len(ff3_sub(hm, h)));
+      h = hm;
+    }
+    path_ray[p] = ri;
     const float sign = (k & 1) ? -1.f : 1.f;
     const float wa = omega * sign * cosv * (float)(0.25 / M_PI);
     for (int rr = 0; rr < rd.nrx; ++rr) {
