@@ -385,7 +385,9 @@ def rooflines(stage_ms, wl, P, counts, peaks, src):
     synthesis (k_synth_mma + k_reduce): the per-antenna complex GEMM sum_p U_p W_p^T with
       N_s = 256 outputs per (path, antenna): 256 complex multiply-adds = 2048 real flops,
       issued three times (fp16 hi.hi + hi.lo + lo.hi) = 6144 tensor flops per (path, antenna),
-      against the measured dense bf16 burst rate (fp16 runs at the same nominal rate)."""
+      against the measured dense bf16 burst rate (fp16 runs at the same nominal rate); and, as
+      terms (path, antenna, sample) per second, against the FP32-pipe bound of the direct
+      per-sample sum (4 FP32 lane-ops per term: 152 x 128 x f_max / 4)."""
     V, Ns = wl.radar.n_virt, wl.radar.n_samples
     R, K = wl.grid.n_rays, wl.max_bounces
     traffic = measured_traffic()
@@ -409,6 +411,15 @@ def rooflines(stage_ms, wl, P, counts, peaks, src):
              "note": "legacy mma.sync path (measured ceiling ~600 TFLOP/s for m16n8k16); operand generation "
                      "on the FP32/MUFU pipes is the limiter",
              "peak_source": f"bf16_tflops of MEASURED_PEAKS.json ({src}, burst; fp16 nominal ratio 1)"}
+    # the same launch against the FP32-pipe bound of the direct per-sample sum (Eq. 8 term by term):
+    # a two-term phasor recurrence and the accumulation take 2 FFMA + 2 FADD lanes per term, and the
+    # GPU issues 152 SMs x 128 FP32 lanes per clock at its maximum SM clock
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_terms = 152 * 128 * mhz * 1e6 / 4
+    synth["fp32_direct_bound"] = {"bound": "alu", "achieved": terms / (stage_ms["synthesize"] * 1e-3),
+                                  "peak": fp32_terms, "unit": "terms/s",
+                                  "frac": terms / (stage_ms["synthesize"] * 1e-3) / fp32_terms,
+                                  "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz / 4 lane-ops per term"}
     dom = trace if stage_ms["trace"] >= stage_ms["synthesize"] else synth
     return dom, [trace, synth]
 

@@ -209,11 +209,16 @@ __device__ inline void test_tri(Best& b, const float4* __restrict__ tris, Ray& r
     consider(b, tris, r, id, slot, t.hi - fabsf(t.hi) * 2.4e-7f, t.hi + fabsf(t.hi) * 2.4e-7f, true, t);
 }
 
+// Entry and exit distances of a padded box.  t = lo idir - o idir, one FMA per
+// plane: rounding o idir moves a plane by at most 2^-24 |o| along its axis, and
+// the final rounding by 2^-24 |lo - o|; both stay far inside the box pads
+// (2^-18 (1 + max |coord|)) for origins within the scene's coordinate range.
 __device__ inline void slab(const float3& o, const float3& idir, float lox, float hix, float loy,
                             float hiy, float loz, float hiz, float& tn, float& tf) {
-  float tx0 = (lox - o.x) * idir.x, tx1 = (hix - o.x) * idir.x;
-  float ty0 = (loy - o.y) * idir.y, ty1 = (hiy - o.y) * idir.y;
-  float tz0 = (loz - o.z) * idir.z, tz1 = (hiz - o.z) * idir.z;
+  const float nx = -(o.x * idir.x), ny = -(o.y * idir.y), nz = -(o.z * idir.z);
+  float tx0 = fmaf(lox, idir.x, nx), tx1 = fmaf(hix, idir.x, nx);
+  float ty0 = fmaf(loy, idir.y, ny), ty1 = fmaf(hiy, idir.y, ny);
+  float tz0 = fmaf(loz, idir.z, nz), tz1 = fmaf(hiz, idir.z, nz);
   tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fminf(tz0, tz1));
   tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
   tf = tf * 1.0000005f + 1e-30f;
