@@ -32,17 +32,28 @@ __device__ inline float2 cmul(float2 a, float2 b) {
 
 __device__ inline int bitrev(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }
 
+// Twiddles tw[j] = e^{sign 2 pi i j / n}, j < n / 2, into shared memory; the
+// stage of length len = 2^m takes tw[j << (logn - m)] (the same float argument
+// 2 j / len as a direct evaluation: both quotients are exact).
+__device__ inline void fill_twiddles(float2* tw, int n, float sign, int lanes, int lane) {
+  for (int j = lane; j < (n >> 1); j += lanes) {
+    float sn, cs;
+    sincospif(sign * 2.f * (float)j / (float)n, &sn, &cs);
+    tw[j] = make_float2(cs, sn);
+  }
+}
+
 // In-place radix-2 DIT FFT of n points held in shared memory (already in
-// bit-reversed order), all threads of the block cooperating.  sign = -1 forward.
-__device__ void smem_fft(float2* s, int n, int logn, float sign, int lanes, int lane) {
-  for (int len = 2; len <= n; len <<= 1) {
-    const int half = len >> 1;
+// bit-reversed order) with the twiddles of fill_twiddles, all threads of the
+// block cooperating.
+__device__ void smem_fft(float2* s, const float2* tw, int logn, int lanes, int lane) {
+  const int n = 1 << logn;
+  for (int m = 1; m <= logn; ++m) {
+    const int half = 1 << (m - 1);
     for (int u = lane; u < (n >> 1); u += lanes) {
-      const int grp = u / half, j = u - grp * half;
-      const int i0 = grp * len + j, i1 = i0 + half;
-      float sn, cs;
-      sincospif(sign * 2.f * (float)j / (float)len, &sn, &cs);
-      const float2 t = cmul(s[i1], make_float2(cs, sn));
+      const int j = u & (half - 1);
+      const int i0 = ((u >> (m - 1)) << m) + j, i1 = i0 + half;
+      const float2 t = cmul(s[i1], tw[j << (logn - m)]);
       const float2 a = s[i0];
       s[i0] = make_float2(a.x + t.x, a.y + t.y);
       s[i1] = make_float2(a.x - t.x, a.y - t.y);
@@ -54,37 +65,43 @@ __device__ void smem_fft(float2* s, int n, int logn, float sign, int lanes, int 
 // FFT along the contiguous last axis: one CTA per row of n points.
 __global__ void k_fft_rows(const float2* __restrict__ in, float2* __restrict__ out, int n, int logn,
                            float sign) {
-  extern __shared__ float2 s[];
+  extern __shared__ float2 s[];  // [n] points, [n / 2] twiddles
+  float2* tw = s + n;
   const size_t row = blockIdx.x;
+  fill_twiddles(tw, n, sign, blockDim.x, threadIdx.x);
   for (int i = threadIdx.x; i < n; i += blockDim.x) s[bitrev(i, logn)] = in[row * n + i];
   __syncthreads();
-  smem_fft(s, n, logn, sign, blockDim.x, threadIdx.x);
+  smem_fft(s, tw, logn, blockDim.x, threadIdx.x);
   for (int i = threadIdx.x; i < n; i += blockDim.x) out[row * n + i] = s[i];
 }
 
 constexpr int kColTile = 16;
 
 // FFT along the chirp axis of [V][C][N_s]: one CTA per (v, 16 consecutive k).
+// Columns sit C + 1 points apart in shared memory, so the 16 columns of one
+// chirp fall in different banks.
 __global__ void k_fft_cols(float2* __restrict__ x, int C, int logc, int Ns, float sign) {
-  extern __shared__ float2 s[];  // [kColTile][C]
+  extern __shared__ float2 s[];  // [kColTile][C + 1] points, [C / 2] twiddles
+  const int ld = C + 1;
+  float2* tw = s + kColTile * ld;
   const int tiles = Ns / kColTile;
   const int v = blockIdx.x / tiles, k0 = (blockIdx.x - v * tiles) * kColTile;
   float2* base = x + (size_t)v * C * Ns + k0;
+  fill_twiddles(tw, C, sign, blockDim.x, threadIdx.x);
   for (int i = threadIdx.x; i < C * kColTile; i += blockDim.x) {
     const int c = i / kColTile, kk = i - c * kColTile;
-    s[kk * C + bitrev(c, logc)] = base[(size_t)c * Ns + kk];
+    s[kk * ld + bitrev(c, logc)] = base[(size_t)c * Ns + kk];
   }
   __syncthreads();
-  for (int len = 2; len <= C; len <<= 1) {
-    const int half = len >> 1;
-    for (int u = threadIdx.x; u < kColTile * (C >> 1); u += blockDim.x) {
-      const int col = u / (C >> 1), w = u - col * (C >> 1);
-      const int grp = w / half, j = w - grp * half;
-      float2* sc = s + col * C;
-      const int i0 = grp * len + j, i1 = i0 + half;
-      float sn, cs;
-      sincospif(sign * 2.f * (float)j / (float)len, &sn, &cs);
-      const float2 t = cmul(sc[i1], make_float2(cs, sn));
+  const int hc = C >> 1;
+  for (int m = 1; m <= logc; ++m) {
+    const int half = 1 << (m - 1);
+    for (int u = threadIdx.x; u < kColTile * hc; u += blockDim.x) {
+      const int col = u >> (logc - 1), w = u & (hc - 1);
+      const int j = w & (half - 1);
+      float2* sc = s + col * ld;
+      const int i0 = ((w >> (m - 1)) << m) + j, i1 = i0 + half;
+      const float2 t = cmul(sc[i1], tw[j << (logc - m)]);
       const float2 a = sc[i0];
       sc[i0] = make_float2(a.x + t.x, a.y + t.y);
       sc[i1] = make_float2(a.x - t.x, a.y - t.y);
@@ -93,7 +110,7 @@ __global__ void k_fft_cols(float2* __restrict__ x, int C, int logc, int Ns, floa
   }
   for (int i = threadIdx.x; i < C * kColTile; i += blockDim.x) {
     const int c = i / kColTile, kk = i - c * kColTile;
-    base[(size_t)c * Ns + kk] = s[kk * C + c];
+    base[(size_t)c * Ns + kk] = s[kk * ld + c];
   }
 }
 
@@ -342,8 +359,8 @@ __global__ void k_points(const float* __restrict__ Pw, PointArg pa, const int32_
 }
 
 // Steps 7-9 in one CTA when the map has at most kSortOneCta cells: compaction
-// of k_detect's keys in cell order (each thread owns a run of consecutive cells;
-// one block scan places them), the stable sort by weight, and the points.  Same
+// of k_detect's keys in cell order (rounds of 4096 cells, four per thread, one
+// block scan per round places them), the stable sort by weight, and the points.  Same
 // results as scan, k_compact, the sort and k_points, in one launch instead of four.
 constexpr int kSelThreads = 1024;
 __global__ void __launch_bounds__(kSelThreads) k_select(const float* __restrict__ Pw, PointArg pa,
@@ -357,20 +374,41 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const float* __restrict_
   const CfarArg& c = pa.c;
   const int cells = c.A * c.Ns, t = threadIdx.x;
   const float floor_v = c.floor_rel * Pw[amax_cell(amax_key)];
-  const int per = (cells + kSelThreads - 1) / kSelThreads;
-  const int c0 = t * per, c1 = min(c0 + per, cells);
-  uint32_t mine = 0;
-  for (int i = c0; i < c1; ++i) mine += key[i] != 0xffffffffu;
-  uint32_t total;
-  uint32_t pos = block_exclusive_sel(mine, &total, wt);
-  for (int i = c0; i < c1; ++i) {
-    const uint32_t kk = key[i];
-    if (kk != 0xffffffffu) {
-      k0[pos] = kk;
-      v0[pos] = i;
-      ++pos;
+  // rounds of 4 x kSelThreads cells (cells is a multiple of 8): thread t loads
+  // cells 4t .. 4t + 3 of the round as one coalesced 16-B load, up to four
+  // rounds' loads in flight before the first scan
+  constexpr int kRound = 4 * kSelThreads, kBatch = 4;
+  const uint4* key4 = reinterpret_cast<const uint4*>(key);
+  uint32_t base = 0;
+  for (int r0 = 0; r0 < cells; r0 += kBatch * kRound) {
+    uint4 q[kBatch];
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      const int cell = r0 + b * kRound + 4 * t;
+      q[b] = cell < cells ? __ldcg(&key4[cell >> 2]) : make_uint4(~0u, ~0u, ~0u, ~0u);
+    }
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      if (r0 + b * kRound >= cells) break;  // the same for every thread
+      const uint32_t kq[4] = {q[b].x, q[b].y, q[b].z, q[b].w};
+      uint32_t mine = 0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) mine += kq[e] != 0xffffffffu;
+      uint32_t total;
+      uint32_t pos = base + block_exclusive_sel(mine, &total, wt);
+      const int cell = r0 + b * kRound + 4 * t;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (kq[e] != 0xffffffffu) {
+          k0[pos] = kq[e];
+          v0[pos] = cell + e;
+          ++pos;
+        }
+      }
+      base += total;
     }
   }
+  const uint32_t total = base;
   __syncthreads();  // the compacted candidates are visible to the whole CTA
   cta::sort_pairs(k0, v0, k1, v1, (int64_t)total, 32, nullptr, sel_sm);
   __syncthreads();
@@ -602,7 +640,11 @@ void launch_angle_bwd(const float2* X, const Steer& xl, const float* dpw, int V,
 
 cudaError_t fft_rows(const float2* in, float2* out, int rows, int n, float sign, cudaStream_t st) {
   const int threads = n / 2 < 256 ? (n / 2 < 32 ? 32 : n / 2) : 256;
-  const size_t sm = sizeof(float2) * n;
+  const size_t sm = sizeof(float2) * (n + n / 2);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
   ::sbr::note_launch();
   k_fft_rows<<<rows, threads, sm, st>>>(in, out, n, ilog2(n), sign);
   return cudaGetLastError();
@@ -610,7 +652,7 @@ cudaError_t fft_rows(const float2* in, float2* out, int rows, int n, float sign,
 
 cudaError_t fft_cols(float2* x, int V, int C, int Ns, float sign, cudaStream_t st) {
   if (C == 1) return cudaSuccess;
-  const size_t sm = sizeof(float2) * C * kColTile;
+  const size_t sm = sizeof(float2) * ((size_t)(C + 1) * kColTile + C / 2);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
