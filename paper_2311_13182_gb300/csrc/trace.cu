@@ -764,6 +764,9 @@ __device__ inline ff ff_frac(ff x) {
 // One (ray, bounce) path per lane: the hits of a warp's 32 rays are dealt out to
 // its lanes (a ray's hits are ragged, 0 to K, so one thread per ray would leave
 // most lanes idle); each lane recomputes its ray's Tx legs and interior length.
+// NTX > 0: that many transmitters, their path lengths held in registers;
+// NTX = 0: rd.ntx of them (up to SBR_MAX_TX).
+template <int NTX>
 __global__ void k_prep(const float4* __restrict__ hit_pos, const float* __restrict__ ray_w,
                        const int32_t* __restrict__ first, int n_rays, int K, RadarArg rd,
                        int64_t cap, float4* __restrict__ prep, float2* __restrict__ plen,
@@ -797,8 +800,12 @@ __global__ void k_prep(const float4* __restrict__ hit_pos, const float* __restri
     const float omega = ray_w[ri];
     float cosv;
     const ff3 h1 = ld_hit(hit_pos, (size_t)ri * K, cosv);
-    ff lin0[SBR_MAX_TX];
-    for (int t = 0; t < rd.ntx; ++t) lin0[t] = ff3_len(ff3_sub(h1, ff3_arr(rd.tx[t])));
+    constexpr int kT = NTX > 0 ? NTX : SBR_MAX_TX;
+    const int ntx = NTX > 0 ? NTX : rd.ntx;
+    ff lin[kT];
+#pragma unroll
+    for (int t = 0; t < kT; ++t)
+      if (t < ntx) lin[t] = ff3_len(ff3_sub(h1, ff3_arr(rd.tx[t])));
     ff interior = ff_of(0.f);
     ff3 h = h1;
     for (int m = 1; m <= k; ++m) {  // same order of additions as a per-ray loop
@@ -806,22 +813,31 @@ __global__ void k_prep(const float4* __restrict__ hit_pos, const float* __restri
       interior = ff_add(interior, ff3_len(ff3_sub(hm, h)));
       h = hm;
     }
+    float rlin[kT];  // 1 / L_in
+#pragma unroll
+    for (int t = 0; t < kT; ++t)
+      if (t < ntx) {
+        lin[t] = ff_add(lin[t], interior);
+        rlin[t] = 1.f / lin[t].hi;
+      }
     path_ray[p] = ri;
     const float sign = (k & 1) ? -1.f : 1.f;
     const float wa = omega * sign * cosv * (float)(0.25 / M_PI);
     for (int rr = 0; rr < rd.nrx; ++rr) {
       const ff lout = ff3_len(ff3_sub(ff3_arr(rd.rx[rr]), h));
-      for (int t = 0; t < rd.ntx; ++t) {
+      const float wo = wa / lout.hi;
+#pragma unroll
+      for (int t = 0; t < kT; ++t) {
+        if (t >= ntx) break;
         const int v = t * rd.nrx + rr;
-        const ff lin = ff_add(lin0[t], interior);
-        const ff L = ff_add(lin, lout);
+        const ff L = ff_add(lin[t], lout);
         const ff x0 = ff_frac(ff_mul(L, rd.k0));
         float phi0 = x0.hi + x0.lo;
         phi0 -= rintf(phi0);
         const ff dl = ff_frac(ff_mul(L, rd.kb));
         const float dhi = rintf(dl.hi * 4096.f) * (1.f / 4096.f);
         const float dlo = (dl.hi - dhi) + dl.lo;  // dl.hi - dhi is exact
-        prep[(size_t)v * cap + p] = make_float4(phi0, dhi, dlo, wa / (lin.hi * lout.hi));
+        prep[(size_t)v * cap + p] = make_float4(phi0, dhi, dlo, wo * rlin[t]);
         plen[(size_t)v * cap + p] = make_float2(L.hi, L.lo);
       }
     }
@@ -1002,11 +1018,33 @@ static sbr_status trace_impl(const sbr_scene* scene, const sbr_radar_cfg* radar,
   SBR_CUDA(cudaGetLastError());
   SBR_CUDA(exclusive_scan(paths->ray_first, paths->ray_first, R, nullptr, paths->scratch, st));
   ::sbr::note_launch();
-  k_prep<<<blocks(R, 128), 128, 0, st>>>(reinterpret_cast<const float4*>(paths->hit_pos),
-                                         paths->ray_weight, paths->ray_first, (int)R, max_bounces,
-                                         rd, paths->path_cap,
-                                         reinterpret_cast<float4*>(paths->prep),
-                                         reinterpret_cast<float2*>(paths->path_len), paths->path_ray);
+  {
+    const float4* hp4 = reinterpret_cast<const float4*>(paths->hit_pos);
+    float4* prep = reinterpret_cast<float4*>(paths->prep);
+    float2* plen = reinterpret_cast<float2*>(paths->path_len);
+    const int nb = blocks(R, 128);
+    switch (rd.ntx) {  // the common transmitter counts keep their legs in registers
+      case 1:
+        k_prep<1><<<nb, 128, 0, st>>>(hp4, paths->ray_weight, paths->ray_first, (int)R, max_bounces, rd,
+                                      paths->path_cap, prep, plen, paths->path_ray);
+        break;
+      case 2:
+        k_prep<2><<<nb, 128, 0, st>>>(hp4, paths->ray_weight, paths->ray_first, (int)R, max_bounces, rd,
+                                      paths->path_cap, prep, plen, paths->path_ray);
+        break;
+      case 3:
+        k_prep<3><<<nb, 128, 0, st>>>(hp4, paths->ray_weight, paths->ray_first, (int)R, max_bounces, rd,
+                                      paths->path_cap, prep, plen, paths->path_ray);
+        break;
+      case 4:
+        k_prep<4><<<nb, 128, 0, st>>>(hp4, paths->ray_weight, paths->ray_first, (int)R, max_bounces, rd,
+                                      paths->path_cap, prep, plen, paths->path_ray);
+        break;
+      default:
+        k_prep<0><<<nb, 128, 0, st>>>(hp4, paths->ray_weight, paths->ray_first, (int)R, max_bounces, rd,
+                                      paths->path_cap, prep, plen, paths->path_ray);
+    }
+  }
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;
 }
