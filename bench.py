@@ -312,14 +312,14 @@ def e2e_arm(sbr, torch, wl, cfg, args, world):
 # used only while the library sources still hash to what was captured.
 TRAFFIC_STAGES = {
     "trace": ("k_trace", "k_trace_coop", "k_tile_sums", "k_scan_single", "k_tile_scan", "k_prep"),
-    "synthesize": ("k_synth_mma", "k_reduce"),
+    "synthesize": ("k_nufft_spread", "k_nufft_finish", "k_reduce"),
 }
 
 
 # the sources each stage's kernels are compiled from
 TRAFFIC_SOURCES = {
     "trace": ("trace.cu", "scan_sort.cu", "cta_sort.cuh", "scene.cuh", "ff.cuh", "common.cuh"),
-    "synthesize": ("synth.cu", "common.cuh"),
+    "synthesize": ("synth.cu", "fft.cuh", "common.cuh"),
 }
 
 
@@ -382,12 +382,13 @@ def rooflines(stage_ms, wl, P, counts, peaks, src):
       + per (path, antenna) the 16-B synthesis record and 8-B path length + 4 B per path,
       against the measured HBM copy bandwidth (the working set is L2-resident, so this is
       the bytes-served rate; `traffic` is the DRAM part, from ncu).
-    synthesis (k_synth_mma + k_reduce): the per-antenna complex GEMM sum_p U_p W_p^T with
-      N_s = 256 outputs per (path, antenna): 256 complex multiply-adds = 2048 real flops,
-      issued three times (fp16 hi.hi + hi.lo + lo.hi) = 6144 tensor flops per (path, antenna),
-      against the measured dense bf16 burst rate (fp16 runs at the same nominal rate); and, as
-      terms (path, antenna, sample) per second, against the FP32-pipe bound of the direct
-      per-sample sum (4 FP32 lane-ops per term: 152 x 128 x f_max / 4)."""
+    synthesis (k_nufft_spread + k_nufft_finish + k_reduce): Eq. 8 as a type-1 non-uniform
+      FFT, 8 grid updates per (path, antenna) and one 2 N_s-point FFT per antenna; counted as
+      terms (path, antenna, sample) per second against the FP32-pipe bound of the direct
+      per-sample sum (a two-term phasor recurrence and the accumulation: 4 FP32 lane-ops per
+      term, 152 SMs x 128 lanes x f_max / 4).  A fraction above 1 is the algorithm doing less
+      work than any term-by-term kernel; the 16-B records it streams are given against the
+      HBM copy rate beside it."""
     V, Ns = wl.radar.n_virt, wl.radar.n_samples
     R, K = wl.grid.n_rays, wl.max_bounces
     traffic = measured_traffic()
@@ -401,25 +402,19 @@ def rooflines(stage_ms, wl, P, counts, peaks, src):
              "units": {"rays": R, "traversals": trav, "nodes": nodes, "triangles": tris, "paths": P},
              "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({src}, burst copy)"}
     terms = P * V * Ns
-    flops = P * V * 6144 * (Ns // 256)
-    s_ach = flops / (stage_ms["synthesize"] * 1e-3) / 1e12
-    tc = float(peaks["bf16_tflops"])
-    synth = {"kernel": "k_synth_mma (+ k_reduce)", "bound": "tensor", "achieved": s_ach, "peak": tc,
-             "unit": "TFLOP/s (fp16 tensor)", "frac": s_ach / tc,
-             "traffic": traffic.get("synthesize", {}).get("bytes_per_launch"), "terms_per_launch": terms,
-             "terms_per_s": terms / (stage_ms["synthesize"] * 1e-3),
-             "note": "legacy mma.sync path (measured ceiling ~600 TFLOP/s for m16n8k16); operand generation "
-                     "on the FP32/MUFU pipes is the limiter",
-             "peak_source": f"bf16_tflops of MEASURED_PEAKS.json ({src}, burst; fp16 nominal ratio 1)"}
-    # the same launch against the FP32-pipe bound of the direct per-sample sum (Eq. 8 term by term):
-    # a two-term phasor recurrence and the accumulation take 2 FFMA + 2 FADD lanes per term, and the
-    # GPU issues 152 SMs x 128 FP32 lanes per clock at its maximum SM clock
+    t_syn = stage_ms["synthesize"] * 1e-3
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_terms = 152 * 128 * mhz * 1e6 / 4
-    synth["fp32_direct_bound"] = {"bound": "alu", "achieved": terms / (stage_ms["synthesize"] * 1e-3),
-                                  "peak": fp32_terms, "unit": "terms/s",
-                                  "frac": terms / (stage_ms["synthesize"] * 1e-3) / fp32_terms,
-                                  "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz / 4 lane-ops per term"}
+    rec_bytes = P * V * 16
+    synth = {"kernel": "k_nufft_spread (+ k_nufft_finish, k_reduce)", "bound": "alu",
+             "achieved": terms / t_syn, "peak": fp32_terms, "unit": "terms/s", "frac": terms / t_syn / fp32_terms,
+             "traffic": traffic.get("synthesize", {}).get("bytes_per_launch"), "terms_per_launch": terms,
+             "grid_updates_per_launch": P * V * 8,
+             "records": {"bytes_per_launch": rec_bytes, "achieved_gbs": rec_bytes / t_syn / 1e9,
+                         "frac_of_hbm": rec_bytes / t_syn / 1e9 / float(peaks["hbm_gbs"])},
+             "note": "type-1 non-uniform FFT: 8 grid updates per path and antenna instead of N_s terms; "
+                     "peak = FP32-pipe bound of the direct per-sample sum (4 lane-ops per term)",
+             "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (MEASURED_PEAKS.json sm_max_mhz) / 4"}
     dom = trace if stage_ms["trace"] >= stage_ms["synthesize"] else synth
     return dom, [trace, synth]
 

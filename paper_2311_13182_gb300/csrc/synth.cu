@@ -3,34 +3,44 @@
 // cube[v, c, n] = sum_p A_{p,v} exp(j 2 pi (f_c tau_{p,v} + mu tau_{p,v} t_n)),
 // t_n = n T / N_s, identical for every chirp c of a static scene.
 //
-// Tensor-core kernel (N_s = 256 or 512, the default for SBR_PHASE_SPLIT): with
-// n = 16 a + b (b < 16), Eq. 8 factorises per path into U_p[a] W_p[b] with
-// U_p[a] = A e^{j 2 pi (phi0 + 16 a delta)} and W_p[b] = e^{j 2 pi b delta}, so
-// each antenna's samples are the complex matrix product sum_p U_p W_p^T, a
-// GEMM whose contraction runs over the paths.  Written as a real GEMM with
-// rows (Re, Im) x a, columns b and two contraction entries (Re, Im) per path,
-// it goes to mma.sync m16n8k16 with every operand split into two fp16 halves
-// (hi + lo, three products hi.hi + hi.lo + lo.hi: ~21-bit products) and FP32
-// accumulation; amplitudes are scaled by a power of two per staged chunk so the
-// halves stay in fp16 range (the accumulators are rescaled exactly when the
-// scale drops).  Per (path, antenna) this generates 32 phasors instead of
-// N_s = 256, and the 256 x 2 complex multiply-adds run on the tensor pipe.
+// Split-phase mode, N_s <= 512 (sbr_synthesize's default path): a type-1
+// non-uniform FFT.  Each (path, antenna) is spread onto a periodic grid of
+// 2 N_s points with a width-8 exponential-of-semicircle kernel, one FFT per
+// antenna follows, and the kernel's Fourier transform is divided out: 8 grid
+// updates per (path, antenna) instead of N_s phasors, about 1e-6 from the FP64
+// sum (details at k_nufft_spread).
 //
-// Forward kernel (persistent, one virtual antenna per CTA): the CTA's threads
-// own M consecutive samples each and together cover all N_s samples, so the
-// sum over paths accumulates in registers with no cross-thread reduction.
-// Paths stream through shared memory in chunks; per (path, thread) one
-// split-precision anchor phase (n0 delta_hi is exact in FP32, frac() before the
-// low part and phi0 are added) goes through one sincos, and the remaining M-1
-// samples follow by complex rotation with the per-path step e^{j 2 pi delta}
-// (4 FP32 multiply/FMA per sample instead of two transcendental ops).  Each CTA
-// writes its partial sums; a second kernel adds them in a fixed order, so the
-// result is bitwise reproducible.
+// Tensor-core kernel (N_s = 256 or 512, run by the allocation-free entry
+// point): with n = 16 a + b (b < 16), Eq. 8 factorises per path into
+// U_p[a] W_p[b] with U_p[a] = A e^{j 2 pi (phi0 + 16 a delta)} and
+// W_p[b] = e^{j 2 pi b delta}, so each antenna's samples are the complex matrix
+// product sum_p U_p W_p^T, a GEMM whose contraction runs over the paths.
+// Written as a real GEMM with rows (Re, Im) x a, columns b and two contraction
+// entries (Re, Im) per path, it goes to mma.sync m16n8k16 with every operand
+// split into two fp16 halves (hi + lo, three products hi.hi + hi.lo + lo.hi:
+// ~21-bit products) and FP32 accumulation; amplitudes are scaled by a power of
+// two per staged chunk so the halves stay in fp16 range (the accumulators are
+// rescaled exactly when the scale drops).
+//
+// Direct FP32 kernel (other sample counts; persistent, one virtual antenna per
+// CTA): the CTA's threads own M consecutive samples each and together cover
+// all N_s samples, so the sum over paths accumulates in registers with no
+// cross-thread reduction.  Paths stream through shared memory in chunks; per
+// (path, thread) one split-precision anchor phase (n0 delta_hi is exact in
+// FP32, frac() before the low part and phi0 are added) goes through one sincos,
+// and the remaining M-1 samples follow by complex rotation with the per-path
+// step e^{j 2 pi delta} (4 FP32 multiply/FMA per sample instead of two
+// transcendental ops).
+//
+// Every path adds per-CTA partial sums that a second kernel adds in a fixed
+// order, so the result is bitwise reproducible.
 #include <cuda_fp16.h>
+#include <math.h>
 
 #include <mutex>
 
 #include "common.cuh"
+#include "fft.cuh"
 
 namespace sbr {
 namespace {
@@ -489,6 +499,265 @@ __global__ void __launch_bounds__(256) k_synth_bwd(const float4* __restrict__ pr
   glen[(size_t)v * cap + p] = kTwoPiF * r.w * fmaf(inv_lambda, s0, b_over_cns * s1);
 }
 
+// ---- non-uniform FFT forward kernel -----------------------------------------
+//
+// For the split-phase mode with N_s <= 512 the samples are computed as a type-1
+// non-uniform FFT (Dutt & Rokhlin 1993; kernel of Barnett, Magland & af Klinteberg
+// 2019) instead of term by term.  With n = n' + N_s / 2 (n' in [-N_s/2, N_s/2)),
+//   S[n] = sum_p c_p e^{j 2 pi n' delta_p},  c_p = A_p e^{j 2 pi (phi0_p + (N_s/2) delta_p)},
+// every path is spread onto a periodic grid of M = 2 N_s points, u_p = M delta_p,
+//   b[l] = sum_p c_p psi(l - u_p),  psi(x) = exp(beta (sqrt(1 - (2x/w)^2) - 1)), |x| < w/2,
+// then B[k] = sum_l b[l] e^{+j 2 pi k l / M} (one M-point FFT) and, by Poisson
+// summation, S[n' + N_s/2] = B[n'] / Psi(n'/M) with Psi the Fourier transform of
+// psi, up to the aliasing terms Psi(n'/M - k), k != 0 (about 1e-7 relative for
+// w = 8, beta = 2.3 w at upsampling 2).  Per (path, antenna) that is w = 8 kernel
+// values instead of N_s phasors.
+//
+// The grid position keeps the split phase's precision: M delta_hi is exact in
+// FP32 (delta_hi is a multiple of 2^-12, M <= 1024), so the offset of the path
+// from its grid cell, t = (M delta_hi - floor(M delta_hi)) + M delta_lo, carries
+// about 2^-24 of one grid step.
+//
+// Each warp spreads into its own grid in shared memory (no atomics): its lanes
+// form four groups of w = 8, one path per group and one grid point per lane,
+// four consecutive paths per step.  Neighbouring rays sit at nearly the same
+// range: when the four paths share their grid cell, the groups' values are
+// added by shuffles (a fixed tree) and one group writes; when they touch the
+// same points otherwise, the groups write one after the other.  The warps'
+// grids are added in a fixed order, and the CTAs' grids by the finishing kernel
+// in a fixed order, so the result is bitwise reproducible.
+constexpr int kNuW = 8;             // kernel width in grid points
+constexpr int kNuWarps = 8;         // warps per CTA, one grid each
+constexpr int kNuThreads = 32 * kNuWarps;
+constexpr int kNuMaxSamples = 512;  // grids of up to 1024 points (8 KB per warp)
+constexpr int kNuQuad = 32;         // Gauss-Legendre nodes for Psi
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+struct NufftArg {
+  float half_n;    // N_s / 2
+  float m;         // M = 2 N_s
+  float beta_l2e;  // beta log2(e)
+  int log_m;
+};
+
+// Psi(xi) = sum_i wpsi[i] cos(2 pi xi x[i]): Gauss-Legendre on [0, w/2] of 2 psi(x) cos(2 pi xi x)
+struct PsiQuad {
+  float x[kNuQuad];
+  float wpsi[kNuQuad];
+};
+
+// CTA (v, q) spreads antenna v; the warps of the Q CTAs take batches of 32
+// consecutive paths in turn.  Writes the CTA's grid: grids[(q V + v) M + l].
+__global__ void __launch_bounds__(kNuThreads) k_nufft_spread(const float4* __restrict__ prep, int64_t cap,
+                                                            const int32_t* __restrict__ d_P, int V, int Q,
+                                                            NufftArg na, float2* __restrict__ grids) {
+  extern __shared__ float2 wgrid[];  // [warp][M]
+  const int M = 1 << na.log_m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 3, j = lane & 7;
+  float2* g = wgrid + (size_t)warp * M;
+  for (int i = lane; i < M; i += 32) g[i] = make_float2(0.f, 0.f);
+  __syncwarp();
+  const int v = blockIdx.x % V, q = blockIdx.x / V;
+  const int64_t P = *d_P;
+  const float4* pv = prep + (size_t)v * cap;
+  const float xo = (float)(j - (kNuW / 2 - 1));  // this lane's grid point minus floor(u), before t
+  for (int64_t b = (int64_t)q * kNuWarps + warp; b * 32 < P; b += (int64_t)Q * kNuWarps) {
+    const int64_t p = b * 32 + lane;  // lane prepares path p
+    float cre = 0.f, cim = 0.f, t = 0.f;
+    int i0 = 0;
+    if (p < P) {
+      const float4 r = __ldg(&pv[p]);  // phi0, delta_hi, delta_lo, A
+      float x = na.half_n * r.y;       // exact
+      x -= rintf(x);
+      x = fmaf(na.half_n, r.z, x) + r.x;
+      x -= rintf(x);
+      float sn, cs;
+      __sincosf(kTwoPiF * x, &sn, &cs);
+      cre = r.w * cs;
+      cim = r.w * sn;
+      const float uh = na.m * r.y;  // exact
+      const float fl = floorf(uh);
+      t = fmaf(na.m, r.z, uh - fl);
+      i0 = (int)fl;
+      if (t < 0.f) {
+        t += 1.f;
+        --i0;
+      } else if (t >= 1.f) {
+        t -= 1.f;
+        ++i0;
+      }
+    }
+    const int nb = (int)min((int64_t)32, P - b * 32);
+    for (int st = 0; 4 * st < nb; ++st) {
+      const int src = 4 * st + grp;
+      const bool live = src < nb;
+      float pr = __shfl_sync(0xffffffffu, cre, src), pi = __shfl_sync(0xffffffffu, cim, src);
+      const float pt = __shfl_sync(0xffffffffu, t, src);
+      const int pl = __shfl_sync(0xffffffffu, i0, src);
+      const float z = (xo - pt) * (2.f / kNuW);
+      // psi = exp(beta (sqrt(1 - z^2) - 1)); |z| <= 1 on the 8 points
+      const float psi = ex2_approx(na.beta_l2e * (sqrt_approx(fmaxf(fmaf(-z, z, 1.f), 0.f)) - 1.f));
+      float cx = live ? psi * pr : 0.f, cy = live ? psi * pi : 0.f;
+      const int l = (pl + j - (kNuW / 2 - 1)) & (M - 1);
+      const int pl0 = __shfl_sync(0xffffffffu, pl, 0);  // group 0's path is always live
+      if (__all_sync(0xffffffffu, !live || pl == pl0)) {
+        // one cell for all four paths: add the groups' values (lane j of each group), group 0 writes
+        cx += __shfl_xor_sync(0xffffffffu, cx, 8);
+        cy += __shfl_xor_sync(0xffffffffu, cy, 8);
+        cx += __shfl_xor_sync(0xffffffffu, cx, 16);
+        cy += __shfl_xor_sync(0xffffffffu, cy, 16);
+        if (grp == 0) {
+          float2 o = g[l];
+          o.x += cx;
+          o.y += cy;
+          g[l] = o;
+        }
+      } else {
+        const unsigned same = __match_any_sync(0xffffffffu, live ? l : -1 - lane);
+        if (__all_sync(0xffffffffu, __popc(same) == 1)) {
+          if (live) {
+            float2 o = g[l];
+            o.x += cx;
+            o.y += cy;
+            g[l] = o;
+          }
+        } else {  // two groups share a point: the groups in turn
+          for (int gg = 0; gg < 4; ++gg) {
+            if (grp == gg && live) {
+              float2 o = g[l];
+              o.x += cx;
+              o.y += cy;
+              g[l] = o;
+            }
+            __syncwarp();
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  float2* out = grids + ((size_t)q * V + v) * M;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    float2 acc = wgrid[i];
+    for (int w = 1; w < kNuWarps; ++w) {
+      const float2 x = wgrid[(size_t)w * M + i];
+      acc.x += x.x;
+      acc.y += x.y;
+    }
+    out[i] = acc;
+  }
+}
+
+// One CTA of kNuFinThreads per antenna: the CTAs' grids added in a fixed order
+// (kNuFinThreads / M threads per grid point, each over every (kNuFinThreads / M)-th
+// CTA with four interleaved sums, then the threads' sums in order), the M-point
+// FFT, the division by Psi(n'/M); writes S[v][n] (one chirp).
+constexpr int kNuFinThreads = 1024;
+__global__ void __launch_bounds__(kNuFinThreads) k_nufft_finish(const float2* __restrict__ grids, int V, int Q,
+                                                                int Ns, int log_m, PsiQuad pq,
+                                                                float2* __restrict__ samples) {
+  extern __shared__ float2 sg[];  // [M] grid, [M / 2] twiddles, [kNuFinThreads] per-thread sums
+  const int M = 1 << log_m, v = blockIdx.x;
+  float2* tw = sg + M;
+  float2* part = tw + M / 2;
+  fft::fill_twiddles(tw, M, 1.f, blockDim.x, threadIdx.x);
+  const int parts = blockDim.x >> log_m, l = threadIdx.x & (M - 1), k0 = threadIdx.x >> log_m;
+  float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+  const float2* src = grids + (size_t)v * M + l;
+  const size_t qs = (size_t)V * M;  // from one CTA's grid to the next
+  int q = k0;
+  for (; q + 3 * parts < Q; q += 4 * parts) {  // four loads in flight, four interleaved sums
+    const float2 x0 = __ldcg(src + (size_t)q * qs), x1 = __ldcg(src + (size_t)(q + parts) * qs);
+    const float2 x2 = __ldcg(src + (size_t)(q + 2 * parts) * qs), x3 = __ldcg(src + (size_t)(q + 3 * parts) * qs);
+    a0.x += x0.x;
+    a0.y += x0.y;
+    a1.x += x1.x;
+    a1.y += x1.y;
+    a2.x += x2.x;
+    a2.y += x2.y;
+    a3.x += x3.x;
+    a3.y += x3.y;
+  }
+  for (; q < Q; q += parts) {
+    const float2 x = __ldcg(src + (size_t)q * qs);
+    a0.x += x.x;
+    a0.y += x.y;
+  }
+  part[threadIdx.x] = make_float2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+  __syncthreads();
+  if (threadIdx.x < M) {
+    float2 acc = part[l];
+    for (int k = 1; k < parts; ++k) {
+      acc.x += part[k * M + l].x;
+      acc.y += part[k * M + l].y;
+    }
+    sg[fft::bitrev(l, log_m)] = acc;
+  }
+  __syncthreads();
+  fft::smem_fft(sg, tw, log_m, blockDim.x, threadIdx.x);
+  const int h = Ns >> 1;
+  for (int n = threadIdx.x; n < Ns; n += blockDim.x) {
+    const float xi = (float)(n - h) / (float)M;
+    float ph = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < kNuQuad; ++i) ph = fmaf(pq.wpsi[i], cospif(2.f * xi * pq.x[i]), ph);
+    const float2 B = sg[(n - h) & (M - 1)];
+    const float inv = 1.f / ph;
+    samples[(size_t)v * Ns + n] = make_float2(B.x * inv, B.y * inv);
+  }
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on the three-term
+// recurrence of the Legendre polynomials), mapped to Psi's quadrature.
+PsiQuad make_psi_quad(double beta) {
+  PsiQuad pq{};
+  const int n = kNuQuad;
+  const double half_w = 0.5 * kNuW;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-15) break;
+    }
+    const double wgt = 2.0 / ((1.0 - z * z) * dp * dp);
+    // [-1, 1] -> [0, w/2]; Psi(xi) = 2 int_0^{w/2} psi(x) cos(2 pi xi x) dx
+    const double x = 0.5 * half_w * (1.0 + z);
+    const double zz = x / half_w;
+    const double psi = exp(beta * (sqrt(1.0 - zz * zz) - 1.0));
+    pq.x[i] = (float)x;
+    pq.wpsi[i] = (float)(2.0 * 0.5 * half_w * wgt * psi);
+  }
+  return pq;
+}
+
+constexpr double kNuBeta = 2.3 * kNuW;
+
+const PsiQuad& psi_quad() {
+  static const PsiQuad pq = make_psi_quad(kNuBeta);
+  return pq;
+}
+
+inline bool nufft_for(sbr_phase_mode mode, int Ns) { return mode == SBR_PHASE_SPLIT && Ns <= kNuMaxSamples; }
+
 int g_sms = 0;
 
 int sm_count() {
@@ -554,12 +823,47 @@ void grid_shape(int V, int Ns, int64_t cap, int* Q) {
   *Q = (int)q;
 }
 
-size_t ws_layout(const sbr_radar_cfg* radar, int64_t cap, int* Q) {
+// dynamic shared memory of the spreading kernel: one grid of M = 2 N_s points per warp
+inline size_t nufft_smem(int Ns) { return sizeof(float2) * kNuWarps * 2 * (size_t)Ns; }
+
+// resident spreading CTAs per SM (shared memory and registers decide); raises
+// the kernel's shared-memory limit once where the grids pass 48 KB
+int nufft_per_sm(int Ns) {
+  static int cache[16] = {};
+  int lg = 0;
+  while ((1 << lg) < Ns) ++lg;
+  if (cache[lg]) return cache[lg];
+  const size_t sm = nufft_smem(Ns);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_nufft_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nufft_spread, kNuThreads, sm);
+  cache[lg] = n > 0 ? n : 1;
+  return cache[lg];
+}
+
+// CTAs per antenna of the spreading kernel: one wave, at most one per 256 paths
+void nufft_shape(int V, int Ns, int64_t cap, int* Qn) {
+  int64_t q = ((int64_t)sm_count() * nufft_per_sm(Ns)) / V;
+  const int64_t batches = (cap + 32 * kNuWarps - 1) / (32 * kNuWarps);
+  if (q > batches) q = batches;
+  if (q < 1) q = 1;
+  *Qn = (int)q;
+}
+
+// Workspace: per-CTA partial sums of the direct kernels, the chirp-summed
+// upstream gradient of the adjoint, and, for the non-uniform FFT, the CTAs'
+// grids and the finished samples of one chirp.
+size_t ws_layout(const sbr_radar_cfg* radar, int64_t cap, int* Q, int* Qn = nullptr) {
   const int V = radar->n_tx * radar->n_rx, Ns = radar->n_samples;
   grid_shape(V, Ns, cap, Q);
+  int qn = 0;
+  if (Ns <= kNuMaxSamples) nufft_shape(V, Ns, cap, &qn);
+  if (Qn) *Qn = qn;
   Carver c(nullptr);
-  c.take<float2>((size_t)V * (*Q) * Ns);  // per-CTA partial sums
-  c.take<float2>((size_t)V * Ns);         // chirp-summed upstream gradient
+  c.take<float2>((size_t)V * (*Q) * Ns);       // per-CTA partial sums
+  c.take<float2>((size_t)V * Ns);              // chirp-summed upstream gradient
+  c.take<float2>((size_t)V * qn * 2 * Ns);     // non-uniform FFT: the CTAs' grids
+  c.take<float2>((size_t)V * Ns);              // non-uniform FFT: samples of one chirp
   return c.bytes();
 }
 
@@ -578,13 +882,15 @@ namespace {
 struct SynthWs {
   float2* partial;
   float2* gsum;
-  int Q;
+  float2* grids;
+  float2* samples;
+  int Q, Qn;
 };
 
 sbr_status bind_ws(const sbr_radar_cfg* radar, int64_t cap, void* ws, size_t bytes, SynthWs* w,
                    const char* who) {
-  int Q;
-  const size_t need = ws_layout(radar, cap, &Q);
+  int Q, Qn;
+  const size_t need = ws_layout(radar, cap, &Q, &Qn);
   SBR_ARG(ws && aligned256(ws), "%s: workspace NULL or not 256-byte aligned", who);
   if (bytes < need) {
     set_error("%s: workspace of %zu bytes, %zu needed", who, bytes, need);
@@ -594,8 +900,28 @@ sbr_status bind_ws(const sbr_radar_cfg* radar, int64_t cap, void* ws, size_t byt
   Carver c(ws);
   w->partial = c.take<float2>((size_t)V * Q * Ns);
   w->gsum = c.take<float2>((size_t)V * Ns);
+  w->grids = c.take<float2>((size_t)V * Qn * 2 * Ns);
+  w->samples = c.take<float2>((size_t)V * Ns);
   w->Q = Q;
+  w->Qn = Qn;
   return SBR_OK;
+}
+
+// Split-phase samples by the non-uniform FFT: spread, finish, one chirp -> all chirps.
+void launch_nufft(const sbr_paths* p, const sbr_radar_cfg* r, const SynthWs& w, float2* cube, cudaStream_t st) {
+  const int V = p->n_virt, Ns = r->n_samples;
+  int log_m = 0;
+  while ((1 << log_m) < 2 * Ns) ++log_m;
+  NufftArg na{0.5f * (float)Ns, 2.f * (float)Ns, (float)(kNuBeta * 1.4426950408889634), log_m};
+  nufft_per_sm(Ns);  // sets the shared-memory limit before the first launch
+  ::sbr::note_launch();
+  k_nufft_spread<<<V * w.Qn, kNuThreads, nufft_smem(Ns), st>>>(reinterpret_cast<const float4*>(p->prep),
+                                                               p->path_cap, p->count, V, w.Qn, na, w.grids);
+  ::sbr::note_launch();
+  k_nufft_finish<<<V, kNuFinThreads, sizeof(float2) * (3 * (size_t)Ns + kNuFinThreads), st>>>(
+      w.grids, V, w.Qn, Ns, log_m, psi_quad(), w.samples);
+  ::sbr::note_launch();
+  k_reduce<<<reduce_grid(V, Ns, r->n_chirps), 256, 0, st>>>(w.samples, V, 1, Ns, r->n_chirps, cube);
 }
 
 template <int M>
@@ -640,6 +966,11 @@ extern "C" sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg
   if (rs != SBR_OK) return rs;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int Ns = radar->n_samples, T = threads_for(Ns), M = Ns / T;
+  if (nufft_for(mode, Ns)) {
+    launch_nufft(paths, radar, w, reinterpret_cast<float2*>(d_cube), st);
+    SBR_CUDA(cudaGetLastError());
+    return SBR_OK;
+  }
   switch (M) {
     case 1: launch_fwd<1>(mode, paths, radar, w, st); break;
     case 2: launch_fwd<2>(mode, paths, radar, w, st); break;

@@ -80,10 +80,10 @@ def test_synthesis_adjoint_matches_oracle(sbr):
     np.testing.assert_allclose(gamp, ga, rtol=0, atol=1e-4 * np.abs(ga).max())
 
 
-@pytest.mark.parametrize("ns", [256, 512])
-def test_tensor_core_sample_counts(sbr, ns):
-    """The split mode at 256 and 512 samples runs the fp16x3 tensor-core factorisation of
-    Eq. 8 (n = 16 a + b); both sit at the FP32 kernels' accuracy, far inside 1e-4."""
+@pytest.mark.parametrize("ns", [32, 64, 128, 256, 512, 1024])
+def test_split_sample_counts(sbr, ns):
+    """The split mode: a type-1 non-uniform FFT of Eq. 8 up to 512 samples (grid of 2 N_s
+    points, width-8 kernel), the direct FP32 recurrence kernel above; both far inside 1e-4."""
     wl = sphere_scene(G=64, distance=2.0, n_samples=ns)
     ref, _, _ = oracle_cube(wl)
     _, paths = gpu_trace(sbr, wl)
@@ -91,6 +91,25 @@ def test_tensor_core_sample_counts(sbr, ns):
     e_split = rel_l2(cube, ref)
     e_fp64 = rel_l2(cube_complex(sbr.synthesize(paths, wl.radar, sbr.PHASE_FP64)), ref)
     assert e_split <= 1e-5 and e_fp64 <= 1e-5, (e_split, e_fp64)
+
+
+@pytest.mark.parametrize("ns", [256, 512])
+def test_direct_tensor_core_path(sbr, ns):
+    """The term-by-term tensor-core evaluation (fp16x3 mma.sync on n = 16 a + b), which the
+    allocation-free entry point runs for 256 and 512 samples, against the oracle."""
+    import ctypes
+    from paper_2311_13182_gb300 import _lib, sim
+    wl = sphere_scene(G=64, distance=2.0, n_samples=ns)
+    ref, _, _ = oracle_cube(wl)
+    _, paths = gpu_trace(sbr, wl)
+    out = torch.empty((wl.radar.n_virt, wl.radar.n_chirps, ns, 2), device="cuda")
+    r = sim.radar_struct(wl.radar)
+    st = _lib.load().sbr_synthesize_noalloc(ctypes.byref(paths.s), ctypes.byref(r), int(sbr.PHASE_SPLIT),
+                                            ctypes.c_void_p(out.data_ptr()),
+                                            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    assert rel_l2(cube_complex(out), ref) <= 1e-5
 
 
 def test_no_paths_gives_zero_cube(sbr):
