@@ -35,6 +35,7 @@
 // Every path adds per-CTA partial sums that a second kernel adds in a fixed
 // order, so the result is bitwise reproducible.
 #include <cuda_fp16.h>
+#include <limits.h>
 #include <math.h>
 
 #include <mutex>
@@ -519,13 +520,14 @@ __global__ void __launch_bounds__(256) k_synth_bwd(const float4* __restrict__ pr
 // about 2^-24 of one grid step.
 //
 // Each warp spreads into its own grid in shared memory (no atomics): its lanes
-// form four groups of w = 8, one path per group and one grid point per lane,
-// four consecutive paths per step.  Neighbouring rays sit at nearly the same
-// range: when the four paths share their grid cell, the groups' values are
-// added by shuffles (a fixed tree) and one group writes; when they touch the
-// same points otherwise, the groups write one after the other.  The warps'
-// grids are added in a fixed order, and the CTAs' grids by the finishing kernel
-// in a fixed order, so the result is bitwise reproducible.
+// form four groups of w = 8, one grid point per lane; each group takes eight
+// consecutive paths of the warp's batch of 32 in turn.  Neighbouring rays sit
+// at nearly the same range, so consecutive paths mostly share a grid cell: a
+// lane keeps the sum for its point of the current cell in registers and adds
+// it to the grid only when its group's cell changes (and at the end of the
+// batch), the flushing groups one after the other, as their cells may overlap.
+// The warps' grids are added in a fixed order, and the CTAs' grids by the
+// finishing kernel in a fixed order, so the result is bitwise reproducible.
 constexpr int kNuW = 8;             // kernel width in grid points
 constexpr int kNuWarps = 8;         // warps per CTA, one grid each
 constexpr int kNuThreads = 32 * kNuWarps;
@@ -598,52 +600,56 @@ __global__ void __launch_bounds__(kNuThreads) k_nufft_spread(const float4* __res
       }
     }
     const int nb = (int)min((int64_t)32, P - b * 32);
-    for (int st = 0; 4 * st < nb; ++st) {
-      const int src = 4 * st + grp;
+    // group grp takes paths 8 grp .. 8 grp + 7 in turn; a lane keeps the sum for its
+    // point of the current cell in registers and adds it to the grid when the cell changes
+    float ax = 0.f, ay = 0.f;
+    int cur = INT_MIN;
+    for (int st = 0; st < 8; ++st) {
+      const int src = 8 * grp + st;
       const bool live = src < nb;
-      float pr = __shfl_sync(0xffffffffu, cre, src), pi = __shfl_sync(0xffffffffu, cim, src);
+      const float pr = __shfl_sync(0xffffffffu, cre, src), pi = __shfl_sync(0xffffffffu, cim, src);
       const float pt = __shfl_sync(0xffffffffu, t, src);
       const int pl = __shfl_sync(0xffffffffu, i0, src);
-      const float z = (xo - pt) * (2.f / kNuW);
-      // psi = exp(beta (sqrt(1 - z^2) - 1)); |z| <= 1 on the 8 points
-      const float psi = ex2_approx(na.beta_l2e * (sqrt_approx(fmaxf(fmaf(-z, z, 1.f), 0.f)) - 1.f));
-      float cx = live ? psi * pr : 0.f, cy = live ? psi * pi : 0.f;
-      const int l = (pl + j - (kNuW / 2 - 1)) & (M - 1);
-      const int pl0 = __shfl_sync(0xffffffffu, pl, 0);  // group 0's path is always live
-      if (__all_sync(0xffffffffu, !live || pl == pl0)) {
-        // one cell for all four paths: add the groups' values (lane j of each group), group 0 writes
-        cx += __shfl_xor_sync(0xffffffffu, cx, 8);
-        cy += __shfl_xor_sync(0xffffffffu, cy, 8);
-        cx += __shfl_xor_sync(0xffffffffu, cx, 16);
-        cy += __shfl_xor_sync(0xffffffffu, cy, 16);
-        if (grp == 0) {
-          float2 o = g[l];
-          o.x += cx;
-          o.y += cy;
-          g[l] = o;
-        }
-      } else {
-        const unsigned same = __match_any_sync(0xffffffffu, live ? l : -1 - lane);
-        if (__all_sync(0xffffffffu, __popc(same) == 1)) {
-          if (live) {
-            float2 o = g[l];
-            o.x += cx;
-            o.y += cy;
-            g[l] = o;
+      const bool flush = live && pl != cur && cur != INT_MIN;
+      unsigned fg = __ballot_sync(0xffffffffu, flush) & 0x01010101u;  // lane 8 g flags group g
+      if (fg) {  // the flushing groups in turn: their cells may overlap
+        const int lc = (cur + j - (kNuW / 2 - 1)) & (M - 1);
+        do {
+          const int gg = (__ffs(fg) - 1) >> 3;
+          if (grp == gg) {
+            float2 o = g[lc];
+            o.x += ax;
+            o.y += ay;
+            g[lc] = o;
           }
-        } else {  // two groups share a point: the groups in turn
-          for (int gg = 0; gg < 4; ++gg) {
-            if (grp == gg && live) {
-              float2 o = g[l];
-              o.x += cx;
-              o.y += cy;
-              g[l] = o;
-            }
-            __syncwarp();
-          }
-        }
+          __syncwarp();
+          fg &= fg - 1;
+        } while (fg);
       }
-      __syncwarp();
+      if (live && pl != cur) {
+        ax = 0.f;
+        ay = 0.f;
+        cur = pl;
+      }
+      if (live) {
+        const float z = (xo - pt) * (2.f / kNuW);
+        // psi = exp(beta (sqrt(1 - z^2) - 1)); |z| <= 1 on the 8 points
+        const float psi = ex2_approx(na.beta_l2e * (sqrt_approx(fmaxf(fmaf(-z, z, 1.f), 0.f)) - 1.f));
+        ax = fmaf(psi, pr, ax);
+        ay = fmaf(psi, pi, ay);
+      }
+    }
+    {  // the last cells
+      const int lc = (cur + j - (kNuW / 2 - 1)) & (M - 1);
+      for (int gg = 0; gg < 4; ++gg) {
+        if (grp == gg && cur != INT_MIN) {
+          float2 o = g[lc];
+          o.x += ax;
+          o.y += ay;
+          g[lc] = o;
+        }
+        __syncwarp();
+      }
     }
   }
   __syncthreads();
