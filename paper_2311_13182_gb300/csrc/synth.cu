@@ -558,8 +558,8 @@ struct PsiQuad {
   float wpsi[kNuQuad];
 };
 
-// CTA (v, q) spreads antenna v; the warps of the Q CTAs take batches of 32
-// consecutive paths in turn.  Writes the CTA's grid: grids[(q V + v) M + l].
+// CTA (v, q) spreads antenna v; the warps of the Q CTAs take contiguous ranges
+// of batches of 32 paths.  Writes the CTA's grid: grids[(q V + v) M + l].
 __global__ void __launch_bounds__(kNuThreads) k_nufft_spread(const float4* __restrict__ prep, int64_t cap,
                                                             const int32_t* __restrict__ d_P, int V, int Q,
                                                             NufftArg na, float2* __restrict__ grids) {
@@ -573,7 +573,13 @@ __global__ void __launch_bounds__(kNuThreads) k_nufft_spread(const float4* __res
   const int64_t P = *d_P;
   const float4* pv = prep + (size_t)v * cap;
   const float xo = (float)(j - (kNuW / 2 - 1));  // this lane's grid point minus floor(u), before t
-  for (int64_t b = (int64_t)q * kNuWarps + warp; b * 32 < P; b += (int64_t)Q * kNuWarps) {
+  // each warp takes a contiguous range of batches of 32 paths, so that a group's
+  // register sums carry over from one batch to the next (neighbouring rays)
+  const int64_t nbat = (P + 31) / 32, nw = (int64_t)Q * kNuWarps, wi = (int64_t)q * kNuWarps + warp;
+  const int64_t b0 = nbat * wi / nw, b1 = nbat * (wi + 1) / nw;
+  float ax = 0.f, ay = 0.f;
+  int cur = INT_MIN;
+  for (int64_t b = b0; b < b1; ++b) {
     const int64_t p = b * 32 + lane;  // lane prepares path p
     float cre = 0.f, cim = 0.f, t = 0.f;
     int i0 = 0;
@@ -602,8 +608,6 @@ __global__ void __launch_bounds__(kNuThreads) k_nufft_spread(const float4* __res
     const int nb = (int)min((int64_t)32, P - b * 32);
     // group grp takes paths 8 grp .. 8 grp + 7 in turn; a lane keeps the sum for its
     // point of the current cell in registers and adds it to the grid when the cell changes
-    float ax = 0.f, ay = 0.f;
-    int cur = INT_MIN;
     for (int st = 0; st < 8; ++st) {
       const int src = 8 * grp + st;
       const bool live = src < nb;
@@ -639,17 +643,17 @@ __global__ void __launch_bounds__(kNuThreads) k_nufft_spread(const float4* __res
         ay = fmaf(psi, pi, ay);
       }
     }
-    {  // the last cells
-      const int lc = (cur + j - (kNuW / 2 - 1)) & (M - 1);
-      for (int gg = 0; gg < 4; ++gg) {
-        if (grp == gg && cur != INT_MIN) {
-          float2 o = g[lc];
-          o.x += ax;
-          o.y += ay;
-          g[lc] = o;
-        }
-        __syncwarp();
+  }
+  {  // the last cells
+    const int lc = (cur + j - (kNuW / 2 - 1)) & (M - 1);
+    for (int gg = 0; gg < 4; ++gg) {
+      if (grp == gg && cur != INT_MIN) {
+        float2 o = g[lc];
+        o.x += ax;
+        o.y += ay;
+        g[lc] = o;
       }
+      __syncwarp();
     }
   }
   __syncthreads();
