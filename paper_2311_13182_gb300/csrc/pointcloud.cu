@@ -122,17 +122,21 @@ __global__ void __launch_bounds__(256) k_angle_power(const float2* __restrict__ 
       sx[i] = X[((size_t)v * C + d) * Ns + k0 + q];
     }
     __syncthreads();
+    // antenna outer, angles inner: each x value is read once per Doppler bin
+    float yr[APT], yi[APT];
 #pragma unroll
-    for (int i = 0; i < APT; ++i) {
-      const int a = ag * APT + i;
-      float yr = 0.f, yi = 0.f;
-      for (int v = 0; v < V; ++v) {
-        const float2 w = sw[a * V + v], x = sx[v * kKT + kk];
-        yr = fmaf(w.x, x.x, fmaf(-w.y, x.y, yr));
-        yi = fmaf(w.x, x.y, fmaf(w.y, x.x, yi));
+    for (int i = 0; i < APT; ++i) yr[i] = yi[i] = 0.f;
+    for (int v = 0; v < V; ++v) {
+      const float2 x = sx[v * kKT + kk];
+#pragma unroll
+      for (int i = 0; i < APT; ++i) {
+        const float2 w = sw[(ag * APT + i) * V + v];
+        yr[i] = fmaf(w.x, x.x, fmaf(-w.y, x.y, yr[i]));
+        yi[i] = fmaf(w.x, x.y, fmaf(w.y, x.x, yi[i]));
       }
-      acc[i] = fmaf(yr, yr, fmaf(yi, yi, acc[i]));
     }
+#pragma unroll
+    for (int i = 0; i < APT; ++i) acc[i] = fmaf(yr[i], yr[i], fmaf(yi[i], yi[i], acc[i]));
   }
 #pragma unroll
   for (int i = 0; i < APT; ++i) part[((size_t)g * A + ag * APT + i) * Ns + k0 + kk] = acc[i];
