@@ -240,8 +240,10 @@ sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg* radar,
  * a fixed memory budget.  This entry point takes no workspace: its per-CTA
  * partial sums live in one file-scope device array of 1 MiB (131072 complex
  * FP32 values) that every GPU which loads the library keeps until the process
- * exits.  Same inputs, outputs and result as sbr_synthesize (up to summation
- * order: fewer CTAs may share the work), with these limits:
+ * exits.  Same inputs and outputs as sbr_synthesize; it always sums Eq. 8 term
+ * by term (for SBR_PHASE_SPLIT with 256 or 512 samples as an fp16x3 tensor-core
+ * GEMM over the paths), where sbr_synthesize evaluates the split mode up to 512
+ * samples as a non-uniform FFT: the two agree to about 1e-6 relative.  Limits:
  *  - n_virt * n_samples must not exceed 131072, otherwise SBR_ERR_UNSUPPORTED
  *    is returned before anything is enqueued;
  *  - the first call on each device looks up the array's device address
