@@ -32,8 +32,8 @@
 // step e^{j 2 pi delta} (4 FP32 multiply/FMA per sample instead of two
 // transcendental ops).
 //
-// Every path adds per-CTA partial sums that a second kernel adds in a fixed
-// order, so the result is bitwise reproducible.
+// Every evaluation writes per-CTA partial sums (or grids) that a second kernel
+// adds in a fixed order, so the result is bitwise reproducible.
 #include <cuda_fp16.h>
 #include <limits.h>
 #include <math.h>
@@ -524,8 +524,9 @@ __global__ void __launch_bounds__(256) k_synth_bwd(const float4* __restrict__ pr
 // consecutive paths of the warp's batch of 32 in turn.  Neighbouring rays sit
 // at nearly the same range, so consecutive paths mostly share a grid cell: a
 // lane keeps the sum for its point of the current cell in registers and adds
-// it to the grid only when its group's cell changes (and at the end of the
-// batch), the flushing groups one after the other, as their cells may overlap.
+// it to the grid only when its group's cell changes (and once after the warp's
+// last batch), the flushing groups one after the other, as their cells may
+// overlap.
 // The warps' grids are added in a fixed order, and the CTAs' grids by the
 // finishing kernel in a fixed order, so the result is bitwise reproducible.
 constexpr int kNuW = 8;             // kernel width in grid points

@@ -1,8 +1,9 @@
 // Ray tracing with specular bounces (Section 3.2.1, Eq. 2-3) and path preparation.
 //
 // One thread per ray.  The ray is carried in float-float (ff.cuh): its FP32 hi
-// parts drive a stack traversal of the LBVH (64-B nodes as four float4 loads,
-// triangles as three float4 loads) with the Moller-Trumbore (1997) test.  Every
+// parts drive a stack traversal of the 4-wide BVH collapsed from the LBVH (a
+// node's four child boxes and links as seven float4 loads, triangles as three
+// float4 loads) with the Moller-Trumbore (1997) test.  Every
 // FP32 decision carries a forward error bound: a triangle is accepted or
 // rejected in FP32 only when the bound says exact arithmetic on the exact ray
 // would decide the same; otherwise the test is repeated in float-float

@@ -2,7 +2,7 @@
 
 A forward step (LBVH build of the current vertices, trace and path preparation
 (Section 3.2.1, Eq. 2-3), synthesis (Section 3.2.2, Eq. 8), point cloud (the map
-T of Section 3.4)) is about twenty-five kernel launches and memsets on fixed
+T of Section 3.4)) is about twenty kernel launches and memsets on fixed
 buffers.  ``Forward`` captures the sequence once and replays it, so a step costs
 one graph launch on the host and no gaps between dependent kernels on the GPU.
 New vertex positions of the same topology are written into ``verts`` between
