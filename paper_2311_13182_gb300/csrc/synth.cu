@@ -563,8 +563,10 @@ struct PsiQuad {
 // of batches of 32 paths.  Writes the CTA's grid: grids[(q V + v) M + l].
 __global__ void __launch_bounds__(kNuThreads) k_nufft_spread(const float4* __restrict__ prep, int64_t cap,
                                                             const int32_t* __restrict__ d_P, int V, int Q,
-                                                            NufftArg na, float2* __restrict__ grids) {
+                                                            NufftArg na, float2* __restrict__ grids,
+                                                            unsigned int* __restrict__ fin_cnt) {
   extern __shared__ float2 wgrid[];  // [warp][M]
+  if (blockIdx.x == 0 && threadIdx.x < V) fin_cnt[threadIdx.x] = 0u;  // the finishing kernel's counters
   const int M = 1 << na.log_m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 3, j = lane & 7;
   float2* g = wgrid + (size_t)warp * M;
@@ -670,20 +672,27 @@ __global__ void __launch_bounds__(kNuThreads) k_nufft_spread(const float4* __res
   }
 }
 
-// One CTA of kNuFinThreads per antenna: the CTAs' grids added in a fixed order
-// (kNuFinThreads / M threads per grid point, each over every (kNuFinThreads / M)-th
-// CTA with four interleaved sums, then the threads' sums in order), the M-point
-// FFT, the division by Psi(n'/M); writes S[v][n] (one chirp).
+// Finishing, kNuFinSlice grid points per CTA: CTA (v, s) adds slice s of the Q
+// CTAs' grids of antenna v in a fixed order (kNuFinThreads / slice threads per
+// point, each over every such CTA with four interleaved sums, then the threads'
+// sums in order) into bsum; the last CTA of the antenna to finish (a counter per
+// antenna, zeroed by the spreading kernel) runs the M-point FFT and the division
+// by Psi(n'/M) and writes S[v][n] (one chirp).
 constexpr int kNuFinThreads = 1024;
+constexpr int kNuFinSlice = 128;
 __global__ void __launch_bounds__(kNuFinThreads) k_nufft_finish(const float2* __restrict__ grids, int V, int Q,
                                                                 int Ns, int log_m, PsiQuad pq,
+                                                                float2* __restrict__ bsum,
+                                                                unsigned int* __restrict__ cnt,
                                                                 float2* __restrict__ samples) {
   extern __shared__ float2 sg[];  // [M] grid, [M / 2] twiddles, [kNuFinThreads] per-thread sums
-  const int M = 1 << log_m, v = blockIdx.x;
+  __shared__ int s_last;
+  const int M = 1 << log_m, slice = M < kNuFinSlice ? M : kNuFinSlice, S = M / slice;
+  const int v = blockIdx.x / S, sl = blockIdx.x - v * S;
   float2* tw = sg + M;
   float2* part = tw + M / 2;
-  fft::fill_twiddles(tw, M, 1.f, blockDim.x, threadIdx.x);
-  const int parts = blockDim.x >> log_m, l = threadIdx.x & (M - 1), k0 = threadIdx.x >> log_m;
+  const int parts = blockDim.x / slice, li = threadIdx.x % slice, k0 = threadIdx.x / slice;
+  const int l = sl * slice + li;
   float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
   const float2* src = grids + (size_t)v * M + l;
   const size_t qs = (size_t)V * M;  // from one CTA's grid to the next
@@ -707,14 +716,22 @@ __global__ void __launch_bounds__(kNuFinThreads) k_nufft_finish(const float2* __
   }
   part[threadIdx.x] = make_float2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
   __syncthreads();
-  if (threadIdx.x < M) {
-    float2 acc = part[l];
+  if (threadIdx.x < slice) {
+    float2 acc = part[li];
     for (int k = 1; k < parts; ++k) {
-      acc.x += part[k * M + l].x;
-      acc.y += part[k * M + l].y;
+      acc.x += part[k * slice + li].x;
+      acc.y += part[k * slice + li].y;
     }
-    sg[fft::bitrev(l, log_m)] = acc;
+    bsum[(size_t)v * M + l] = acc;
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&cnt[v], 1u) == (unsigned)(S - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  fft::fill_twiddles(tw, M, 1.f, blockDim.x, threadIdx.x);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) sg[fft::bitrev(i, log_m)] = __ldcg(&bsum[(size_t)v * M + i]);
   __syncthreads();
   fft::smem_fft(sg, tw, log_m, blockDim.x, threadIdx.x);
   const int h = Ns >> 1;
@@ -875,6 +892,8 @@ size_t ws_layout(const sbr_radar_cfg* radar, int64_t cap, int* Q, int* Qn = null
   c.take<float2>((size_t)V * Ns);              // chirp-summed upstream gradient
   c.take<float2>((size_t)V * qn * 2 * Ns);     // non-uniform FFT: the CTAs' grids
   c.take<float2>((size_t)V * Ns);              // non-uniform FFT: samples of one chirp
+  c.take<float2>((size_t)V * 2 * Ns);          // non-uniform FFT: the summed grids
+  c.take<unsigned int>((size_t)V);             // non-uniform FFT: finishing counters
   return c.bytes();
 }
 
@@ -895,6 +914,8 @@ struct SynthWs {
   float2* gsum;
   float2* grids;
   float2* samples;
+  float2* bsum;
+  unsigned int* fin_cnt;
   int Q, Qn;
 };
 
@@ -913,6 +934,8 @@ sbr_status bind_ws(const sbr_radar_cfg* radar, int64_t cap, void* ws, size_t byt
   w->gsum = c.take<float2>((size_t)V * Ns);
   w->grids = c.take<float2>((size_t)V * Qn * 2 * Ns);
   w->samples = c.take<float2>((size_t)V * Ns);
+  w->bsum = c.take<float2>((size_t)V * 2 * Ns);
+  w->fin_cnt = c.take<unsigned int>((size_t)V);
   w->Q = Q;
   w->Qn = Qn;
   return SBR_OK;
@@ -927,10 +950,12 @@ void launch_nufft(const sbr_paths* p, const sbr_radar_cfg* r, const SynthWs& w, 
   nufft_per_sm(Ns);  // sets the shared-memory limit before the first launch
   ::sbr::note_launch();
   k_nufft_spread<<<V * w.Qn, kNuThreads, nufft_smem(Ns), st>>>(reinterpret_cast<const float4*>(p->prep),
-                                                               p->path_cap, p->count, V, w.Qn, na, w.grids);
+                                                               p->path_cap, p->count, V, w.Qn, na, w.grids,
+                                                               w.fin_cnt);
+  const int M = 2 * Ns, slices = M < kNuFinSlice ? 1 : M / kNuFinSlice;
   ::sbr::note_launch();
-  k_nufft_finish<<<V, kNuFinThreads, sizeof(float2) * (3 * (size_t)Ns + kNuFinThreads), st>>>(
-      w.grids, V, w.Qn, Ns, log_m, psi_quad(), w.samples);
+  k_nufft_finish<<<V * slices, kNuFinThreads, sizeof(float2) * (3 * (size_t)Ns + kNuFinThreads), st>>>(
+      w.grids, V, w.Qn, Ns, log_m, psi_quad(), w.bsum, w.fin_cnt, w.samples);
   ::sbr::note_launch();
   k_reduce<<<reduce_grid(V, Ns, r->n_chirps), 256, 0, st>>>(w.samples, V, 1, Ns, r->n_chirps, cube);
 }
