@@ -418,3 +418,208 @@ def test_chamfer_and_laplacian_definitions():
     # icosphere: every vertex sits off its ring centroid by the same radial amount pattern (> 0)
     vi, fi = icosphere(1, 1.0)
     assert pc.laplacian(vi, fi) > 0
+
+
+# --------------------------------------------------------------------------
+# Pins of the frozen-structure evaluator, the loss terms, the multi-bounce
+# cos term and the soft-detection weight
+# --------------------------------------------------------------------------
+
+def test_trace_frozen_reproduces_trace():
+    """With unmoved vertices, re-evaluating a trace's rays on their recorded triangles
+    (plane intersection + specular reflection, Section 3.2.1) gives the brute-force
+    trace's hits, normals, incident directions and t: a slip in the plane test or in the
+    reflection update of ``trace_frozen`` (the FD reference of every adjoint) fails here."""
+    C = np.array([0.25, 0.125, 2.0])
+    v, f = corner_reflector(C, 0.75)
+    grid = axis_grid(40, 0.12, axis=C)
+    cases = [(v, f, grid, 3)]
+    vp, fp = square((-2.0, -1.5, 1.25), (4.0, 0, 0.5), (0, 3.0, 0.25))      # tilted plate
+    cases.append((vp, fp, axis_grid(24, 0.3), 2))
+    for vv, ff, gg, K in cases:
+        tr = oracle.trace(vv, ff, gg, K)
+        fr = oracle.trace_frozen(vv, ff, tr, gg)
+        ok = tr["tri"] >= 0
+        assert ok.sum() > 100
+        np.testing.assert_allclose(fr["hit"][ok], tr["hit"][ok], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(fr["nrm"][ok], tr["nrm"][ok], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(fr["din"][ok], tr["din"][ok], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(fr["tuv"][ok][:, 0], tr["tuv"][ok][:, 0], rtol=1e-12)
+
+
+def test_trace_frozen_moved_plate_closed_form():
+    """Frozen triangle sequence, moved geometry: a plate traced at z = D and then
+    translated to z = D' is hit at t = D' / cos(psi); rotated about the x axis through
+    (0, 0, D) it is hit on the plane n.(x - p0) = 0 with t = n.p0 / n.d and the ray
+    leaves along d - 2 (d.n) n."""
+    D, D2 = 1.25, 1.5
+    v, f = square((-2.0, -2.0, D), (4.0, 0, 0), (0, 4.0, 0))
+    grid = axis_grid(20, 0.3)
+    tr = oracle.trace(v, f, grid, 2)
+    assert (tr["tri"][:, 0] >= 0).all()
+    d = tr["din"][:, 0]
+    v2 = v.astype(np.float64).copy()
+    v2[:, 2] = D2
+    fr = oracle.trace_frozen(v2, f, tr, grid)
+    np.testing.assert_allclose(fr["tuv"][:, 0, 0], D2 / d[:, 2], rtol=1e-13)
+    np.testing.assert_allclose(fr["hit"][:, 0], D2 * d / d[:, 2:3], rtol=0, atol=1e-13)
+    # rotation by 0.2 rad about the x axis through p0 = (0, 0, D)
+    a = 0.2
+    p0 = np.array([0.0, 0.0, D])
+    Rx = np.array([[1, 0, 0], [0, math.cos(a), -math.sin(a)], [0, math.sin(a), math.cos(a)]])
+    v3 = (v.astype(np.float64) - p0) @ Rx.T + p0
+    n = Rx @ np.array([0.0, 0.0, 1.0])
+    fr = oracle.trace_frozen(v3, f, tr, grid)
+    t = (p0 @ n) / (d @ n)
+    np.testing.assert_allclose(fr["tuv"][:, 0, 0], t, rtol=1e-12)
+    np.testing.assert_allclose(fr["hit"][:, 0], t[:, None] * d, atol=1e-12)
+    np.testing.assert_allclose(np.abs(fr["nrm"][:, 0] @ n), 1.0, rtol=1e-14)
+    out = d - 2 * (d @ n)[:, None] * n
+    np.testing.assert_allclose(fr["din"][:, 1], out, atol=1e-12)
+
+
+def test_chamfer_loss_hand_computed():
+    """Weighted squared Chamfer of two hand-built point sets (Eq. 14 objective term):
+    nearest neighbours found by inspection, sums typed out; the frozen-assignment path
+    uses the given pairs instead.  Catches swapped weights, a missing normalisation or a
+    non-squared distance."""
+    P = np.array([[0, 0, 0, 1.0], [2, 0, 0, 2.0], [0, 4, 0, 0.5]])
+    Q = np.array([[0, 0, 1, 1.0], [2, 1, 0, 3.0]])
+    # P -> Q: P1->Q1 (1), P2->Q2 (1), P3->Q2 (4 + 9 = 13);  Q -> P: Q1->P1 (1), Q2->P2 (1)
+    ref = (1 * 1 + 2 * 1 + 0.5 * 13) / 3.5 + (1 * 1 + 3 * 1) / 4.0
+    assert pc.chamfer_loss(P, Q) == pytest.approx(ref, rel=1e-15)
+    # frozen pairs P1->Q2 (5), P2->Q2 (1), P3->Q1 (17); Q1->P2 (5), Q2->P1 (5)
+    ref_frozen = (1 * 5 + 2 * 1 + 0.5 * 17) / 3.5 + (1 * 5 + 3 * 5) / 4.0
+    got = pc.chamfer_loss(P, Q, nn_pq=np.array([1, 1, 0]), nn_qp=np.array([1, 0]))
+    assert got == pytest.approx(ref_frozen, rel=1e-15)
+    # parity metric: the non-squared weighted mean distances, averaged
+    par = 0.5 * ((1 * 1 + 2 * 1 + 0.5 * math.sqrt(13)) / 3.5 + (1 * 1 + 3 * 1) / 4.0)
+    assert pc.chamfer_parity(P, Q) == pytest.approx(par, rel=1e-15)
+
+
+def test_laplacian_closed_forms():
+    """Uniform Laplacian mean_i |v_i - mean N(v_i)|^2: an octahedron with vertices +-R
+    on the axes gives exactly R^2 (every vertex's four neighbours average to the
+    origin); a tetrahedron gives mean_i |4 v_i - S|^2 / 9 (S = sum of vertices); a
+    square pyramid against neighbour lists typed by hand."""
+    R = 0.37
+    v = np.array([[R, 0, 0], [-R, 0, 0], [0, R, 0], [0, -R, 0], [0, 0, R], [0, 0, -R]])
+    f = np.array([[0, 2, 4], [2, 1, 4], [1, 3, 4], [3, 0, 4],
+                  [2, 0, 5], [1, 2, 5], [3, 1, 5], [0, 3, 5]])
+    assert pc.laplacian(v, f) == pytest.approx(R * R, rel=1e-14)
+    rng = np.random.default_rng(4)
+    t = rng.normal(size=(4, 3))
+    ft = np.array([[0, 1, 2], [0, 3, 1], [1, 3, 2], [0, 2, 3]])
+    S = t.sum(0)
+    ref = np.mean([((4 * t[i] - S) ** 2).sum() / 9.0 for i in range(4)])
+    assert pc.laplacian(t, ft) == pytest.approx(ref, rel=1e-13)
+    # square pyramid: apex 4 over base 0-1-2-3, base split along the diagonal 0-2
+    p = rng.normal(size=(5, 3))
+    fp = np.array([[0, 1, 2], [0, 2, 3], [0, 1, 4], [1, 2, 4], [2, 3, 4], [3, 0, 4]])
+    nb = {0: [1, 2, 3, 4], 1: [0, 2, 4], 2: [0, 1, 3, 4], 3: [0, 2, 4], 4: [0, 1, 2, 3]}
+    ref = np.mean([((p[i] - p[nb[i]].mean(0)) ** 2).sum() for i in range(5)])
+    assert pc.laplacian(p, fp) == pytest.approx(ref, rel=1e-13)
+
+
+def test_multibounce_amplitude_cos_term():
+    """On the trihedral every plate is normal to a coordinate axis and a reflection only
+    flips the sign of one component of d, so the cos term |d_k . n_k| of Eq. 1 at
+    interaction k equals |d_1| along that plate's axis.  The amplitude of every path is
+    then omega (-1)^(k-1) |d_1[axis_k]| / (4 pi L_in L_out) with the legs measured from
+    the recorded hit points: using d_1 . n_k, d_k of another bounce or the wrong sign
+    fails here."""
+    C = np.array([0.25, 0.125, 2.0])
+    v, f = corner_reflector(C, 0.75)
+    axis_of_tri = np.array([2, 2, 0, 0, 1, 1])           # plates z = cz, x = cx, y = cy
+    grid = axis_grid(40, 0.12, axis=C)
+    tr = oracle.trace(v, f, grid, 3)
+    radar = radar_mimo_3x4(256, 1)
+    radar.rx = radar.rx + np.array([0.0, 0.004, 0.0])    # receivers off the launch point
+    pa = oracle.paths(tr, radar)
+    ray, k = pa["ray"], pa["bounce"]
+    h = tr["hit"]
+    d1 = tr["din"][ray, 0]
+    cos = np.abs(d1[np.arange(ray.size), axis_of_tri[tr["tri"][ray, k]]])
+    seg = [np.zeros(ray.size)]
+    for j in range(1, 3):
+        seg.append(np.where(k >= j, np.linalg.norm(h[ray, j] - h[ray, j - 1], axis=1), 0.0))
+    interior = seg[0] + seg[1] + seg[2]
+    counts = np.bincount(k, minlength=3)
+    assert counts[1] > 50 and counts[2] > 50
+    for t in range(radar.n_tx):
+        lin = np.linalg.norm(h[ray, 0] - radar.tx[t], axis=1) + interior
+        for r in range(radar.n_rx):
+            vv = t * radar.n_rx + r
+            lout = np.linalg.norm(radar.rx[r] - h[ray, k], axis=1)
+            ref = tr["omega"][ray] * (-1.0) ** k * cos / (4 * np.pi * lin * lout)
+            np.testing.assert_allclose(pa["amp"][vv], ref, rtol=1e-12)
+            np.testing.assert_allclose(pa["tau"][vv] * C_LIGHT, lin + lout, rtol=1e-14)
+
+
+def test_soft_weight_formula():
+    """Soft CA-CFAR weight w = sigmoid((ln Pw - ln(alpha N + P_floor)) / beta) with
+    alpha = 10^(12/10), beta = 0.5, P_floor = 1e-4 max Pw, on a flat floor F with one
+    spike S: the training cells of the spike see only the floor (N = F); a cell five
+    bins away has the spike among its 16 training cells (N = (15 F + S) / 16).  The
+    spike's point sits at the bin centre (the parabola through a symmetric peak has
+    its vertex there): r = k c / (2B), u = -1 + 2a/64."""
+    A, Nr = 64, 256
+    F, S = 1.0, 30.0
+    a0, k0 = 20, 100
+    Pw = np.full((A, Nr), F)
+    Pw[a0, k0] = S
+    radar = radar_single_tx(Nr, 1)
+    cfg = pc.CfarConfig()
+    alpha, beta, floor = 10 ** 1.2, 0.5, 1e-4 * S
+    sig = lambda z: 1.0 / (1.0 + math.exp(-z))
+    pts = pc.points_at(Pw, radar, cfg, np.array([a0, a0, 7]), np.array([k0, k0 + 5, 40]))
+    w_ref = [sig((math.log(S) - math.log(alpha * F + floor)) / beta),
+             sig((math.log(F) - math.log(alpha * (15 * F + S) / 16 + floor)) / beta),
+             sig((math.log(F) - math.log(alpha * F + floor)) / beta)]
+    np.testing.assert_allclose(pts[:, 3], w_ref, rtol=1e-13)
+    assert 0.5 < pts[0, 3] < 0.9                          # the weight is not saturated
+    r = k0 * C_LIGHT / (2 * radar.bandwidth)
+    u = -1 + 2 * a0 / 64
+    np.testing.assert_allclose(pts[0, :3], [r * u, 0.0, r * math.sqrt(1 - u * u)], rtol=1e-14)
+
+
+def test_wedge_second_bounce_cos_term():
+    """Two plates through the line x = 0, z = 2 (parallel to y), opening 60 degrees
+    toward the radar.  In the xz plane a specular reflection off a plate whose trace has
+    angle phi maps a direction's angle psi to 2 phi - psi and keeps |d_xz| and d_y, so
+    the cos term of the second interaction is |d_xz| |cos(2 phi_first - psi_1 -
+    angle(n_second))|, generally not |d_1 . n_second|: the amplitude of every 2-bounce
+    path pins the use of d_k (not d_1) in |d_k . n_k|."""
+    E = np.array([0.0, -1.0, 2.0])
+    uA = np.array([-0.5, 0.0, -0.875])
+    uB = np.array([0.5, 0.0, -0.875])
+    a = square(E, (0, 2.0, 0), uA)
+    b = square(E, (0, 2.0, 0), uB)
+    v, f = merge_meshes(a, b)
+    plate = np.array([0, 0, 1, 1])
+    phi = np.array([math.atan2(uA[2], uA[0]), math.atan2(uB[2], uB[0])])   # plate traces
+    nang = phi - math.pi / 2                                                # normal angles
+    grid = axis_grid(48, 0.3)
+    tr = oracle.trace(v, f, grid, 2)
+    radar = radar_single_tx(256, 1)
+    pa = oracle.paths(tr, radar)
+    ray, k = pa["ray"], pa["bounce"]
+    d1 = tr["din"][ray, 0]
+    m = np.hypot(d1[:, 0], d1[:, 2])
+    psi1 = np.arctan2(d1[:, 2], d1[:, 0])
+    first = plate[tr["tri"][ray, 0]]
+    here = plate[tr["tri"][ray, k]]
+    psi = np.where(k == 0, psi1, 2 * phi[first] - psi1)
+    cos = m * np.abs(np.cos(psi - nang[here]))
+    two = k == 1
+    assert two.sum() > 100
+    assert (np.abs(cos[two] - np.abs((d1[two] * np.stack([np.cos(nang[here[two]]), 0 * m[two],
+                                                         np.sin(nang[here[two]])], 1)).sum(1)))
+            > 0.05).mean() > 0.9                 # d_1 . n_k differs on these paths
+    h = tr["hit"]
+    lin = np.linalg.norm(h[ray, 0] - radar.tx[0], axis=1) + np.where(
+        two, np.linalg.norm(h[ray, 1] - h[ray, 0], axis=1), 0.0)
+    for r in range(radar.n_rx):
+        lout = np.linalg.norm(radar.rx[r] - h[ray, k], axis=1)
+        ref = tr["omega"][ray] * np.where(two, -1.0, 1.0) * cos / (4 * np.pi * lin * lout)
+        np.testing.assert_allclose(pa["amp"][r], ref, rtol=1e-9)
