@@ -50,11 +50,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recon", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the long-range precision sweep")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--write-traffic", metavar="NCU_CSV",
-                    help="write profiles/traffic.json from an ncu --csv log of dram__bytes_read.sum and "
-                         "dram__bytes_write.sum for the step's kernels, then exit")
+    ap.add_argument("--write-counters", metavar="NCU_CSV", nargs="+",
+                    help="write profiles/counters.json from ncu --csv logs (one capture per kernel) of "
+                         "dram__bytes_read.sum, dram__bytes_write.sum and smsp__inst_executed.sum, then exit")
     return ap.parse_args()
 
 
@@ -237,6 +238,7 @@ def gpu_arm(args, rank, world, local):
     roof, roofs = rooflines(stage_ms, wl, P, counts, peaks, src)
 
     recon = None if args.no_recon else recon_arm(sbr, torch, args)
+    sweep = None if args.no_sweep else precision_sweep_arm(sbr, torch, args)
     serve = None if args.no_serve else serve_arm(sbr, torch, args)
     out = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
@@ -253,6 +255,7 @@ def gpu_arm(args, rank, world, local):
         "recon_iters_per_s": None if recon is None else recon["iters_per_s"],
         "recon": recon,
         "serving": serve,
+        "precision_sweep": sweep,
         "e2e": e2e,
         "gpu_launches": launches,
         "wall_s_timed_region": t_wall,
@@ -308,115 +311,239 @@ def e2e_arm(sbr, torch, wl, cfg, args, world):
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
 
-# DRAM traffic per launch of each roofline stage, from one ncu capture (profiles/traffic.json);
-# used only while the library sources still hash to what was captured.
-TRAFFIC_STAGES = {
-    "trace": ("k_trace", "k_trace_coop", "k_tile_sums", "k_scan_single", "k_tile_scan", "k_prep"),
+# Counters per launch of each roofline stage (DRAM bytes, warp instructions), from ncu captures
+# of one kernel each (profiles/counters.json); used only while the library sources still hash to
+# what was captured.  Each kernel runs once per stage call.
+COUNTER_STAGES = {
+    "trace": ("k_trace", "k_trace_coop", "k_tile_sums", "k_scan_single", "k_tile_scan", "k_scan_small", "k_prep"),
     "synthesize": ("k_nufft_spread", "k_nufft_finish", "k_reduce"),
+    "pointcloud": ("k_fft_rows", "k_fft_cols", "k_angle_power", "k_angle_tc", "k_power_reduce", "k_detect",
+                   "k_select"),
 }
-
 
 # the sources each stage's kernels are compiled from
-TRAFFIC_SOURCES = {
+COUNTER_SOURCES = {
     "trace": ("trace.cu", "scan_sort.cu", "cta_sort.cuh", "scene.cuh", "ff.cuh", "common.cuh"),
     "synthesize": ("synth.cu", "fft.cuh", "common.cuh"),
+    "pointcloud": ("pointcloud.cu", "tcgen05.cuh", "fft.cuh", "cta_sort.cuh", "common.cuh"),
 }
+COUNTERS_FILE = os.path.join("profiles", "counters.json")
+COUNTER_METRICS = {"dram__bytes_read.sum": "dram", "dram__bytes_write.sum": "dram", "smsp__inst_executed.sum": "inst"}
 
 
 def sources_sha1(stage: str) -> str:
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2311_13182_gb300", "csrc")
-    for f in [os.path.join(csrc, n) for n in TRAFFIC_SOURCES[stage]] + [os.path.join(ROOT, "include", "sbr.h")]:
-        with open(f, "rb") as fh:
-            h.update(os.path.basename(f).encode() + fh.read())
+    for f in [os.path.join(csrc, n) for n in COUNTER_SOURCES[stage]] + [os.path.join(ROOT, "include", "sbr.h")]:
+        if os.path.exists(f):
+            with open(f, "rb") as fh:
+                h.update(os.path.basename(f).encode() + fh.read())
     return h.hexdigest()
 
 
-def write_traffic(csv_path: str):
-    """Per-launch DRAM bytes of each stage from an ncu CSV (the timed steps' launches)."""
+def _kernel_name(raw: str) -> str:
+    return raw.split("(")[0].split("::")[-1].split("<")[0].replace("void ", "").strip()
+
+
+def write_counters(csv_paths):
+    """Per-launch DRAM bytes and warp instructions of each stage from ncu --csv logs (one capture per
+    kernel): per kernel the mean over its captured launches, per stage the sum over its kernels."""
     import csv
-    with open(csv_path) as fh:
-        rows = list(csv.reader(fh))
-    head = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
-    hdr = rows[head]
-    ki, mi, vi, ui = (hdr.index("Kernel Name"), hdr.index("Metric Name"), hdr.index("Metric Value"),
-                      hdr.index("Metric Unit"))
-    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
-    per_kernel = {}
-    for r in rows[head + 1:]:
-        if len(r) <= vi or r[mi] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
-            continue
-        name = r[ki].split("(")[0].split("::")[-1].split("<")[0].replace("void ", "").strip()
-        per_kernel.setdefault(name, []).append(float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0))
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "inst": 1.0, "Kinst": 1e3, "Minst": 1e6,
+             "": 1.0}
+    per = {}  # kernel -> {launch id -> {"dram": x, "inst": y}}
+    for path in csv_paths:
+        with open(path) as fh:
+            rows = list(csv.reader(fh))
+        head = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
+        hdr = rows[head]
+        ii, ki, mi, vi, ui = (hdr.index("ID"), hdr.index("Kernel Name"), hdr.index("Metric Name"),
+                              hdr.index("Metric Value"), hdr.index("Metric Unit"))
+        for r in rows[head + 1:]:
+            if len(r) <= vi or r[mi] not in COUNTER_METRICS:
+                continue
+            k = _kernel_name(r[ki])
+            launch = per.setdefault(k, {}).setdefault((path, r[ii]), {"dram": 0.0, "inst": 0.0})
+            launch[COUNTER_METRICS[r[mi]]] += float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0)
+    kernels = {k: {"launches": len(v), "dram_bytes": sum(x["dram"] for x in v.values()) / len(v),
+                   "inst": sum(x["inst"] for x in v.values()) / len(v)} for k, v in per.items()}
     stages = {}
-    for st, names in TRAFFIC_STAGES.items():
-        # two metrics per launch: sum them, average over the launches of the stage's first kernel
-        n = max(1, len(per_kernel.get(names[0], [])) // 2)
-        total = sum(sum(per_kernel.get(k, [])) for k in names)
-        stages[st] = {"bytes_per_launch": total / n, "launches": n, "kernels": list(names),
-                      "sources_sha1": sources_sha1(st)}
-    out = {"stages": stages, "from": os.path.basename(csv_path)}
-    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
+    for st, names in COUNTER_STAGES.items():
+        got = [k for k in names if k in kernels]
+        if not got:
+            continue
+        stages[st] = {"dram_bytes_per_launch": sum(kernels[k]["dram_bytes"] for k in got),
+                      "inst_per_launch": sum(kernels[k]["inst"] for k in got),
+                      "kernels": got, "sources_sha1": sources_sha1(st)}
+    out = {"stages": stages, "kernels": kernels, "from": [os.path.basename(p) for p in csv_paths]}
+    with open(os.path.join(ROOT, COUNTERS_FILE), "w") as fh:
         json.dump(out, fh, indent=1)
     print(json.dumps(out))
 
 
-def measured_traffic() -> dict:
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+def measured_counters() -> dict:
     try:
-        with open(p) as fh:
+        with open(os.path.join(ROOT, COUNTERS_FILE)) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
         return {}
     return {st: v for st, v in d.get("stages", {}).items()
-            if st in TRAFFIC_SOURCES and v.get("sources_sha1") == sources_sha1(st)}
+            if st in COUNTER_SOURCES and v.get("sources_sha1") == sources_sha1(st)}
 
 
 def rooflines(stage_ms, wl, P, counts, peaks, src):
-    """Rooflines of the step's two large kernels; per-unit figures in the design doc.
+    """Rooflines of the step's two large stages, each against the bound that limits it.
 
-    trace (sbr_trace = k_trace + scan + k_prep, timed together): bytes a launch moves
-      4-wide BVH nodes fetched x 112 B + triangles tested x 48 B (counted by sbr_trace_counts)
-      + hit records 16 B + float-float hit data 32 B per ray-bounce slot + 8 B per ray
-      + per (path, antenna) the 16-B synthesis record and 8-B path length + 4 B per path,
-      against the measured HBM copy bandwidth (the working set is L2-resident, so this is
-      the bytes-served rate; `traffic` is the DRAM part, from ncu).
-    synthesis (k_nufft_spread + k_nufft_finish + k_reduce): Eq. 8 as a type-1 non-uniform
-      FFT, 8 grid updates per (path, antenna) and one 2 N_s-point FFT per antenna; counted as
-      terms (path, antenna, sample) per second against the FP32-pipe bound of the direct
-      per-sample sum (a two-term phasor recurrence and the accumulation: 4 FP32 lane-ops per
-      term, 152 SMs x 128 lanes x f_max / 4).  A fraction above 1 is the algorithm doing less
-      work than any term-by-term kernel; the 16-B records it streams are given against the
-      HBM copy rate beside it."""
+    Both stages are issue-bound (ncu: profiles/k_trace_*, profiles/k_nufft_spread_*), so `frac` is
+    issue slots used: warp instructions per call (smsp__inst_executed.sum, profiles/counters.json)
+    / (CUDA-event time x 152 SMs x 4 schedulers x f_max).  Beside it:
+    trace (sbr_trace = k_trace + k_trace_coop + scan + k_prep, timed together):
+      served: the algorithmic bytes of a call (4-wide nodes fetched x 112 B + triangles tested x 48 B,
+      both counted by sbr_trace_counts, + 48 B per ray-bounce slot + 8 B per ray + 24 B per (path,
+      antenna) + 4 B per path) per second against the HBM copy rate: the working set is L2-resident,
+      so these bytes are served mostly by L1/L2 (a bytes-served rate, not DRAM);
+      dram: the call's DRAM bytes (ncu) per second against the HBM copy rate.
+    synthesis (k_nufft_spread + k_nufft_finish + k_reduce; Eq. 8 as a type-1 non-uniform FFT):
+      dram as above; speedup_vs_direct_sum: Eq. 8 terms (path, antenna, sample) per second over the
+      FP32-pipe bound of a term-by-term kernel (152 SMs x 128 lanes x f_max / 4 lane-ops per term)."""
     V, Ns = wl.radar.n_virt, wl.radar.n_samples
     R, K = wl.grid.n_rays, wl.max_bounces
-    traffic = measured_traffic()
+    ctr = measured_counters()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    issue_peak = 152 * 4 * mhz * 1e6
+    hbm = float(peaks["hbm_gbs"])
+    issue_src = f"152 SMs x 4 schedulers x {mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json, {src})"
+
+    def issue(stage, t):
+        inst = ctr.get(stage, {}).get("inst_per_launch")
+        return (None, None) if inst is None else (inst / t, inst / t / issue_peak)
+
+    def dram(stage, t):
+        b = ctr.get(stage, {}).get("dram_bytes_per_launch")
+        return {"bytes_per_launch": b, "achieved_gbs": None if b is None else b / t / 1e9,
+                "frac_of_hbm": None if b is None else b / t / 1e9 / hbm}
+
     nodes, tris, trav = counts
     tb = nodes * 112 + tris * 48 + R * K * 48 + R * 8 + P * V * 24 + P * 4
-    t_ach = tb / (stage_ms["trace"] * 1e-3) / 1e9
-    hbm = float(peaks["hbm_gbs"])
-    trace = {"kernel": "k_trace (+ k_trace_coop, scan, k_prep)", "bound": "hbm", "achieved": t_ach, "peak": hbm, "unit": "GB/s",
-             "frac": t_ach / hbm, "traffic": traffic.get("trace", {}).get("bytes_per_launch"),
-             "bytes_per_launch": tb,
+    t_tr = stage_ms["trace"] * 1e-3
+    ach, frac = issue("trace", t_tr)
+    trace = {"kernel": "k_trace (+ k_trace_coop, scan, k_prep)", "bound": "alu", "limiter": "issue slots",
+             "achieved": ach, "peak": issue_peak, "unit": "warp-inst/s", "frac": frac,
+             "inst_per_launch": ctr.get("trace", {}).get("inst_per_launch"),
+             "traffic": ctr.get("trace", {}).get("dram_bytes_per_launch"),
+             "dram": dram("trace", t_tr),
+             "served": {"bytes_per_launch": tb, "achieved_gbs": tb / t_tr / 1e9, "frac_of_hbm": tb / t_tr / 1e9 / hbm,
+                        "note": "algorithmic bytes (nodes, triangles, records) per second: mostly L1/L2 hits"},
              "units": {"rays": R, "traversals": trav, "nodes": nodes, "triangles": tris, "paths": P},
-             "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({src}, burst copy)"}
+             "peak_source": issue_src, "hbm_peak_gbs": hbm}
     terms = P * V * Ns
-    t_syn = stage_ms["synthesize"] * 1e-3
-    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    t_sy = stage_ms["synthesize"] * 1e-3
+    ach, frac = issue("synthesize", t_sy)
     fp32_terms = 152 * 128 * mhz * 1e6 / 4
-    rec_bytes = P * V * 16
-    synth = {"kernel": "k_nufft_spread (+ k_nufft_finish, k_reduce)", "bound": "alu",
-             "achieved": terms / t_syn, "peak": fp32_terms, "unit": "terms/s", "frac": terms / t_syn / fp32_terms,
-             "traffic": traffic.get("synthesize", {}).get("bytes_per_launch"), "terms_per_launch": terms,
-             "grid_updates_per_launch": P * V * 8,
-             "records": {"bytes_per_launch": rec_bytes, "achieved_gbs": rec_bytes / t_syn / 1e9,
-                         "frac_of_hbm": rec_bytes / t_syn / 1e9 / float(peaks["hbm_gbs"])},
-             "note": "type-1 non-uniform FFT: 8 grid updates per path and antenna instead of N_s terms; "
-                     "peak = FP32-pipe bound of the direct per-sample sum (4 lane-ops per term)",
-             "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (MEASURED_PEAKS.json sm_max_mhz) / 4"}
+    rec = P * V * 16
+    synth = {"kernel": "k_nufft_spread (+ k_nufft_finish, k_reduce)", "bound": "alu", "limiter": "issue slots",
+             "achieved": ach, "peak": issue_peak, "unit": "warp-inst/s", "frac": frac,
+             "inst_per_launch": ctr.get("synthesize", {}).get("inst_per_launch"),
+             "traffic": ctr.get("synthesize", {}).get("dram_bytes_per_launch"),
+             "dram": dram("synthesize", t_sy),
+             "terms_per_launch": terms, "grid_updates_per_launch": P * V * 8,
+             "speedup_vs_direct_sum": {"terms_per_s": terms / t_sy, "direct_sum_bound_terms_per_s": fp32_terms,
+                                       "ratio": terms / t_sy / fp32_terms},
+             "records": {"bytes_per_launch": rec, "achieved_gbs": rec / t_sy / 1e9, "frac_of_hbm": rec / t_sy / 1e9 / hbm},
+             "peak_source": issue_src}
+    for r in (trace, synth):
+        if r["achieved"] is None:
+            # no instruction counts for these sources: report the bytes-served figure in their place
+            r.update(bound="hbm", limiter="bytes served (issue counters absent for these sources)",
+                     unit="GB/s", peak=hbm, peak_source=f"hbm_gbs of MEASURED_PEAKS.json ({src}, burst copy)")
+            if "served" in r:
+                r.update(achieved=r["served"]["achieved_gbs"], frac=r["served"]["frac_of_hbm"])
+            else:
+                r.update(achieved=r["records"]["achieved_gbs"], frac=r["records"]["frac_of_hbm"])
     dom = trace if stage_ms["trace"] >= stage_ms["synthesize"] else synth
     return dom, [trace, synth]
+
+
+def _chamfer_mm(P, Q):
+    """Weighted mean nearest-neighbour distance of point sets (x, y, z, w), both ways, averaged [mm]."""
+    if len(P) == 0 or len(Q) == 0:
+        return 0.0 if len(P) == len(Q) else float("inf")
+    d = np.sqrt(((P[:, None, :3] - Q[None, :, :3]) ** 2).sum(-1))
+    a = (P[:, 3] * d.min(1)).sum() / P[:, 3].sum()
+    b = (Q[:, 3] * d.min(0)).sum() / Q[:, 3].sum()
+    return float(500.0 * (a + b))
+
+
+def precision_sweep_arm(sbr, torch, args):
+    """Long-range precision sweep: the 320-triangle sphere (radius 0.2 m) centred 5, 10 and 20 m
+    out, 1024, 2048 and 4096 samples per chirp, 2048 x 2048 rays (4,194,304), up to 2 bounces,
+    1 Tx / 4 Rx.  Per (distance, samples) the full trace is timed (rays/s), then the synthesis in
+    each carrier-phase mode (path-samples/s = P x V x N_s per call).  Beside each mode: IF-cube
+    relative L2 and point-cloud Chamfer against the FP64 oracle on a seeded 4096-ray subset of the
+    same grid, the oracle's values read from tests/golden/precision_sweep_subset4096.npz (written
+    from the oracle alone by tests/golden/make_golden.py)."""
+    from sbr_inputs import CfarParams, ray_subset, sphere_scene
+    gold = np.load(os.path.join(ROOT, "tests", "golden", "precision_sweep_subset4096.npz"))
+    cfg = CfarParams()
+    modes = (("split", sbr.PHASE_SPLIT), ("fp64", sbr.PHASE_FP64), ("naive", sbr.PHASE_NAIVE))
+    reps = 3
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        a, b = ev(), ev()
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    rows = []
+    for dist in (5.0, 10.0, 20.0):
+        wl0 = sphere_scene(G=2048, distance=dist, n_samples=1024)
+        v = torch.from_numpy(wl0.verts).cuda()
+        f = torch.from_numpy(wl0.faces).cuda()
+        scene = sbr.Scene(v, f)
+        paths = sbr.PathBuffers(wl0.grid.n_rays, wl0.max_bounces, wl0.radar.n_virt)
+        ids = torch.from_numpy(ray_subset(11, wl0.grid.n_rays, 4096)).cuda()
+        sub = sbr.PathBuffers(4096, wl0.max_bounces, wl0.radar.n_virt)
+        for ns in (1024, 2048, 4096):
+            wl = sphere_scene(G=2048, distance=dist, n_samples=ns)
+            t_tr = timed(lambda: sbr.trace(scene, wl.radar, wl.grid, wl.max_bounces, out=paths))
+            P = paths.count()
+            sbr.trace(scene, wl.radar, wl.grid, wl.max_bounces, ray_ids=ids, out=sub)
+            key = f"d{int(dist)}_ns{ns}"
+            ref = gold["cube_" + key]
+            ref_pts = gold["points_" + key]
+            cube = torch.empty((wl.radar.n_virt, 1, ns, 2), device="cuda")
+            ws = torch.empty(sbr.synth_ws_bytes(wl.radar, paths.cap), dtype=torch.uint8, device="cuda")
+            row = {"distance_m": dist, "n_samples": ns, "rays": wl.grid.n_rays, "paths": P,
+                   "trace_ms": t_tr, "rays_per_s": wl.grid.n_rays / (t_tr * 1e-3), "modes": {}}
+            for name, m in modes:
+                t_sy = timed(lambda: sbr.synthesize(paths, wl.radar, m, out=cube, ws=ws))
+                c_sub = sbr.synthesize(sub, wl.radar, m)
+                pts, st = sbr.pointcloud(c_sub, wl.radar, cfg)
+                got = c_sub.double().cpu().numpy()
+                got = got[:, 0, :, 0] + 1j * got[:, 0, :, 1]
+                err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+                n = st.n_points()
+                ch = _chamfer_mm(pts[:n].cpu().numpy().astype(np.float64), ref_pts)
+                row["modes"][name] = {"synth_ms": t_sy,
+                                      "path_samples_per_s": P * wl.radar.n_virt * ns / (t_sy * 1e-3),
+                                      "cube_rel_l2_vs_oracle": err, "chamfer_mm_vs_oracle": ch}
+            rows.append(row)
+            del ws
+        del paths, sub, scene
+        torch.cuda.empty_cache()
+    return {"workload": "icosphere 320 tris r 0.2 m at 5/10/20 m; 2048x2048 rays, <=2 bounces; 1 Tx x 4 Rx; "
+                        "1024/2048/4096 samples, 1 chirp",
+            "timing": f"CUDA events, mean of {reps} calls after one warm-up call, inputs resident",
+            "accuracy": "4096 seeded rays of the same grid vs the FP64 oracle's stored cube and points "
+                        "(tests/golden/precision_sweep_subset4096.npz)",
+            "rows": rows}
 
 
 def recon_arm(sbr, torch, args):
@@ -562,8 +689,8 @@ def reference_arm(args, rank, world):
 
 def main():
     args = parse()
-    if args.write_traffic:
-        write_traffic(args.write_traffic)
+    if args.write_counters:
+        write_counters(args.write_counters)
         return
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":

@@ -149,7 +149,11 @@ sbr_status sbr_scene_create(const float* d_verts, int32_t nv, const int32_t* d_f
                             int32_t nt, void* d_mem, size_t mem_bytes, sbr_stream stream,
                             sbr_scene** out);
 /* Rebuilds the scene for new vertex positions of the same topology (the
- * per-iteration update of the reconstruction loop). */
+ * per-iteration update of the reconstruction loop).  This is the refit step of
+ * a mesh-optimisation loop, done as a full rebuild (Morton order, tree and
+ * boxes from the new positions): after large vertex moves a refit of the old
+ * tree would leave loose boxes, and the cooperative build costs about as much
+ * as a refit pass. */
 sbr_status sbr_scene_update(sbr_scene* scene, const float* d_verts, sbr_stream stream);
 /* Synchronises the stream and reports a device-side error word set by the
  * build: bit 0 (a face index outside [0, nv)) gives SBR_ERR_INVALID_ARG; bit 1
@@ -247,8 +251,10 @@ sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg* radar,
  *  - n_virt * n_samples must not exceed 131072, otherwise SBR_ERR_UNSUPPORTED
  *    is returned before anything is enqueued;
  *  - the first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture on the device;
+ *    (cudaGetSymbolAddress) with that device current and keeps it for the
+ *    life of the process; make that first call before any stream capture on
+ *    the device.  A cudaDeviceReset of that device leaves the kept address
+ *    stale: do not call this entry point on the device again in that process;
  *  - every call shares the one array: calls whose work overlaps on the GPU
  *    (different streams, concurrent host threads) race on it and must be
  *    serialised by the caller.  Each call overwrites every partial sum it

@@ -20,7 +20,7 @@ MAX_VIRT = 64
 
 PHASE_SPLIT, PHASE_FP64, PHASE_NAIVE = 0, 1, 2
 STATUS = {0: "SBR_OK", 1: "SBR_ERR_INVALID_ARG", 2: "SBR_ERR_OOM", 3: "SBR_ERR_TIMEOUT", 4: "SBR_ERR_CUDA",
-          5: "SBR_ERR_UNSUPPORTED"}
+          5: "SBR_ERR_UNSUPPORTED", 6: "SBR_ERR_CANCELLED"}
 
 
 class SbrError(RuntimeError):

@@ -10,7 +10,9 @@ With ``recompute=True`` the path records of the forward trace are not kept:
 their buffer is released after synthesis and the backward re-traces the same
 vertices (triangle sequences are a deterministic function of the vertices),
 trading one trace for the path memory (R x K x (48 + 24 V) bytes).
-``SimulateFn`` exposes it as a torch.autograd.Function.
+``SimulateFn`` exposes it as a torch.autograd.Function.  A Simulator holds the
+state of its latest forward pass only, so each backward must follow its own
+forward with no other forward on the same Simulator in between (checked).
 """
 from __future__ import annotations
 
@@ -38,6 +40,8 @@ class Simulator:
         self.points = torch.empty((cfar.k_max, 4), dtype=torch.float32, device=device)
         self.state = sim.PcState(radar, cfar, device)
         self.gcube = torch.empty_like(self.cube)
+        # forward passes so far: the backward reads the state of the latest one only
+        self.generation = 0
 
     def _trace(self, verts):
         if self.scene is None:
@@ -50,6 +54,7 @@ class Simulator:
         return paths
 
     def forward(self, verts: torch.Tensor):
+        self.generation += 1
         paths = self._trace(verts)
         sim.synthesize(paths, self.radar, self.mode, out=self.cube, ws=self.synth_ws)
         sim.pointcloud(self.cube, self.radar, self.cfar, state=self.state, out=self.points)
@@ -72,11 +77,17 @@ class SimulateFn(torch.autograd.Function):
         v = verts.detach().contiguous()
         pts, _ = simulator.forward(v)
         ctx.sim = simulator
+        ctx.generation = simulator.generation
         ctx.save_for_backward(v)
         return pts.clone()
 
     @staticmethod
     def backward(ctx, gpoints):
+        # the simulator keeps one forward's point-cloud state (and path records):
+        # a backward through an older forward would silently use the newer one's
+        if ctx.generation != ctx.sim.generation:
+            raise RuntimeError("SimulateFn.backward: the Simulator ran another forward pass since this one; "
+                               "run one forward per backward, or one Simulator per pending graph")
         (v,) = ctx.saved_tensors
         g = torch.zeros_like(v)
         ctx.sim.backward(v, gpoints.float(), g)

@@ -786,16 +786,25 @@ const PsiQuad& psi_quad() {
 
 inline bool nufft_for(sbr_phase_mode mode, int Ns) { return mode == SBR_PHASE_SPLIT && Ns <= kNuMaxSamples; }
 
-int g_sms = 0;
+// Launch-shape queries are cached per device ordinal (kernel attributes such as
+// a raised shared-memory limit are per device too); ordinals at or beyond
+// kDevCache are queried on every call.
+constexpr int kDevCache = 64;
+
+inline int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  return dev;
+}
 
 int sm_count() {
-  if (g_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_sms <= 0)
-      g_sms = 152;
-  }
-  return g_sms;
+  static int cache[kDevCache] = {};
+  const int dev = current_device();
+  if (dev < kDevCache && cache[dev]) return cache[dev];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+  if (dev < kDevCache) cache[dev] = n;
+  return n;
 }
 
 // Grid: V * Q CTAs, Q the largest that keeps every CTA resident at once (one
@@ -808,9 +817,11 @@ inline size_t split_smem(int Ns) {
 
 // resident CTAs of the split kernel per SM (registers and shared memory decide)
 int split_per_sm(int Ns) {
-  static int cache[17] = {};
+  static int cache[kDevCache][17] = {};
   const int T = threads_for(Ns), M = Ns / T;
-  if (M > 16 || cache[M]) return M > 16 ? 1 : cache[M];
+  if (M > 16) return 1;
+  const int dev = current_device();
+  if (dev < kDevCache && cache[dev][M]) return cache[dev][M];
   int n = 0;
   const size_t sm = split_smem(Ns);
   switch (M) {
@@ -820,20 +831,23 @@ int split_per_sm(int Ns) {
     case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_synth_split<8>, kSplitThreads, sm); break;
     default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_synth_split<16>, kSplitThreads, sm); break;
   }
-  cache[M] = n > 0 ? n : 1;
-  return cache[M];
+  n = n > 0 ? n : 1;
+  if (dev < kDevCache) cache[dev][M] = n;
+  return n;
 }
 
 // resident CTAs of the tensor-core kernel per SM (N_s = 256 or 512)
 int mma_per_sm(int Ns) {
-  static int cache[3] = {};
+  static int cache[kDevCache][3] = {};
   const int mt = Ns / 256;
-  if (cache[mt]) return cache[mt];
+  const int dev = current_device();
+  if (dev < kDevCache && cache[dev][mt]) return cache[dev][mt];
   int n = 0;
   if (mt == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_synth_mma<1>, kMmaThreads, 0);
   else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_synth_mma<2>, kMmaThreads, 0);
-  cache[mt] = n > 0 ? n : 1;
-  return cache[mt];
+  n = n > 0 ? n : 1;
+  if (dev < kDevCache) cache[dev][mt] = n;
+  return n;
 }
 
 void grid_shape(int V, int Ns, int64_t cap, int* Q) {
@@ -857,16 +871,18 @@ inline size_t nufft_smem(int Ns) { return sizeof(float2) * kNuWarps * 2 * (size_
 // resident spreading CTAs per SM (shared memory and registers decide); raises
 // the kernel's shared-memory limit once where the grids pass 48 KB
 int nufft_per_sm(int Ns) {
-  static int cache[16] = {};
+  static int cache[kDevCache][16] = {};
   int lg = 0;
   while ((1 << lg) < Ns) ++lg;
-  if (cache[lg]) return cache[lg];
+  const int dev = current_device();
+  if (dev < kDevCache && cache[dev][lg]) return cache[dev][lg];
   const size_t sm = nufft_smem(Ns);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_nufft_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_nufft_spread, kNuThreads, sm);
-  cache[lg] = n > 0 ? n : 1;
-  return cache[lg];
+  n = n > 0 ? n : 1;
+  if (dev < kDevCache) cache[dev][lg] = n;
+  return n;
 }
 
 // CTAs per antenna of the spreading kernel: one wave, at most one per 256 paths

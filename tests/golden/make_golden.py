@@ -21,6 +21,13 @@ centred 1.0 m on boresight; 77 GHz, 4 GHz over 40 us, 256 samples, 1 chirp;
   sphere_g16_cube.txt    IF samples S[v, n] of Eq. 8 (one chirp: the scene is static)
   sphere_g64_points.txt  point cloud of the map T (Section 3.4, Eq. 16 reading) from the
                          64 x 64-ray cube: x, y, z, w
+  precision_sweep_subset4096.npz
+                         the long-range precision sweep: the same sphere centred 5, 10 and
+                         20 m out, 1024, 2048 and 4096 samples per chirp, 2048 x 2048 ray
+                         grid of which a seeded subset of 4096 rays (sbr_inputs.ray_subset,
+                         seed 11) is traced; per (distance, samples) the oracle's FP64 IF
+                         cube (Eq. 8, complex128 [4, N_s]) and its point cloud.  Binary
+                         (numpy .npz) because the cubes hold 86,016 complex samples in all.
 """
 from __future__ import annotations
 
@@ -52,6 +59,34 @@ def compute() -> dict:
     pc = opc.pointcloud(cube64, wl64.radar, CfarParams())
     return dict(tri=tr["tri"], flag=tr["flag"], tau=pa["tau"], amp=pa["amp"], ray=pa["ray"],
                 bounce=pa["bounce"], cube=cube16[:, 0, :], points=pc["points"])
+
+
+SWEEP_DISTANCES = (5.0, 10.0, 20.0)
+SWEEP_SAMPLES = (1024, 2048, 4096)
+SWEEP_FILE = "precision_sweep_subset4096.npz"
+SWEEP_RAYS = 4096
+SWEEP_SEED = 11
+
+
+def sweep_key(dist: float, ns: int) -> str:
+    return f"d{int(dist)}_ns{ns}"
+
+
+def compute_sweep() -> dict:
+    """Oracle cubes and point clouds of the precision-sweep configurations (subset rays)."""
+    from sbr_inputs import ray_subset
+    out = {}
+    for dist in SWEEP_DISTANCES:
+        for ns in SWEEP_SAMPLES:
+            wl = sphere_scene(G=2048, distance=dist, n_samples=ns)
+            ids = ray_subset(SWEEP_SEED, wl.grid.n_rays, SWEEP_RAYS)
+            cube, _, pa = oracle.simulate_cube(wl, ids)
+            pc = opc.pointcloud(cube, wl.radar, CfarParams())
+            k = sweep_key(dist, ns)
+            out["cube_" + k] = cube[:, 0, :]
+            out["points_" + k] = pc["points"]
+            out["paths_" + k] = np.int64(pa["P"])
+    return out
 
 
 def _write(name: str, header: list, rows: list):
@@ -105,7 +140,8 @@ def main():
             GENERATOR,
             "columns: x y z w"],
            [" ".join(f"{x:.17e}" for x in p) for p in pts])
-    print("wrote", ", ".join(sorted(f for f in os.listdir(HERE) if f.endswith(".txt"))))
+    np.savez_compressed(os.path.join(HERE, SWEEP_FILE), **compute_sweep())
+    print("wrote", ", ".join(sorted(f for f in os.listdir(HERE) if f.endswith((".txt", ".npz")))))
 
 
 if __name__ == "__main__":

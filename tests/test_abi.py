@@ -67,3 +67,11 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_every_status_code_has_a_name():
+    """Each sbr_status value the header declares has a name in the binding's error messages."""
+    from paper_2311_13182_gb300 import _lib
+    txt = open(os.path.join(ROOT, "include", "sbr.h")).read()
+    codes = {int(v): n for n, v in re.findall(r"\b(SBR_(?:OK|ERR_[A-Z_]+))\s*=\s*(\d+)", txt)}
+    assert codes and all(_lib.STATUS.get(v) == n for v, n in codes.items()), (codes, _lib.STATUS)

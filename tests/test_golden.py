@@ -74,3 +74,20 @@ def test_cuda_path_matches_golden(sbr):
     n = st.n_points()
     got = pts.cpu().numpy()[:n].astype(np.float64)
     assert n > 0 and opc.chamfer_parity(got, g["points"]) <= 1e-3
+
+
+def test_oracle_reproduces_precision_sweep():
+    """The stored long-range sweep (sphere at 5/10/20 m, 1024-4096 samples, 4096 seeded rays
+    of the 2048 x 2048 grid) is what the oracle computes now."""
+    from tests.golden.make_golden import SWEEP_FILE, compute_sweep
+    g = np.load(os.path.join(GOLDEN, SWEEP_FILE))
+    d = compute_sweep()
+    assert sorted(g.files) == sorted(d)
+    for k in d:
+        if k.startswith("cube_"):
+            assert np.linalg.norm(d[k] - g[k]) <= 1e-12 * np.linalg.norm(g[k]), k
+        elif k.startswith("points_"):
+            assert d[k].shape == g[k].shape, k
+            np.testing.assert_allclose(d[k], g[k], rtol=0, atol=1e-9, err_msg=k)
+        else:
+            assert int(d[k]) == int(g[k]), k

@@ -29,3 +29,29 @@ def test_graph_replay_matches_eager(sbr):
     # the moved scene's nearest points are ~1 cm farther
     r_moved = np.linalg.norm(g.points[:g.n_points(), :3].cpu().numpy(), axis=1)
     assert r_moved.min() > 0
+
+
+def test_bench_step_full_cube_and_points_against_oracle(sbr):
+    """The bench workload at full size (20,002 triangles, all 1,048,576 rays, 3 bounces,
+    12 x 128 x 256 cube), run as the bench runs it (the graph-replayed sbr.Forward step):
+    every ray traced and every path summed by the FP64 oracle.  IF cube relative L2 <= 1e-4
+    and point cloud Chamfer <= 1 mm."""
+    import oracle
+    from oracle import pointcloud as opc
+    from tests._util import cube_complex, rel_l2
+    wl = superquadric_scene(seed=0, G=1024)
+    cfg = CfarParams()
+    fw = sbr.Forward(torch.from_numpy(wl.verts).cuda(), torch.from_numpy(wl.faces).cuda(), wl.radar, wl.grid,
+                     wl.max_bounces, cfg)
+    fw.run()
+    torch.cuda.synchronize()
+    ref, _, pa = oracle.simulate_cube(wl)
+    assert fw.paths.count() == pa["P"]
+    err = rel_l2(cube_complex(fw.cube), ref)
+    ref_pts = opc.pointcloud(ref, wl.radar, cfg)["points"]
+    n = fw.n_points()
+    got = fw.points[:n].cpu().numpy().astype(np.float64)
+    ch = opc.chamfer_parity(got, ref_pts)
+    print(f"\nbench workload: {pa['P']} paths, cube rel L2 {err:.2e}, {n} points, Chamfer {ch:.2e} m")
+    assert err <= 1e-4
+    assert n > 0 and ch <= 1e-3

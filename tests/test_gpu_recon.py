@@ -64,3 +64,20 @@ def test_recompute_paths_same_gradient(sbr):
         loss.backward()
         grads.append(v.grad.cpu().numpy())
     np.testing.assert_allclose(grads[1], grads[0], rtol=1e-4, atol=1e-6 * np.abs(grads[0]).max())
+
+
+def test_simulate_fn_rejects_backward_through_an_older_forward(sbr):
+    """The Simulator keeps one forward pass's state: a backward through the first of two
+    forwards on the same Simulator raises instead of returning the second one's gradient."""
+    from paper_2311_13182_gb300.autograd import SimulateFn, Simulator
+    from sbr_inputs import sphere_scene
+    wl = sphere_scene(G=16)
+    s = Simulator(wl.faces, wl.verts.shape[0], wl.radar, wl.grid, wl.max_bounces, CfarParams())
+    v1 = torch.from_numpy(wl.verts).cuda().requires_grad_(True)
+    v2 = (v1.detach() * 1.001).requires_grad_(True)
+    p1 = SimulateFn.apply(v1, s)
+    p2 = SimulateFn.apply(v2, s)
+    p2.sum().backward()                          # the latest forward: fine
+    assert v2.grad is not None
+    with pytest.raises(RuntimeError, match="another forward"):
+        p1.sum().backward()

@@ -41,18 +41,31 @@ def test_superquadric_mimo_cube_subset(sbr):
     assert (cube == cube[:, :1]).all()
 
 
-@pytest.mark.parametrize("dist,ns", [(5.0, 1024), (10.0, 2048), (20.0, 4096)])
-def test_long_range_precision_modes(sbr, dist, ns):
-    """Sphere at 5-20 m, 1024-4096 samples: split and FP64 phase meet 1e-4, naive FP32 does not."""
+@pytest.mark.parametrize("ns", [1024, 2048, 4096])
+@pytest.mark.parametrize("dist", [5.0, 10.0, 20.0])
+def test_precision_sweep_cube_and_points(sbr, dist, ns):
+    """The long-range sweep: the sphere at 5-20 m, 1024-4096 samples, a seeded 4096-ray subset
+    of the 2048 x 2048 grid.  Against the FP64 oracle, the split and FP64 phase modes keep the
+    IF cube within relative L2 1e-4 and the point cloud within 1 mm Chamfer; naive FP32 phase
+    (f_c tau spans ~10^4 cycles at 20 m) is reported and must be the worst of the three."""
+    from oracle import pointcloud as opc
+    from sbr_inputs import CfarParams
     wl = sphere_scene(G=2048, distance=dist, n_samples=ns)
     ids = ray_subset(11, wl.grid.n_rays, 4096)
     ref, _, _ = oracle_cube(wl, ids)
+    ref_pts = opc.pointcloud(ref, wl.radar, CfarParams())["points"]
     _, paths = gpu_trace(sbr, wl, ray_ids=ids)
-    errs = {}
+    errs, cham = {}, {}
     for name, m in (("split", sbr.PHASE_SPLIT), ("fp64", sbr.PHASE_FP64), ("naive", sbr.PHASE_NAIVE)):
-        errs[name] = rel_l2(cube_complex(sbr.synthesize(paths, wl.radar, m)), ref)
+        cube_t = sbr.synthesize(paths, wl.radar, m)
+        errs[name] = rel_l2(cube_complex(cube_t), ref)
+        pts, st = sbr.pointcloud(cube_t, wl.radar, CfarParams())
+        n = st.n_points()
+        cham[name] = opc.chamfer_parity(pts[:n].cpu().numpy().astype(np.float64), ref_pts)
+    print(f"\nsweep {dist:g} m, {ns} samples: cube rel L2 {errs}, Chamfer [m] {cham}")
     assert errs["split"] <= TOL and errs["fp64"] <= TOL, errs
-    assert errs["naive"] > errs["split"], errs
+    assert cham["split"] <= 1e-3 and cham["fp64"] <= 1e-3, cham
+    assert errs["naive"] > max(errs["split"], errs["fp64"]), errs
 
 
 def test_deterministic(sbr):

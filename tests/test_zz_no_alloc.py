@@ -57,3 +57,28 @@ def test_noalloc_rejects_oversized_cube(sbr):
     out = torch.empty((64, 1, 4096, 2), device="cuda")
     st = noalloc(sbr, paths, radar, sbr.PHASE_SPLIT, out)
     assert st == 5 and "131072" in _lib.last_error()
+
+
+@pytest.mark.parametrize("mode", ["split", "fp64", "naive"])
+def test_noalloc_partial_cap_all_modes(sbr, mode):
+    """12 virtual antennas x 1024 samples: one partial cube is 12288 values, so the fixed
+    array holds at most 10 CTAs per antenna, while the workspace entry point launches at
+    least one CTA per SM over the 12 antennas (152 / 12 > 10) whenever the paths fill more
+    than 10 chunks of 512: the allocation-free call runs with its grid cut to the array's
+    size, its CTAs looping over more path chunks each, in every phase mode."""
+    wl = superquadric_scene(seed=3, G=512, n_chirps=1, n_samples=1024)
+    _, paths = gpu_trace(sbr, wl)
+    V, Ns = wl.radar.n_virt, wl.radar.n_samples
+    qmax = 131072 // (V * Ns)
+    assert qmax == 10 and 152 // V > qmax
+    assert paths.count() > 4 * qmax * 512            # several chunks per capped CTA
+    m = dict(split=sbr.PHASE_SPLIT, fp64=sbr.PHASE_FP64, naive=sbr.PHASE_NAIVE)[mode]
+    ref = cube_complex(sbr.synthesize(paths, wl.radar, m))
+    out = torch.empty((V, 1, Ns, 2), device="cuda")
+    for call in range(2):
+        out.fill_(float("nan"))
+        assert noalloc(sbr, paths, wl.radar, m, out) == 0
+        torch.cuda.synchronize()
+        got = cube_complex(out)
+        assert np.isfinite(got).all()
+        assert rel_l2(got, ref) <= TOL, (mode, call)
