@@ -291,10 +291,20 @@ sbr_status sbr_pc_bind(void* d_mem, size_t bytes, const sbr_radar_cfg* radar,
                        const sbr_cfar_cfg* cfar, sbr_pc_state* out);
 
 /* d_points [k_max][4] = (x, y, z, w) ordered by (w desc, cell asc); rows at
- * and beyond *n_points are zero. */
+ * and beyond *n_points are zero.  The angle DFT runs on the tensor cores
+ * (tcgen05, TF32 with a hi/lo operand split: ~1e-6 relative to FP32) when
+ * n_theta <= 64, V <= 16 and N_s is a multiple of 64, on CUDA cores otherwise. */
 sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* radar,
                           const sbr_cfar_cfg* cfar, float* d_points, sbr_pc_state* state,
                           sbr_stream stream);
+
+/* Synchronises the stream and reports the device-side status of the last
+ * sbr_pointcloud on `state` (each call clears it on entry): SBR_ERR_TIMEOUT
+ * when the tensor-core angle DFT (used for n_theta <= 64, at most 16 virtual
+ * antennas and N_s a multiple of 64) gave up its bounded wait for its matrix
+ * products, in which case the power map holds NaN. */
+sbr_status sbr_pc_check(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const sbr_pc_state* state,
+                        sbr_stream stream);
 
 /* Adjoint: d_gpoints [k_max][4] -> d_gcube [V][C][N_s] complex (overwritten). */
 sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar,

@@ -145,6 +145,18 @@ def pointcloud(cube: np.ndarray, radar, cfg: CfarConfig = None) -> dict:
     return dict(points=pts[order], a=a[order], k=k[order], Pw=Pw, X=X, Y=Y)
 
 
+def image_loss(cube: np.ndarray, target: np.ndarray, radar, cfg: CfarConfig = None) -> float:
+    """Spatial multi-antenna loss of Eq. 16 (Section 3.4): the mean over the N image cells of
+    the squared difference between the image T(y) of the cube and a target image.
+
+    Reading: T maps the MIMO IF cube to the range-angle power map Pw of steps 1-4 above
+    (range DFT, Doppler DFT, angle DFT over n_theta bins, |Y|^2 summed over Doppler), a
+    spatial image of n_theta x N_s cells (the 1D virtual array resolves azimuth only)."""
+    cfg = cfg or CfarConfig()
+    _, _, Pw = power_map(cube, radar, cfg)
+    return float(((Pw - np.asarray(target, dtype=np.float64)) ** 2).mean())
+
+
 # ----------------------------------------------------------------------------
 # Chamfer terms and Laplacian smoothness
 # ----------------------------------------------------------------------------

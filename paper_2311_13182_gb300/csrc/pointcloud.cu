@@ -23,6 +23,7 @@
 
 #include "cta_sort.cuh"
 #include "fft.cuh"
+#include "tcgen05.cuh"
 
 namespace sbr {
 namespace {
@@ -140,6 +141,160 @@ __global__ void __launch_bounds__(256) k_angle_power(const float2* __restrict__ 
   }
 #pragma unroll
   for (int i = 0; i < APT; ++i) part[((size_t)g * A + ag * APT + i) * Ns + k0 + kk] = acc[i];
+}
+
+// ---- angle DFT on the tensor cores ------------------------------------------
+//
+// Per Doppler bin d the angle DFT of kTcM range bins is one real GEMM
+//   D[k][2a + part] = sum_j A[k][j] B[2a + part][j],   j = 2v + (0: Re, 1: Im)
+// with A = X^T (M = kTcM range bins, K = 2V) and B = the steering matrix as
+// N = 128 real rows: row 2a = (W_re, -W_im) and row 2a + 1 = (W_im, W_re) at
+// columns (2v, 2v + 1), so D[k][2a] = Re Y[a,d,k] and D[k][2a + 1] = Im Y[a,d,k].
+// It runs as tcgen05.mma kind::tf32 from shared memory into TMEM.  Each
+// operand is split as hi = tf32(x), lo = x - hi, and three products
+// A_lo B_hi + A_hi B_lo + A_hi B_hi (small terms first) keep ~21 bits; the
+// dropped lo.lo term is ~2^-22 relative, so Y matches the FP32 CUDA-core
+// contraction to ~1e-6.  A CTA takes kTcM range bins of kTcDG Doppler bins, one
+// kTcM x 128 FP32 accumulator per Doppler bin in TMEM; thread t of the CTA owns
+// TMEM lane t (range bin k0 + t) and every angle, so |Y|^2 = D[2a]^2 + D[2a+1]^2
+// needs no data exchange, and its sum over the CTA's Doppler bins stays in
+// registers until one coalesced store per angle.
+#ifndef SBR_ANGLE_DG
+#define SBR_ANGLE_DG 2
+#endif
+constexpr int kTcM = 128;                      // range bins per CTA (MMA M: one TMEM lane each)
+constexpr int kTcN = 128;                      // 64 angles x (Re, Im) (MMA N)
+constexpr int kTcDG = SBR_ANGLE_DG;            // Doppler bins per CTA
+constexpr int kTcCols = kTcN * kTcDG;          // TMEM columns: a power of two >= 32
+constexpr int kTcThreads = 128;                // four warps: the four TMEM lane quadrants
+constexpr int kTcK = 32;                       // K capacity: up to 16 antennas
+constexpr uint32_t kTcTile = 128 * kTcK * 4;   // bytes of one 128-row operand (hi or lo)
+constexpr uint32_t kTcLbo = 128;               // K-adjacent core matrices
+constexpr uint32_t kTcSbo = (kTcK / 4) * 128;  // M/N-adjacent core matrices (8-row groups)
+constexpr size_t kTcSmem = 2 * (size_t)kTcTile * (1 + kTcDG) + 64;
+constexpr uint64_t kTcWaitNs = 200000000ull;   // bounded wait for the MMAs: 0.2 s
+static_assert(kTcCols >= 32 && kTcCols <= 512 && (kTcCols & (kTcCols - 1)) == 0, "TMEM columns");
+
+inline bool angle_tc_ok(int A, int V, int Ns) { return A <= 64 && V <= 16 && Ns % kTcM == 0; }
+
+// Byte offset of the 16-byte row chunk (row, k .. k + 3), k a multiple of 4, in
+// the no-swizzle K-major layout of a K = 32 operand: 8-row x 4-element core
+// matrices of 128 contiguous bytes, the 8 core matrices of a row group side by
+// side along K (kTcLbo apart), row groups kTcSbo apart.
+__device__ inline uint32_t tc_off(int row, int k) {
+  return (uint32_t)((((row >> 3) * (kTcK / 4) + (k >> 2)) << 7) + ((row & 7) << 4));
+}
+
+// Stores hi = tf32(x) and lo = x - hi of four consecutive K entries.
+__device__ inline void tc_put4(unsigned char* hi, unsigned char* lo, uint32_t off, float4 x) {
+  const float4 h = make_float4(tc::to_tf32(x.x), tc::to_tf32(x.y), tc::to_tf32(x.z), tc::to_tf32(x.w));
+  *reinterpret_cast<float4*>(hi + off) = h;
+  *reinterpret_cast<float4*>(lo + off) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+}
+
+// part[g][a][k] = sum over the Doppler bins of group g of |Y[a,d,k]|^2; on a
+// timed-out wait the CTA writes NaN and sets bit 0 of *err.
+__global__ void __launch_bounds__(kTcThreads) k_angle_tc(const float2* __restrict__ X, const Steer xl, int A,
+                                                         int V, int C, int Ns, float* __restrict__ part,
+                                                         int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char* sw_hi = tsm;                  // B: steering rows
+  unsigned char* sw_lo = tsm + kTcTile;
+  unsigned char* sx_hi = tsm + 2 * kTcTile;    // A: X^T per Doppler bin, hi then lo
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + 2 * (size_t)kTcTile * (1 + kTcDG));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int k0 = blockIdx.x * kTcM, g = blockIdx.y, d0 = g * kTcDG;
+  const int nd = min(kTcDG, C - d0);  // Doppler bins of this CTA (>= 1)
+  const int ks = (2 * V + 7) / 8;      // MMA K steps of 8 used
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, kTcCols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) tc::mbar_init(mbar, 1);
+  // A: thread t takes range bin k0 + t; per Doppler bin and antenna pair one 16-byte chunk
+  // (Re, Im of antenna 2j, Re, Im of antenna 2j + 1); antennas >= V and bins >= nd are zero.
+  // Every load is issued before the steering matrix is generated, which hides their latency.
+  float2 xv[kTcDG][kTcK / 2];
+#pragma unroll
+  for (int dd = 0; dd < kTcDG; ++dd)
+#pragma unroll
+    for (int v = 0; v < kTcK / 2; ++v)
+      xv[dd][v] = (dd < nd && v < V) ? X[((size_t)v * C + d0 + dd) * Ns + k0 + tid] : make_float2(0.f, 0.f);
+  // B: row pair (2a, 2a + 1) of angle a, antenna pair j: one 16-byte chunk per row
+  for (int i = tid; i < 64 * (kTcK / 4); i += kTcThreads) {
+    const int a = i >> 3, j = i & 7;
+    float c0 = 0.f, s0 = 0.f, c1 = 0.f, s1 = 0.f;
+    if (a < A) {
+      const float u = -1.f + 2.f * (float)a / (float)A;
+      if (2 * j < V) sincospif(2.f * xl.xl[2 * j] * u, &s0, &c0);
+      if (2 * j + 1 < V) sincospif(2.f * xl.xl[2 * j + 1] * u, &s1, &c1);
+    }
+    tc_put4(sw_hi, sw_lo, tc_off(2 * a, 4 * j), make_float4(c0, -s0, c1, -s1));
+    tc_put4(sw_hi, sw_lo, tc_off(2 * a + 1, 4 * j), make_float4(s0, c0, s1, c1));
+  }
+#pragma unroll
+  for (int dd = 0; dd < kTcDG; ++dd) {
+    unsigned char* xh = sx_hi + 2 * (size_t)kTcTile * dd;
+#pragma unroll
+    for (int j = 0; j < kTcK / 4; ++j)
+      tc_put4(xh, xh + kTcTile, tc_off(tid, 4 * j),
+              make_float4(xv[dd][2 * j].x, xv[dd][2 * j].y, xv[dd][2 * j + 1].x, xv[dd][2 * j + 1].y));
+  }
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  if (tid == 0) {
+    constexpr uint32_t idesc = tc::idesc_tf32(kTcM, kTcN);
+    const uint32_t wh = tc::smem_u32(sw_hi), wl = tc::smem_u32(sw_lo);
+    for (int dd = 0; dd < nd; ++dd) {
+      const uint32_t xh = tc::smem_u32(sx_hi + 2 * (size_t)kTcTile * dd), xlo = xh + kTcTile;
+      bool acc = false;
+      for (int pass = 0; pass < 3; ++pass) {  // lo.hi, hi.lo, hi.hi
+        const uint32_t pa = pass == 0 ? xlo : xh, pb = pass == 1 ? wl : wh;
+        for (int j = 0; j < ks; ++j) {  // K step j covers columns 8j .. 8j + 7: two core matrices
+          tc::mma_tf32(tbase + (uint32_t)(dd * kTcN), tc::smem_desc(pa + 256u * j, kTcLbo, kTcSbo),
+                       tc::smem_desc(pb + 256u * j, kTcLbo, kTcSbo), idesc, acc);
+          acc = true;
+        }
+      }
+    }
+    tc::mma_commit(mbar);
+  }
+  const bool ok = __all_sync(0xffffffffu, tc::mbar_wait_bounded(mbar, 0, kTcWaitNs));
+  tc::fence_after_sync();
+  float acc[64];
+#pragma unroll
+  for (int a = 0; a < 64; ++a) acc[a] = 0.f;
+  if (ok) {
+    const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
+    for (int dd = 0; dd < nd; ++dd) {
+#pragma unroll
+      for (int h = 0; h < kTcN / 32; ++h) {
+        float y[32];
+        tc::tmem_ld32(lane_base + (uint32_t)(dd * kTcN + h * 32), y);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[h * 16 + j] = fmaf(y[2 * j], y[2 * j], fmaf(y[2 * j + 1], y[2 * j + 1], acc[h * 16 + j]));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 64; ++a) acc[a] = __int_as_float(0x7fc00000);
+    if ((tid & 31) == 0) atomicOr(err, 1);
+    if (tid == 0) tc::mbar_wait_bounded(mbar, 0, kTcWaitNs);  // the MMAs' own completion, once more
+  }
+  float* out = part + (size_t)g * A * Ns + k0 + tid;
+#pragma unroll
+  for (int a = 0; a < 64; ++a)
+    if (a < A) out[(size_t)a * Ns] = acc[a];
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tbase, kTcCols);
+  }
 }
 
 // Pw = fixed-order sum of the Doppler-group partials; also the argmax of Pw as
@@ -516,6 +671,7 @@ struct Layout {
   int32_t* n_points;
   int32_t* argmax;
   unsigned long long* amax_key;
+  int32_t* err;
   float* part;
   int32_t* flag;
   int32_t* off;
@@ -542,17 +698,30 @@ cudaError_t select_attr() {
   return e;
 }
 
+// k_angle_tc's shared memory exceeds the 48 KB default: raise the limit once per device.
+cudaError_t angle_tc_attr() {
+  static std::atomic<uint64_t> done{0};  // bit per device ordinal below 64
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && ((done.load() >> dev) & 1u)) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_angle_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e == cudaSuccess && dev < 64) done.fetch_or(1ull << dev);
+  return e;
+}
+
 size_t pc_layout(Layout* L, void* mem, const sbr_radar_cfg* r, const sbr_cfar_cfg* f) {
   Carver c(mem);
   const int V = r->n_tx * r->n_rx, C = r->n_chirps, Ns = r->n_samples, A = f->n_theta;
   const int64_t cells = (int64_t)A * Ns;
-  L->groups = dgroups(C);
+  L->groups = angle_tc_ok(A, V, Ns) ? (C + kTcDG - 1) / kTcDG : dgroups(C);
   L->spec = c.take<float2>((size_t)V * C * Ns);
   L->power = c.take<float>(cells);
   L->peak_cell = c.take<int32_t>(f->k_max > 0 ? f->k_max : 1);
   L->n_points = c.take<int32_t>(1);
   L->argmax = c.take<int32_t>(1);
-  L->amax_key = c.take<unsigned long long>(1);
+  L->amax_key = c.take<unsigned long long>(2);  // [0] argmax key, [1] low word: bounded-wait error bits
+  L->err = reinterpret_cast<int32_t*>(L->amax_key + 1);
   L->part = c.take<float>((size_t)L->groups * cells);
   L->flag = c.take<int32_t>(cells);
   L->off = c.take<int32_t>(cells + 1);
@@ -705,7 +874,12 @@ extern "C" sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* r
   SBR_CUDA(fft_rows(reinterpret_cast<const float2*>(d_cube), L.spec, V * C, Ns, -1.f, st));
   SBR_CUDA(fft_cols(L.spec, V, C, Ns, -1.f, st));
   // 3-4: angle DFT and power map (partials per Doppler group, fixed-order sum)
-  switch (A / 8) {
+  SBR_CUDA(cudaMemsetAsync(L.amax_key, 0, 2 * sizeof(unsigned long long), st));
+  if (angle_tc_ok(A, V, Ns)) {
+    SBR_CUDA(angle_tc_attr());
+    ::sbr::note_launch();
+    k_angle_tc<<<dim3(Ns / kTcM, L.groups), kTcThreads, kTcSmem, st>>>(L.spec, xl, A, V, C, Ns, L.part, L.err);
+  } else switch (A / 8) {
     case 1: launch_angle_power<1>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
     case 2: launch_angle_power<2>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
     case 4: launch_angle_power<4>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
@@ -715,7 +889,6 @@ extern "C" sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* r
     default: set_error("sbr_pointcloud: n_theta=%d unsupported", A); return SBR_ERR_UNSUPPORTED;
   }
   SBR_CUDA(cudaGetLastError());
-  SBR_CUDA(cudaMemsetAsync(L.amax_key, 0, sizeof(unsigned long long), st));
   ::sbr::note_launch();
   k_power_reduce<<<(cells + 255) / 256, 256, 0, st>>>(L.part, L.groups, cells, L.power, L.amax_key);
   // 5-9: soft CFAR, peaks, compaction in cell order, stable sort by weight, points
@@ -745,6 +918,28 @@ extern "C" sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* r
                                                        reinterpret_cast<float4*>(d_points), L.peak_cell,
                                                        L.n_points);
   SBR_CUDA(cudaGetLastError());
+  return SBR_OK;
+}
+
+extern "C" sbr_status sbr_pc_check(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar,
+                                   const sbr_pc_state* state, sbr_stream stream) {
+  sbr_status rs = check_radar(radar, "sbr_pc_check");
+  if (rs != SBR_OK) return rs;
+  rs = check_cfar(cfar, radar, "sbr_pc_check");
+  if (rs != SBR_OK) return rs;
+  Layout L;
+  rs = state_layout(state, radar, cfar, &L, "sbr_pc_check");
+  if (rs != SBR_OK) return rs;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  SBR_CUDA(cudaStreamSynchronize(st));
+  int32_t err = 0;
+  SBR_CUDA(cudaMemcpy(&err, L.err, sizeof(err), cudaMemcpyDeviceToHost));
+  if (err) {
+    set_error("sbr_pc_check: the tensor-core angle kernel gave up waiting for its matrix products "
+              "(status 0x%x); the power map holds NaN",
+              (unsigned)err);
+    return SBR_ERR_TIMEOUT;
+  }
   return SBR_OK;
 }
 

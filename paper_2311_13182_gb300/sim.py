@@ -248,6 +248,10 @@ class PcState:
     def peak_cells(self):
         return _region(self.mem, self.s.peak_cell, torch.int32, (self.k_max,))
 
+    def check(self, stream=None):
+        """sbr_pc_check: raises if the last point-cloud call's bounded device wait gave up."""
+        L.call("sbr_pc_check", ctypes.byref(self.r), ctypes.byref(self.c), ctypes.byref(self.s), _stream(stream))
+
 
 def pointcloud(cube: torch.Tensor, radar, cfar, state: PcState | None = None, out: torch.Tensor | None = None,
                stream=None):

@@ -106,3 +106,30 @@ def test_pointcloud_adjoint_directional_fd(sbr):
         fd = (L(cube + h * D) - L(cube - h * D)) / (2 * h)
         an = float((gc.real * D.real + gc.imag * D.imag).sum())
         assert abs(an - fd) <= 1e-3 * abs(fd), (trial, an, fd)
+
+
+@pytest.mark.parametrize("n_tx,n_rx,C,Ns,A", [
+    (1, 4, 1, 256, 64),     # the 1 Tx x 4 Rx radar, one chirp
+    (3, 4, 128, 256, 64),   # the 3 Tx x 4 Rx radar of the bench step
+    (1, 5, 1, 128, 64),     # odd antenna count, one range tile, a Doppler group of one bin
+    (3, 4, 8, 128, 64),     # several Doppler groups
+    (4, 4, 8, 128, 32),     # 16 antennas (the full K of the tensor path), 32 angle bins
+    (2, 3, 4, 4096, 16),    # 4096 samples per chirp, 16 angle bins
+    (4, 5, 2, 128, 64),     # 20 antennas: beyond the tensor path, CUDA cores
+    (1, 4, 2, 64, 64),      # 64 samples: below one 128-bin tile, CUDA cores
+    (1, 4, 1, 256, 128),    # 128 angle bins: CUDA cores
+])
+def test_power_map_shapes(sbr, n_tx, n_rx, C, Ns, A):
+    """Angle DFT + power map (the tensor-core kernel where the shape allows, CUDA cores
+    otherwise) against the oracle's direct FP64 chain on a random cube: relative L2 < 1e-5,
+    and the device status word clean."""
+    from sbr_inputs import _radar
+    radar = _radar(77e9, 4e9, 40e-6, Ns, C, n_tx, 0.5 * n_rx, n_rx=n_rx)
+    rng = np.random.default_rng(n_tx * 1000 + n_rx * 100 + C + Ns + A)
+    V = n_tx * n_rx
+    cube = rng.normal(size=(V, C, Ns)) + 1j * rng.normal(size=(V, C, Ns))
+    cfg = CfarParams(n_theta=A)
+    _, _, Pw = opc.power_map(cube, radar, cfg)
+    _, st = sbr.pointcloud(to_cube_t(cube), radar, cfg)
+    st.check()
+    assert rel_l2(st.power().double().cpu().numpy(), Pw) < 1e-5

@@ -623,3 +623,30 @@ def test_wedge_second_bounce_cos_term():
         lout = np.linalg.norm(radar.rx[r] - h[ray, k], axis=1)
         ref = tr["omega"][ray] * np.where(two, -1.0, 1.0) * cos / (4 * np.pi * lin * lout)
         np.testing.assert_allclose(pa["amp"][r], ref, rtol=1e-9)
+
+
+def test_image_loss_closed_forms():
+    """Eq. 16 image loss on the range-angle power map: a single antenna at the origin sees
+    W = 1 at every angle, and a tone exactly on range bin k0 has the DFT N_s A0 there and
+    0 elsewhere, so Pw = (N_s A0)^2 on column k0 of every angle row: against a zero target
+    the mean squared image is n_theta (N_s A0)^4 / (n_theta N_s).  The loss is zero against
+    its own image and scales as c^4 when the cube scales by c and the target by c^2."""
+    from sbr_inputs import RadarConfig
+    Ns, A0, k0 = 64, 0.3, 11
+    radar = RadarConfig(77e9, 4e9, 40e-6, Ns, 1, 40e-6, np.zeros((1, 3)), np.zeros((1, 3)))
+    cfg = pc.CfarConfig(n_theta=16)
+    cube = (A0 * np.exp(2j * np.pi * k0 * np.arange(Ns) / Ns))[None, None, :]
+    ref = (Ns * A0) ** 4 * 16 / (16 * Ns)
+    assert pc.image_loss(cube, np.zeros((16, Ns)), radar, cfg) == pytest.approx(ref, rel=1e-12)
+    rng = np.random.default_rng(8)
+    r3 = radar_mimo_3x4(32, 4)
+    c3 = rng.normal(size=(12, 4, 32)) + 1j * rng.normal(size=(12, 4, 32))
+    _, _, Pw = pc.power_map(c3, r3, pc.CfarConfig())
+    assert pc.image_loss(c3, Pw, r3) == pytest.approx(0.0, abs=1e-20)
+    t = rng.uniform(0, Pw.max(), size=Pw.shape)
+    l1 = pc.image_loss(c3, t, r3)
+    assert pc.image_loss(1.7 * c3, 1.7 ** 2 * t, r3) == pytest.approx(1.7 ** 4 * l1, rel=1e-12)
+    # the mean runs over all n_theta x N_s cells: one cell off by D gives D^2 / N
+    t2 = Pw.copy()
+    t2[5, 7] += 2.0
+    assert pc.image_loss(c3, t2, r3) == pytest.approx(4.0 / Pw.size, rel=1e-9)
