@@ -298,6 +298,25 @@ sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* radar,
                           const sbr_cfar_cfg* cfar, float* d_points, sbr_pc_state* state,
                           sbr_stream stream);
 
+/* Steps 1-4 of sbr_pointcloud only: range FFT, Doppler FFT, angle DFT and the
+ * range-angle power map Pw [n_theta][N_s] = sum over Doppler bins of |Y|^2, left
+ * in state->power (and the spectrum in state->spec, for the adjoint); no
+ * detection, no points.  This is the image T(y) of the spatial loss below. */
+sbr_status sbr_power_map(const float* d_cube, const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar,
+                         sbr_pc_state* state, sbr_stream stream);
+
+/* Spatial multi-antenna loss (Section 3.4, Eq. 16):
+ *   loss = (1/N) sum_i (T(y)_i - T(ybar)_i)^2,  N = n_theta x N_s,
+ * with T(y) the power map Pw of the last sbr_power_map or sbr_pointcloud on
+ * `state` (the paper names T only as a signal-processing map to a spatial
+ * image; this library's image is the range-angle power map) and d_target
+ * [n_theta][N_s] the target image T(ybar).  Writes *d_loss (device float) and,
+ * when d_gcube is not NULL, dloss/dcube [V][C][N_s] complex (overwritten)
+ * through the adjoints of the power map, the angle DFT and the two FFTs.
+ * Deterministic (fixed-order sums). */
+sbr_status sbr_image_loss(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const sbr_pc_state* state,
+                          const float* d_target, float* d_loss, float* d_gcube, sbr_stream stream);
+
 /* Synchronises the stream and reports the device-side status of the last
  * sbr_pointcloud on `state` (each call clears it on entry): SBR_ERR_TIMEOUT
  * when the tensor-core angle DFT (used for n_theta <= 64, at most 16 virtual

@@ -115,6 +115,8 @@ _SIGS = {
     "sbr_pointcloud": (c_i32, [c_p, P(RadarCfg), P(CfarCfg), c_p, P(PcState), c_p]),
     "sbr_pointcloud_bwd": (c_i32, [P(RadarCfg), P(CfarCfg), P(PcState), c_p, c_p, c_p]),
     "sbr_pc_check": (c_i32, [P(RadarCfg), P(CfarCfg), P(PcState), c_p]),
+    "sbr_power_map": (c_i32, [c_p, P(RadarCfg), P(CfarCfg), P(PcState), c_p]),
+    "sbr_image_loss": (c_i32, [P(RadarCfg), P(CfarCfg), P(PcState), c_p, c_p, c_p, c_p]),
     "sbr_trace_bwd": (c_i32, [c_p, c_p, P(RadarCfg), P(RayGrid), c_p, P(Paths), c_p, c_p, c_p, c_p]),
     "sbr_chamfer": (c_i32, [c_p, c_p, c_i32, c_p, c_i32, c_p, c_p, c_p]),
     "sbr_mesh_adjacency": (c_i32, [c_p, c_i32, c_i32, c_p, c_p, c_i32, P(c_i32)]),

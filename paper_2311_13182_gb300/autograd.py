@@ -60,11 +60,23 @@ class Simulator:
         sim.pointcloud(self.cube, self.radar, self.cfar, state=self.state, out=self.points)
         return self.points, self.state.n_points_tensor()
 
+    def forward_image(self, verts: torch.Tensor):
+        """vertices -> range-angle power map [n_theta, N_s] (the image T(y) of Eq. 16)."""
+        self.generation += 1
+        paths = self._trace(verts)
+        sim.synthesize(paths, self.radar, self.mode, out=self.cube, ws=self.synth_ws)
+        sim.power_map(self.cube, self.radar, self.cfar, state=self.state)
+        return self.state.power()
+
     def backward(self, verts: torch.Tensor, gpoints: torch.Tensor, gverts: torch.Tensor):
         """Adds dL/dverts to gverts for upstream dL/dpoints [k_max, 4]."""
-        paths = self.paths if self.paths is not None else self._trace(verts)
         sim.pointcloud_bwd(self.state, gpoints.contiguous(), out=self.gcube)
-        glen, gamp = sim.synthesize_bwd(paths, self.radar, self.gcube, ws=self.synth_ws)
+        return self.backward_cube(verts, self.gcube, gverts)
+
+    def backward_cube(self, verts: torch.Tensor, gcube: torch.Tensor, gverts: torch.Tensor):
+        """Adds dL/dverts to gverts for upstream dL/dcube [V, C, N_s, 2]."""
+        paths = self.paths if self.paths is not None else self._trace(verts)
+        glen, gamp = sim.synthesize_bwd(paths, self.radar, gcube, ws=self.synth_ws)
         sim.trace_bwd(self.scene, verts, self.radar, self.grid, paths, glen, gamp, self.ray_ids, gverts=gverts)
         return gverts
 

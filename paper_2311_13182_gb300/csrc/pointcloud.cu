@@ -855,18 +855,11 @@ sbr_status state_layout(const sbr_pc_state* s, const sbr_radar_cfg* r, const sbr
 }
 }  // namespace
 
-extern "C" sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* radar,
-                                     const sbr_cfar_cfg* cfar, float* d_points, sbr_pc_state* state,
-                                     sbr_stream stream) {
-  SBR_ARG(d_cube && d_points, "sbr_pointcloud: NULL cube or points");
-  sbr_status rs = check_radar(radar, "sbr_pointcloud");
-  if (rs != SBR_OK) return rs;
-  rs = check_cfar(cfar, radar, "sbr_pointcloud");
-  if (rs != SBR_OK) return rs;
-  Layout L;
-  rs = state_layout(state, radar, cfar, &L, "sbr_pointcloud");
-  if (rs != SBR_OK) return rs;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+namespace sbr {
+namespace {
+// Steps 1-4 of T: range FFT, Doppler FFT, angle DFT, power map Pw (and its argmax key).
+sbr_status power_map_impl(const float* d_cube, const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const Layout& L,
+                          cudaStream_t st) {
   const int V = radar->n_tx * radar->n_rx, C = radar->n_chirps, Ns = radar->n_samples, A = cfar->n_theta;
   const int cells = A * Ns;
   const Steer xl = steering_table(radar);
@@ -891,6 +884,41 @@ extern "C" sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* r
   SBR_CUDA(cudaGetLastError());
   ::sbr::note_launch();
   k_power_reduce<<<(cells + 255) / 256, 256, 0, st>>>(L.part, L.groups, cells, L.power, L.amax_key);
+  SBR_CUDA(cudaGetLastError());
+  return SBR_OK;
+}
+}  // namespace
+}  // namespace sbr
+
+extern "C" sbr_status sbr_power_map(const float* d_cube, const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar,
+                                    sbr_pc_state* state, sbr_stream stream) {
+  SBR_ARG(d_cube, "sbr_power_map: NULL cube");
+  sbr_status rs = check_radar(radar, "sbr_power_map");
+  if (rs != SBR_OK) return rs;
+  rs = check_cfar(cfar, radar, "sbr_power_map");
+  if (rs != SBR_OK) return rs;
+  Layout L;
+  rs = state_layout(state, radar, cfar, &L, "sbr_power_map");
+  if (rs != SBR_OK) return rs;
+  return power_map_impl(d_cube, radar, cfar, L, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* radar,
+                                     const sbr_cfar_cfg* cfar, float* d_points, sbr_pc_state* state,
+                                     sbr_stream stream) {
+  SBR_ARG(d_cube && d_points, "sbr_pointcloud: NULL cube or points");
+  sbr_status rs = check_radar(radar, "sbr_pointcloud");
+  if (rs != SBR_OK) return rs;
+  rs = check_cfar(cfar, radar, "sbr_pointcloud");
+  if (rs != SBR_OK) return rs;
+  Layout L;
+  rs = state_layout(state, radar, cfar, &L, "sbr_pointcloud");
+  if (rs != SBR_OK) return rs;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int A = cfar->n_theta, Ns = radar->n_samples;
+  const int cells = A * Ns;
+  rs = power_map_impl(d_cube, radar, cfar, L, st);
+  if (rs != SBR_OK) return rs;
   // 5-9: soft CFAR, peaks, compaction in cell order, stable sort by weight, points
   CfarArg ca{A, Ns, cfar->guard, cfar->train, cfar->alpha, cfar->floor_rel, cfar->beta, cfar->w_min};
   PointArg pa{ca, cfar->k_max, (float)(kC / (2.0 * radar->bandwidth))};
@@ -943,6 +971,76 @@ extern "C" sbr_status sbr_pc_check(const sbr_radar_cfg* radar, const sbr_cfar_cf
   return SBR_OK;
 }
 
+namespace sbr {
+namespace {
+// dL/dcube from dL/dPw (L.dpw): dY = 2 Y dPw, dX = W^H dY, then the adjoints of the
+// forward DFTs (unnormalised inverse transforms, in place).
+sbr_status cube_adjoint(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const Layout& L, float* d_gcube,
+                        cudaStream_t st) {
+  const int V = radar->n_tx * radar->n_rx, C = radar->n_chirps, Ns = radar->n_samples, A = cfar->n_theta;
+  const Steer xl = steering_table(radar);
+  float2* g = reinterpret_cast<float2*>(d_gcube);
+  switch (A / 8) {
+    case 1: launch_angle_bwd<1>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    case 2: launch_angle_bwd<2>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    case 4: launch_angle_bwd<4>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    case 8: launch_angle_bwd<8>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    case 16: launch_angle_bwd<16>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    case 32: launch_angle_bwd<32>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    default: set_error("n_theta=%d unsupported", A); return SBR_ERR_UNSUPPORTED;
+  }
+  SBR_CUDA(cudaGetLastError());
+  SBR_CUDA(fft_cols(g, V, C, Ns, +1.f, st));
+  SBR_CUDA(fft_rows(g, g, V * C, Ns, +1.f, st));
+  return SBR_OK;
+}
+
+constexpr int kMseThreads = 1024;
+
+// Eq. 16 on the power map: loss = (1/N) sum_i (Pw_i - T_i)^2 and dL/dPw_i = 2 (Pw_i - T_i) / N;
+// one CTA, each thread over a fixed stride of cells, then a fixed-order block sum.
+__global__ void __launch_bounds__(kMseThreads) k_image_mse(const float* __restrict__ Pw, const float* __restrict__ T,
+                                                           int cells, float* __restrict__ loss,
+                                                           float* __restrict__ dpw) {
+  __shared__ float red[kMseThreads / 32];
+  const float inv_n = 1.f / (float)cells;
+  float s = 0.f;
+  for (int i = threadIdx.x; i < cells; i += kMseThreads) {
+    const float d = Pw[i] - T[i];
+    s = fmaf(d, d, s);
+    if (dpw) dpw[i] = 2.f * d * inv_n;
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = red[threadIdx.x];
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) *loss = t * inv_n;
+  }
+}
+}  // namespace
+}  // namespace sbr
+
+extern "C" sbr_status sbr_image_loss(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const sbr_pc_state* state,
+                                     const float* d_target, float* d_loss, float* d_gcube, sbr_stream stream) {
+  SBR_ARG(d_target && d_loss, "sbr_image_loss: NULL target or loss");
+  sbr_status rs = check_radar(radar, "sbr_image_loss");
+  if (rs != SBR_OK) return rs;
+  rs = check_cfar(cfar, radar, "sbr_image_loss");
+  if (rs != SBR_OK) return rs;
+  Layout L;
+  rs = state_layout(state, radar, cfar, &L, "sbr_image_loss");
+  if (rs != SBR_OK) return rs;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int cells = cfar->n_theta * radar->n_samples;
+  ::sbr::note_launch();
+  k_image_mse<<<1, kMseThreads, 0, st>>>(L.power, d_target, cells, d_loss, d_gcube ? L.dpw : nullptr);
+  SBR_CUDA(cudaGetLastError());
+  if (!d_gcube) return SBR_OK;
+  return cube_adjoint(radar, cfar, L, d_gcube, st);
+}
+
 extern "C" sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar,
                                          const sbr_pc_state* state, const float* d_gpoints,
                                          float* d_gcube, sbr_stream stream) {
@@ -955,28 +1053,13 @@ extern "C" sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_c
   rs = state_layout(state, radar, cfar, &L, "sbr_pointcloud_bwd");
   if (rs != SBR_OK) return rs;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int V = radar->n_tx * radar->n_rx, C = radar->n_chirps, Ns = radar->n_samples, A = cfar->n_theta;
+  const int Ns = radar->n_samples, A = cfar->n_theta;
   const int cells = A * Ns;
-  const Steer xl = steering_table(radar);
   SBR_CUDA(cudaMemsetAsync(L.dpw, 0, sizeof(float) * cells, st));
   CfarArg ca{A, Ns, cfar->guard, cfar->train, cfar->alpha, cfar->floor_rel, cfar->beta, cfar->w_min};
   PointArg pa{ca, cfar->k_max, (float)(kC / (2.0 * radar->bandwidth))};
   ::sbr::note_launch();
   k_points_bwd<<<(cfar->k_max + 255) / 256, 256, 0, st>>>(L.power, pa, L.argmax, L.peak_cell, L.n_points,
                                                            reinterpret_cast<const float4*>(d_gpoints), L.dpw);
-  float2* g = reinterpret_cast<float2*>(d_gcube);
-  switch (A / 8) {
-    case 1: launch_angle_bwd<1>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
-    case 2: launch_angle_bwd<2>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
-    case 4: launch_angle_bwd<4>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
-    case 8: launch_angle_bwd<8>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
-    case 16: launch_angle_bwd<16>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
-    case 32: launch_angle_bwd<32>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
-    default: set_error("sbr_pointcloud_bwd: n_theta=%d unsupported", A); return SBR_ERR_UNSUPPORTED;
-  }
-  SBR_CUDA(cudaGetLastError());
-  // adjoint of the forward DFTs: unnormalised inverse transforms, in place
-  SBR_CUDA(fft_cols(g, V, C, Ns, +1.f, st));
-  SBR_CUDA(fft_rows(g, g, V * C, Ns, +1.f, st));
-  return SBR_OK;
+  return cube_adjoint(radar, cfar, L, d_gcube, st);
 }

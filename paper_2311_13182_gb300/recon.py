@@ -1,10 +1,14 @@
-"""Gradient-based mesh reconstruction against a target radar point cloud (Section 3.4).
+"""Gradient-based mesh reconstruction against a target radar observation (Section 3.4).
 
 One iteration (Eq. 14 objective, Eq. 15 update; Adam in place of plain SGD):
   scene update -> trace -> synthesize -> point cloud            (forward, Eq. 8, Eq. 16's T)
   loss = weighted squared Chamfer(points, target) + w_lap * uniform Laplacian
   point-cloud adjoint -> synthesis adjoint (Eq. 11-12) -> trace adjoint (Eq. 13)
   Adam step on the vertex positions
+or, with loss="image", the paper's spatial multi-antenna loss (Eq. 16): the
+target is a range-angle power map [n_theta, N_s], the forward stops at the power
+map, and loss = mean squared image difference + w_lap * Laplacian, whose adjoint
+enters the synthesis adjoint directly.
 Every step is a library kernel on one stream with no host synchronisation, so
 the whole iteration is captured once into a CUDA graph and replayed.
 """
@@ -19,7 +23,10 @@ from .autograd import Simulator
 
 class Reconstruction:
     def __init__(self, verts0: np.ndarray, faces: np.ndarray, target: torch.Tensor, radar, grid, max_bounces,
-                 cfar, lr=1e-3, lap_weight=0.1, ray_ids=None, recompute=False, device="cuda"):
+                 cfar, lr=1e-3, lap_weight=0.1, ray_ids=None, recompute=False, loss="chamfer", device="cuda"):
+        if loss not in ("chamfer", "image"):
+            raise ValueError(f"loss must be 'chamfer' or 'image', not {loss!r}")
+        self.kind = loss
         self.verts = torch.from_numpy(np.ascontiguousarray(verts0, np.float32)).to(device)
         self.nv = self.verts.shape[0]
         self.sim = Simulator(faces, self.nv, radar, grid, max_bounces, cfar, ray_ids=ray_ids,
@@ -36,11 +43,18 @@ class Reconstruction:
         self.graph = None
 
     def _iteration(self):
-        pts, n = self.sim.forward(self.verts)
-        sim.chamfer(pts, n, self.target, loss=self.loss, gpred=self.gpoints)
+        if self.kind == "image":
+            self.sim.forward_image(self.verts)
+            sim.image_loss(self.sim.state, self.target, loss=self.loss, gcube=self.sim.gcube)
+        else:
+            pts, n = self.sim.forward(self.verts)
+            sim.chamfer(pts, n, self.target, loss=self.loss, gpred=self.gpoints)
         self.grad.zero_()
         sim.laplacian(self.verts, self.adj, self.lap_weight, self.loss, self.grad)
-        self.sim.backward(self.verts, self.gpoints, self.grad)
+        if self.kind == "image":
+            self.sim.backward_cube(self.verts, self.sim.gcube, self.grad)
+        else:
+            self.sim.backward(self.verts, self.gpoints, self.grad)
         sim.adam_step(self.verts, self.grad, self.m, self.v, self.step_count, lr=self.lr)
 
     def step(self):

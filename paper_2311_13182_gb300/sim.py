@@ -266,6 +266,30 @@ def pointcloud(cube: torch.Tensor, radar, cfar, state: PcState | None = None, ou
     return out, state
 
 
+def power_map(cube: torch.Tensor, radar, cfar, state: PcState | None = None, stream=None) -> PcState:
+    """sbr_power_map: the range-angle power map [n_theta, N_s] of the cube, left in ``state.power()``."""
+    _need_cuda(cube, torch.float32, "cube")
+    if state is None:
+        state = PcState(radar, cfar, device=cube.device)
+    L.call("sbr_power_map", _vp(cube), ctypes.byref(state.r), ctypes.byref(state.c), ctypes.byref(state.s),
+           _stream(stream))
+    return state
+
+
+def image_loss(state: PcState, target: torch.Tensor, loss: torch.Tensor | None = None,
+               gcube: torch.Tensor | None = None, want_grad: bool = True, stream=None):
+    """sbr_image_loss (Eq. 16): loss [1] = mean (Pw - target)^2 over the power map of ``state``,
+    and dloss/dcube [V, C, N_s, 2] when ``want_grad``."""
+    _need_cuda(target, torch.float32, "target")
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=target.device)
+    if want_grad and gcube is None:
+        gcube = torch.empty((*state.shape, 2), dtype=torch.float32, device=target.device)
+    L.call("sbr_image_loss", ctypes.byref(state.r), ctypes.byref(state.c), ctypes.byref(state.s), _vp(target),
+           _vp(loss), _vp(gcube if want_grad else None), _stream(stream))
+    return loss, gcube
+
+
 def pointcloud_bwd(state: PcState, gpoints: torch.Tensor, out: torch.Tensor | None = None, stream=None):
     """sbr_pointcloud_bwd: dL/dcube [V, C, N_s, 2] from dL/dpoints [k_max, 4]."""
     _need_cuda(gpoints, torch.float32, "gpoints")

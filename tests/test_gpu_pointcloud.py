@@ -133,3 +133,32 @@ def test_power_map_shapes(sbr, n_tx, n_rx, C, Ns, A):
     _, st = sbr.pointcloud(to_cube_t(cube), radar, cfg)
     st.check()
     assert rel_l2(st.power().double().cpu().numpy(), Pw) < 1e-5
+
+
+def test_image_loss_value_and_cube_gradient(sbr):
+    """Eq. 16 image loss of a random 4-antenna, 2-chirp cube against a perturbed copy of its own
+    power map: the value against the oracle's FP64 chain, dloss/dcube against FP64 central
+    differences of the oracle along random directions."""
+    from sbr_inputs import _radar
+    radar = _radar(77e9, 4e9, 40e-6, 128, 2, 1, 2.0, n_rx=4)
+    rng = np.random.default_rng(21)
+    cube = rng.normal(size=(4, 2, 128)) + 1j * rng.normal(size=(4, 2, 128))
+    cfg = CfarParams()
+    _, _, Pw = opc.power_map(cube, radar, cfg)
+    target = Pw * rng.uniform(0.5, 1.5, size=Pw.shape)
+    st = sbr.power_map(to_cube_t(cube), radar, cfg)
+    st.check()
+    loss, gcube = sbr.image_loss(st, torch.from_numpy(target.astype(np.float32)).cuda())
+    ref = opc.image_loss(cube, target, radar, cfg)
+    assert abs(float(loss.item()) - ref) <= 1e-5 * abs(ref)
+    g = gcube.double().cpu().numpy()
+    g = g[..., 0] + 1j * g[..., 1]
+    h = 1e-5
+    for _ in range(3):
+        u = rng.normal(size=cube.shape) + 1j * rng.normal(size=cube.shape)
+        fd = (opc.image_loss(cube + h * u, target, radar, cfg) - opc.image_loss(cube - h * u, target, radar, cfg)) / (2 * h)
+        an = float(np.sum(g.real * u.real + g.imag * u.imag))
+        assert abs(an - fd) <= 1e-3 * abs(fd), (an, fd)
+    # the loss alone (no gradient requested) gives the same value
+    loss2, _ = sbr.image_loss(st, torch.from_numpy(target.astype(np.float32)).cuda(), want_grad=False)
+    assert float(loss2.item()) == float(loss.item())
