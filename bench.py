@@ -619,12 +619,16 @@ def serve_arm(sbr, torch, args):
     sat = srv.drain(600)
     sat_wall = time.perf_counter() - t0
     srv.close()
+    gpu = [d["gpu_ms"] for d in ok]
     out = {"requests": len(items), "completed_ok": len(ok), "rate_hz": rate,
            "rate_rule": "0.8 x one-at-a-time capacity", "capacity_one_at_a_time_hz": capacity,
-           "paced": {"wall_s": wall, **S.percentiles(lat)},
+           "paced": {"wall_s": wall, **S.percentiles(lat),
+                     "gpu_ms": {k.replace("_ms", ""): v for k, v in S.percentiles(gpu).items()},
+                     "device": S.device_overlap(ok)},
            "one_at_a_time_same_arrivals": S.percentiles(seq_lat),
            "saturated": {"rays_per_s": sum(rays) / sat_wall, "wall_s": sat_wall,
-                         "completed_ok": sum(1 for d in sat if d["status"] == 0)},
+                         "completed_ok": sum(1 for d in sat if d["status"] == 0),
+                         "device": S.device_overlap(sat)},
            "one_at_a_time": {"rays_per_s": sum(rays) / (sum(seq) * 1e-3), "wall_s": sum(seq) * 1e-3,
                              "service_p50_ms": float(np.percentile(seq, 50)),
                              "service_p99_ms": float(np.percentile(seq, 99))},

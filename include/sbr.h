@@ -325,7 +325,9 @@ sbr_status sbr_image_loss(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, 
 sbr_status sbr_pc_check(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const sbr_pc_state* state,
                         sbr_stream stream);
 
-/* Adjoint: d_gpoints [k_max][4] -> d_gcube [V][C][N_s] complex (overwritten). */
+/* Adjoint: d_gpoints [k_max][4] -> d_gcube [V][C][N_s] complex (overwritten).
+ * Bitwise reproducible: the gradients of overlapping point neighbourhoods are
+ * summed per power-map cell as fixed-point integers, the rest in fixed orders. */
 sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar,
                               const sbr_pc_state* state, const float* d_gpoints,
                               float* d_gcube, sbr_stream stream);
@@ -334,18 +336,25 @@ sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cf
 /* Trace adjoint (Section 3.3, Eq. 13; interior derivative, Eq. 4-5)        */
 /* ------------------------------------------------------------------------ */
 
+/* Scratch bytes of sbr_trace_bwd for a scene of nv vertices (a 64-bit
+ * accumulator per vertex coordinate and one status word). */
+size_t sbr_trace_bwd_ws_bytes(int32_t nv);
+
 /* Accumulates dL/dverts [nv][3] (added to d_gverts) from per-path gradients
  * d_glen (dL/d path length, [V*path_cap]) and d_gamp (dL/dA) through the
  * hit points, reflection directions and |d.n| of every bounce; triangle
  * indices stay those of the forward trace (visibility is held fixed).
  * d_verts are the vertices the scene was built from; d_ray_ids is the
- * forward call's ray list (NULL when it traced the whole grid).  Gradients
- * are added with float atomics (order-dependent in the last bits).
- * max_bounces <= 8. */
+ * forward call's ray list (NULL when it traced the whole grid).  The per-corner
+ * contributions are summed per vertex as 64-bit fixed-point integers (scaled by
+ * a power of two set from the largest contribution; resolution ~1e-12 of it),
+ * so the gradient is bitwise reproducible whatever order threads run in.
+ * d_ws (256-byte aligned) holds sbr_trace_bwd_ws_bytes(nv) bytes, else
+ * SBR_ERR_OOM.  max_bounces <= 8. */
 sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts, const sbr_radar_cfg* radar,
                          const sbr_ray_grid* grid, const int32_t* d_ray_ids,
                          const sbr_paths* paths, const float* d_glen, const float* d_gamp,
-                         float* d_gverts, sbr_stream stream);
+                         float* d_gverts, void* d_ws, size_t ws_bytes, sbr_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Reconstruction loss and optimiser (Section 3.4: Eq. 14 objective and the */
@@ -401,8 +410,10 @@ void sbr_arena_destroy(sbr_arena* a);
 
 typedef enum { SBR_REQ_FORWARD = 0, SBR_REQ_RECON = 1 } sbr_request_kind;
 
-/* A request.  Host arrays are copied at submission; out_* must stay valid
- * until the request's completion is returned by sbr_server_poll. */
+/* A request.  Host arrays are copied at submission (and, at admission, into the
+ * slot's page-locked staging buffer, from which the device copies run
+ * asynchronously); out_* must stay valid until the request's completion is
+ * returned by sbr_server_poll. */
 typedef struct {
   int32_t kind;         /* sbr_request_kind */
   int32_t max_bounces;
@@ -431,6 +442,9 @@ typedef struct {
   float gpu_ms;         /* device time from admission to completion (CUDA events) */
   double t_submit_us, t_admit_us, t_done_us; /* host clock, microseconds since sbr_server_create */
   uint64_t footprint;   /* device bytes the request held while running */
+  double gpu_t0_ms, gpu_t1_ms; /* device clock (CUDA events), ms since sbr_server_create: start and end of
+                                  the request's work on its slot stream; intervals of different requests
+                                  that overlap ran concurrently on the device */
 } sbr_completion;
 
 typedef struct {

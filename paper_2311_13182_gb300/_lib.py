@@ -68,7 +68,8 @@ class Request(ctypes.Structure):
 class Completion(ctypes.Structure):
     _fields_ = [("ticket", c_i64), ("status", c_i32), ("n_points", c_i32), ("scene_cached", c_i32),
                 ("cube_cached", c_i32), ("loss", c_f32), ("gpu_ms", c_f32), ("t_submit_us", c_f64),
-                ("t_admit_us", c_f64), ("t_done_us", c_f64), ("footprint", ctypes.c_uint64)]
+                ("t_admit_us", c_f64), ("t_done_us", c_f64), ("footprint", ctypes.c_uint64),
+                ("gpu_t0_ms", c_f64), ("gpu_t1_ms", c_f64)]
 
 
 class ServerStats(ctypes.Structure):
@@ -117,7 +118,8 @@ _SIGS = {
     "sbr_pc_check": (c_i32, [P(RadarCfg), P(CfarCfg), P(PcState), c_p]),
     "sbr_power_map": (c_i32, [c_p, P(RadarCfg), P(CfarCfg), P(PcState), c_p]),
     "sbr_image_loss": (c_i32, [P(RadarCfg), P(CfarCfg), P(PcState), c_p, c_p, c_p, c_p]),
-    "sbr_trace_bwd": (c_i32, [c_p, c_p, P(RadarCfg), P(RayGrid), c_p, P(Paths), c_p, c_p, c_p, c_p]),
+    "sbr_trace_bwd_ws_bytes": (c_sz, [c_i32]),
+    "sbr_trace_bwd": (c_i32, [c_p, c_p, P(RadarCfg), P(RayGrid), c_p, P(Paths), c_p, c_p, c_p, c_p, c_sz, c_p]),
     "sbr_chamfer": (c_i32, [c_p, c_p, c_i32, c_p, c_i32, c_p, c_p, c_p]),
     "sbr_mesh_adjacency": (c_i32, [c_p, c_i32, c_i32, c_p, c_p, c_i32, P(c_i32)]),
     "sbr_laplacian_ws_bytes": (c_sz, [c_i32]),

@@ -40,6 +40,7 @@ class Simulator:
         self.points = torch.empty((cfar.k_max, 4), dtype=torch.float32, device=device)
         self.state = sim.PcState(radar, cfar, device)
         self.gcube = torch.empty_like(self.cube)
+        self.bwd_ws = torch.empty(sim.trace_bwd_ws_bytes(nv), dtype=torch.uint8, device=device)
         # forward passes so far: the backward reads the state of the latest one only
         self.generation = 0
 
@@ -77,7 +78,8 @@ class Simulator:
         """Adds dL/dverts to gverts for upstream dL/dcube [V, C, N_s, 2]."""
         paths = self.paths if self.paths is not None else self._trace(verts)
         glen, gamp = sim.synthesize_bwd(paths, self.radar, gcube, ws=self.synth_ws)
-        sim.trace_bwd(self.scene, verts, self.radar, self.grid, paths, glen, gamp, self.ray_ids, gverts=gverts)
+        sim.trace_bwd(self.scene, verts, self.radar, self.grid, paths, glen, gamp, self.ray_ids, gverts=gverts,
+                      ws=self.bwd_ws)
         return gverts
 
 

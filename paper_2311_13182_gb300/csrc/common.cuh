@@ -70,6 +70,42 @@ __device__ inline uint32_t warp_peers8(uint32_t d, bool ok) {
   return m;
 }
 
+// ---- order-independent (bitwise deterministic) scatter-add -------------------
+//
+// Float atomics add in whatever order threads arrive, so such sums change in
+// their last bits from run to run.  This scatter adds integers instead, whose sum
+// does not depend on the order: pass 1 finds the largest magnitude m among the
+// contributions (atomicMax on the float bits), pass 2 adds each contribution x as
+// round(x 2^E) to a 64-bit accumulator, E chosen so that 2^log2n contributions of
+// magnitude <= m stay below 2^62, and a finishing pass converts acc 2^-E back to
+// float.  The resolution 2^-E is about m 2^(log2n - 61), ~1e-12 m for a million
+// contributions: far finer than the FP32 sum it replaces.
+struct FixScatter {
+  unsigned long long* acc;  // zeroed before pass 2
+  unsigned int* max_bits;   // zeroed before pass 1
+  int log2n;                // ceil(log2(a bound on the number of contributions))
+};
+
+__host__ inline int ceil_log2(int64_t n) {
+  int l = 0;
+  while (l < 62 && ((int64_t)1 << l) < n) ++l;
+  return l;
+}
+
+// Exponent E for the largest magnitude recorded: m < 2^e with e = biased exponent - 126.
+__device__ inline int fix_exp(unsigned int max_bits, int log2n) {
+  return 62 - log2n - ((int)((max_bits >> 23) & 0xffu) - 126);
+}
+__device__ inline void fix_add(unsigned long long* acc, float x, int E) {
+  atomicAdd(acc, (unsigned long long)__double2ll_rn(ldexp((double)x, E)));
+}
+__device__ inline float fix_get(unsigned long long a, int E) { return (float)ldexp((double)(long long)a, -E); }
+// Warp-reduced max of |x| over the calling warp's lanes (all 32 must call), one atomic per warp.
+__device__ inline void fix_note_warp(unsigned int* max_bits, float local_max_abs) {
+  const unsigned int b = __reduce_max_sync(0xffffffffu, __float_as_uint(local_max_abs));
+  if ((threadIdx.x & 31) == 0 && b) atomicMax(max_bits, b);
+}
+
 // Argument validation shared by the entry points (trace.cu).
 sbr_status check_radar(const sbr_radar_cfg* r, const char* who);
 sbr_status check_grid(const sbr_ray_grid* g, const char* who);

@@ -554,16 +554,29 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const float* __restrict_
 
 // ---- adjoint ----------------------------------------------------------------
 
-__device__ inline void add_dl(float* dPw, const float* Pw, size_t cell, float dl) {
+// dPw contributions go through the order-independent fixed-point scatter
+// (common.cuh): pass 0 records the largest magnitude, pass 1 adds the integers.
+template <int kPass>
+struct DpwScatter {
+  const FixScatter& fs;
+  int E;
+  float& lmax;
+  __device__ void add(size_t cell, float x) const {
+    if (kPass == 0) lmax = fmaxf(lmax, fabsf(x));
+    else fix_add(&fs.acc[cell], x, E);
+  }
+};
+
+template <int kPass>
+__device__ inline void add_dl(const DpwScatter<kPass>& sc, const float* Pw, size_t cell, float dl) {
   const float p = Pw[cell];
-  if (p > 1e-30f && dl != 0.f) atomicAdd(&dPw[cell], dl / p);
+  if (p > 1e-30f && dl != 0.f) sc.add(cell, dl / p);
 }
 
-__global__ void k_points_bwd(const float* __restrict__ Pw, PointArg pa, const int32_t* __restrict__ amax,
-                             const int32_t* __restrict__ cells, const int32_t* __restrict__ n_pts,
-                             const float4* __restrict__ gpts, float* __restrict__ dPw) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *n_pts) return;
+template <int kPass>
+__device__ void point_adjoint(int i, const float* __restrict__ Pw, const PointArg& pa, const int32_t* __restrict__ amax,
+                              const int32_t* __restrict__ cells, const float4* __restrict__ gpts,
+                              const DpwScatter<kPass>& sc) {
   const CfarArg& c = pa.c;
   const int cell = cells[i];
   const int a = cell / c.Ns, k = cell - a * c.Ns;
@@ -579,13 +592,13 @@ __global__ void k_points_bwd(const float* __restrict__ Pw, PointArg pa, const in
   float dl0 = gz;
   const float dN = -gz * c.alpha / den;
   const float dF = -gz / den;
-  atomicAdd(&dPw[am], dF * c.floor_rel);
+  sc.add((size_t)am, dF * c.floor_rel);
   if (cnt > 0) {
     int lo0, lo1, hi0, hi1;
     noise_cells(c, k, lo0, lo1, hi0, hi1);
     const float e = dN / (float)cnt;
-    for (int j = lo0; j < lo1; ++j) atomicAdd(&dPw[(size_t)a * c.Ns + j], e);
-    for (int j = hi0; j < hi1; ++j) atomicAdd(&dPw[(size_t)a * c.Ns + j], e);
+    for (int j = lo0; j < lo1; ++j) sc.add((size_t)a * c.Ns + j, e);
+    for (int j = hi0; j < hi1; ++j) sc.add((size_t)a * c.Ns + j, e);
   }
   // position: r = (k + dk) bin, u = -1 + 2 (a + da) / A, p = (r u, 0, r sqrt(1 - u^2))
   const float* row = Pw + (size_t)a * c.Ns;
@@ -603,15 +616,32 @@ __global__ void k_points_bwd(const float* __restrict__ Pw, PointArg pa, const in
   const float ddk = dr * pa.range_bin;
   const float dda = du * 2.f / (float)c.A;
   dl0 += ddk * r0 + dda * a0;
-  add_dl(dPw, Pw, (size_t)cell, dl0);
+  add_dl(sc, Pw, (size_t)cell, dl0);
   if (k > 0 && k < c.Ns - 1) {
-    add_dl(dPw, Pw, (size_t)cell - 1, ddk * rm);
-    add_dl(dPw, Pw, (size_t)cell + 1, ddk * rp);
+    add_dl(sc, Pw, (size_t)cell - 1, ddk * rm);
+    add_dl(sc, Pw, (size_t)cell + 1, ddk * rp);
   }
   if (a > 0 && a < c.A - 1) {
-    add_dl(dPw, Pw, (size_t)cell - c.Ns, dda * am_);
-    add_dl(dPw, Pw, (size_t)cell + c.Ns, dda * ap);
+    add_dl(sc, Pw, (size_t)cell - c.Ns, dda * am_);
+    add_dl(sc, Pw, (size_t)cell + c.Ns, dda * ap);
   }
+}
+
+template <int kPass>
+__global__ void k_points_bwd(const float* __restrict__ Pw, PointArg pa, const int32_t* __restrict__ amax,
+                             const int32_t* __restrict__ cells, const int32_t* __restrict__ n_pts,
+                             const float4* __restrict__ gpts, FixScatter fs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float lmax = 0.f;
+  const DpwScatter<kPass> sc{fs, kPass == 0 ? 0 : fix_exp(*fs.max_bits, fs.log2n), lmax};
+  if (i < *n_pts) point_adjoint<kPass>(i, Pw, pa, amax, cells, gpts, sc);
+  if (kPass == 0) fix_note_warp(fs.max_bits, lmax);  // every lane of the warp reaches this
+}
+
+// dPw[i] = acc[i] 2^-E
+__global__ void k_fix_finish(FixScatter fs, int n, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = fix_get(fs.acc[i], fix_exp(*fs.max_bits, fs.log2n));
 }
 
 // dX[v,d,k] = sum_a conj(W[a,v]) 2 Y[a,d,k] dPw[a,k], Y recomputed from X.
@@ -681,6 +711,8 @@ struct Layout {
   void* scan_scr;
   void* sort_scr;
   float* dpw;
+  unsigned long long* dpw_acc;  // fixed-point dPw of the point adjoint, then its max word
+  unsigned int* dpw_max;
   int groups;
 };
 
@@ -733,6 +765,8 @@ size_t pc_layout(Layout* L, void* mem, const sbr_radar_cfg* r, const sbr_cfar_cf
   L->scan_scr = c.take<char>(scan_scratch_bytes(cells));
   L->sort_scr = c.take<char>(sort_scratch_bytes(cells));
   L->dpw = c.take<float>(cells);
+  L->dpw_acc = c.take<unsigned long long>(cells);
+  L->dpw_max = c.take<unsigned int>(1);
   return c.bytes();
 }
 
@@ -1055,11 +1089,19 @@ extern "C" sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_c
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int Ns = radar->n_samples, A = cfar->n_theta;
   const int cells = A * Ns;
-  SBR_CUDA(cudaMemsetAsync(L.dpw, 0, sizeof(float) * cells, st));
+  // accumulator and max word are adjacent: one memset clears both
+  SBR_CUDA(cudaMemsetAsync(L.dpw_acc, 0,
+                           reinterpret_cast<char*>(L.dpw_max + 1) - reinterpret_cast<char*>(L.dpw_acc), st));
   CfarArg ca{A, Ns, cfar->guard, cfar->train, cfar->alpha, cfar->floor_rel, cfar->beta, cfar->w_min};
   PointArg pa{ca, cfar->k_max, (float)(kC / (2.0 * radar->bandwidth))};
+  FixScatter fs{L.dpw_acc, L.dpw_max, ceil_log2((int64_t)cfar->k_max * (6 + 2 * (int64_t)cfar->train))};
+  const float4* gp = reinterpret_cast<const float4*>(d_gpoints);
+  const int nb = (cfar->k_max + 255) / 256;
   ::sbr::note_launch();
-  k_points_bwd<<<(cfar->k_max + 255) / 256, 256, 0, st>>>(L.power, pa, L.argmax, L.peak_cell, L.n_points,
-                                                           reinterpret_cast<const float4*>(d_gpoints), L.dpw);
+  k_points_bwd<0><<<nb, 256, 0, st>>>(L.power, pa, L.argmax, L.peak_cell, L.n_points, gp, fs);
+  ::sbr::note_launch();
+  k_points_bwd<1><<<nb, 256, 0, st>>>(L.power, pa, L.argmax, L.peak_cell, L.n_points, gp, fs);
+  ::sbr::note_launch();
+  k_fix_finish<<<(cells + 255) / 256, 256, 0, st>>>(fs, cells, L.dpw);
   return cube_adjoint(radar, cfar, L, d_gcube, st);
 }

@@ -148,7 +148,7 @@ struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t start = nullptr, done = nullptr;
   Req* req = nullptr;
-  char* pinned = nullptr;  // staging for results
+  char* pinned = nullptr;  // page-locked staging: the request's results, then its inputs
   size_t pinned_bytes = 0;
 };
 
@@ -166,6 +166,7 @@ struct sbr_server {
   std::map<uint64_t, std::unique_ptr<sbr::SceneEntry>> scenes;
   std::map<std::pair<uint64_t, uint64_t>, std::unique_ptr<sbr::CubeEntry>> cubes;
   std::chrono::steady_clock::time_point t0;
+  cudaEvent_t t0_event = nullptr;  // device-clock origin of the completions' gpu_t0_ms / gpu_t1_ms
   int64_t next_ticket = 1, submitted = 0, completed = 0, cache_hits = 0;
   uint64_t clock = 0;
 };
@@ -195,7 +196,8 @@ Sizes request_sizes(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const 
               + s.cube                                              // gcube
               + sbr_arena::round(sizeof(int32_t) * ((size_t)q->nv + 1)) +
               sbr_arena::round(sizeof(int32_t) * 6 * (size_t)q->nt)  // adjacency (<= 6 per face)
-              + sbr_arena::round(sbr_laplacian_ws_bytes(q->nv)) + 2 * kAlign;  // step, loss
+              + sbr_arena::round(sbr_laplacian_ws_bytes(q->nv))
+              + sbr_arena::round(sbr_trace_bwd_ws_bytes(q->nv)) + 2 * kAlign;  // step, loss
   }
   return s;
 }
@@ -271,9 +273,39 @@ bool ensure_pinned(Slot& sl, size_t bytes) {
   return true;
 }
 
-size_t pinned_need(const sbr_server* s, const Req* q) {
-  return sizeof(float) * 4 * (size_t)s->cfar.k_max + 64 + (q->r.out_verts ? sizeof(float) * 3 * (size_t)q->r.nv : 0);
+inline size_t round256(size_t n) { return (n + 255) / 256 * 256; }
+
+// Results area of a slot's pinned buffer: points, status words, final vertices.
+size_t pinned_out(const sbr_server* s, const Req* q) {
+  return round256(sizeof(float) * 4 * (size_t)s->cfar.k_max + 64 +
+                  (q->r.out_verts ? sizeof(float) * 3 * (size_t)q->r.nv : 0));
 }
+
+// Inputs area after it: the host arrays the request's device work reads.
+size_t pinned_in(const Req* q) {
+  size_t n = round256(q->verts.size() * sizeof(float)) + round256(q->faces.size() * sizeof(int32_t));
+  if (q->r.kind == SBR_REQ_RECON)
+    n += round256(q->target.size() * sizeof(float)) + round256(q->adj_off.size() * sizeof(int32_t)) +
+         round256(q->adj.size() * sizeof(int32_t));
+  return n;
+}
+
+size_t pinned_need(const sbr_server* s, const Req* q) { return pinned_out(s, q) + pinned_in(q); }
+
+// Copies a request's host arrays into the inputs area of its slot's pinned buffer,
+// so the host-to-device copies from there run asynchronously on the slot's stream
+// (a copy from pageable memory is staged through a driver buffer by the calling
+// thread, which would hold up the poll loop while other slots run).
+struct Staging {
+  char* at;
+  template <class T>
+  const T* put(const std::vector<T>& v) {
+    T* p = reinterpret_cast<T*>(at);
+    if (!v.empty()) memcpy(p, v.data(), v.size() * sizeof(T));
+    at += round256(v.size() * sizeof(T));
+    return p;
+  }
+};
 
 #define ENQ(call)                        \
   do {                                   \
@@ -305,8 +337,11 @@ sbr_status enqueue_forward(sbr_server* s, Req* q, Slot& sl) {
     float* dv = m.take<float>(3 * (size_t)r.nv);
     int32_t* df = m.take<int32_t>(3 * (size_t)r.nt);
     void* dmem = m.take<char>(q->sz.scene);
-    ENQ_CUDA(cudaMemcpyAsync(dv, q->verts.data(), sizeof(float) * 3 * r.nv, cudaMemcpyHostToDevice, st));
-    ENQ_CUDA(cudaMemcpyAsync(df, q->faces.data(), sizeof(int32_t) * 3 * r.nt, cudaMemcpyHostToDevice, st));
+    Staging in{sl.pinned + pinned_out(s, q)};
+    const float* hv = in.put(q->verts);
+    const int32_t* hf = in.put(q->faces);
+    ENQ_CUDA(cudaMemcpyAsync(dv, hv, sizeof(float) * 3 * r.nv, cudaMemcpyHostToDevice, st));
+    ENQ_CUDA(cudaMemcpyAsync(df, hf, sizeof(int32_t) * 3 * r.nt, cudaMemcpyHostToDevice, st));
     ENQ(sbr_scene_create(dv, r.nv, df, r.nt, dmem, q->sz.scene, reinterpret_cast<sbr_stream>(st), &scene));
     if (q->scene_ref) {
       q->scene_ref->scene = scene;
@@ -374,14 +409,22 @@ sbr_status enqueue_recon(sbr_server* s, Req* q, Slot& sl) {
   int32_t* adj = c.take<int32_t>(q->adj.size() ? q->adj.size() : 1);
   const size_t lws = sbr_laplacian_ws_bytes(r.nv);
   void* lap = c.take<char>(lws);
+  const size_t bws = sbr_trace_bwd_ws_bytes(r.nv);
+  void* bwd = c.take<char>(bws);
   int32_t* step = c.take<int32_t>(1);
   float* loss = c.take<float>(1);
-  ENQ_CUDA(cudaMemcpyAsync(dv, q->verts.data(), sizeof(float) * 3 * r.nv, cudaMemcpyHostToDevice, st));
-  ENQ_CUDA(cudaMemcpyAsync(df, q->faces.data(), sizeof(int32_t) * 3 * r.nt, cudaMemcpyHostToDevice, st));
-  ENQ_CUDA(cudaMemcpyAsync(tgt, q->target.data(), sizeof(float) * 4 * r.n_target, cudaMemcpyHostToDevice, st));
-  ENQ_CUDA(cudaMemcpyAsync(aoff, q->adj_off.data(), sizeof(int32_t) * (r.nv + 1), cudaMemcpyHostToDevice, st));
+  Staging in{sl.pinned + pinned_out(s, q)};
+  const float* hv = in.put(q->verts);
+  const int32_t* hf = in.put(q->faces);
+  const float* ht = in.put(q->target);
+  const int32_t* ho = in.put(q->adj_off);
+  const int32_t* ha = in.put(q->adj);
+  ENQ_CUDA(cudaMemcpyAsync(dv, hv, sizeof(float) * 3 * r.nv, cudaMemcpyHostToDevice, st));
+  ENQ_CUDA(cudaMemcpyAsync(df, hf, sizeof(int32_t) * 3 * r.nt, cudaMemcpyHostToDevice, st));
+  ENQ_CUDA(cudaMemcpyAsync(tgt, ht, sizeof(float) * 4 * r.n_target, cudaMemcpyHostToDevice, st));
+  ENQ_CUDA(cudaMemcpyAsync(aoff, ho, sizeof(int32_t) * (r.nv + 1), cudaMemcpyHostToDevice, st));
   if (!q->adj.empty())
-    ENQ_CUDA(cudaMemcpyAsync(adj, q->adj.data(), sizeof(int32_t) * q->adj.size(), cudaMemcpyHostToDevice, st));
+    ENQ_CUDA(cudaMemcpyAsync(adj, ha, sizeof(int32_t) * q->adj.size(), cudaMemcpyHostToDevice, st));
   ENQ_CUDA(cudaMemsetAsync(m1, 0, sizeof(float) * 3 * r.nv, st));
   ENQ_CUDA(cudaMemsetAsync(m2, 0, sizeof(float) * 3 * r.nv, st));
   ENQ_CUDA(cudaMemsetAsync(step, 0, sizeof(int32_t), st));
@@ -398,7 +441,7 @@ sbr_status enqueue_recon(sbr_server* s, Req* q, Slot& sl) {
     ENQ(sbr_laplacian(dv, r.nv, aoff, adj, r.lap_weight, loss, grad, lap, lws, ss));
     ENQ(sbr_pointcloud_bwd(&s->radar, &s->cfar, &pc, gpts, gcube, ss));
     ENQ(sbr_synthesize_bwd(&paths, &s->radar, gcube, glen, gamp, ws, q->sz.ws, ss));
-    ENQ(sbr_trace_bwd(scene, dv, &s->radar, &r.grid, nullptr, &paths, glen, gamp, grad, ss));
+    ENQ(sbr_trace_bwd(scene, dv, &s->radar, &r.grid, nullptr, &paths, glen, gamp, grad, bwd, bws, ss));
     ENQ(sbr_adam_step(dv, grad, m1, m2, 3 * (int64_t)r.nv, step, r.lr, 0.9f, 0.999f, 1e-8f, ss));
   }
   float* hp = reinterpret_cast<float*>(sl.pinned);
@@ -467,6 +510,8 @@ void complete(sbr_server* s, Req* q, sbr_status status, Slot* sl) {
     if (err) cpl.status = SBR_ERR_INVALID_ARG;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, sl->start, sl->done) == cudaSuccess) cpl.gpu_ms = ms;
+    if (cudaEventElapsedTime(&ms, s->t0_event, sl->start) == cudaSuccess) cpl.gpu_t0_ms = ms;
+    if (cudaEventElapsedTime(&ms, s->t0_event, sl->done) == cudaSuccess) cpl.gpu_t1_ms = ms;
   }
   s->done.push_back(cpl);
   s->completed++;
@@ -592,6 +637,8 @@ extern "C" sbr_status sbr_server_create(void* d_arena, size_t arena_bytes, int32
     SBR_CUDA(cudaEventCreate(&sl.start));
     SBR_CUDA(cudaEventCreate(&sl.done));
   }
+  SBR_CUDA(cudaEventCreate(&s->t0_event));
+  SBR_CUDA(cudaEventRecord(s->t0_event, s->slots[0].stream));
   *out = s.release();
   return SBR_OK;
 }
@@ -732,5 +779,6 @@ extern "C" void sbr_server_destroy(sbr_server* s) {
   }
   for (auto& kv : s->cubes) cudaEventDestroy(kv.second->ready);
   for (auto* q : s->waiting) delete q;
+  if (s->t0_event) cudaEventDestroy(s->t0_event);
   delete s;
 }

@@ -11,7 +11,10 @@
 //   L_in = |h_1 - Tx_t| + sum_{j=2..k} |h_j - h_{j-1}|,  L_out = |Rx_r - h_k|.
 // One thread per ray accumulates the adjoints of its path lengths and
 // strengths onto the hit points and |d.n| terms, then sweeps the bounces in
-// reverse, and adds the per-corner vertex gradients with atomics.
+// reverse, and adds the per-corner vertex gradients to the vertices with the
+// order-independent fixed-point scatter of common.cuh (two passes over the rays:
+// the largest contribution, then the integer sums), so the gradient is bitwise
+// the same on every run.
 #include <math.h>
 
 #include "scene.cuh"
@@ -23,7 +26,7 @@ constexpr int kMaxK = 8;
 
 struct GridF {
   float o[3], ax[3], ua[3], va[3];
-  double th;
+  float start, step;  // first cell centre -tan_half (1 - 1/G) and the cell pitch 2 tan_half / G
   int G;
 };
 
@@ -37,34 +40,38 @@ __device__ inline float3 ld3(const float* v, int i) { return f3(v[3 * i], v[3 * 
 __device__ inline float len3(float3 a) { return sqrtf(dot(a, a)); }
 __device__ inline void add3(float3& a, float3 b) { a = a + b; }
 
-__device__ inline void scatter(float* g, int vi, float3 d) {
-  atomicAdd(&g[3 * vi], d.x);
-  atomicAdd(&g[3 * vi + 1], d.y);
-  atomicAdd(&g[3 * vi + 2], d.z);
+// Pass 0 records the largest |component|, pass 1 adds the fixed-point values.
+template <int kPass>
+__device__ inline void scatter(const FixScatter& fs, int E, float& lmax, int vi, float3 d) {
+  if (kPass == 0) {
+    lmax = fmaxf(lmax, fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z))));
+  } else {
+    fix_add(&fs.acc[3 * vi], d.x, E);
+    fix_add(&fs.acc[3 * vi + 1], d.y, E);
+    fix_add(&fs.acc[3 * vi + 2], d.z, E);
+  }
 }
 
-__global__ void __launch_bounds__(128) k_trace_bwd(
-    const float* __restrict__ verts, int nv, const int32_t* __restrict__ faces, GridF g, RadarF rd,
-    const int32_t* __restrict__ ray_ids, int n_rays, int K, const sbr_hit* __restrict__ hits,
-    const float4* __restrict__ hit_pos, const int32_t* __restrict__ first,
-    const float4* __restrict__ prep, int64_t cap, const float* __restrict__ glen,
-    const float* __restrict__ gamp, float* __restrict__ gverts) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_rays) return;
+template <int kPass>
+__device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, const int32_t* __restrict__ faces,
+                            const GridF& g, const RadarF& rd, const int32_t* __restrict__ ray_ids, int K,
+                            const sbr_hit* __restrict__ hits, const float4* __restrict__ hit_pos,
+                            const int32_t* __restrict__ first, const float4* __restrict__ prep, int64_t cap,
+                            const float* __restrict__ glen, const float* __restrict__ gamp, const FixScatter& fs,
+                            int E, float& lmax) {
   const int p0 = first[i], m = first[i + 1] - p0;
   if (m <= 0) return;
-  // launch direction (FP64 grid formula, then FP32)
+  // launch direction in FP32 (cell centre a = start + col step, likewise b with row)
   const int rid = ray_ids ? ray_ids[i] : i;
   const int row = rid / g.G, col = rid - row * g.G;
-  const double a0 = g.th * (2.0 * (col + 0.5) / g.G - 1.0);
-  const double b0 = g.th * (2.0 * (row + 0.5) / g.G - 1.0);
-  double wx = g.ax[0] + g.ua[0] * a0 + g.va[0] * b0, wy = g.ax[1] + g.ua[1] * a0 + g.va[1] * b0,
-         wz = g.ax[2] + g.ua[2] * a0 + g.va[2] * b0;
-  const double wl = 1.0 / sqrt(wx * wx + wy * wy + wz * wz);
+  const float a0 = fmaf(g.step, (float)col, g.start), b0 = fmaf(g.step, (float)row, g.start);
+  const float wx = g.ax[0] + g.ua[0] * a0 + g.va[0] * b0, wy = g.ax[1] + g.ua[1] * a0 + g.va[1] * b0,
+              wz = g.ax[2] + g.ua[2] * a0 + g.va[2] * b0;
+  const float wl = rsqrtf(wx * wx + wy * wy + wz * wz);
   float3 d[kMaxK], h[kMaxK], nh[kMaxK], N[kMaxK], A[kMaxK];
   float nlen[kMaxK], t[kMaxK], cdn[kMaxK];
   int fv[kMaxK][3];
-  d[0] = f3((float)(wx * wl), (float)(wy * wl), (float)(wz * wl));
+  d[0] = f3(wx * wl, wy * wl, wz * wl);
   for (int k = 0; k < m; ++k) {
     const size_t sl = (size_t)i * K + k;
     const int id = hits[sl].tri;
@@ -161,12 +168,35 @@ __global__ void __launch_bounds__(128) k_trace_bwd(
     const float3 e1 = vb - A[k], e2 = vc - A[k];
     const float3 e1b = cross(e2, Nb), e2b = cross(Nb, e1);
     ab = ab - e1b - e2b;
-    scatter(gverts, fv[k][0], ab);
-    scatter(gverts, fv[k][1], e1b);
-    scatter(gverts, fv[k][2], e2b);
+    scatter<kPass>(fs, E, lmax, fv[k][0], ab);
+    scatter<kPass>(fs, E, lmax, fv[k][1], e1b);
+    scatter<kPass>(fs, E, lmax, fv[k][2], e2b);
     db_next = db;
     ob_next = ob;
   }
+}
+
+template <int kPass>
+__global__ void __launch_bounds__(128) k_trace_bwd(
+    const float* __restrict__ verts, int nv, const int32_t* __restrict__ faces, GridF g, RadarF rd,
+    const int32_t* __restrict__ ray_ids, int n_rays, int K, const sbr_hit* __restrict__ hits,
+    const float4* __restrict__ hit_pos, const int32_t* __restrict__ first,
+    const float4* __restrict__ prep, int64_t cap, const float* __restrict__ glen,
+    const float* __restrict__ gamp, FixScatter fs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int E = kPass == 0 ? 0 : fix_exp(*fs.max_bits, fs.log2n);
+  float lmax = 0.f;
+  if (i < n_rays)
+    ray_adjoint<kPass>(i, verts, nv, faces, g, rd, ray_ids, K, hits, hit_pos, first, prep, cap, glen, gamp, fs, E,
+                       lmax);
+  if (kPass == 0) fix_note_warp(fs.max_bits, lmax);  // every lane of the warp reaches this
+}
+
+// gverts[i] += acc[i] 2^-E
+__global__ void k_fix_finish_add(FixScatter fs, int n, float* __restrict__ gverts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  gverts[i] += fix_get(fs.acc[i], fix_exp(*fs.max_bits, fs.log2n));
 }
 
 }  // namespace
@@ -174,11 +204,24 @@ __global__ void __launch_bounds__(128) k_trace_bwd(
 
 using namespace sbr;
 
+extern "C" size_t sbr_trace_bwd_ws_bytes(int32_t nv) {
+  if (nv < 0) return 0;
+  Carver c(nullptr);
+  c.take<unsigned long long>(3 * (size_t)nv);
+  c.take<unsigned int>(1);
+  return c.bytes();
+}
+
 extern "C" sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts, const sbr_radar_cfg* radar,
                                     const sbr_ray_grid* grid, const int32_t* d_ray_ids,
                                     const sbr_paths* paths, const float* d_glen, const float* d_gamp,
-                                    float* d_gverts, sbr_stream stream) {
+                                    float* d_gverts, void* d_ws, size_t ws_bytes, sbr_stream stream) {
   SBR_ARG(scene && paths && d_verts && d_glen && d_gamp && d_gverts, "sbr_trace_bwd: NULL argument");
+  SBR_ARG(d_ws && aligned256(d_ws), "sbr_trace_bwd: workspace NULL or not 256-byte aligned");
+  if (ws_bytes < sbr_trace_bwd_ws_bytes(scene->nv)) {
+    set_error("sbr_trace_bwd: workspace of %zu bytes, %zu needed", ws_bytes, sbr_trace_bwd_ws_bytes(scene->nv));
+    return SBR_ERR_OOM;
+  }
   sbr_status rs = check_radar(radar, "sbr_trace_bwd");
   if (rs != SBR_OK) return rs;
   rs = check_grid(grid, "sbr_trace_bwd");
@@ -196,7 +239,8 @@ extern "C" sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts
     g.ua[j] = (float)grid->u_axis[j];
     g.va[j] = (float)grid->v_axis[j];
   }
-  g.th = grid->tan_half;
+  g.start = (float)(grid->tan_half * (1.0 / grid->G - 1.0));
+  g.step = (float)(2.0 * grid->tan_half / grid->G);
   g.G = grid->G;
   RadarF rd;
   for (int t = 0; t < SBR_MAX_TX; ++t)
@@ -207,11 +251,27 @@ extern "C" sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts
   rd.nrx = radar->n_rx;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int R = paths->n_rays;
+  Carver c(d_ws);
+  FixScatter fs;
+  fs.acc = c.take<unsigned long long>(3 * (size_t)scene->nv);
+  fs.max_bits = c.take<unsigned int>(1);
+  fs.log2n = ceil_log2(3 * (int64_t)R * paths->max_bounces);  // contributions per axis, at most
+  SBR_CUDA(cudaMemsetAsync(d_ws, 0, sbr_trace_bwd_ws_bytes(scene->nv), st));
+  const float4* hp = reinterpret_cast<const float4*>(paths->hit_pos);
+  const float4* pr = reinterpret_cast<const float4*>(paths->prep);
   ::sbr::note_launch();
-  k_trace_bwd<<<(R + 127) / 128, 128, 0, st>>>(
-      d_verts, scene->nv, scene->faces, g, rd, d_ray_ids, R, paths->max_bounces, paths->hits,
-      reinterpret_cast<const float4*>(paths->hit_pos), paths->ray_first,
-      reinterpret_cast<const float4*>(paths->prep), paths->path_cap, d_glen, d_gamp, d_gverts);
+  k_trace_bwd<0><<<(R + 127) / 128, 128, 0, st>>>(d_verts, scene->nv, scene->faces, g, rd, d_ray_ids, R,
+                                                   paths->max_bounces, paths->hits, hp, paths->ray_first, pr,
+                                                   paths->path_cap, d_glen, d_gamp, fs);
+  ::sbr::note_launch();
+  k_trace_bwd<1><<<(R + 127) / 128, 128, 0, st>>>(d_verts, scene->nv, scene->faces, g, rd, d_ray_ids, R,
+                                                   paths->max_bounces, paths->hits, hp, paths->ray_first, pr,
+                                                   paths->path_cap, d_glen, d_gamp, fs);
+  const int n3 = 3 * scene->nv;
+  if (n3 > 0) {
+    ::sbr::note_launch();
+    k_fix_finish_add<<<(n3 + 255) / 256, 256, 0, st>>>(fs, n3, d_gverts);
+  }
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;
 }

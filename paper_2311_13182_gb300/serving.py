@@ -120,7 +120,7 @@ class Server:
                             points=None if pts is None else pts[: c.n_points], verts=outv, loss=c.loss,
                             gpu_ms=c.gpu_ms, scene_cached=bool(c.scene_cached), cube_cached=bool(c.cube_cached),
                             t_submit_us=c.t_submit_us, t_admit_us=c.t_admit_us, t_done_us=c.t_done_us,
-                            footprint=int(c.footprint)))
+                            footprint=int(c.footprint), gpu_t0_ms=c.gpu_t0_ms, gpu_t1_ms=c.gpu_t1_ms))
         return out
 
     def stats(self) -> dict:
@@ -161,6 +161,26 @@ def run_stream(server: Server, items, rate_hz: float, seed: int = 0):
         done += server.poll()
     wall = time.perf_counter() - t0
     return done, wall, tickets
+
+
+def device_overlap(done):
+    """From the completions' device-clock intervals [gpu_t0_ms, gpu_t1_ms]: the time the device
+    had at least one request in flight, and the fraction of it with two or more at once."""
+    ev = []
+    for d in done:
+        if d["status"] == 0 and d["gpu_t1_ms"] > d["gpu_t0_ms"]:
+            ev += [(d["gpu_t0_ms"], 1), (d["gpu_t1_ms"], -1)]
+    ev.sort()
+    busy = multi = 0.0
+    depth, last = 0, None
+    for t, step in ev:
+        if last is not None and depth >= 1:
+            busy += t - last
+            if depth >= 2:
+                multi += t - last
+        depth += step
+        last = t
+    return {"busy_ms": busy, "two_or_more_frac": multi / busy if busy > 0 else 0.0}
 
 
 def percentiles(ms):

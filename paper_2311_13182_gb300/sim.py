@@ -300,16 +300,23 @@ def pointcloud_bwd(state: PcState, gpoints: torch.Tensor, out: torch.Tensor | No
     return out
 
 
+def trace_bwd_ws_bytes(nv: int) -> int:
+    return int(L.load().sbr_trace_bwd_ws_bytes(nv))
+
+
 def trace_bwd(scene: Scene, verts: torch.Tensor, radar, grid, paths: PathBuffers, glen: torch.Tensor,
               gamp: torch.Tensor, ray_ids: torch.Tensor | None = None, gverts: torch.Tensor | None = None,
-              stream=None):
+              ws: torch.Tensor | None = None, stream=None):
     """sbr_trace_bwd: adds dL/dverts [nv, 3] from per-path (dL/dlength, dL/dA)."""
     _need_cuda(verts, torch.float32, "verts")
     if gverts is None:
         gverts = torch.zeros_like(verts)
+    nb = trace_bwd_ws_bytes(scene.nv)
+    if ws is None or ws.numel() < nb:
+        ws = torch.empty(nb, dtype=torch.uint8, device=verts.device)
     r, g = radar_struct(radar), grid_struct(grid)
     L.call("sbr_trace_bwd", scene.handle, _vp(verts), ctypes.byref(r), ctypes.byref(g), _vp(ray_ids),
-           ctypes.byref(paths.s), _vp(glen), _vp(gamp), _vp(gverts), _stream(stream))
+           ctypes.byref(paths.s), _vp(glen), _vp(gamp), _vp(gverts), _vp(ws), nb, _stream(stream))
     return gverts
 
 

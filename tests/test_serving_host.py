@@ -84,3 +84,17 @@ def test_serving_workload_is_seeded_and_shaped():
     assert all(256 <= q["G"] <= 2048 for q in r1)
     kinds = [q["kind"] for q in r1]
     assert 0.35 < kinds.count("forward") / len(kinds) < 0.65
+
+
+def test_device_overlap_of_intervals():
+    from paper_2311_13182_gb300.serving import device_overlap
+    d = lambda a, b: dict(status=0, gpu_t0_ms=a, gpu_t1_ms=b)
+    # [0, 4] and [2, 6]: busy 6 ms, two at once on [2, 4]
+    o = device_overlap([d(0, 4), d(2, 6)])
+    assert o["busy_ms"] == 6 and abs(o["two_or_more_frac"] - 2 / 6) < 1e-12
+    # disjoint intervals never overlap; failed requests are ignored
+    o = device_overlap([d(0, 1), d(2, 3), dict(status=4, gpu_t0_ms=0, gpu_t1_ms=3)])
+    assert o["busy_ms"] == 2 and o["two_or_more_frac"] == 0
+    # three nested
+    o = device_overlap([d(0, 10), d(1, 9), d(2, 3)])
+    assert o["busy_ms"] == 10 and abs(o["two_or_more_frac"] - 0.8) < 1e-12
