@@ -160,6 +160,59 @@ def paths(tr: dict, radar) -> dict:
 
 
 # ----------------------------------------------------------------------------
+# Materials: Fresnel reflection (Section 3.2.2, Eq. 9-10)
+# ----------------------------------------------------------------------------
+
+
+def fresnel(cos_i, eps):
+    """Fresnel reflection coefficients (r_s, r_p) of Eq. 9 for incidence cosines ``cos_i``
+    (|d . n|, two-sided surfaces) from air onto a material of complex relative permittivity
+    ``eps`` (eps' - j eps'' with eps'' = sigma / (omega eps_0) >= 0).
+
+    Eq. 10 in the order the paper gives it, with two readings of its garbled parts:
+      cos d_i = |i . n|,  sin d_i = sqrt(1 - cos^2 d_i),
+      sin d_t = sin d_i / sqrt(eps)      (Snell's law from air into the material; the printed
+                                          sqrt(eps) sin d_i inverts it),
+      cos d_t = sqrt(1 - sin^2 d_t)      (principal complex root: Re >= 0, a decaying wave),
+      eta     = sqrt(eps)                (used as the ratio of the two media's refractive
+                                          indices, which makes Eq. 9 the textbook equations)
+      r_p = (eta cos d_i - cos d_t) / (eta cos d_i + cos d_t),
+      r_s = (cos d_i - eta cos d_t) / (cos d_i + eta cos d_t)."""
+    c = np.asarray(cos_i, dtype=np.float64)
+    eps = np.asarray(eps, dtype=np.complex128)
+    sin_i = np.sqrt(np.maximum(1.0 - c * c, 0.0))
+    eta = np.sqrt(eps)
+    sin_t = sin_i / eta
+    cos_t = np.sqrt(1.0 - sin_t * sin_t)
+    cos_t = np.where(cos_t.real < 0, -cos_t, cos_t)
+    r_p = (eta * c - cos_t) / (eta * c + cos_t)
+    r_s = (c - eta * cos_t) / (c + eta * cos_t)
+    return r_s, r_p
+
+
+def path_fresnel(tr: dict, pa: dict, tri_material, eps) -> np.ndarray:
+    """Complex factor F of every path (ray-major, bounce-minor, as ``paths``): each surface
+    interaction multiplies the path by its Fresnel coefficient (Section 3.2.2: "every time a
+    ray interacts with a surface, these coefficients are applied and accumulated").
+
+    Readings: the radar's polarisation is taken perpendicular to each plane of incidence, so
+    the coefficient applied is r_s; a material with eps' <= 0 is a perfect conductor
+    (r_s = -1).  Path k (1-based) reflects at hits 1..k-1 and scatters back at hit k:
+      F = prod_{j<k} r_s(j) * (-r_s(k)),
+    so with perfect conductors everywhere F = (-1)^(k-1), the factor of ``paths``."""
+    tri = tr["tri"]
+    cos = np.abs((tr["din"] * tr["nrm"]).sum(-1))          # [n, K] |d_j . n_j|
+    mat = np.asarray(tri_material)[np.maximum(tri, 0)]
+    e = np.asarray(eps, dtype=np.complex128)[mat]
+    r, _ = fresnel(cos, e)
+    r = np.where(e.real <= 0, -1.0 + 0j, r)
+    F = np.empty(pa["P"], np.complex128)
+    for i, (ray, k) in enumerate(zip(pa["ray"], pa["bounce"])):
+        F[i] = -np.prod(r[ray, :k + 1])
+    return F
+
+
+# ----------------------------------------------------------------------------
 # Synthesis (Section 3.2.2, Eq. 8) and its adjoint (Eq. 11-12)
 # ----------------------------------------------------------------------------
 
@@ -174,7 +227,11 @@ def synthesize(tau, amp, radar) -> np.ndarray:
     """IF cube [V, C, N_s] complex128 by the direct FP64 sum of Eq. 8.
 
     Reading: t_n = n / f_s with f_s = N_s / T (no ADC offset); the sum runs over
-    every (hit, antenna) path; the scene is static, so every chirp is equal."""
+    every (hit, antenna) path; the scene is static, so every chirp is equal.
+    A complex strength (material paths) enters through the linearity of Eq. 8 in
+    I^s: the sum of Re(A) and j times the sum of Im(A)."""
+    if np.iscomplexobj(amp):
+        return synthesize(tau, np.real(amp), radar) + 1j * synthesize(tau, np.imag(amp), radar)
     tau = np.ascontiguousarray(tau, dtype=np.float64)
     amp = np.ascontiguousarray(amp, dtype=np.float64)
     V, P = tau.shape
@@ -209,10 +266,18 @@ def synthesize_grad(tau, amp, radar, g_cube):
     return gtau, gamp
 
 
-def simulate_cube(wl, ray_ids=None) -> tuple:
-    """Trace + paths + synthesis of a workload; returns (cube, trace, paths)."""
+def simulate_cube(wl, ray_ids=None, materials=None) -> tuple:
+    """Trace + paths + synthesis of a workload; returns (cube, trace, paths).  With
+    ``materials = (tri_material, eps)`` every path carries its Fresnel factor (pa["amp_c"])."""
     tr = trace(wl.verts, wl.faces, wl.grid, wl.max_bounces, ray_ids)
     pa = paths(tr, wl.radar)
+    if materials is not None:
+        F = path_fresnel(tr, pa, *materials)
+        # the perfect-conductor sign (-1)^(k-1) of pa["amp"] is replaced by F
+        sign = np.where(pa["bounce"] % 2 == 0, 1.0, -1.0)
+        pa["fresnel"] = F
+        pa["amp_c"] = pa["amp"] * sign[None, :] * F[None, :]
+        return synthesize(pa["tau"], pa["amp_c"], wl.radar), tr, pa
     return synthesize(pa["tau"], pa["amp"], wl.radar), tr, pa
 
 

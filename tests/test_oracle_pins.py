@@ -650,3 +650,61 @@ def test_image_loss_closed_forms():
     t2 = Pw.copy()
     t2[5, 7] += 2.0
     assert pc.image_loss(c3, t2, r3) == pytest.approx(4.0 / Pw.size, rel=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Fresnel materials (Section 3.2.2, Eq. 9-10)
+# --------------------------------------------------------------------------
+
+def test_fresnel_closed_forms():
+    """Eq. 9-10 (Snell read as sin d_t = sin d_i / sqrt(eps), eta = sqrt(eps)) against facts
+    that fix them: normal incidence r_s = (1 - n) / (1 + n) = -r_p with n = sqrt(eps);
+    Brewster's angle tan d_i = n zeroes r_p for a lossless dielectric; grazing incidence
+    reflects totally (r_s, r_p -> -1); a very good conductor tends to r_s = -1; a lossless
+    dielectric conserves energy, |r_s|^2 + (n cos d_t / cos d_i) |t_s|^2 = 1 with
+    t_s = 2 cos d_i / (cos d_i + n cos d_t)."""
+    for eps in (4.0, 2.5 - 0.3j, 10.0 - 5.0j):
+        n = np.sqrt(complex(eps))
+        rs, rp = oracle.fresnel(1.0, eps)
+        assert abs(rs - (1 - n) / (1 + n)) < 1e-15 and abs(rp + rs) < 1e-15
+        rs, rp = oracle.fresnel(1e-9, eps)
+        assert abs(rs + 1) < 1e-8 and abs(rp + 1) < 1e-8
+    for eps in (2.0, 4.0, 9.0):
+        th = math.atan(math.sqrt(eps))
+        _, rp = oracle.fresnel(math.cos(th), eps)
+        assert abs(rp) < 1e-14
+        _, rp2 = oracle.fresnel(math.cos(th + 0.1), eps)
+        assert abs(rp2) > 1e-3                          # a zero at Brewster's angle only
+    for c in (0.2, 0.6, 0.95):
+        rs, _ = oracle.fresnel(c, 1e8 - 1e9j)
+        assert abs(rs + 1) < 1e-3
+        eps = 3.7
+        rs, _ = oracle.fresnel(c, eps)
+        n = math.sqrt(eps)
+        ct = math.sqrt(1 - (1 - c * c) / eps)
+        ts = 2 * c / (c + n * ct)
+        assert abs(abs(rs) ** 2 + n * ct / c * ts ** 2 - 1) < 1e-14
+
+
+def test_fresnel_path_factor_on_plates():
+    """Path factors on the plate and the wedge: a single interaction scatters back with
+    -r_s(cos d_1); a 2-bounce path reflects with r_s(cos d_1) and scatters back with
+    -r_s(cos d_2), each cosine that plate's own; perfect conductors give (-1)^(k-1)."""
+    E = np.array([0.0, -1.0, 2.0])
+    a = square(E, (0, 2.0, 0), (-0.5, 0.0, -0.875))
+    b = square(E, (0, 2.0, 0), (0.5, 0.0, -0.875))
+    v, f = merge_meshes(a, b)
+    tr = oracle.trace(v, f, axis_grid(40, 0.3), 2)
+    pa = oracle.paths(tr, radar_single_tx())
+    tri_mat = np.array([0, 0, 1, 1])
+    eps = np.array([4.0 - 0.5j, 9.0 - 2.0j])
+    F = oracle.path_fresnel(tr, pa, tri_mat, eps)
+    cos = np.abs((tr["din"] * tr["nrm"]).sum(-1))
+    for i, (ray, k) in enumerate(zip(pa["ray"], pa["bounce"])):
+        m = tri_mat[tr["tri"][ray, :k + 1]]
+        r = [oracle.fresnel(cos[ray, j], eps[m[j]])[0] for j in range(k + 1)]
+        ref = -r[0] if k == 0 else r[0] * -r[1]
+        assert abs(F[i] - ref) < 1e-14
+    assert (pa["bounce"] == 1).sum() > 50
+    pec = oracle.path_fresnel(tr, pa, tri_mat, np.array([-1.0, -1.0]))
+    np.testing.assert_array_equal(pec, np.where(pa["bounce"] % 2 == 0, 1.0, -1.0))
