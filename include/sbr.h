@@ -59,6 +59,7 @@ typedef enum {
 #define SBR_MAX_TX 16
 #define SBR_MAX_RX 16
 #define SBR_MAX_VIRT 64
+#define SBR_MAX_MATERIALS 16
 
 /* FMCW radar (Section 3.2.2, Eq. 8: carrier f_c, sweep B over chirp time T,
  * mu = B / T).  Samples t_n = n T / N_s, n = 0..N_s-1.  Virtual antenna
@@ -163,6 +164,36 @@ sbr_status sbr_scene_update(sbr_scene* scene, const float* d_verts, sbr_stream s
 sbr_status sbr_scene_check(const sbr_scene* scene, sbr_stream stream);
 void sbr_scene_destroy(sbr_scene* scene);
 
+/* Surface materials (Section 3.2.2, Eq. 9-10: Fresnel reflection with a complex
+ * relative permittivity per material).  Material m has eps_m = eps_re[m] -
+ * j eps_im[m] (eps_im = sigma / (omega eps_0) >= 0); eps_re[m] <= 0 marks a
+ * perfect conductor.  Reading of the paper (whose Eq. 10 inverts Snell's law
+ * and calls the index ratio an impedance): cos d_i = |d . n|, sin d_t =
+ * sin d_i / sqrt(eps), eta = sqrt(eps), so that Eq. 9 is the textbook pair
+ *   r_s = (cos d_i - w) / (cos d_i + w),  r_p = (eps cos d_i - w) / (eps cos d_i + w),
+ *   w = eta cos d_t = sqrt(eps - sin^2 d_i)   (principal root, Re w >= 0);
+ * the radar's polarisation is taken perpendicular to each plane of incidence,
+ * so every interaction applies r_s: a path scattering back at its k-th hit
+ * carries F = prod_{j<k} r_s(j) * (-r_s(k)), and with perfect conductors
+ * everywhere F = (-1)^(k-1), the conductor model used without materials. */
+typedef struct {
+  int32_t n_materials;           /* 0: every surface a perfect conductor (the rest unread) */
+  int32_t _pad;
+  const int32_t* tri_material;   /* device [nt], material of each triangle in the caller's face order;
+                                    NULL: every triangle material 0.  Borrowed: must stay valid while
+                                    the scene is traced or differentiated. */
+  float eps_re[SBR_MAX_MATERIALS];
+  float eps_im[SBR_MAX_MATERIALS];
+} sbr_materials;
+
+/* Attaches (or, with NULL or n_materials = 0, removes) materials: the scene's
+ * later sbr_trace calls fold each path's Fresnel factor F into its strength
+ * and phase, and sbr_trace_bwd can return dL/d eps.  Host-side only (the table
+ * is copied); SBR_ERR_INVALID_ARG for more than SBR_MAX_MATERIALS materials,
+ * eps_im < 0, or |eps - 1| < 1e-6 (a surface that does not reflect).
+ * Material indices outside [0, n_materials) are clamped to the last material. */
+sbr_status sbr_scene_set_materials(sbr_scene* scene, const sbr_materials* materials);
+
 /* ------------------------------------------------------------------------ */
 /* Trace (Section 3.2.1, Eq. 2-3) and path preparation                      */
 /* ------------------------------------------------------------------------ */
@@ -185,6 +216,9 @@ typedef struct {
                          float-float pair (hi, lo); tau = L / c */
   int32_t* count;     /* [1] P (device) */
   void* scratch;      /* scan scratch */
+  float* phase_ofs;   /* [path_cap] phase of the path's Fresnel factor F in cycles (0 without
+                         materials); folded into phi0 of prep, read by the FP64 and naive
+                         synthesis modes, which form the carrier phase from path_len */
 } sbr_paths;
 
 size_t sbr_paths_bytes(int32_t n_rays, int32_t max_bounces, int32_t n_virt);
@@ -201,6 +235,9 @@ sbr_status sbr_paths_bind(void* d_mem, size_t bytes, int32_t n_rays, int32_t max
  * float-float delay tau = (|h_1 - Tx_t| + sum |h_j - h_{j-1}| +
  * |Rx_r - h_k|) / c, its phase terms frac(f_c tau), frac(mu tau T / N_s) split
  * hi/lo, and the strength A = omega (-1)^(k-1) |d_k . n_k| / (4 pi L_in L_out).
+ * With materials attached to the scene (sbr_scene_set_materials) the factor
+ * (-1)^(k-1) becomes the path's Fresnel factor F: prep holds A |F| and
+ * phi0 + arg(F) / (2 pi), phase_ofs[p] = arg(F) / (2 pi).
  * paths must come from sbr_paths_bind with n_rays = (n_ids < 0 ? G*G : n_ids). */
 sbr_status sbr_trace(const sbr_scene* scene, const sbr_radar_cfg* radar,
                      const sbr_ray_grid* grid, const int32_t* d_ray_ids, int32_t n_ids,
@@ -265,9 +302,11 @@ sbr_status sbr_synthesize_noalloc(const sbr_paths* paths, const sbr_radar_cfg* r
 
 /* Adjoint through Eq. 11-12: for upstream d_gcube = dL/dRe + j dL/dIm of the
  * cube, writes d_gtau [V*path_cap] = dL/dtau (per metre of path length, i.e.
- * dL/dtau / c) and d_gamp [V*path_cap] = dL/dA. */
+ * dL/dtau / c), d_gamp [V*path_cap] = dL/dA and, when d_gphase is not NULL,
+ * d_gphase [V*path_cap] = dL/d(phase offset in cycles) (the path's Fresnel
+ * phase; needed by sbr_trace_bwd when the scene has materials). */
 sbr_status sbr_synthesize_bwd(const sbr_paths* paths, const sbr_radar_cfg* radar,
-                              const float* d_gcube, float* d_glen, float* d_gamp,
+                              const float* d_gcube, float* d_glen, float* d_gamp, float* d_gphase,
                               void* d_ws, size_t ws_bytes, sbr_stream stream);
 
 /* ------------------------------------------------------------------------ */
@@ -337,7 +376,7 @@ sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cf
 /* ------------------------------------------------------------------------ */
 
 /* Scratch bytes of sbr_trace_bwd for a scene of nv vertices (a 64-bit
- * accumulator per vertex coordinate and one status word). */
+ * accumulator per vertex coordinate and per material parameter, status words). */
 size_t sbr_trace_bwd_ws_bytes(int32_t nv);
 
 /* Accumulates dL/dverts [nv][3] (added to d_gverts) from per-path gradients
@@ -349,12 +388,18 @@ size_t sbr_trace_bwd_ws_bytes(int32_t nv);
  * contributions are summed per vertex as 64-bit fixed-point integers (scaled by
  * a power of two set from the largest contribution; resolution ~1e-12 of it),
  * so the gradient is bitwise reproducible whatever order threads run in.
+ * With materials on the scene, d_gphase (sbr_synthesize_bwd's dL/d phase
+ * offset) is required: the Fresnel factors depend on every bounce's incidence
+ * angle, and d_geps, when not NULL, receives (added) dL/d eps_re[m] and
+ * dL/d eps_im[m] at [2m], [2m + 1] for m < n_materials (eps = eps_re - j eps_im),
+ * summed the same deterministic way.
  * d_ws (256-byte aligned) holds sbr_trace_bwd_ws_bytes(nv) bytes, else
  * SBR_ERR_OOM.  max_bounces <= 8. */
 sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts, const sbr_radar_cfg* radar,
                          const sbr_ray_grid* grid, const int32_t* d_ray_ids,
                          const sbr_paths* paths, const float* d_glen, const float* d_gamp,
-                         float* d_gverts, void* d_ws, size_t ws_bytes, sbr_stream stream);
+                         const float* d_gphase, float* d_gverts, float* d_geps, void* d_ws, size_t ws_bytes,
+                         sbr_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Reconstruction loss and optimiser (Section 3.4: Eq. 14 objective and the */

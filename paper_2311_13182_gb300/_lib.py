@@ -49,7 +49,15 @@ class Paths(ctypes.Structure):
     _fields_ = [("n_rays", c_i32), ("max_bounces", c_i32), ("n_virt", c_i32), ("_pad", c_i32),
                 ("path_cap", c_i64), ("hits", c_p), ("hit_pos", c_p), ("ray_weight", c_p),
                 ("ray_first", c_p), ("path_ray", c_p), ("prep", c_p), ("path_len", c_p), ("count", c_p),
-                ("scratch", c_p)]
+                ("scratch", c_p), ("phase_ofs", c_p)]
+
+
+MAX_MATERIALS = 16
+
+
+class Materials(ctypes.Structure):
+    _fields_ = [("n_materials", c_i32), ("_pad", c_i32), ("tri_material", c_p),
+                ("eps_re", c_f32 * MAX_MATERIALS), ("eps_im", c_f32 * MAX_MATERIALS)]
 
 
 class PcState(ctypes.Structure):
@@ -109,7 +117,8 @@ _SIGS = {
     "sbr_trace_counts": (c_i32, [c_p, P(RadarCfg), P(RayGrid), c_p, c_i32, c_i32, P(Paths), c_p, c_p]),
     "sbr_synth_ws_bytes": (c_sz, [P(RadarCfg), c_i64]),
     "sbr_synthesize": (c_i32, [P(Paths), P(RadarCfg), c_i32, c_p, c_p, c_sz, c_p]),
-    "sbr_synthesize_bwd": (c_i32, [P(Paths), P(RadarCfg), c_p, c_p, c_p, c_p, c_sz, c_p]),
+    "sbr_synthesize_bwd": (c_i32, [P(Paths), P(RadarCfg), c_p, c_p, c_p, c_p, c_p, c_sz, c_p]),
+    "sbr_scene_set_materials": (c_i32, [c_p, P(Materials)]),
     "sbr_synthesize_noalloc": (c_i32, [P(Paths), P(RadarCfg), c_i32, c_p, c_p]),
     "sbr_pc_bytes": (c_sz, [P(RadarCfg), P(CfarCfg)]),
     "sbr_pc_bind": (c_i32, [c_p, c_sz, P(RadarCfg), P(CfarCfg), P(PcState)]),
@@ -119,7 +128,8 @@ _SIGS = {
     "sbr_power_map": (c_i32, [c_p, P(RadarCfg), P(CfarCfg), P(PcState), c_p]),
     "sbr_image_loss": (c_i32, [P(RadarCfg), P(CfarCfg), P(PcState), c_p, c_p, c_p, c_p]),
     "sbr_trace_bwd_ws_bytes": (c_sz, [c_i32]),
-    "sbr_trace_bwd": (c_i32, [c_p, c_p, P(RadarCfg), P(RayGrid), c_p, P(Paths), c_p, c_p, c_p, c_p, c_sz, c_p]),
+    "sbr_trace_bwd": (c_i32, [c_p, c_p, P(RadarCfg), P(RayGrid), c_p, P(Paths), c_p, c_p, c_p, c_p, c_p, c_p, c_sz,
+                              c_p]),
     "sbr_chamfer": (c_i32, [c_p, c_p, c_i32, c_p, c_i32, c_p, c_p, c_p]),
     "sbr_mesh_adjacency": (c_i32, [c_p, c_i32, c_i32, c_p, c_p, c_i32, P(c_i32)]),
     "sbr_laplacian_ws_bytes": (c_sz, [c_i32]),

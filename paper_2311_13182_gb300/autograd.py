@@ -24,7 +24,17 @@ from . import sim
 
 class Simulator:
     def __init__(self, faces: np.ndarray, nv: int, radar, grid, max_bounces: int, cfar, ray_ids=None,
-                 phase_mode: int = sim.PHASE_SPLIT, recompute: bool = False, device="cuda"):
+                 phase_mode: int = sim.PHASE_SPLIT, recompute: bool = False, materials=None, device="cuda"):
+        """materials: None (perfect conductors) or (eps, tri_material): complex relative
+        permittivities (eps_re - j eps_im; eps_re <= 0 a perfect conductor) and each triangle's
+        material index (None: all material 0), Section 3.2.2 Eq. 9-10."""
+        self.eps = None
+        self.tri_material = None
+        if materials is not None:
+            eps, tri_mat = materials
+            self.eps = [complex(e) for e in eps]
+            if tri_mat is not None:
+                self.tri_material = torch.as_tensor(np.asarray(tri_mat, np.int32)).to(device)
         self.faces_np = np.ascontiguousarray(faces, dtype=np.int32)
         self.faces = torch.from_numpy(self.faces_np).to(device)
         self.nv, self.radar, self.grid, self.K, self.cfar = nv, radar, grid, max_bounces, cfar
@@ -47,6 +57,8 @@ class Simulator:
     def _trace(self, verts):
         if self.scene is None:
             self.scene = sim.Scene(verts, self.faces)
+            if self.eps:
+                self.scene.set_materials(self.eps, self.tri_material)
         else:
             self.scene.update(verts)
         paths = self.paths if self.paths is not None else sim.PathBuffers(self.n_rays, self.K, self.radar.n_virt,
@@ -74,12 +86,18 @@ class Simulator:
         sim.pointcloud_bwd(self.state, gpoints.contiguous(), out=self.gcube)
         return self.backward_cube(verts, self.gcube, gverts)
 
-    def backward_cube(self, verts: torch.Tensor, gcube: torch.Tensor, gverts: torch.Tensor):
-        """Adds dL/dverts to gverts for upstream dL/dcube [V, C, N_s, 2]."""
+    def backward_cube(self, verts: torch.Tensor, gcube: torch.Tensor, gverts: torch.Tensor,
+                      geps: torch.Tensor | None = None):
+        """Adds dL/dverts to gverts for upstream dL/dcube [V, C, N_s, 2]; with materials also
+        dL/d eps [n_materials, 2] (d eps_re, d eps_im) to ``geps`` when given."""
         paths = self.paths if self.paths is not None else self._trace(verts)
-        glen, gamp = sim.synthesize_bwd(paths, self.radar, gcube, ws=self.synth_ws)
+        gph = None
+        if self.eps:
+            glen, gamp, gph = sim.synthesize_bwd(paths, self.radar, gcube, ws=self.synth_ws, phase=True)
+        else:
+            glen, gamp = sim.synthesize_bwd(paths, self.radar, gcube, ws=self.synth_ws)
         sim.trace_bwd(self.scene, verts, self.radar, self.grid, paths, glen, gamp, self.ray_ids, gverts=gverts,
-                      ws=self.bwd_ws)
+                      ws=self.bwd_ws, gphase=gph, geps=geps)
         return gverts
 
 

@@ -11,6 +11,8 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <cmath>
+
 #include <cuda/atomic>
 
 #include "scene.cuh"
@@ -1050,3 +1052,28 @@ extern "C" sbr_status sbr_scene_check(const sbr_scene* scene, sbr_stream stream)
 }
 
 extern "C" void sbr_scene_destroy(sbr_scene* scene) { free(scene); }
+
+extern "C" sbr_status sbr_scene_set_materials(sbr_scene* scene, const sbr_materials* m) {
+  SBR_ARG(scene, "sbr_scene_set_materials: scene is NULL");
+  if (!m || m->n_materials == 0) {
+    scene->n_mat = 0;
+    scene->tri_mat = nullptr;
+    return SBR_OK;
+  }
+  SBR_ARG(m->n_materials > 0 && m->n_materials <= SBR_MAX_MATERIALS,
+          "sbr_scene_set_materials: n_materials=%d outside [0, %d]", m->n_materials, SBR_MAX_MATERIALS);
+  for (int i = 0; i < m->n_materials; ++i) {
+    const float er = m->eps_re[i], ei = m->eps_im[i];
+    SBR_ARG(std::isfinite(er) && std::isfinite(ei) && ei >= 0.f,
+            "sbr_scene_set_materials: material %d: eps_im must be finite and >= 0", i);
+    SBR_ARG(er <= 0.f || std::hypot((double)er - 1.0, (double)ei) >= 1e-6,
+            "sbr_scene_set_materials: material %d: eps = 1 does not reflect", i);
+  }
+  scene->n_mat = m->n_materials;
+  scene->tri_mat = m->tri_material;
+  for (int i = 0; i < SBR_MAX_MATERIALS; ++i) {
+    scene->eps_re[i] = i < m->n_materials ? m->eps_re[i] : -1.f;
+    scene->eps_im[i] = i < m->n_materials ? m->eps_im[i] : 0.f;
+  }
+  return SBR_OK;
+}

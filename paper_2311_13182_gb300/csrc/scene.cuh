@@ -48,4 +48,54 @@ struct sbr_scene {
   int coop;            // build with one cooperative launch (all tiles resident at once)
   void* sort_scratch;
   size_t bytes;
+  // materials (sbr_scene_set_materials): 0 = perfect conductors everywhere
+  int n_mat;
+  const int32_t* tri_mat;  // caller's device [nt] or NULL (all material 0)
+  float eps_re[SBR_MAX_MATERIALS], eps_im[SBR_MAX_MATERIALS];
 };
+
+namespace sbr {
+// Materials as a kernel argument (by value).
+struct MatArg {
+  int n;
+  const int32_t* tri_mat;
+  float2 eps[SBR_MAX_MATERIALS];  // (eps_re, eps_im), eps = eps_re - j eps_im; eps_re <= 0: conductor
+};
+
+inline MatArg mat_arg(const sbr_scene* s) {
+  MatArg m{};
+  m.n = s->n_mat;
+  m.tri_mat = s->tri_mat;
+  for (int i = 0; i < SBR_MAX_MATERIALS; ++i) m.eps[i] = make_float2(s->eps_re[i], s->eps_im[i]);
+  return m;
+}
+
+__device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ inline float2 cdiv(float2 a, float2 b) {
+  const float d = 1.f / (b.x * b.x + b.y * b.y);
+  return make_float2((a.x * b.x + a.y * b.y) * d, (a.y * b.x - a.x * b.y) * d);
+}
+// principal square root (Re >= 0)
+__device__ inline float2 csqrt(float2 z) {
+  const float r = hypotf(z.x, z.y);
+  const float re = sqrtf(fmaxf(0.5f * (r + z.x), 0.f));
+  const float im = sqrtf(fmaxf(0.5f * (r - z.x), 0.f));
+  return make_float2(re, z.y < 0.f ? -im : im);
+}
+
+// Material of triangle `id` (original index), clamped into the table.
+__device__ inline int material_of(const MatArg& m, int id) {
+  if (!m.tri_mat) return 0;
+  const int k = m.tri_mat[id];
+  return k < 0 ? 0 : (k >= m.n ? m.n - 1 : k);
+}
+
+// Fresnel r_s for incidence cosine c on material e; w = sqrt(eps - 1 + c^2) is returned
+// for the adjoint (d log r_s / dc = -2 / w, d log r_s / d eps = c / (w (eps - 1))).
+__device__ inline float2 fresnel_rs(float c, float2 e, float2* w_out) {
+  const float2 eps = make_float2(e.x, -e.y);
+  const float2 w = csqrt(make_float2(eps.x - 1.f + c * c, eps.y));
+  if (w_out) *w_out = w;
+  return cdiv(make_float2(c - w.x, -w.y), make_float2(c + w.x, w.y));
+}
+}  // namespace sbr

@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(kMmaThreads) k_synth_mma(const float4* __restr
 // Per-sample phase in FP64: x = f_c tau + (B / N_s) tau n, reduced mod 1.
 template <int M>
 __global__ void __launch_bounds__(256) k_synth_fp64(const float4* __restrict__ prep,
-                                                    const float2* __restrict__ plen, int64_t cap,
+                                                    const float2* __restrict__ plen,
+                                                    const float* __restrict__ phase_ofs, int64_t cap,
                                                     const int32_t* __restrict__ d_P, int V, int Q,
                                                     int Ns, double f0, double b_over_ns,
                                                     float2* __restrict__ partial) {
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(256) k_synth_fp64(const float4* __restrict__ p
       const double t = ((double)L.x + (double)L.y) * (1.0 / kC);
       const double x0 = f0 * t;
       const double d = b_over_ns * t;
-      sx[j] = make_double2(x0 - rint(x0), d - rint(d));
+      sx[j] = make_double2(x0 - rint(x0) + (double)phase_ofs[c0 + j], d - rint(d));
       sa[j] = prep[(size_t)v * cap + c0 + j].w;
     }
     __syncthreads();
@@ -379,11 +380,13 @@ __global__ void __launch_bounds__(256) k_synth_fp64(const float4* __restrict__ p
 // Everything in FP32: tau, f_c tau and mu tau t_n (no split, no FP64).
 template <int M>
 __global__ void __launch_bounds__(256) k_synth_naive(const float4* __restrict__ prep,
-                                                     const float2* __restrict__ plen, int64_t cap,
+                                                     const float2* __restrict__ plen,
+                                                     const float* __restrict__ phase_ofs, int64_t cap,
                                                      const int32_t* __restrict__ d_P, int V, int Q,
                                                      int Ns, float f0, float mu, float dt,
                                                      float2* __restrict__ partial) {
   __shared__ float2 sx[kChunk];
+  __shared__ float so[kChunk];
   const int v = blockIdx.x % V, q = blockIdx.x / V;
   const int64_t P = *d_P;
   const int n0 = threadIdx.x * M;
@@ -393,14 +396,16 @@ __global__ void __launch_bounds__(256) k_synth_naive(const float4* __restrict__ 
   for (int64_t c0 = (int64_t)q * kChunk; c0 < P; c0 += (int64_t)Q * kChunk) {
     const int cnt = (int)min((int64_t)kChunk, P - c0);
     __syncthreads();
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x)
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       sx[j] = make_float2(plen[(size_t)v * cap + c0 + j].x * (float)(1.0 / kC), prep[(size_t)v * cap + c0 + j].w);
+      so[j] = phase_ofs[c0 + j];
+    }
     __syncthreads();
     for (int j = 0; j < cnt; ++j) {
-      const float t = sx[j].x, a = sx[j].y;
+      const float t = sx[j].x, a = sx[j].y, o = so[j];
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        float x = fmaf(mu * t, (float)(n0 + m) * dt, f0 * t);
+        float x = fmaf(mu * t, (float)(n0 + m) * dt, f0 * t) + o;
         x -= rintf(x);
         float s, c;
         __sincosf(kTwoPiF * x, &s, &c);
@@ -461,7 +466,7 @@ __global__ void __launch_bounds__(256) k_synth_bwd(const float4* __restrict__ pr
                                                    const int32_t* __restrict__ d_P, int Ns,
                                                    const float2* __restrict__ gs, float inv_lambda,
                                                    float b_over_cns, float* __restrict__ glen,
-                                                   float* __restrict__ gamp) {
+                                                   float* __restrict__ gamp, float* __restrict__ gphase) {
   extern __shared__ float2 sg[];
   const int v = blockIdx.y;
   for (int n = threadIdx.x; n < Ns; n += blockDim.x) sg[n] = gs[(size_t)v * Ns + n];
@@ -498,6 +503,8 @@ __global__ void __launch_bounds__(256) k_synth_bwd(const float4* __restrict__ pr
   }
   gamp[(size_t)v * cap + p] = sa;
   glen[(size_t)v * cap + p] = kTwoPiF * r.w * fmaf(inv_lambda, s0, b_over_cns * s1);
+  // a phase offset o (cycles) enters every sample as e^{j 2 pi o}: dL/do = 2 pi A sum_n Re(conj(g_n) j e_n)
+  if (gphase) gphase[(size_t)v * cap + p] = kTwoPiF * r.w * s0;
 }
 
 // ---- non-uniform FFT forward kernel -----------------------------------------
@@ -992,13 +999,14 @@ void launch_fwd(sbr_phase_mode mode, const sbr_paths* p, const sbr_radar_cfg* r,
                                                                    w.partial);
   } else if (mode == SBR_PHASE_FP64) {
     ::sbr::note_launch();
-    k_synth_fp64<M><<<grid, T, 0, st>>>(prep, reinterpret_cast<const float2*>(p->path_len), p->path_cap, p->count, V, w.Q, Ns, r->f0,
-                                        r->bandwidth / Ns, w.partial);
+    k_synth_fp64<M><<<grid, T, 0, st>>>(prep, reinterpret_cast<const float2*>(p->path_len), p->phase_ofs,
+                                        p->path_cap, p->count, V, w.Q, Ns, r->f0, r->bandwidth / Ns, w.partial);
   } else {
     const double mu = r->bandwidth / r->chirp_time, dt = r->chirp_time / Ns;
     ::sbr::note_launch();
-    k_synth_naive<M><<<grid, T, 0, st>>>(prep, reinterpret_cast<const float2*>(p->path_len), p->path_cap, p->count, V, w.Q, Ns,
-                                         (float)r->f0, (float)mu, (float)dt, w.partial);
+    k_synth_naive<M><<<grid, T, 0, st>>>(prep, reinterpret_cast<const float2*>(p->path_len), p->phase_ofs,
+                                         p->path_cap, p->count, V, w.Q, Ns, (float)r->f0, (float)mu, (float)dt,
+                                         w.partial);
   }
 }
 }  // namespace
@@ -1117,7 +1125,7 @@ extern "C" sbr_status sbr_synthesize_noalloc(const sbr_paths* paths, const sbr_r
 }
 
 extern "C" sbr_status sbr_synthesize_bwd(const sbr_paths* paths, const sbr_radar_cfg* radar,
-                                         const float* d_gcube, float* d_glen, float* d_gamp,
+                                         const float* d_gcube, float* d_glen, float* d_gamp, float* d_gphase,
                                          void* d_ws, size_t ws_bytes, sbr_stream stream) {
   SBR_ARG(paths && d_gcube && d_glen && d_gamp, "sbr_synthesize_bwd: NULL argument");
   sbr_status rs = check_radar(radar, "sbr_synthesize_bwd");
@@ -1139,7 +1147,7 @@ extern "C" sbr_status sbr_synthesize_bwd(const sbr_paths* paths, const sbr_radar
     ::sbr::note_launch();
     k_synth_bwd<<<grid, 256, Ns * sizeof(float2), st>>>(
         reinterpret_cast<const float4*>(paths->prep), cap, paths->count, Ns, w.gsum,
-        (float)lam_inv, (float)bcn, d_glen, d_gamp);
+        (float)lam_inv, (float)bcn, d_glen, d_gamp, d_gphase);
   }
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;

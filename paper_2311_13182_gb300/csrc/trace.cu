@@ -768,10 +768,10 @@ __device__ inline ff ff_frac(ff x) {
 // NTX > 0: that many transmitters, their path lengths held in registers;
 // NTX = 0: rd.ntx of them (up to SBR_MAX_TX).
 template <int NTX>
-__global__ void k_prep(const float4* __restrict__ hit_pos, const float* __restrict__ ray_w,
-                       const int32_t* __restrict__ first, int n_rays, int K, RadarArg rd,
-                       int64_t cap, float4* __restrict__ prep, float2* __restrict__ plen,
-                       int32_t* __restrict__ path_ray) {
+__global__ void k_prep(const float4* __restrict__ hit_pos, const sbr_hit* __restrict__ hits,
+                       const float* __restrict__ ray_w, const int32_t* __restrict__ first, int n_rays, int K,
+                       RadarArg rd, MatArg mat, int64_t cap, float4* __restrict__ prep, float2* __restrict__ plen,
+                       int32_t* __restrict__ path_ray, float* __restrict__ phase_ofs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   int p0 = 0, nh = 0;
@@ -801,6 +801,15 @@ __global__ void k_prep(const float4* __restrict__ hit_pos, const float* __restri
     const float omega = ray_w[ri];
     float cosv;
     const ff3 h1 = ld_hit(hit_pos, (size_t)ri * K, cosv);
+    // Fresnel factor F = prod_{j<k} r_s(j) * (-r_s(k)) of the path (materials only)
+    float2 F = make_float2(1.f, 0.f);
+    auto fresnel_at = [&](int j, float c) {
+      const float2 e = mat.eps[material_of(mat, hits[(size_t)ri * K + j].tri)];
+      float2 r = e.x <= 0.f ? make_float2(-1.f, 0.f) : fresnel_rs(c, e, nullptr);
+      if (j == k) r = make_float2(-r.x, -r.y);
+      F = cmul(F, r);
+    };
+    if (mat.n > 0) fresnel_at(0, cosv);
     constexpr int kT = NTX > 0 ? NTX : SBR_MAX_TX;
     const int ntx = NTX > 0 ? NTX : rd.ntx;
     ff lin[kT];
@@ -813,6 +822,7 @@ __global__ void k_prep(const float4* __restrict__ hit_pos, const float* __restri
       const ff3 hm = ld_hit(hit_pos, (size_t)ri * K + m, cosv);
       interior = ff_add(interior, ff3_len(ff3_sub(hm, h)));
       h = hm;
+      if (mat.n > 0) fresnel_at(m, cosv);
     }
     float rlin[kT];  // 1 / L_in
 #pragma unroll
@@ -822,8 +832,15 @@ __global__ void k_prep(const float4* __restrict__ hit_pos, const float* __restri
         rlin[t] = 1.f / lin[t].hi;
       }
     path_ray[p] = ri;
-    const float sign = (k & 1) ? -1.f : 1.f;
-    const float wa = omega * sign * cosv * (float)(0.25 / M_PI);
+    // perfect conductors: the sign (-1)^(k-1); materials: |F| here, arg F in the phase
+    float fphase = 0.f;
+    float fmag = (k & 1) ? -1.f : 1.f;
+    if (mat.n > 0) {
+      fmag = hypotf(F.x, F.y);
+      fphase = atan2f(F.y, F.x) * (float)(0.5 / M_PI);
+    }
+    phase_ofs[p] = fphase;
+    const float wa = omega * fmag * cosv * (float)(0.25 / M_PI);
     for (int rr = 0; rr < rd.nrx; ++rr) {
       const ff lout = ff3_len(ff3_sub(ff3_arr(rd.rx[rr]), h));
       const float wo = wa / lout.hi;
@@ -835,6 +852,10 @@ __global__ void k_prep(const float4* __restrict__ hit_pos, const float* __restri
         const ff x0 = ff_frac(ff_mul(L, rd.k0));
         float phi0 = x0.hi + x0.lo;
         phi0 -= rintf(phi0);
+        if (mat.n > 0) {
+          phi0 += fphase;
+          phi0 -= rintf(phi0);
+        }
         const ff dl = ff_frac(ff_mul(L, rd.kb));
         const float dhi = rintf(dl.hi * 4096.f) * (1.f / 4096.f);
         const float dlo = (dl.hi - dhi) + dl.lo;  // dl.hi - dhi is exact
@@ -882,6 +903,7 @@ size_t paths_layout(sbr_paths* p, void* mem, int32_t R, int32_t K, int32_t V) {
   p->prep = c.take<float>(4 * (int64_t)V * capc);
   p->path_len = c.take<float>(2 * (int64_t)V * capc);
   p->scratch = c.take<char>(scan_part(R) + kCtrBytes + sizeof(RayDump) * (size_t)kDumpMax);
+  p->phase_ofs = c.take<float>(capc);
   p->count = p->ray_first ? p->ray_first + R : nullptr;
   return c.bytes();
 }
@@ -1024,26 +1046,32 @@ static sbr_status trace_impl(const sbr_scene* scene, const sbr_radar_cfg* radar,
     float4* prep = reinterpret_cast<float4*>(paths->prep);
     float2* plen = reinterpret_cast<float2*>(paths->path_len);
     const int nb = blocks(R, 128);
+    const MatArg mat = mat_arg(scene);
     switch (rd.ntx) {  // the common transmitter counts keep their legs in registers
       case 1:
-        k_prep<1><<<nb, 128, 0, st>>>(hp4, paths->ray_weight, paths->ray_first, (int)R, max_bounces, rd,
-                                      paths->path_cap, prep, plen, paths->path_ray);
+        k_prep<1><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R,
+                                      max_bounces, rd, mat, paths->path_cap, prep, plen, paths->path_ray,
+                                      paths->phase_ofs);
         break;
       case 2:
-        k_prep<2><<<nb, 128, 0, st>>>(hp4, paths->ray_weight, paths->ray_first, (int)R, max_bounces, rd,
-                                      paths->path_cap, prep, plen, paths->path_ray);
+        k_prep<2><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R,
+                                      max_bounces, rd, mat, paths->path_cap, prep, plen, paths->path_ray,
+                                      paths->phase_ofs);
         break;
       case 3:
-        k_prep<3><<<nb, 128, 0, st>>>(hp4, paths->ray_weight, paths->ray_first, (int)R, max_bounces, rd,
-                                      paths->path_cap, prep, plen, paths->path_ray);
+        k_prep<3><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R,
+                                      max_bounces, rd, mat, paths->path_cap, prep, plen, paths->path_ray,
+                                      paths->phase_ofs);
         break;
       case 4:
-        k_prep<4><<<nb, 128, 0, st>>>(hp4, paths->ray_weight, paths->ray_first, (int)R, max_bounces, rd,
-                                      paths->path_cap, prep, plen, paths->path_ray);
+        k_prep<4><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R,
+                                      max_bounces, rd, mat, paths->path_cap, prep, plen, paths->path_ray,
+                                      paths->phase_ofs);
         break;
       default:
-        k_prep<0><<<nb, 128, 0, st>>>(hp4, paths->ray_weight, paths->ray_first, (int)R, max_bounces, rd,
-                                      paths->path_cap, prep, plen, paths->path_ray);
+        k_prep<0><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R,
+                                      max_bounces, rd, mat, paths->path_cap, prep, plen, paths->path_ray,
+                                      paths->phase_ofs);
     }
   }
   SBR_CUDA(cudaGetLastError());

@@ -9,6 +9,13 @@
 // and each path (k, t, r) has length L_in + L_out and strength
 //   A = omega (-1)^(k-1) |d_k.n_k| / (4 pi L_in L_out),
 //   L_in = |h_1 - Tx_t| + sum_{j=2..k} |h_j - h_{j-1}|,  L_out = |Rx_r - h_k|.
+// With materials each path also carries its Fresnel factor F = prod_{j<k} r_s(j)
+// (-r_s(k)) (Section 3.2.2, Eq. 9-10): the strength is A |F| and the phase has
+// arg F / (2 pi) added, so with G_A = sum_v dL/dA' A' and G_o = sum_v dL/d(phase
+// offset) every bounce j of the path adds, through d log F = sum_j d log r_s(j),
+//   dL/d cos_j += G_A Re(q) + G_o Im(q) / (2 pi),  q = d log r_s / d cos = -2 / w,
+//   dL/d eps_m += the same with q = d log r_s / d eps = cos / (w (eps - 1)),
+// w = sqrt(eps - 1 + cos^2), for eps = eps_re - j eps_im (d eps / d eps_im = -j).
 // One thread per ray accumulates the adjoints of its path lengths and
 // strengths onto the hit points and |d.n| terms, then sweeps the bounces in
 // reverse, and adds the per-corner vertex gradients to the vertices with the
@@ -52,13 +59,25 @@ __device__ inline void scatter(const FixScatter& fs, int E, float& lmax, int vi,
   }
 }
 
+// Material gradients: pass 0 records the largest magnitude, pass 1 adds.
+template <int kPass>
+__device__ inline void scatter_eps(const FixScatter& fe, int Ee, float& emax, int m, float dre, float dim) {
+  if (kPass == 0) {
+    emax = fmaxf(emax, fmaxf(fabsf(dre), fabsf(dim)));
+  } else {
+    fix_add(&fe.acc[2 * m], dre, Ee);
+    fix_add(&fe.acc[2 * m + 1], dim, Ee);
+  }
+}
+
 template <int kPass>
 __device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, const int32_t* __restrict__ faces,
-                            const GridF& g, const RadarF& rd, const int32_t* __restrict__ ray_ids, int K,
-                            const sbr_hit* __restrict__ hits, const float4* __restrict__ hit_pos,
+                            const GridF& g, const RadarF& rd, const MatArg& mat, const int32_t* __restrict__ ray_ids,
+                            int K, const sbr_hit* __restrict__ hits, const float4* __restrict__ hit_pos,
                             const int32_t* __restrict__ first, const float4* __restrict__ prep, int64_t cap,
-                            const float* __restrict__ glen, const float* __restrict__ gamp, const FixScatter& fs,
-                            int E, float& lmax) {
+                            const float* __restrict__ glen, const float* __restrict__ gamp,
+                            const float* __restrict__ gphase, const FixScatter& fs, int E, float& lmax,
+                            const FixScatter& fe, int Ee, float& emax) {
   const int p0 = first[i], m = first[i + 1] - p0;
   if (m <= 0) return;
   // launch direction in FP32 (cell centre a = start + col step, likewise b with row)
@@ -71,6 +90,8 @@ __device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, cons
   float3 d[kMaxK], h[kMaxK], nh[kMaxK], N[kMaxK], A[kMaxK];
   float nlen[kMaxK], t[kMaxK], cdn[kMaxK];
   int fv[kMaxK][3];
+  int mj[kMaxK];        // material of bounce j (-1: perfect conductor or no materials)
+  float2 wj[kMaxK];     // w = sqrt(eps - 1 + cos^2) of bounce j
   d[0] = f3(wx * wl, wy * wl, wz * wl);
   for (int k = 0; k < m; ++k) {
     const size_t sl = (size_t)i * K + k;
@@ -89,6 +110,14 @@ __device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, cons
     nh[k] = N[k] * (1.f / nlen[k]);
     cdn[k] = dot(d[k], nh[k]);
     if (k + 1 < m) d[k + 1] = d[k] - nh[k] * (2.f * cdn[k]);
+    mj[k] = -1;
+    if (mat.n > 0) {
+      const int mm = material_of(mat, id);
+      if (mat.eps[mm].x > 0.f) {
+        mj[k] = mm;
+        fresnel_rs(fabsf(cdn[k]), mat.eps[mm], &wj[k]);
+      }
+    }
   }
   // adjoints of hit points and of |d.n| from every path of this ray
   float3 hb[kMaxK];
@@ -104,6 +133,7 @@ __device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, cons
     if (k > 0) interior += len3(h[k] - h[k - 1]);
     const int64_t p = p0 + k;
     float lin_sum_b = 0.f;  // sum over antennas of dL/dL_in (for the interior segments)
+    float g_a = 0.f, g_o = 0.f;  // sum over antennas of dL/dA' A' and of dL/d(phase offset)
     for (int tt = 0; tt < rd.ntx; ++tt) {
       const float3 et = h[0] - f3(rd.tx[tt][0], rd.tx[tt][1], rd.tx[tt][2]);
       const float l1 = len3(et);
@@ -116,6 +146,8 @@ __device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, cons
         const float gl = glen[(size_t)v * cap + p], ga = gamp[(size_t)v * cap + p];
         const float amp = prep[(size_t)v * cap + p].w;
         const float ab = ga * amp;
+        g_a += ab;
+        if (mat.n > 0) g_o += gphase[(size_t)v * cap + p];
         linb += gl - ab / lin;
         const float loutb = gl - ab / lout;
         add3(hb[k], er * (loutb / lout));
@@ -127,6 +159,18 @@ __device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, cons
       lin_sum_b += linb;
     }
     for (int j = 1; j <= k; ++j) segb[j] += lin_sum_b;
+    if (mat.n > 0) {  // the Fresnel factor: every bounce j <= k of this path
+      const float go = g_o * (float)(0.5 / M_PI);
+      for (int j = 0; j <= k; ++j) {
+        if (mj[j] < 0) continue;
+        const float2 w = wj[j];
+        const float2 qc = cdiv(make_float2(-2.f, 0.f), w);                 // d log r_s / d cos
+        cb[j] += g_a * qc.x + go * qc.y;
+        const float2 e = mat.eps[mj[j]];
+        const float2 qe = cdiv(make_float2(fabsf(cdn[j]), 0.f), cmul(w, make_float2(e.x - 1.f, -e.y)));
+        scatter_eps<kPass>(fe, Ee, emax, mj[j], g_a * qe.x + go * qe.y, g_a * qe.y - go * qe.x);
+      }
+    }
   }
   for (int j = 1; j < m; ++j) {
     const float3 e = h[j] - h[j - 1];
@@ -178,18 +222,22 @@ __device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, cons
 
 template <int kPass>
 __global__ void __launch_bounds__(128) k_trace_bwd(
-    const float* __restrict__ verts, int nv, const int32_t* __restrict__ faces, GridF g, RadarF rd,
+    const float* __restrict__ verts, int nv, const int32_t* __restrict__ faces, GridF g, RadarF rd, MatArg mat,
     const int32_t* __restrict__ ray_ids, int n_rays, int K, const sbr_hit* __restrict__ hits,
     const float4* __restrict__ hit_pos, const int32_t* __restrict__ first,
     const float4* __restrict__ prep, int64_t cap, const float* __restrict__ glen,
-    const float* __restrict__ gamp, FixScatter fs) {
+    const float* __restrict__ gamp, const float* __restrict__ gphase, FixScatter fs, FixScatter fe) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int E = kPass == 0 ? 0 : fix_exp(*fs.max_bits, fs.log2n);
-  float lmax = 0.f;
+  const int Ee = kPass == 0 ? 0 : fix_exp(*fe.max_bits, fe.log2n);
+  float lmax = 0.f, emax = 0.f;
   if (i < n_rays)
-    ray_adjoint<kPass>(i, verts, nv, faces, g, rd, ray_ids, K, hits, hit_pos, first, prep, cap, glen, gamp, fs, E,
-                       lmax);
-  if (kPass == 0) fix_note_warp(fs.max_bits, lmax);  // every lane of the warp reaches this
+    ray_adjoint<kPass>(i, verts, nv, faces, g, rd, mat, ray_ids, K, hits, hit_pos, first, prep, cap, glen, gamp,
+                       gphase, fs, E, lmax, fe, Ee, emax);
+  if (kPass == 0) {  // every lane of the warp reaches this
+    fix_note_warp(fs.max_bits, lmax);
+    if (mat.n > 0) fix_note_warp(fe.max_bits, emax);
+  }
 }
 
 // gverts[i] += acc[i] 2^-E
@@ -204,19 +252,35 @@ __global__ void k_fix_finish_add(FixScatter fs, int n, float* __restrict__ gvert
 
 using namespace sbr;
 
+namespace {
+struct BwdWs {
+  FixScatter fs, fe;
+};
+// vertex accumulators, their max word; material accumulators, their max word
+size_t bwd_ws_layout(void* base, int32_t nv, BwdWs* w) {
+  Carver c(base);
+  w->fs.acc = c.take<unsigned long long>(3 * (size_t)nv);
+  w->fs.max_bits = c.take<unsigned int>(1);
+  w->fe.acc = c.take<unsigned long long>(2 * SBR_MAX_MATERIALS);
+  w->fe.max_bits = c.take<unsigned int>(1);
+  return c.bytes();
+}
+}  // namespace
+
 extern "C" size_t sbr_trace_bwd_ws_bytes(int32_t nv) {
   if (nv < 0) return 0;
-  Carver c(nullptr);
-  c.take<unsigned long long>(3 * (size_t)nv);
-  c.take<unsigned int>(1);
-  return c.bytes();
+  BwdWs w;
+  return bwd_ws_layout(nullptr, nv, &w);
 }
 
 extern "C" sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts, const sbr_radar_cfg* radar,
                                     const sbr_ray_grid* grid, const int32_t* d_ray_ids,
                                     const sbr_paths* paths, const float* d_glen, const float* d_gamp,
-                                    float* d_gverts, void* d_ws, size_t ws_bytes, sbr_stream stream) {
+                                    const float* d_gphase, float* d_gverts, float* d_geps, void* d_ws,
+                                    size_t ws_bytes, sbr_stream stream) {
   SBR_ARG(scene && paths && d_verts && d_glen && d_gamp && d_gverts, "sbr_trace_bwd: NULL argument");
+  SBR_ARG(scene->n_mat == 0 || d_gphase,
+          "sbr_trace_bwd: the scene has materials: d_gphase (sbr_synthesize_bwd's phase gradient) is required");
   SBR_ARG(d_ws && aligned256(d_ws), "sbr_trace_bwd: workspace NULL or not 256-byte aligned");
   if (ws_bytes < sbr_trace_bwd_ws_bytes(scene->nv)) {
     set_error("sbr_trace_bwd: workspace of %zu bytes, %zu needed", ws_bytes, sbr_trace_bwd_ws_bytes(scene->nv));
@@ -251,26 +315,30 @@ extern "C" sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts
   rd.nrx = radar->n_rx;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int R = paths->n_rays;
-  Carver c(d_ws);
-  FixScatter fs;
-  fs.acc = c.take<unsigned long long>(3 * (size_t)scene->nv);
-  fs.max_bits = c.take<unsigned int>(1);
-  fs.log2n = ceil_log2(3 * (int64_t)R * paths->max_bounces);  // contributions per axis, at most
+  BwdWs w;
+  bwd_ws_layout(d_ws, scene->nv, &w);
+  w.fs.log2n = ceil_log2(3 * (int64_t)R * paths->max_bounces);  // contributions per axis, at most
+  w.fe.log2n = ceil_log2((int64_t)R * paths->max_bounces * paths->max_bounces);  // per material, at most
+  const MatArg mat = mat_arg(scene);
   SBR_CUDA(cudaMemsetAsync(d_ws, 0, sbr_trace_bwd_ws_bytes(scene->nv), st));
   const float4* hp = reinterpret_cast<const float4*>(paths->hit_pos);
   const float4* pr = reinterpret_cast<const float4*>(paths->prep);
   ::sbr::note_launch();
-  k_trace_bwd<0><<<(R + 127) / 128, 128, 0, st>>>(d_verts, scene->nv, scene->faces, g, rd, d_ray_ids, R,
+  k_trace_bwd<0><<<(R + 127) / 128, 128, 0, st>>>(d_verts, scene->nv, scene->faces, g, rd, mat, d_ray_ids, R,
                                                    paths->max_bounces, paths->hits, hp, paths->ray_first, pr,
-                                                   paths->path_cap, d_glen, d_gamp, fs);
+                                                   paths->path_cap, d_glen, d_gamp, d_gphase, w.fs, w.fe);
   ::sbr::note_launch();
-  k_trace_bwd<1><<<(R + 127) / 128, 128, 0, st>>>(d_verts, scene->nv, scene->faces, g, rd, d_ray_ids, R,
+  k_trace_bwd<1><<<(R + 127) / 128, 128, 0, st>>>(d_verts, scene->nv, scene->faces, g, rd, mat, d_ray_ids, R,
                                                    paths->max_bounces, paths->hits, hp, paths->ray_first, pr,
-                                                   paths->path_cap, d_glen, d_gamp, fs);
+                                                   paths->path_cap, d_glen, d_gamp, d_gphase, w.fs, w.fe);
   const int n3 = 3 * scene->nv;
   if (n3 > 0) {
     ::sbr::note_launch();
-    k_fix_finish_add<<<(n3 + 255) / 256, 256, 0, st>>>(fs, n3, d_gverts);
+    k_fix_finish_add<<<(n3 + 255) / 256, 256, 0, st>>>(w.fs, n3, d_gverts);
+  }
+  if (mat.n > 0 && d_geps) {
+    ::sbr::note_launch();
+    k_fix_finish_add<<<1, 64, 0, st>>>(w.fe, 2 * mat.n, d_geps);
   }
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;

@@ -97,6 +97,24 @@ class Scene:
     def check(self, stream=None):
         L.call("sbr_scene_check", self.handle, _stream(stream))
 
+    def set_materials(self, eps, tri_material: torch.Tensor | None = None):
+        """sbr_scene_set_materials: complex relative permittivities ``eps`` (eps_re - j eps_im, a
+        material with eps_re <= 0 is a perfect conductor) and the material of each triangle
+        (device int32 [nt], None: all material 0); ``eps`` empty or None removes them."""
+        m = L.Materials()
+        eps = [] if eps is None else [complex(e) for e in eps]
+        if len(eps) > L.MAX_MATERIALS:
+            raise ValueError(f"at most {L.MAX_MATERIALS} materials")
+        m.n_materials = len(eps)
+        for i, e in enumerate(eps):
+            m.eps_re[i], m.eps_im[i] = e.real, -e.imag
+        if tri_material is not None:
+            _need_cuda(tri_material, torch.int32, "tri_material")
+        self._tri_material = tri_material          # borrowed by the library: keep it alive
+        m.tri_material = tri_material.data_ptr() if tri_material is not None else None
+        L.call("sbr_scene_set_materials", self.handle, ctypes.byref(m))
+        self.n_materials = len(eps)
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value and L._LIB is not None:
@@ -149,6 +167,10 @@ class PathBuffers:
         """Path lengths L_in + L_out [V, path_cap] in float64 (hi + lo of the stored pairs)."""
         raw = _region(self.mem, self.s.path_len, torch.float32, (self.V, max(self.cap, 1), 2)).double()
         return raw[..., 0] + raw[..., 1]
+
+    def phase_ofs(self):
+        """Per-path Fresnel phase [path_cap] in cycles (0 without materials)."""
+        return _region(self.mem, self.s.phase_ofs, torch.float32, (max(self.cap, 1),))
 
     def count_tensor(self):
         return _region(self.mem, self.s.count, torch.int32, (1,))
@@ -203,18 +225,20 @@ def synthesize(paths: PathBuffers, radar, mode: int = PHASE_SPLIT, out: torch.Te
 
 
 def synthesize_bwd(paths: PathBuffers, radar, gcube: torch.Tensor, ws: torch.Tensor | None = None,
-                   stream=None):
-    """sbr_synthesize_bwd: (dL/d path length, dL/dA), each [V, path_cap] float32."""
+                   phase: bool = False, stream=None):
+    """sbr_synthesize_bwd: (dL/d path length, dL/dA), each [V, path_cap] float32, and with
+    ``phase`` also dL/d(phase offset in cycles) as a third array."""
     _need_cuda(gcube, torch.float32, "gcube")
     r = radar_struct(radar)
     glen = torch.empty((paths.V, max(paths.cap, 1)), dtype=torch.float32, device=gcube.device)
     gamp = torch.empty_like(glen)
+    gph = torch.empty_like(glen) if phase else None
     nb = synth_ws_bytes(radar, paths.cap)
     if ws is None or ws.numel() < nb:
         ws = torch.empty(nb, dtype=torch.uint8, device=gcube.device)
     L.call("sbr_synthesize_bwd", ctypes.byref(paths.s), ctypes.byref(r), _vp(gcube), _vp(glen), _vp(gamp),
-           _vp(ws), nb, _stream(stream))
-    return glen, gamp
+           _vp(gph), _vp(ws), nb, _stream(stream))
+    return (glen, gamp, gph) if phase else (glen, gamp)
 
 
 class PcState:
@@ -306,8 +330,11 @@ def trace_bwd_ws_bytes(nv: int) -> int:
 
 def trace_bwd(scene: Scene, verts: torch.Tensor, radar, grid, paths: PathBuffers, glen: torch.Tensor,
               gamp: torch.Tensor, ray_ids: torch.Tensor | None = None, gverts: torch.Tensor | None = None,
-              ws: torch.Tensor | None = None, stream=None):
-    """sbr_trace_bwd: adds dL/dverts [nv, 3] from per-path (dL/dlength, dL/dA)."""
+              ws: torch.Tensor | None = None, gphase: torch.Tensor | None = None, geps: torch.Tensor | None = None,
+              stream=None):
+    """sbr_trace_bwd: adds dL/dverts [nv, 3] from per-path (dL/dlength, dL/dA) and, on a scene
+    with materials, the Fresnel terms from dL/d(phase offset) ``gphase``; adds dL/d eps
+    [n_materials, 2] (d eps_re, d eps_im) to ``geps`` when given."""
     _need_cuda(verts, torch.float32, "verts")
     if gverts is None:
         gverts = torch.zeros_like(verts)
@@ -316,7 +343,8 @@ def trace_bwd(scene: Scene, verts: torch.Tensor, radar, grid, paths: PathBuffers
         ws = torch.empty(nb, dtype=torch.uint8, device=verts.device)
     r, g = radar_struct(radar), grid_struct(grid)
     L.call("sbr_trace_bwd", scene.handle, _vp(verts), ctypes.byref(r), ctypes.byref(g), _vp(ray_ids),
-           ctypes.byref(paths.s), _vp(glen), _vp(gamp), _vp(gverts), _vp(ws), nb, _stream(stream))
+           ctypes.byref(paths.s), _vp(glen), _vp(gamp), _vp(gphase), _vp(gverts), _vp(geps), _vp(ws), nb,
+           _stream(stream))
     return gverts
 
 
