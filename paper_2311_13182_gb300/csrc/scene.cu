@@ -875,6 +875,53 @@ __global__ void k_collapse4(const Node* __restrict__ nodes, int n, Node4* __rest
   out[i] = o;
 }
 
+// Breadth-first copy of the top kTopLevels levels of the 4-wide tree (one CTA,
+// level by level): staged entries link to each other as kStaged + position.
+__global__ void __launch_bounds__(128) k_top_table(const Node4* __restrict__ nodes4, int nt, Node4* __restrict__ top,
+                                                   int32_t* __restrict__ top_n) {
+  __shared__ int idx[kTopMax];  // full-tree index of each staged entry
+  __shared__ int lvl_begin, lvl_end;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    lvl_begin = 0;
+    lvl_end = nt > 1 ? 1 : 0;
+    idx[0] = 0;
+  }
+  __syncthreads();
+  for (int level = 1; level < kTopLevels; ++level) {
+    const int b = lvl_begin, e = lvl_end;
+    __syncthreads();
+    if (t == 0) {  // append the internal children of this level in (entry, slot) order
+      int n = e;
+      for (int q = b; q < e; ++q) {
+        const int4 ch = nodes4[idx[q]].child;
+        const int c[4] = {ch.x, ch.y, ch.z, ch.w};
+        for (int k = 0; k < 4; ++k)
+          if (c[k] >= 0 && n < kTopMax) idx[n++] = c[k];
+      }
+      lvl_begin = e;
+      lvl_end = n;
+    }
+    __syncthreads();
+  }
+  const int n = lvl_end;
+  for (int q = t; q < n; q += blockDim.x) {
+    Node4 o = nodes4[idx[q]];
+    int c[4] = {o.child.x, o.child.y, o.child.z, o.child.w};
+    for (int k = 0; k < 4; ++k)
+      if (c[k] >= 0)
+        for (int r = 1; r < n; ++r)
+          if (idx[r] == c[k]) {
+            c[k] = kStaged + r;
+            break;
+          }
+    o.child = make_int4(c[0], c[1], c[2], c[3]);
+    o.pad.y = idx[q];
+    top[q] = o;
+  }
+  if (t == 0) *top_n = n;
+}
+
 inline int blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 size_t layout(sbr_scene* s, void* mem, int32_t nt) {
@@ -884,6 +931,8 @@ size_t layout(sbr_scene* s, void* mem, int32_t nt) {
   s->tris = c.take<float4>(3 * n);
   s->nodes = c.take<Node>(ni);
   s->nodes4 = c.take<Node4>(ni);
+  s->top = c.take<Node4>(kTopMax);
+  s->top_n = c.take<int32_t>(1);
   s->parent = c.take<int32_t>(2 * n);
   s->visits = c.take<uint32_t>(ni);
   s->keys[0] = c.take<uint32_t>(n);
@@ -914,6 +963,10 @@ sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
                                          dim3(kBuildTile), args, build_smem(nt), st));
     ::sbr::note_launch();
     k_collapse4<<<blocks(nt - 1, 128), 128, 0, st>>>(s->nodes, nt, s->nodes4);
+    if (kTopLevels > 0) {
+      ::sbr::note_launch();
+      k_top_table<<<1, 128, 0, st>>>(s->nodes4, nt, s->top, s->top_n);
+    }
     SBR_CUDA(cudaGetLastError());
     return SBR_OK;
   }
@@ -940,6 +993,10 @@ sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
                                              s->bounds);
     ::sbr::note_launch();
     k_collapse4<<<blocks(nt - 1, 128), 128, 0, st>>>(s->nodes, nt, s->nodes4);
+  }
+  if (kTopLevels > 0) {
+    ::sbr::note_launch();
+    k_top_table<<<1, 128, 0, st>>>(s->nodes4, nt, s->top, s->top_n);
   }
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;

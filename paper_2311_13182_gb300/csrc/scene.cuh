@@ -27,6 +27,18 @@ struct __align__(128) Node4 {
   int4 pad;
 };
 
+// Shared-memory staging of the top levels of the 4-wide tree: the scene build
+// copies the entries of the first kTopLevels levels, breadth first, into a
+// table whose links to other staged entries read kStaged + position; every
+// trace CTA loads the table into shared memory once.  pad.y of a staged entry
+// holds its index in the full tree.  kTopLevels = 0 turns the staging off.
+#ifndef SBR_TRACE_TOP_LEVELS
+#define SBR_TRACE_TOP_LEVELS 0
+#endif
+constexpr int kTopLevels = SBR_TRACE_TOP_LEVELS;
+constexpr int kTopMax = kTopLevels == 0 ? 1 : ((1 << (2 * kTopLevels)) - 1) / 3;  // 1 + 4 + 16 + ...
+constexpr int kStaged = 1 << 30;  // above any node index (nt <= 2^26)
+
 }  // namespace sbr
 
 struct sbr_scene {
@@ -34,6 +46,8 @@ struct sbr_scene {
   float4* tris;        // [nt*3] sorted: (v0, original id bits), (v1, 0), (v2, 0)
   sbr::Node* nodes;    // [max(nt-1, 1)] binary tree
   sbr::Node4* nodes4;  // [max(nt-1, 1)] 4-wide entries, indexed like the binary nodes
+  sbr::Node4* top;     // [kTopMax] breadth-first copy of the top levels (staging), count in top_n
+  int32_t* top_n;      // [1]
   int32_t* parent;     // [2nt-1]: internal 0..nt-2, leaves nt-1..2nt-2
   uint32_t* visits;    // [max(nt-1,1)] refit arrival counters, or the crossing-node mask
   uint32_t* keys[2];   // [nt] Morton codes (sort ping-pong)

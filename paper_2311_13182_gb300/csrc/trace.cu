@@ -227,6 +227,12 @@ __device__ inline void slab(const float3& o, const float3& idir, float lox, floa
 
 constexpr int kStack = 192;  // 3 pending siblings per 4-wide level, 64 binary levels at most
 
+// Order of a node's children on the stack: 2 = fully sorted by entry distance
+// (a 5-exchange network), 1 = nearest child first, the other three partly ordered.
+#ifndef SBR_TRACE_SORT
+#define SBR_TRACE_SORT 2
+#endif
+
 // compare-exchange of (distance, child) pairs
 __device__ inline void cswap(float& da, int& ca, float& db, int& cb) {
   if (db < da) {
@@ -269,6 +275,11 @@ constexpr int kHanded = -2;  // Best::id of a ray handed over
 
 // Records a straggler's state; false when the hand-over area is full (the
 // lane then finishes the ray itself).  Out of line: it runs for few rays.
+__shared__ Node4 s_top[kTopMax];  // staged top levels (k_trace only)
+
+// Full-tree index of a traversal entry (staged entries carry theirs in pad.y).
+__device__ inline int unstage(int e) { return (kTopLevels > 0 && e >= kStaged) ? s_top[e - kStaged].pad.y : e; }
+
 __device__ __noinline__ bool hand_over(DumpCtx dc, ff3 o, ff3 d, int rid, int skip, bool has_ff, Best b, int node,
                                        const int* stack, int sp) {
   const unsigned di = atomicAdd(dc.n, 1u);
@@ -280,7 +291,7 @@ __device__ __noinline__ bool hand_over(DumpCtx dc, ff3 o, ff3 d, int rid, int sk
   D.nh = dc.nh;
   D.skip = skip;
   D.has_ff = has_ff;
-  D.node = node;
+  D.node = unstage(node);
   D.sp = sp;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -297,7 +308,7 @@ __device__ __noinline__ bool hand_over(DumpCtx dc, ff3 o, ff3 d, int rid, int sk
   D.bhi = b.hi;
   D.bt_hi = b.t.hi;
   D.bt_lo = b.t.lo;
-  for (int j = 0; j < sp; ++j) D.stack[j] = stack[j];
+  for (int j = 0; j < sp; ++j) D.stack[j] = unstage(stack[j]);
   return true;
 }
 
@@ -316,7 +327,7 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node4* __restrict
   if (nt <= 0) return b;
   int stack[kStack];
   int sp = 0;
-  int node = nt > 1 ? 0 : ~0;
+  int node = nt > 1 ? (kTopLevels > 0 ? kStaged : 0) : ~0;
   // a valid tree is visited at most once per node: the cap only guards
   // against a corrupted hierarchy turning into an endless loop
   const int hand_at = 2 * nt + 64 - kStragglerSteps;  // the guard's value after kStragglerSteps entries
@@ -328,10 +339,18 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node4* __restrict
     }
     if (node >= 0) {
       if (kCount) ++n_nodes;
-      const Node4* q = nodes + node;
-      const float4 lx = __ldg(&q->lox), hx = __ldg(&q->hix), ly = __ldg(&q->loy), hy = __ldg(&q->hiy),
-                   lz = __ldg(&q->loz), hz = __ldg(&q->hiz);
-      const int4 ch = __ldg(&q->child);
+      float4 lx, hx, ly, hy, lz, hz;
+      int4 ch;
+      if (kTopLevels > 0 && node >= kStaged) {
+        const Node4& q = s_top[node - kStaged];
+        lx = q.lox, hx = q.hix, ly = q.loy, hy = q.hiy, lz = q.loz, hz = q.hiz;
+        ch = q.child;
+      } else {
+        const Node4* q = nodes + node;
+        lx = __ldg(&q->lox), hx = __ldg(&q->hix), ly = __ldg(&q->loy), hy = __ldg(&q->hiy);
+        lz = __ldg(&q->loz), hz = __ldg(&q->hiz);
+        ch = __ldg(&q->child);
+      }
       const float lim = b.hi;
       float d0, d1, d2, d3, tf;
       int c0 = ch.x, c1 = ch.y, c2 = ch.z, c3 = ch.w;
@@ -347,8 +366,10 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node4* __restrict
       cswap(d0, c0, d1, c1);
       cswap(d2, c2, d3, c3);
       cswap(d0, c0, d2, c2);
-      cswap(d1, c1, d3, c3);
-      cswap(d1, c1, d2, c2);
+      if (SBR_TRACE_SORT > 1) {  // else: nearest child first, the others in a partial order
+        cswap(d1, c1, d3, c3);
+        cswap(d1, c1, d2, c2);
+      }
       if (d0 < INFINITY) {
         if (d3 < INFINITY && sp < kStack) stack[sp++] = c3;
         if (d2 < INFINITY && sp < kStack) stack[sp++] = c2;
@@ -497,9 +518,17 @@ __global__ void __launch_bounds__(128, SBR_TRACE_MIN_BLOCKS) k_trace(const float
                                                float* __restrict__ ray_w,
                                                int32_t* __restrict__ nvalid,
                                                RayDump* __restrict__ dumps, unsigned int* __restrict__ n_dumps,
-                                               unsigned long long* __restrict__ counts) {
+                                               unsigned long long* __restrict__ counts,
+                                               const Node4* __restrict__ top, const int32_t* __restrict__ top_n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   int n_nodes = 0, n_tris = 0, n_trav = 0;
+  if (kTopLevels > 0) {  // every thread of the CTA, before any may return
+    const int n = *top_n;
+    const float4* src = reinterpret_cast<const float4*>(top);
+    float4* dst = reinterpret_cast<float4*>(s_top);
+    for (int j = threadIdx.x; j < n * (int)(sizeof(Node4) / sizeof(float4)); j += blockDim.x) dst[j] = __ldg(&src[j]);
+    __syncthreads();
+  }
   if (kCount) {
     // whole warps stay to the reduction below; idle lanes count nothing
     if (i - (int)(threadIdx.x & 31) >= n_rays) return;
@@ -1026,14 +1055,14 @@ static sbr_status trace_impl(const sbr_scene* scene, const sbr_radar_cfg* radar,
     SBR_CUDA(cudaMemsetAsync(d_counts, 0, 4 * sizeof(unsigned long long), st));
     k_trace<true><<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, d_ray_ids, (int)R,
                                                   max_bounces, paths->hits, hp, paths->ray_weight, paths->ray_first,
-                                                  dumps, dctr, d_counts);
+                                                  dumps, dctr, d_counts, scene->top, scene->top_n);
     ::sbr::note_launch();
     k_trace_coop<true><<<coop_grid(), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, max_bounces, dumps,
                                                     dctr, dctr + 1, paths->hits, hp, paths->ray_first, d_counts);
   } else {
     k_trace<false><<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, d_ray_ids, (int)R,
                                                    max_bounces, paths->hits, hp, paths->ray_weight,
-                                                   paths->ray_first, dumps, dctr, nullptr);
+                                                   paths->ray_first, dumps, dctr, nullptr, scene->top, scene->top_n);
     ::sbr::note_launch();
     k_trace_coop<false><<<coop_grid(), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, max_bounces, dumps,
                                                      dctr, dctr + 1, paths->hits, hp, paths->ray_first, nullptr);
