@@ -78,8 +78,10 @@ typedef struct {
 
 /* Stratified G x G ray grid: the Monte-Carlo sample set of Eq. 3.  Ray
  * index = row * G + col; direction = normalize(axis + a u_axis + b v_axis),
- * a = tan_half (2 (col + 1/2) / G - 1), b likewise with row; weight = cell
- * solid angle (2 tan_half / G)^2 cos^3 of the direction's angle to axis. */
+ * a = tan_half (2 (col + jx) / G - 1), b = tan_half (2 (row + jy) / G - 1) with
+ * (jx, jy) = (1/2, 1/2) (cell centres) or, with `jitter`, the ray's own offsets
+ * in its cell (stratified jittered sampling); weight = (2 tan_half / G)^2 cos^3
+ * of the direction's angle to axis (the cell's solid angle at the sample). */
 typedef struct {
   int32_t G;
   int32_t _pad;
@@ -88,6 +90,8 @@ typedef struct {
   double u_axis[3]; /* unit, orthogonal to axis */
   double v_axis[3]; /* unit, orthogonal to axis and u_axis */
   double tan_half;
+  const float* jitter; /* device [G*G][2] offsets (jx, jy) in [0, 1) per ray, or NULL (cell centres);
+                          borrowed: must stay valid while traces and adjoints of the grid run */
 } sbr_ray_grid;
 
 /* Soft CA-CFAR and point extraction (the map T of Eq. 16; parameters are

@@ -62,7 +62,7 @@ def _lib():
     if _LIB is None:
         lib = ctypes.CDLL(build())
         P = ctypes.c_void_p
-        lib.orc_trace.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int,
+        lib.orc_trace.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P, P, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                   P, P, P, P, P, P, P]
         lib.orc_synth.argtypes = [P, P, ctypes.c_long, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -89,7 +89,8 @@ def grid_array(grid) -> np.ndarray:
 
 def trace(verts, faces, grid, max_bounces: int, ray_ids=None, tmin=TMIN, edge_eps=EDGE_EPS,
           tie_rel=TIE_REL) -> dict:
-    """Brute-force FP64 trace of the G x G grid (or of ``ray_ids``).
+    """Brute-force FP64 trace of the G x G grid (or of ``ray_ids``); a grid with ``jitter``
+    (offsets in [0, 1)^2 per ray) samples each cell there instead of at its centre.
 
     Returns arrays indexed [ray, bounce]: tri (-1 = no hit), t/u/v, hit point,
     incident direction, unit normal; per ray omega (solid-angle weight) and flag
@@ -107,7 +108,11 @@ def trace(verts, faces, grid, max_bounces: int, ray_ids=None, tmin=TMIN, edge_ep
     nrm = np.empty((n, K, 3), np.float64)
     omega = np.empty(n, np.float64)
     flag = np.empty(n, np.int32)
-    rc = _lib().orc_trace(_ptr(v), v.shape[0], _ptr(f), f.shape[0], _ptr(g), grid.G, _ptr(ids), n, K,
+    jit = getattr(grid, "jitter", None)
+    jit = None if jit is None else np.ascontiguousarray(jit, dtype=np.float32).reshape(-1, 2)
+    if jit is not None and jit.shape[0] != grid.G * grid.G:
+        raise ValueError("jitter must hold G*G offset pairs")
+    rc = _lib().orc_trace(_ptr(v), v.shape[0], _ptr(f), f.shape[0], _ptr(g), grid.G, _ptr(jit), _ptr(ids), n, K,
                           tmin, edge_eps, tie_rel, _ptr(tri), _ptr(tuv), _ptr(hit), _ptr(din),
                           _ptr(nrm), _ptr(omega), _ptr(flag))
     if rc != 0:
@@ -266,9 +271,58 @@ def synthesize_grad(tau, amp, radar, g_cube):
     return gtau, gamp
 
 
-def simulate_cube(wl, ray_ids=None, materials=None) -> tuple:
+# ----------------------------------------------------------------------------
+# Moving objects: path-length rates and the per-chirp IF signal (Section 3.1's
+# scene dynamics; Eq. 8 evaluated chirp by chirp)
+# ----------------------------------------------------------------------------
+
+
+def path_rates(tr: dict, pa: dict, radar, tri_object, velocity) -> np.ndarray:
+    """Rate of change dL/dt [V, P] of every path's length when each object translates with
+    its velocity (m/s) and every hit point moves with its object.
+
+    From L = |h_1 - Tx| + sum_{j=2..k} |h_j - h_{j-1}| + |Rx - h_k|:
+      dL/dt = sum_j v_j . (u_in,j - u_out,j),
+    u_in,j the unit vector of the leg arriving at h_j (from Tx for j = 1), u_out,j that of the
+    leg leaving it (towards Rx for j = k)."""
+    hit, tri = tr["hit"], tr["tri"]
+    vel = np.asarray(velocity, dtype=np.float64).reshape(-1, 3)
+    obj = np.asarray(tri_object)
+    unit = lambda x: x / np.linalg.norm(x, axis=-1, keepdims=True)
+    V = radar.n_virt
+    out = np.zeros((V, pa["P"]))
+    for i, (ray, k) in enumerate(zip(pa["ray"], pa["bounce"])):
+        h = hit[ray, :k + 1]
+        vj = vel[obj[tri[ray, :k + 1]]]
+        interior = 0.0
+        for j in range(k + 1):
+            if j >= 1:
+                interior += vj[j] @ unit(h[j] - h[j - 1])
+            if j < k:
+                interior -= vj[j] @ unit(h[j + 1] - h[j])
+        for t in range(radar.n_tx):
+            for r in range(radar.n_rx):
+                out[t * radar.n_rx + r, i] = (interior + vj[0] @ unit(h[0] - radar.tx[t])
+                                              - vj[k] @ unit(radar.rx[r] - h[k]))
+    return out
+
+
+def synthesize_moving(tau, amp, radar, rate) -> np.ndarray:
+    """IF cube [V, C, N_s] of Eq. 8 chirp by chirp: chirp c starts at c T_rep, when every
+    path's delay has become tau + c T_rep dL/dt / c (amplitudes held over the frame)."""
+    C = radar.n_chirps
+    out = []
+    for c in range(C):
+        tc = np.asarray(tau) + c * radar.chirp_rep * np.asarray(rate) / C_LIGHT
+        one = synthesize(tc, amp, radar)[:, :1]
+        out.append(one)
+    return np.concatenate(out, axis=1)
+
+
+def simulate_cube(wl, ray_ids=None, materials=None, motion=None) -> tuple:
     """Trace + paths + synthesis of a workload; returns (cube, trace, paths).  With
-    ``materials = (tri_material, eps)`` every path carries its Fresnel factor (pa["amp_c"])."""
+    ``materials = (tri_material, eps)`` every path carries its Fresnel factor (pa["amp_c"]);
+    with ``motion = (tri_object, velocities)`` the chirps follow the moving objects."""
     tr = trace(wl.verts, wl.faces, wl.grid, wl.max_bounces, ray_ids)
     pa = paths(tr, wl.radar)
     if materials is not None:
@@ -277,8 +331,11 @@ def simulate_cube(wl, ray_ids=None, materials=None) -> tuple:
         sign = np.where(pa["bounce"] % 2 == 0, 1.0, -1.0)
         pa["fresnel"] = F
         pa["amp_c"] = pa["amp"] * sign[None, :] * F[None, :]
-        return synthesize(pa["tau"], pa["amp_c"], wl.radar), tr, pa
-    return synthesize(pa["tau"], pa["amp"], wl.radar), tr, pa
+    amp = pa.get("amp_c", pa["amp"])
+    if motion is not None:
+        pa["rate"] = path_rates(tr, pa, wl.radar, *motion)
+        return synthesize_moving(pa["tau"], amp, wl.radar, pa["rate"]), tr, pa
+    return synthesize(pa["tau"], amp, wl.radar), tr, pa
 
 
 # ----------------------------------------------------------------------------

@@ -67,12 +67,16 @@ static int mt_hit(d3 o, d3 d, d3 a, d3 b, d3 c, double tmin,
 }
 
 /* Launch direction and solid-angle weight of ray `rid` of a G x G grid.
- * grid = [origin(3), axis(3), u_axis(3), v_axis(3), tan_half]. */
-static void grid_ray(const double* grid, int G, int rid, d3* o, d3* d, double* omega) {
+ * grid = [origin(3), axis(3), u_axis(3), v_axis(3), tan_half]; jitter = the
+ * rays' offsets (jx, jy) in their cells (stratified jittered sampling of the
+ * Monte-Carlo estimate of Eq. 3), or NULL for the cell centres (1/2, 1/2). */
+static void grid_ray(const double* grid, int G, const float* jitter, int rid, d3* o, d3* d, double* omega) {
   int row = rid / G, col = rid % G;
   double th = grid[12];
-  double a = th * (2.0 * (col + 0.5) / G - 1.0);
-  double b = th * (2.0 * (row + 0.5) / G - 1.0);
+  double jx = jitter ? (double)jitter[2 * (size_t)rid] : 0.5;
+  double jy = jitter ? (double)jitter[2 * (size_t)rid + 1] : 0.5;
+  double a = th * (2.0 * (col + jx) / G - 1.0);
+  double b = th * (2.0 * (row + jy) / G - 1.0);
   d3 ax = v3(grid[3], grid[4], grid[5]);
   d3 ua = v3(grid[6], grid[7], grid[8]);
   d3 va = v3(grid[9], grid[10], grid[11]);
@@ -96,7 +100,7 @@ static void grid_ray(const double* grid, int G, int rid, d3* o, d3* d, double* o
  * bounce, 1-based, or 0).
  */
 int orc_trace(const float* verts, int nv, const int* faces, int nt,
-              const double* grid, int G, const int* ray_ids, int n_rays, int K,
+              const double* grid, int G, const float* jitter, const int* ray_ids, int n_rays, int K,
               double tmin, double edge_eps, double tie_rel,
               int* tri, double* tuv, double* hit, double* din, double* nrm,
               double* omega, int* flag) {
@@ -107,7 +111,7 @@ int orc_trace(const float* verts, int nv, const int* faces, int nt,
   for (int i = 0; i < n_rays; ++i) {
     int rid = ray_ids ? ray_ids[i] : i;
     d3 o, d;
-    grid_ray(grid, G, rid, &o, &d, &omega[i]);
+    grid_ray(grid, G, jitter, rid, &o, &d, &omega[i]);
     flag[i] = 0;
     int prev = -1, alive = 1;
     for (int k = 0; k < K; ++k) {

@@ -37,7 +37,7 @@ class RadarCfg(ctypes.Structure):
 
 class RayGrid(ctypes.Structure):
     _fields_ = [("G", c_i32), ("_pad", c_i32), ("origin", c_f64 * 3), ("axis", c_f64 * 3),
-                ("u_axis", c_f64 * 3), ("v_axis", c_f64 * 3), ("tan_half", c_f64)]
+                ("u_axis", c_f64 * 3), ("v_axis", c_f64 * 3), ("tan_half", c_f64), ("jitter", c_p)]
 
 
 class CfarCfg(ctypes.Structure):

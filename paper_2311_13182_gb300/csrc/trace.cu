@@ -34,8 +34,10 @@ struct GridArg {
   ff o[3], ax[3], ua[3], va[3];
   ff start;    // -tan_half + tan_half / G: the first cell centre
   ff step;     // 2 tan_half / G: the cell pitch
+  ff lo;       // -tan_half: the first cell's edge (jittered sampling)
   float cell;  // 2 tan_half / G
   int G;
+  const float* jitter;  // [G*G][2] offsets in the cell, or NULL (cell centres)
 };
 
 struct RadarArg {
@@ -56,8 +58,15 @@ __device__ inline ff3 ff3_arr(const ff* a) { return ff3{a[0], a[1], a[2]}; }
 // direction = normalize(axis + a u + b v).
 __device__ inline ff3 grid_dir_ff(const GridArg& g, int rid) {
   const int row = rid / g.G, col = rid - row * g.G;
-  const ff a = ff_add(g.start, ff_mulf(g.step, (float)col));
-  const ff b = ff_add(g.start, ff_mulf(g.step, (float)row));
+  ff a, b;
+  if (g.jitter) {  // a = -tan_half + (col + jx) step, col + jx exact as a float-float sum
+    const float2 j = reinterpret_cast<const float2*>(g.jitter)[rid];
+    a = ff_add(g.lo, ff_mul(g.step, ff_add(ff_of((float)col), ff_of(j.x))));
+    b = ff_add(g.lo, ff_mul(g.step, ff_add(ff_of((float)row), ff_of(j.y))));
+  } else {
+    a = ff_add(g.start, ff_mulf(g.step, (float)col));
+    b = ff_add(g.start, ff_mulf(g.step, (float)row));
+  }
   const ff3 w = ff3_add(ff3_arr(g.ax), ff3_add(ff3_scale(ff3_arr(g.ua), a), ff3_scale(ff3_arr(g.va), b)));
   return ff3_scale(w, ff_rsqrt(ff3_dot(w, w)));
 }
@@ -66,7 +75,15 @@ __device__ inline ff3 grid_dir_ff(const GridArg& g, int rid) {
 // 64) and the ray's solid-angle weight cell^2 cos^3.
 __device__ inline float3 grid_dir_f32(const GridArg& g, int rid, float& omega) {
   const int row = rid / g.G, col = rid - row * g.G;
-  const float a = fmaf(g.step.hi, (float)col, g.start.hi), b = fmaf(g.step.hi, (float)row, g.start.hi);
+  float a, b;
+  if (g.jitter) {
+    const float2 j = reinterpret_cast<const float2*>(g.jitter)[rid];
+    a = fmaf(g.step.hi, (float)col + j.x, g.lo.hi);
+    b = fmaf(g.step.hi, (float)row + j.y, g.lo.hi);
+  } else {
+    a = fmaf(g.step.hi, (float)col, g.start.hi);
+    b = fmaf(g.step.hi, (float)row, g.start.hi);
+  }
   const float3 w = f3(g.ax[0].hi + a * g.ua[0].hi + b * g.va[0].hi, g.ax[1].hi + a * g.ua[1].hi + b * g.va[1].hi,
                       g.ax[2].hi + a * g.ua[2].hi + b * g.va[2].hi);
   const float inv = rsqrtf(dot(w, w));
@@ -1031,8 +1048,10 @@ static sbr_status trace_impl(const sbr_scene* scene, const sbr_radar_cfg* radar,
   }
   g.start = ff_from_double(-grid->tan_half + grid->tan_half / grid->G);
   g.step = ff_from_double(2.0 * grid->tan_half / grid->G);
+  g.lo = ff_from_double(-grid->tan_half);
   g.cell = (float)(2.0 * grid->tan_half / grid->G);
   g.G = grid->G;
+  g.jitter = grid->jitter;
   RadarArg rd;
   for (int t = 0; t < SBR_MAX_TX; ++t)
     for (int j = 0; j < 3; ++j) rd.tx[t][j] = ff_from_double(radar->tx[t][j]);

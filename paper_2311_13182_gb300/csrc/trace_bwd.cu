@@ -34,7 +34,9 @@ constexpr int kMaxK = 8;
 struct GridF {
   float o[3], ax[3], ua[3], va[3];
   float start, step;  // first cell centre -tan_half (1 - 1/G) and the cell pitch 2 tan_half / G
+  float lo;           // -tan_half (jittered sampling)
   int G;
+  const float* jitter;
 };
 
 struct RadarF {
@@ -83,7 +85,15 @@ __device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, cons
   // launch direction in FP32 (cell centre a = start + col step, likewise b with row)
   const int rid = ray_ids ? ray_ids[i] : i;
   const int row = rid / g.G, col = rid - row * g.G;
-  const float a0 = fmaf(g.step, (float)col, g.start), b0 = fmaf(g.step, (float)row, g.start);
+  float a0, b0;
+  if (g.jitter) {
+    const float2 jt = reinterpret_cast<const float2*>(g.jitter)[rid];
+    a0 = fmaf(g.step, (float)col + jt.x, g.lo);
+    b0 = fmaf(g.step, (float)row + jt.y, g.lo);
+  } else {
+    a0 = fmaf(g.step, (float)col, g.start);
+    b0 = fmaf(g.step, (float)row, g.start);
+  }
   const float wx = g.ax[0] + g.ua[0] * a0 + g.va[0] * b0, wy = g.ax[1] + g.ua[1] * a0 + g.va[1] * b0,
               wz = g.ax[2] + g.ua[2] * a0 + g.va[2] * b0;
   const float wl = rsqrtf(wx * wx + wy * wy + wz * wz);
@@ -305,7 +315,9 @@ extern "C" sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts
   }
   g.start = (float)(grid->tan_half * (1.0 / grid->G - 1.0));
   g.step = (float)(2.0 * grid->tan_half / grid->G);
+  g.lo = (float)(-grid->tan_half);
   g.G = grid->G;
+  g.jitter = grid->jitter;
   RadarF rd;
   for (int t = 0; t < SBR_MAX_TX; ++t)
     for (int j = 0; j < 3; ++j) rd.tx[t][j] = (float)radar->tx[t][j];

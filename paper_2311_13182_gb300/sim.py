@@ -45,6 +45,25 @@ def radar_struct(radar) -> L.RadarCfg:
     return r
 
 
+_JITTER = {}  # id(grid offsets array) -> (array, device copy): the library borrows the device pointer
+
+
+def jitter_device(grid, device="cuda"):
+    """Device copy of a grid's jitter offsets [G*G, 2] (cached per offsets array), or None."""
+    jit = getattr(grid, "jitter", None)
+    if jit is None:
+        return None
+    key = id(jit)
+    hit = _JITTER.get(key)
+    if hit is None or hit[0] is not jit:
+        arr = np.ascontiguousarray(jit, dtype=np.float32).reshape(-1, 2)
+        if arr.shape[0] != grid.G * grid.G:
+            raise ValueError("jitter must hold G*G offset pairs")
+        hit = (jit, torch.from_numpy(arr).to(device))
+        _JITTER[key] = hit
+    return hit[1]
+
+
 def grid_struct(grid) -> L.RayGrid:
     g = L.RayGrid()
     g.G = grid.G
@@ -54,6 +73,8 @@ def grid_struct(grid) -> L.RayGrid:
         g.u_axis[j] = float(grid.u_axis[j])
         g.v_axis[j] = float(grid.v_axis[j])
     g.tan_half = float(grid.tan_half)
+    jd = jitter_device(grid)
+    g.jitter = jd.data_ptr() if jd is not None else None
     return g
 
 

@@ -96,10 +96,19 @@ class RayGrid:
     u_axis: np.ndarray   # [3] unit, orthogonal to axis
     v_axis: np.ndarray   # [3] unit, axis x u_axis
     tan_half: float
+    jitter: np.ndarray | None = None   # [G*G, 2] float32 offsets in [0, 1) per ray, or None (cell centres)
 
     @property
     def n_rays(self) -> int:
         return self.G * self.G
+
+
+def jittered(grid: RayGrid, seed: int) -> RayGrid:
+    """The same grid sampled at seeded uniform offsets inside each cell (stratified jittered
+    Monte-Carlo samples of Eq. 3); offsets are float32 in [0, 1)."""
+    rng = np.random.default_rng(seed)
+    off = rng.random((grid.G * grid.G, 2), dtype=np.float32)
+    return dataclasses.replace(grid, jitter=off)
 
 
 def ray_grid_for_sphere(center, radius: float, G: int, origin=(0.0, 0.0, 0.0)) -> RayGrid:

@@ -207,3 +207,11 @@ def test_image_loss_reconstruction_descends(sbr):
     torch.cuda.synchronize()
     loss1 = float(rec.loss.item())
     assert np.isfinite(loss1) and loss1 < loss0, (loss0, loss1)
+
+
+def test_trace_adjoint_jittered_grid(sbr):
+    """The trace adjoint on a jittered grid (its launch directions come from the offsets)."""
+    import dataclasses
+    from sbr_inputs import jittered
+    wl = sphere_scene(G=32)
+    check_trace_adjoint(sbr, dataclasses.replace(wl, grid=jittered(wl.grid, 6)))
