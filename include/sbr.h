@@ -60,6 +60,7 @@ typedef enum {
 #define SBR_MAX_RX 16
 #define SBR_MAX_VIRT 64
 #define SBR_MAX_MATERIALS 16
+#define SBR_MAX_OBJECTS 16
 
 /* FMCW radar (Section 3.2.2, Eq. 8: carrier f_c, sweep B over chirp time T,
  * mu = B / T).  Samples t_n = n T / N_s, n = 0..N_s-1.  Virtual antenna
@@ -113,6 +114,11 @@ typedef enum {
   SBR_PHASE_FP64 = 1,  /* per-sample carrier phase f_c tau + mu tau t_n in FP64 */
   SBR_PHASE_NAIVE = 2  /* tau, f_c tau and mu tau t_n all in FP32 */
 } sbr_phase_mode;
+
+/* OR'ed into sbr_synthesize's mode: synthesise every chirp from the paths'
+ * dL/dt (a trace of a scene with motion) instead of one chirp broadcast to all;
+ * SBR_PHASE_SPLIT (N_s <= 512) and SBR_PHASE_FP64 only. */
+#define SBR_SYNTH_MOVING 0x100
 
 /* One surface interaction of a ray (16 B).  tri = original triangle index or
  * -1 (no hit; every later bounce of that ray is -1 too). */
@@ -198,6 +204,28 @@ typedef struct {
  * Material indices outside [0, n_materials) are clamped to the last material. */
 sbr_status sbr_scene_set_materials(sbr_scene* scene, const sbr_materials* materials);
 
+/* Moving objects (the scene dynamics of Section 3.1).  Each triangle belongs to
+ * an object that translates with a constant velocity (m/s, radar frame) over the
+ * frame of chirps; every hit point moves with its object, so a path's length
+ * changes at dL/dt = sum_j v_j . (u_in,j - u_out,j) (u_in,j and u_out,j the unit
+ * vectors of the legs arriving at and leaving hit j; the first leg from Tx, the
+ * last towards Rx), and chirp c, starting c chirp_rep after the first, sees the
+ * delay tau + c chirp_rep (dL/dt) / c_0.  Amplitudes are held over the frame. */
+typedef struct {
+  int32_t n_objects;            /* 0: a static scene (the rest unread) */
+  int32_t _pad;
+  const int32_t* tri_object;    /* device [nt], object of each triangle in the caller's face order; NULL:
+                                   all object 0.  Borrowed: must stay valid while the scene is traced. */
+  float velocity[SBR_MAX_OBJECTS][3];
+} sbr_motion;
+
+/* Attaches (or, with NULL or n_objects = 0, removes) object motion: later
+ * sbr_trace calls write every path's dL/dt to paths->path_rate, which
+ * sbr_synthesize reads in SBR_SYNTH_MOVING mode.  Host-side only;
+ * SBR_ERR_INVALID_ARG for more than SBR_MAX_OBJECTS objects or non-finite
+ * velocities.  Object indices outside [0, n_objects) are clamped. */
+sbr_status sbr_scene_set_motion(sbr_scene* scene, const sbr_motion* motion);
+
 /* ------------------------------------------------------------------------ */
 /* Trace (Section 3.2.1, Eq. 2-3) and path preparation                      */
 /* ------------------------------------------------------------------------ */
@@ -223,6 +251,7 @@ typedef struct {
   float* phase_ofs;   /* [path_cap] phase of the path's Fresnel factor F in cycles (0 without
                          materials); folded into phi0 of prep, read by the FP64 and naive
                          synthesis modes, which form the carrier phase from path_len */
+  float* path_rate;   /* [V*path_cap] dL/dt [m/s] per (v, p), written only when the scene has motion */
 } sbr_paths;
 
 size_t sbr_paths_bytes(int32_t n_rays, int32_t max_bounces, int32_t n_virt);
@@ -272,7 +301,9 @@ size_t sbr_synth_ws_bytes(const sbr_radar_cfg* radar, int64_t path_cap);
  * a width-8 exponential-of-semicircle kernel, one FFT, deconvolution; ~1e-6
  * relative to the FP64 sum), term by term otherwise.  SBR_PHASE_FP64 forms each
  * sample's phase in FP64 from paths->path_len; SBR_PHASE_NAIVE rounds the delay
- * to FP32. */
+ * to FP32.  With SBR_SYNTH_MOVING OR'ed into mode (paths traced on a scene with
+ * motion) every chirp c is synthesised from the delays tau + c chirp_rep
+ * (dL/dt) / c_0, chirp by chirp; the adjoint below is the static model's. */
 sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg* radar,
                           sbr_phase_mode mode, float* d_cube, void* d_ws, size_t ws_bytes,
                           sbr_stream stream);

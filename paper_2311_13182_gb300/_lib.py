@@ -49,10 +49,16 @@ class Paths(ctypes.Structure):
     _fields_ = [("n_rays", c_i32), ("max_bounces", c_i32), ("n_virt", c_i32), ("_pad", c_i32),
                 ("path_cap", c_i64), ("hits", c_p), ("hit_pos", c_p), ("ray_weight", c_p),
                 ("ray_first", c_p), ("path_ray", c_p), ("prep", c_p), ("path_len", c_p), ("count", c_p),
-                ("scratch", c_p), ("phase_ofs", c_p)]
+                ("scratch", c_p), ("phase_ofs", c_p), ("path_rate", c_p)]
 
 
 MAX_MATERIALS = 16
+MAX_OBJECTS = 16
+SYNTH_MOVING = 0x100
+
+
+class Motion(ctypes.Structure):
+    _fields_ = [("n_objects", c_i32), ("_pad", c_i32), ("tri_object", c_p), ("velocity", (c_f32 * 3) * MAX_OBJECTS)]
 
 
 class Materials(ctypes.Structure):
@@ -119,6 +125,7 @@ _SIGS = {
     "sbr_synthesize": (c_i32, [P(Paths), P(RadarCfg), c_i32, c_p, c_p, c_sz, c_p]),
     "sbr_synthesize_bwd": (c_i32, [P(Paths), P(RadarCfg), c_p, c_p, c_p, c_p, c_p, c_sz, c_p]),
     "sbr_scene_set_materials": (c_i32, [c_p, P(Materials)]),
+    "sbr_scene_set_motion": (c_i32, [c_p, P(Motion)]),
     "sbr_synthesize_noalloc": (c_i32, [P(Paths), P(RadarCfg), c_i32, c_p, c_p]),
     "sbr_pc_bytes": (c_sz, [P(RadarCfg), P(CfarCfg)]),
     "sbr_pc_bind": (c_i32, [c_p, c_sz, P(RadarCfg), P(CfarCfg), P(PcState)]),

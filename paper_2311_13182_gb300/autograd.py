@@ -24,10 +24,22 @@ from . import sim
 
 class Simulator:
     def __init__(self, faces: np.ndarray, nv: int, radar, grid, max_bounces: int, cfar, ray_ids=None,
-                 phase_mode: int = sim.PHASE_SPLIT, recompute: bool = False, materials=None, device="cuda"):
+                 phase_mode: int = sim.PHASE_SPLIT, recompute: bool = False, materials=None, motion=None,
+                 device="cuda"):
         """materials: None (perfect conductors) or (eps, tri_material): complex relative
         permittivities (eps_re - j eps_im; eps_re <= 0 a perfect conductor) and each triangle's
-        material index (None: all material 0), Section 3.2.2 Eq. 9-10."""
+        material index (None: all material 0), Section 3.2.2 Eq. 9-10.
+        motion: None (a static scene) or (velocities, tri_object): a velocity [m/s] per object
+        and each triangle's object; the forward pass then synthesises every chirp from the
+        moving delays (no gradients through the motion)."""
+        self.velocities = None
+        self.tri_object = None
+        if motion is not None:
+            vel, tri_obj = motion
+            self.velocities = [tuple(float(x) for x in v) for v in vel]
+            if tri_obj is not None:
+                self.tri_object = torch.as_tensor(np.asarray(tri_obj, np.int32)).to(device)
+            phase_mode = phase_mode | sim.SYNTH_MOVING
         self.eps = None
         self.tri_material = None
         if materials is not None:
@@ -59,6 +71,8 @@ class Simulator:
             self.scene = sim.Scene(verts, self.faces)
             if self.eps:
                 self.scene.set_materials(self.eps, self.tri_material)
+            if self.velocities:
+                self.scene.set_motion(self.velocities, self.tri_object)
         else:
             self.scene.update(verts)
         paths = self.paths if self.paths is not None else sim.PathBuffers(self.n_rays, self.K, self.radar.n_virt,
@@ -90,6 +104,8 @@ class Simulator:
                       geps: torch.Tensor | None = None):
         """Adds dL/dverts to gverts for upstream dL/dcube [V, C, N_s, 2]; with materials also
         dL/d eps [n_materials, 2] (d eps_re, d eps_im) to ``geps`` when given."""
+        if self.velocities:
+            raise NotImplementedError("gradients through moving objects are not built (static model only)")
         paths = self.paths if self.paths is not None else self._trace(verts)
         gph = None
         if self.eps:

@@ -1110,6 +1110,25 @@ extern "C" sbr_status sbr_scene_check(const sbr_scene* scene, sbr_stream stream)
 
 extern "C" void sbr_scene_destroy(sbr_scene* scene) { free(scene); }
 
+extern "C" sbr_status sbr_scene_set_motion(sbr_scene* scene, const sbr_motion* m) {
+  SBR_ARG(scene, "sbr_scene_set_motion: scene is NULL");
+  if (!m || m->n_objects == 0) {
+    scene->n_obj = 0;
+    scene->tri_obj = nullptr;
+    return SBR_OK;
+  }
+  SBR_ARG(m->n_objects > 0 && m->n_objects <= SBR_MAX_OBJECTS, "sbr_scene_set_motion: n_objects=%d outside [0, %d]",
+          m->n_objects, SBR_MAX_OBJECTS);
+  for (int i = 0; i < m->n_objects; ++i)
+    for (int j = 0; j < 3; ++j)
+      SBR_ARG(std::isfinite(m->velocity[i][j]), "sbr_scene_set_motion: object %d: non-finite velocity", i);
+  scene->n_obj = m->n_objects;
+  scene->tri_obj = m->tri_object;
+  for (int i = 0; i < SBR_MAX_OBJECTS; ++i)
+    for (int j = 0; j < 3; ++j) scene->vel[i][j] = i < m->n_objects ? m->velocity[i][j] : 0.f;
+  return SBR_OK;
+}
+
 extern "C" sbr_status sbr_scene_set_materials(sbr_scene* scene, const sbr_materials* m) {
   SBR_ARG(scene, "sbr_scene_set_materials: scene is NULL");
   if (!m || m->n_materials == 0) {

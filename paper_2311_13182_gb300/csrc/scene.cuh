@@ -66,6 +66,10 @@ struct sbr_scene {
   int n_mat;
   const int32_t* tri_mat;  // caller's device [nt] or NULL (all material 0)
   float eps_re[SBR_MAX_MATERIALS], eps_im[SBR_MAX_MATERIALS];
+  // object motion (sbr_scene_set_motion): 0 = static
+  int n_obj;
+  const int32_t* tri_obj;  // caller's device [nt] or NULL (all object 0)
+  float vel[SBR_MAX_OBJECTS][3];
 };
 
 namespace sbr {
@@ -95,6 +99,27 @@ __device__ inline float2 csqrt(float2 z) {
   const float re = sqrtf(fmaxf(0.5f * (r + z.x), 0.f));
   const float im = sqrtf(fmaxf(0.5f * (r - z.x), 0.f));
   return make_float2(re, z.y < 0.f ? -im : im);
+}
+
+// Object motion as a kernel argument (by value).
+struct MotionArg {
+  int n;
+  const int32_t* tri_obj;
+  float3 vel[SBR_MAX_OBJECTS];
+};
+
+inline MotionArg motion_arg(const sbr_scene* s) {
+  MotionArg m{};
+  m.n = s->n_obj;
+  m.tri_obj = s->tri_obj;
+  for (int i = 0; i < SBR_MAX_OBJECTS; ++i) m.vel[i] = make_float3(s->vel[i][0], s->vel[i][1], s->vel[i][2]);
+  return m;
+}
+
+__device__ inline float3 velocity_of(const MotionArg& m, int id) {
+  int k = m.tri_obj ? m.tri_obj[id] : 0;
+  k = k < 0 ? 0 : (k >= m.n ? m.n - 1 : k);
+  return m.vel[k];
 }
 
 // Material of triangle `id` (original index), clamped into the table.

@@ -337,7 +337,9 @@ __global__ void __launch_bounds__(256) k_synth_fp64(const float4* __restrict__ p
                                                     const float* __restrict__ phase_ofs, int64_t cap,
                                                     const int32_t* __restrict__ d_P, int V, int Q,
                                                     int Ns, double f0, double b_over_ns,
-                                                    float2* __restrict__ partial) {
+                                                    float2* __restrict__ partial,
+                                                    const float* __restrict__ rate = nullptr,
+                                                    double crep = 0.0) {
   __shared__ double2 sx[kChunk];
   __shared__ float sa[kChunk];
   const int v = blockIdx.x % V, q = blockIdx.x / V;
@@ -351,7 +353,8 @@ __global__ void __launch_bounds__(256) k_synth_fp64(const float4* __restrict__ p
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       const float2 L = plen[(size_t)v * cap + c0 + j];
-      const double t = ((double)L.x + (double)L.y) * (1.0 / kC);
+      double t = ((double)L.x + (double)L.y) * (1.0 / kC);
+      if (rate) t += crep * (double)rate[(size_t)v * cap + c0 + j];  // this chirp's delay
       const double x0 = f0 * t;
       const double d = b_over_ns * t;
       sx[j] = make_double2(x0 - rint(x0) + (double)phase_ofs[c0 + j], d - rint(d));
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(256) k_synth_naive(const float4* __restrict__ 
 // the group's chirps (a static scene: every chirp equal).
 constexpr int kRedChirps = 16;
 __global__ void k_reduce(const float2* __restrict__ partial, int V, int Q, int Ns, int C,
-                         float2* __restrict__ cube) {
+                         float2* __restrict__ cube, int only = -1) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V * Ns) return;
   const int v = i / Ns, n = i - v * Ns;
@@ -433,6 +436,10 @@ __global__ void k_reduce(const float2* __restrict__ partial, int V, int Q, int N
     const float2 x = partial[((size_t)q * V + v) * Ns + n];
     re += x.x;
     im += x.y;
+  }
+  if (only >= 0) {  // a moving scene: this chirp only
+    cube[((size_t)v * C + only) * Ns + n] = make_float2(re, im);
+    return;
   }
   const int c1 = min(C, (int)(blockIdx.y + 1) * kRedChirps);
   for (int c = blockIdx.y * kRedChirps; c < c1; ++c) cube[((size_t)v * C + c) * Ns + n] = make_float2(re, im);
@@ -571,7 +578,9 @@ struct PsiQuad {
 __global__ void __launch_bounds__(kNuThreads) k_nufft_spread(const float4* __restrict__ prep, int64_t cap,
                                                             const int32_t* __restrict__ d_P, int V, int Q,
                                                             NufftArg na, float2* __restrict__ grids,
-                                                            unsigned int* __restrict__ fin_cnt) {
+                                                            unsigned int* __restrict__ fin_cnt,
+                                                            const float* __restrict__ rate = nullptr,
+                                                            float cnu = 0.f, float ceps = 0.f) {
   extern __shared__ float2 wgrid[];  // [warp][M]
   if (blockIdx.x == 0 && threadIdx.x < V) fin_cnt[threadIdx.x] = 0u;  // the finishing kernel's counters
   const int M = 1 << na.log_m;
@@ -594,7 +603,19 @@ __global__ void __launch_bounds__(kNuThreads) k_nufft_spread(const float4* __res
     float cre = 0.f, cim = 0.f, t = 0.f;
     int i0 = 0;
     if (p < P) {
-      const float4 r = __ldg(&pv[p]);  // phi0, delta_hi, delta_lo, A
+      float4 r = __ldg(&pv[p]);  // phi0, delta_hi, delta_lo, A
+      if (rate) {
+        // a moving scene's chirp: phi0 + dL/dt cnu and delta + dL/dt ceps, whole multiples of
+        // 2^-12 of the delta shift moved into delta_hi (which stays exact)
+        const float ld = __ldg(&rate[(size_t)v * cap + p]);
+        float ph = fmaf(ld, cnu, r.x);
+        r.x = ph - rintf(ph);
+        const float dl = fmaf(ld, ceps, r.z);
+        const float kq = rintf(dl * 4096.f);
+        const float dh = r.y + kq * (1.f / 4096.f);
+        r.y = dh - rintf(dh);
+        r.z = dl - kq * (1.f / 4096.f);
+      }
       float x = na.half_n * r.y;       // exact
       x -= rintf(x);
       x = fmaf(na.half_n, r.z, x) + r.x;
@@ -964,6 +985,56 @@ sbr_status bind_ws(const sbr_radar_cfg* radar, int64_t cap, void* ws, size_t byt
   return SBR_OK;
 }
 
+// A moving scene: every chirp synthesised from its own delays (split phase by the
+// non-uniform FFT up to 512 samples, or the FP64 phase), chirp by chirp.
+sbr_status launch_moving(sbr_phase_mode mode, const sbr_paths* p, const sbr_radar_cfg* r, const SynthWs& w,
+                         float2* cube, cudaStream_t st) {
+  const int V = p->n_virt, Ns = r->n_samples, C = r->n_chirps;
+  const double per_chirp = r->chirp_rep / kC;  // delay change per chirp per (m/s) of dL/dt
+  if (mode == SBR_PHASE_SPLIT && Ns <= kNuMaxSamples) {
+    int log_m = 0;
+    while ((1 << log_m) < 2 * Ns) ++log_m;
+    NufftArg na{0.5f * (float)Ns, 2.f * (float)Ns, (float)(kNuBeta * 1.4426950408889634), log_m};
+    nufft_per_sm(Ns);
+    const int M = 2 * Ns, slices = M < kNuFinSlice ? 1 : M / kNuFinSlice;
+    for (int c = 0; c < C; ++c) {
+      const float cnu = (float)(c * per_chirp * r->f0), ceps = (float)(c * per_chirp * r->bandwidth / Ns);
+      ::sbr::note_launch();
+      k_nufft_spread<<<V * w.Qn, kNuThreads, nufft_smem(Ns), st>>>(reinterpret_cast<const float4*>(p->prep),
+                                                                   p->path_cap, p->count, V, w.Qn, na, w.grids,
+                                                                   w.fin_cnt, p->path_rate, cnu, ceps);
+      ::sbr::note_launch();
+      k_nufft_finish<<<V * slices, kNuFinThreads, sizeof(float2) * (3 * (size_t)Ns + kNuFinThreads), st>>>(
+          w.grids, V, w.Qn, Ns, log_m, psi_quad(), w.bsum, w.fin_cnt, w.samples);
+      ::sbr::note_launch();
+      k_reduce<<<dim3((V * Ns + 255) / 256, 1), 256, 0, st>>>(w.samples, V, 1, Ns, C, cube, c);
+    }
+    return SBR_OK;
+  }
+  if (mode == SBR_PHASE_FP64) {
+    const int T = threads_for(Ns), Mv = Ns / T;
+    const int grid = V * w.Q;
+    const float4* prep = reinterpret_cast<const float4*>(p->prep);
+    const float2* plen = reinterpret_cast<const float2*>(p->path_len);
+    for (int c = 0; c < C; ++c) {
+      ::sbr::note_launch();
+      switch (Mv) {
+        case 1: k_synth_fp64<1><<<grid, T, 0, st>>>(prep, plen, p->phase_ofs, p->path_cap, p->count, V, w.Q, Ns, r->f0, r->bandwidth / Ns, w.partial, p->path_rate, c * per_chirp); break;
+        case 2: k_synth_fp64<2><<<grid, T, 0, st>>>(prep, plen, p->phase_ofs, p->path_cap, p->count, V, w.Q, Ns, r->f0, r->bandwidth / Ns, w.partial, p->path_rate, c * per_chirp); break;
+        case 4: k_synth_fp64<4><<<grid, T, 0, st>>>(prep, plen, p->phase_ofs, p->path_cap, p->count, V, w.Q, Ns, r->f0, r->bandwidth / Ns, w.partial, p->path_rate, c * per_chirp); break;
+        case 8: k_synth_fp64<8><<<grid, T, 0, st>>>(prep, plen, p->phase_ofs, p->path_cap, p->count, V, w.Q, Ns, r->f0, r->bandwidth / Ns, w.partial, p->path_rate, c * per_chirp); break;
+        default: k_synth_fp64<16><<<grid, T, 0, st>>>(prep, plen, p->phase_ofs, p->path_cap, p->count, V, w.Q, Ns, r->f0, r->bandwidth / Ns, w.partial, p->path_rate, c * per_chirp); break;
+      }
+      ::sbr::note_launch();
+      k_reduce<<<dim3((V * Ns + 255) / 256, 1), 256, 0, st>>>(w.partial, V, w.Q, Ns, C, cube, c);
+    }
+    return SBR_OK;
+  }
+  set_error("sbr_synthesize: SBR_SYNTH_MOVING supports SBR_PHASE_SPLIT up to %d samples and SBR_PHASE_FP64",
+            kNuMaxSamples);
+  return SBR_ERR_UNSUPPORTED;
+}
+
 // Split-phase samples by the non-uniform FFT: spread, finish, one chirp -> all chirps.
 void launch_nufft(const sbr_paths* p, const sbr_radar_cfg* r, const SynthWs& w, float2* cube, cudaStream_t st) {
   const int V = p->n_virt, Ns = r->n_samples;
@@ -1012,9 +1083,11 @@ void launch_fwd(sbr_phase_mode mode, const sbr_paths* p, const sbr_radar_cfg* r,
 }  // namespace
 
 extern "C" sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg* radar,
-                                     sbr_phase_mode mode, float* d_cube, void* d_ws,
+                                     sbr_phase_mode mode_flags, float* d_cube, void* d_ws,
                                      size_t ws_bytes, sbr_stream stream) {
   SBR_ARG(paths && d_cube, "sbr_synthesize: NULL paths or cube");
+  const bool moving = ((int)mode_flags & SBR_SYNTH_MOVING) != 0;
+  const sbr_phase_mode mode = (sbr_phase_mode)((int)mode_flags & ~SBR_SYNTH_MOVING);
   sbr_status rs = check_radar(radar, "sbr_synthesize");
   if (rs != SBR_OK) return rs;
   SBR_ARG(paths->n_virt == radar->n_tx * radar->n_rx, "sbr_synthesize: paths have V=%d, radar %d",
@@ -1026,6 +1099,12 @@ extern "C" sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg
   if (rs != SBR_OK) return rs;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int Ns = radar->n_samples, T = threads_for(Ns), M = Ns / T;
+  if (moving) {
+    rs = launch_moving(mode, paths, radar, w, reinterpret_cast<float2*>(d_cube), st);
+    if (rs != SBR_OK) return rs;
+    SBR_CUDA(cudaGetLastError());
+    return SBR_OK;
+  }
   if (nufft_for(mode, Ns)) {
     launch_nufft(paths, radar, w, reinterpret_cast<float2*>(d_cube), st);
     SBR_CUDA(cudaGetLastError());

@@ -813,11 +813,12 @@ __device__ inline ff ff_frac(ff x) {
 // most lanes idle); each lane recomputes its ray's Tx legs and interior length.
 // NTX > 0: that many transmitters, their path lengths held in registers;
 // NTX = 0: rd.ntx of them (up to SBR_MAX_TX).
-template <int NTX>
+template <int NTX, bool kMotion>
 __global__ void k_prep(const float4* __restrict__ hit_pos, const sbr_hit* __restrict__ hits,
                        const float* __restrict__ ray_w, const int32_t* __restrict__ first, int n_rays, int K,
-                       RadarArg rd, MatArg mat, int64_t cap, float4* __restrict__ prep, float2* __restrict__ plen,
-                       int32_t* __restrict__ path_ray, float* __restrict__ phase_ofs) {
+                       RadarArg rd, MatArg mat, MotionArg mot, int64_t cap, float4* __restrict__ prep,
+                       float2* __restrict__ plen, int32_t* __restrict__ path_ray, float* __restrict__ phase_ofs,
+                       float* __restrict__ path_rate) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   int p0 = 0, nh = 0;
@@ -856,6 +857,11 @@ __global__ void k_prep(const float4* __restrict__ hit_pos, const sbr_hit* __rest
       F = cmul(F, r);
     };
     if (mat.n > 0) fresnel_at(0, cosv);
+    // moving objects: the antenna-independent part of dL/dt (the legs between hits)
+    const float3 h0f = f3(h1.x.hi, h1.y.hi, h1.z.hi);
+    float3 hpf = h0f, v0 = f3(0.f, 0.f, 0.f), vp = v0;
+    float rate_in = 0.f;
+    if (kMotion) vp = v0 = velocity_of(mot, hits[(size_t)ri * K].tri);
     constexpr int kT = NTX > 0 ? NTX : SBR_MAX_TX;
     const int ntx = NTX > 0 ? NTX : rd.ntx;
     ff lin[kT];
@@ -869,6 +875,15 @@ __global__ void k_prep(const float4* __restrict__ hit_pos, const sbr_hit* __rest
       interior = ff_add(interior, ff3_len(ff3_sub(hm, h)));
       h = hm;
       if (mat.n > 0) fresnel_at(m, cosv);
+      if (kMotion) {  // leg m-1 -> m: arrives at hit m, leaves hit m-1
+        const float3 hmf = f3(hm.x.hi, hm.y.hi, hm.z.hi);
+        const float3 vm = velocity_of(mot, hits[(size_t)ri * K + m].tri);
+        const float3 e = hmf - hpf;
+        const float3 u = e * rsqrtf(dot(e, e));
+        rate_in += dot(vm, u) - dot(vp, u);
+        hpf = hmf;
+        vp = vm;
+      }
     }
     float rlin[kT];  // 1 / L_in
 #pragma unroll
@@ -887,9 +902,23 @@ __global__ void k_prep(const float4* __restrict__ hit_pos, const sbr_hit* __rest
     }
     phase_ofs[p] = fphase;
     const float wa = omega * fmag * cosv * (float)(0.25 / M_PI);
+    float rate_tx[kT];  // v_1 . unit(h_1 - Tx_t)
+    if (kMotion) {
+#pragma unroll
+      for (int t = 0; t < kT; ++t)
+        if (t < ntx) {
+          const float3 e = h0f - f3(rd.tx[t][0].hi, rd.tx[t][1].hi, rd.tx[t][2].hi);
+          rate_tx[t] = dot(v0, e) * rsqrtf(dot(e, e));
+        }
+    }
     for (int rr = 0; rr < rd.nrx; ++rr) {
       const ff lout = ff3_len(ff3_sub(ff3_arr(rd.rx[rr]), h));
       const float wo = wa / lout.hi;
+      float rate_rx = 0.f;  // v_k . unit(Rx_r - h_k)
+      if (kMotion) {
+        const float3 e = f3(rd.rx[rr][0].hi, rd.rx[rr][1].hi, rd.rx[rr][2].hi) - hpf;
+        rate_rx = dot(vp, e) * rsqrtf(dot(e, e));
+      }
 #pragma unroll
       for (int t = 0; t < kT; ++t) {
         if (t >= ntx) break;
@@ -907,12 +936,45 @@ __global__ void k_prep(const float4* __restrict__ hit_pos, const sbr_hit* __rest
         const float dlo = (dl.hi - dhi) + dl.lo;  // dl.hi - dhi is exact
         prep[(size_t)v * cap + p] = make_float4(phi0, dhi, dlo, wo * rlin[t]);
         plen[(size_t)v * cap + p] = make_float2(L.hi, L.lo);
+        if (kMotion) path_rate[(size_t)v * cap + p] = rate_in + rate_tx[t] - rate_rx;
       }
     }
   }
 }
 
 inline int blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+// k_prep for the common transmitter counts (their legs stay in registers), with or without motion
+template <bool kMotion>
+void launch_prep(int nb, cudaStream_t st, const float4* hp4, const sbr_paths* paths, int64_t R, int K,
+                 const RadarArg& rd, const MatArg& mat, const MotionArg& mot, float4* prep, float2* plen) {
+  switch (rd.ntx) {
+    case 1:
+      k_prep<1, kMotion><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R, K, rd,
+                                              mat, mot, paths->path_cap, prep, plen, paths->path_ray,
+                                              paths->phase_ofs, paths->path_rate);
+      break;
+    case 2:
+      k_prep<2, kMotion><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R, K, rd,
+                                              mat, mot, paths->path_cap, prep, plen, paths->path_ray,
+                                              paths->phase_ofs, paths->path_rate);
+      break;
+    case 3:
+      k_prep<3, kMotion><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R, K, rd,
+                                              mat, mot, paths->path_cap, prep, plen, paths->path_ray,
+                                              paths->phase_ofs, paths->path_rate);
+      break;
+    case 4:
+      k_prep<4, kMotion><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R, K, rd,
+                                              mat, mot, paths->path_cap, prep, plen, paths->path_ray,
+                                              paths->phase_ofs, paths->path_rate);
+      break;
+    default:
+      k_prep<0, kMotion><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R, K, rd,
+                                              mat, mot, paths->path_cap, prep, plen, paths->path_ray,
+                                              paths->phase_ofs, paths->path_rate);
+  }
+}
 
 // After the scan's scratch in the paths region: the straggler hand-over's two
 // counters (handed over, claimed) and its records.
@@ -950,6 +1012,7 @@ size_t paths_layout(sbr_paths* p, void* mem, int32_t R, int32_t K, int32_t V) {
   p->path_len = c.take<float>(2 * (int64_t)V * capc);
   p->scratch = c.take<char>(scan_part(R) + kCtrBytes + sizeof(RayDump) * (size_t)kDumpMax);
   p->phase_ofs = c.take<float>(capc);
+  p->path_rate = c.take<float>((int64_t)V * capc);
   p->count = p->ray_first ? p->ray_first + R : nullptr;
   return c.bytes();
 }
@@ -1095,32 +1158,11 @@ static sbr_status trace_impl(const sbr_scene* scene, const sbr_radar_cfg* radar,
     float2* plen = reinterpret_cast<float2*>(paths->path_len);
     const int nb = blocks(R, 128);
     const MatArg mat = mat_arg(scene);
-    switch (rd.ntx) {  // the common transmitter counts keep their legs in registers
-      case 1:
-        k_prep<1><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R,
-                                      max_bounces, rd, mat, paths->path_cap, prep, plen, paths->path_ray,
-                                      paths->phase_ofs);
-        break;
-      case 2:
-        k_prep<2><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R,
-                                      max_bounces, rd, mat, paths->path_cap, prep, plen, paths->path_ray,
-                                      paths->phase_ofs);
-        break;
-      case 3:
-        k_prep<3><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R,
-                                      max_bounces, rd, mat, paths->path_cap, prep, plen, paths->path_ray,
-                                      paths->phase_ofs);
-        break;
-      case 4:
-        k_prep<4><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R,
-                                      max_bounces, rd, mat, paths->path_cap, prep, plen, paths->path_ray,
-                                      paths->phase_ofs);
-        break;
-      default:
-        k_prep<0><<<nb, 128, 0, st>>>(hp4, paths->hits, paths->ray_weight, paths->ray_first, (int)R,
-                                      max_bounces, rd, mat, paths->path_cap, prep, plen, paths->path_ray,
-                                      paths->phase_ofs);
-    }
+    const MotionArg mot = motion_arg(scene);
+    if (mot.n > 0)
+      launch_prep<true>(nb, st, hp4, paths, R, max_bounces, rd, mat, mot, prep, plen);
+    else
+      launch_prep<false>(nb, st, hp4, paths, R, max_bounces, rd, mat, mot, prep, plen);
   }
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;

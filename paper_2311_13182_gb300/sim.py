@@ -13,6 +13,7 @@ import torch
 from . import _lib as L
 
 PHASE_SPLIT, PHASE_FP64, PHASE_NAIVE = L.PHASE_SPLIT, L.PHASE_FP64, L.PHASE_NAIVE
+SYNTH_MOVING = L.SYNTH_MOVING  # OR into a phase mode: every chirp from the paths' dL/dt
 
 
 def _vp(t):
@@ -136,6 +137,24 @@ class Scene:
         L.call("sbr_scene_set_materials", self.handle, ctypes.byref(m))
         self.n_materials = len(eps)
 
+    def set_motion(self, velocities, tri_object: torch.Tensor | None = None):
+        """sbr_scene_set_motion: a velocity [m/s] per object and the object of each triangle
+        (device int32 [nt], None: all object 0); empty or None makes the scene static."""
+        m = L.Motion()
+        vel = [] if velocities is None else [tuple(float(x) for x in v) for v in velocities]
+        if len(vel) > L.MAX_OBJECTS:
+            raise ValueError(f"at most {L.MAX_OBJECTS} objects")
+        m.n_objects = len(vel)
+        for i, v in enumerate(vel):
+            for j in range(3):
+                m.velocity[i][j] = v[j]
+        if tri_object is not None:
+            _need_cuda(tri_object, torch.int32, "tri_object")
+        self._tri_object = tri_object              # borrowed by the library: keep it alive
+        m.tri_object = tri_object.data_ptr() if tri_object is not None else None
+        L.call("sbr_scene_set_motion", self.handle, ctypes.byref(m))
+        self.n_objects = len(vel)
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value and L._LIB is not None:
@@ -188,6 +207,10 @@ class PathBuffers:
         """Path lengths L_in + L_out [V, path_cap] in float64 (hi + lo of the stored pairs)."""
         raw = _region(self.mem, self.s.path_len, torch.float32, (self.V, max(self.cap, 1), 2)).double()
         return raw[..., 0] + raw[..., 1]
+
+    def path_rate(self):
+        """dL/dt [V, path_cap] in m/s (written by a trace of a scene with motion)."""
+        return _region(self.mem, self.s.path_rate, torch.float32, (self.V, max(self.cap, 1)))
 
     def phase_ofs(self):
         """Per-path Fresnel phase [path_cap] in cycles (0 without materials)."""
