@@ -9,9 +9,11 @@ clouds (Section 4).  The reading implemented here, step by step in FP64:
   1. range DFT over samples    X[v,c,k] = sum_n S[v,c,n] e^{-j2pi kn/N_s}   (direct O(N^2))
   2. Doppler DFT over chirps   X[v,d,k] = sum_c X[v,c,k] e^{-j2pi dc/C}     (direct O(C^2))
   3. angle DFT                 Y[a,d,k] = sum_v W[a,v] X[v,d,k],
-                               W[a,v] = e^{+j2pi x_v u_a / lambda},  u_a = -1 + 2a/N_theta,
-                               x_v = x(Tx_t) + x(Rx_r)  (a target at u = sin(theta) gives
-                               phase -2pi x_v u / lambda across the array, so W peaks there);
+                               W[a,v] = e^{+j2pi (x_v u_a + y_v w_e) / lambda}, u_a = -1 + 2a/N_theta,
+                               w_e = (2e + 1 - N_elev)/N_elev (w = 0 with one elevation bin),
+                               x_v, y_v = position of Tx_t + Rx_r  (a target at direction
+                               cosines (u, w) gives phase -2pi (x_v u + y_v w) / lambda across
+                               the array, so W peaks there); rows e * N_theta + a;
                                lambda = c / (f_c + B/2), the sweep's centre wavelength: the
                                range DFT at the peak bin carries each element's delay at the
                                mean instantaneous frequency of the chirp, not at f_c
@@ -20,13 +22,14 @@ clouds (Section 4).  The reading implemented here, step by step in FP64:
                                `guard` cells (cells outside [0, N_s) are skipped)
   6. soft detection            w = sigmoid((ln Pw - ln(alpha N + P_floor)) / beta),
                                P_floor = floor_rel * max Pw
-  7. peaks                     local maxima of Pw over the 3x3 (angle, range) neighbourhood
+  7. peaks                     local maxima of Pw over the 3x3x3 (elevation, azimuth, range) neighbourhood
                                that exceed P_floor (an all-zero map has no peak);
                                equal values: the lower linear index a*N_s+k wins
-  8. sub-bin refine            3-point parabola on l = ln(max(Pw, 1e-30)) per axis,
+  8. sub-bin refine            3-point parabola on l = ln(max(Pw, 1e-30)) per axis (range, azimuth, elevation),
                                clamped to +-0.5 bin, 0 on the border
   9. points                    r = (k + dk) c / (2B), u = -1 + 2(a + da)/N_theta,
-                               p = (r u, 0, r sqrt(1 - u^2)), weight w;
+                               w = (2(e + de) + 1 - N_elev)/N_elev,
+                               p = (r u, r w, r sqrt(1 - u^2 - w^2)), weight w;
                                keep w >= w_min, order by (w desc, linear index asc),
                                at most k_max points
 """
@@ -55,12 +58,23 @@ def dft(x: np.ndarray, axis: int) -> np.ndarray:
     return np.moveaxis(y, -1, axis)
 
 
-def steering(radar, n_theta: int) -> np.ndarray:
-    """W [n_theta, V] = exp(+j 2 pi x_v u_a / lambda_c), lambda_c = c / (f_c + B/2)."""
+def n_elev_of(cfg) -> int:
+    return max(1, int(getattr(cfg, "n_elev", 1)))
+
+
+def steering(radar, n_theta: int, n_elev: int = 1) -> np.ndarray:
+    """W [n_elev * n_theta, V] = exp(+j 2 pi (x_v u_a + y_v w_e) / lambda_c),
+    lambda_c = c / (f_c + B/2), row e * n_theta + a; u_a = -1 + 2a / n_theta (azimuth
+    direction cosine), w_e = (2e + 1 - n_elev) / n_elev (elevation direction cosine, bin
+    centres: w = 0 for a single bin); x_v, y_v the virtual element's position (Tx + Rx)."""
     lam = C_LIGHT / (radar.f0 + 0.5 * radar.bandwidth)
-    xv = np.array([radar.tx[t, 0] + radar.rx[r, 0] for t in range(radar.n_tx) for r in range(radar.n_rx)])
+    pairs = [(t, r) for t in range(radar.n_tx) for r in range(radar.n_rx)]
+    xv = np.array([radar.tx[t, 0] + radar.rx[r, 0] for t, r in pairs])
+    yv = np.array([radar.tx[t, 1] + radar.rx[r, 1] for t, r in pairs])
     u = -1.0 + 2.0 * np.arange(n_theta) / n_theta
-    return np.exp(2j * np.pi * np.outer(u, xv) / lam)
+    w = (2.0 * np.arange(n_elev) + 1.0 - n_elev) / n_elev
+    ph = (w[:, None, None] * yv[None, None, :] + u[None, :, None] * xv[None, None, :]) / lam
+    return np.exp(2j * np.pi * ph.reshape(n_elev * n_theta, -1))
 
 
 def cfar_noise(Pw: np.ndarray, guard: int, train: int) -> np.ndarray:
@@ -74,60 +88,73 @@ def cfar_noise(Pw: np.ndarray, guard: int, train: int) -> np.ndarray:
     return noise
 
 
-def local_max(Pw: np.ndarray) -> np.ndarray:
-    A, N = Pw.shape
-    pad = np.full((A + 2, N + 2), -np.inf)
-    pad[1:-1, 1:-1] = Pw
-    peak = np.ones((A, N), bool)
-    for da in (-1, 0, 1):
-        for dk in (-1, 0, 1):
-            if da == 0 and dk == 0:
-                continue
-            q = pad[1 + da:1 + da + A, 1 + dk:1 + dk + N]
-            earlier = da < 0 or (da == 0 and dk < 0)
-            peak &= (Pw > q) if earlier else (Pw >= q)
-    return peak
+def local_max(Pw: np.ndarray, n_elev: int = 1) -> np.ndarray:
+    """Local maxima over the 3 x 3 x 3 (elevation, azimuth, range) neighbourhood of the map
+    [n_elev * n_theta, N]; equal values: the lower linear index wins."""
+    R, N = Pw.shape
+    E, A = n_elev, R // n_elev
+    P3 = Pw.reshape(E, A, N)
+    pad = np.full((E + 2, A + 2, N + 2), -np.inf)
+    pad[1:-1, 1:-1, 1:-1] = P3
+    peak = np.ones((E, A, N), bool)
+    for de in (-1, 0, 1):
+        for da in (-1, 0, 1):
+            for dk in (-1, 0, 1):
+                if de == 0 and da == 0 and dk == 0:
+                    continue
+                q = pad[1 + de:1 + de + E, 1 + da:1 + da + A, 1 + dk:1 + dk + N]
+                earlier = (de, da, dk) < (0, 0, 0)
+                peak &= (P3 > q) if earlier else (P3 >= q)
+    return peak.reshape(R, N)
 
 
-def _refine(l: np.ndarray, a: np.ndarray, k: np.ndarray):
-    A, N = l.shape
-    dk = np.zeros(a.shape)
-    da = np.zeros(a.shape)
-    for i in range(a.shape[0]):
-        ai, ki = a[i], k[i]
+def _refine(l: np.ndarray, rows: np.ndarray, k: np.ndarray, n_elev: int = 1):
+    """3-point parabola on l = ln Pw per axis (range, azimuth, elevation), clamped to +-1/2
+    bin, 0 on the border of that axis."""
+    R, N = l.shape
+    A = R // n_elev
+
+    def par(lm, l0, lp):
+        den = lm - 2.0 * l0 + lp
+        return np.clip(0.5 * (lm - lp) / den, -0.5, 0.5) if den < 0 else 0.0
+
+    dk, da, de = np.zeros(rows.shape), np.zeros(rows.shape), np.zeros(rows.shape)
+    for i in range(rows.shape[0]):
+        ri, ki = rows[i], k[i]
+        e, a = divmod(int(ri), A)
         if 0 < ki < N - 1:
-            lm, l0, lp = l[ai, ki - 1], l[ai, ki], l[ai, ki + 1]
-            den = lm - 2.0 * l0 + lp
-            if den < 0:
-                dk[i] = np.clip(0.5 * (lm - lp) / den, -0.5, 0.5)
-        if 0 < ai < A - 1:
-            lm, l0, lp = l[ai - 1, ki], l[ai, ki], l[ai + 1, ki]
-            den = lm - 2.0 * l0 + lp
-            if den < 0:
-                da[i] = np.clip(0.5 * (lm - lp) / den, -0.5, 0.5)
-    return dk, da
+            dk[i] = par(l[ri, ki - 1], l[ri, ki], l[ri, ki + 1])
+        if 0 < a < A - 1:
+            da[i] = par(l[ri - 1, ki], l[ri, ki], l[ri + 1, ki])
+        if 0 < e < n_elev - 1:
+            de[i] = par(l[ri - A, ki], l[ri, ki], l[ri + A, ki])
+    return dk, da, de
 
 
 def power_map(cube: np.ndarray, radar, cfg: CfarConfig):
     X = dft(cube, axis=2)                  # range
     X = dft(X, axis=1)                     # Doppler
-    W = steering(radar, cfg.n_theta)
-    Y = np.einsum("av,vdk->adk", W, X)     # angle
+    W = steering(radar, cfg.n_theta, n_elev_of(cfg))
+    Y = np.einsum("av,vdk->adk", W, X)     # angle (azimuth x elevation rows)
     Pw = (np.abs(Y) ** 2).sum(axis=1)
     return X, Y, Pw
 
 
 def points_at(Pw: np.ndarray, radar, cfg: CfarConfig, a: np.ndarray, k: np.ndarray):
-    """Soft weights and refined 3D points at given (angle, range) cells."""
+    """Soft weights and refined 3D points at given (angle row, range) cells; row
+    a = e * n_theta + azimuth bin."""
+    E = n_elev_of(cfg)
     noise = cfar_noise(Pw, cfg.guard, cfg.train)
     floor = cfg.floor_rel * Pw.max()
     l = np.log(np.maximum(Pw, L_FLOOR))
     z = (l[a, k] - np.log(cfg.alpha * noise[a, k] + floor)) / cfg.beta
     w = 1.0 / (1.0 + np.exp(-z))
-    dk, da = _refine(l, a, k)
+    dk, da, de = _refine(l, a, k, E)
+    az, el = a % cfg.n_theta, a // cfg.n_theta
     r = (k + dk) * C_LIGHT / (2.0 * radar.bandwidth)
-    u = np.clip(-1.0 + 2.0 * (a + da) / cfg.n_theta, -1.0, 1.0)
-    pts = np.stack([r * u, np.zeros_like(r), r * np.sqrt(1.0 - u * u), w], axis=1)
+    u = np.clip(-1.0 + 2.0 * (az + da) / cfg.n_theta, -1.0, 1.0)
+    v = (2.0 * (el + de) + 1.0 - E) / E
+    pts = np.stack([r * u, r * v, r * np.sqrt(np.maximum(1.0 - u * u - v * v, 0.0)), w], axis=1)
     return pts
 
 
@@ -135,7 +162,7 @@ def pointcloud(cube: np.ndarray, radar, cfg: CfarConfig = None) -> dict:
     """Point cloud [n, 4] (x, y, z, w) from an IF cube [V, C, N_s]."""
     cfg = cfg or CfarConfig()
     X, Y, Pw = power_map(cube, radar, cfg)
-    peak = local_max(Pw) & (Pw > cfg.floor_rel * Pw.max())
+    peak = local_max(Pw, n_elev_of(cfg)) & (Pw > cfg.floor_rel * Pw.max())
     a, k = np.nonzero(peak)
     pts = points_at(Pw, radar, cfg, a, k) if a.size else np.zeros((0, 4))
     keep = pts[:, 3] >= cfg.w_min if a.size else np.zeros(0, bool)

@@ -71,6 +71,16 @@ def radar_single_tx(n_samples: int = 256, n_chirps: int = 1) -> RadarConfig:
     return _radar(77e9, 4e9, 40e-6, n_samples, n_chirps, 1, 0.0)
 
 
+def radar_awr1843(n_samples: int = 256, n_chirps: int = 128) -> RadarConfig:
+    """77 GHz 3 Tx x 4 Rx with the middle transmitter raised by lambda/2 (the AWR1843
+    layout): Tx at (0, 0), (lambda, lambda/2), (2 lambda, 0); Rx at r lambda/2 along x.
+    Eight virtual elements span azimuth at y = 0 and four sit lambda/2 higher."""
+    lam = C_LIGHT / 77e9
+    tx = np.array([[0.0, 0.0, 0.0], [lam, 0.5 * lam, 0.0], [2 * lam, 0.0, 0.0]])
+    rx = np.array([[r * 0.5 * lam, 0.0, 0.0] for r in range(4)])
+    return RadarConfig(77e9, 4e9, 40e-6, n_samples, n_chirps, 40e-6, tx, rx)
+
+
 def radar_mimo_3x4(n_samples: int = 256, n_chirps: int = 128) -> RadarConfig:
     """77 GHz 3 Tx x 4 Rx: Tx at t*2*lambda, Rx at r*lambda/2 -> 12 uniform virtual elements."""
     return _radar(77e9, 4e9, 40e-6, n_samples, n_chirps, 3, 2.0)
@@ -348,6 +358,7 @@ class CfarParams:
     beta: float = 0.5
     w_min: float = 0.01
     k_max: int = 2000
+    n_elev: int = 1          # elevation bins (a 2D virtual array); 1: azimuth only
 
     @property
     def alpha(self) -> float:

@@ -816,3 +816,24 @@ def test_moving_point_target_doppler_bin():
     assert int(np.argmax(np.abs(X[0]).sum(axis=1))) == 20
     still = oracle.synthesize_moving(tau, amp, radar, np.zeros((4, 1)))
     np.testing.assert_allclose(still, np.repeat(still[:, :1], radar.n_chirps, axis=1), atol=1e-12)
+
+
+def test_elevation_of_point_scatterers():
+    """The AWR1843-like array (middle Tx raised by lambda/2) with 8 elevation bins: the
+    strongest detection of a point target at direction cosines (u0, w0) and range r0 lies at
+    (u0, w0) within 0.01 and at r0 within a quarter bin; with one elevation bin the same
+    target's points have y = 0 (azimuth only)."""
+    from sbr_inputs import radar_awr1843
+    radar = radar_awr1843(256, 1)
+    binw = C_LIGHT / (2 * radar.bandwidth)
+    for u0, w0, r0 in ((0.3, 0.2, 2.1), (-0.4, -0.5, 3.3), (0.05, 0.6, 1.6)):
+        p = (r0 * u0, r0 * w0, r0 * math.sqrt(1 - u0 * u0 - w0 * w0))
+        cube = point_target_cube(radar, [(p, 1.0)])
+        out = pc.pointcloud(cube, radar, pc.CfarConfig(n_elev=8))
+        i = int(np.argmax(out["Pw"][out["a"], out["k"]]))
+        top = out["points"][i]
+        rr = np.linalg.norm(top[:3])
+        assert abs(top[0] / rr - u0) < 0.01 and abs(top[1] / rr - w0) < 0.01, top
+        assert abs(rr - r0) < 0.25 * binw
+        flat = pc.pointcloud(cube, radar, pc.CfarConfig())
+        assert (flat["points"][:, 1] == 0).all()
