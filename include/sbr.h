@@ -97,9 +97,13 @@ typedef struct {
 
 /* Soft CA-CFAR and point extraction (the map T of Eq. 16; parameters are
  * this library's reading: the paper names T only as "a signal processing
- * algorithm").  Angle bins u_a = -1 + 2a / n_theta. */
+ * algorithm").  Angle rows rho = e * n_theta + a, R = n_elev * n_theta of them:
+ * azimuth cosine u_a = -1 + 2a / n_theta, elevation cosine
+ * w_e = (2e + 1 - n_elev) / n_elev (w = 0 with one elevation bin); the steering
+ * phase of virtual element v is 2 pi (x_v u + y_v w) / lambda_c with x_v, y_v
+ * the sums of its Tx and Rx x and y coordinates. */
 typedef struct {
-  int32_t n_theta; /* angle bins, power of two in [8, 256] */
+  int32_t n_theta; /* azimuth bins, power of two in [8, 256] */
   int32_t guard;   /* CFAR guard cells each side along range */
   int32_t train;   /* CFAR training cells each side beyond the guard */
   int32_t k_max;   /* maximum points returned */
@@ -107,6 +111,9 @@ typedef struct {
   float floor_rel; /* absolute floor as a fraction of the map's maximum power */
   float beta;      /* sigmoid temperature in natural-log power units */
   float w_min;     /* minimum soft weight for a point to be kept */
+  int32_t n_elev;  /* elevation bins (0 reads as 1), power of two; R = n_elev * n_theta <= 256
+                      and R * V <= 4096 */
+  int32_t _pad;
 } sbr_cfar_cfg;
 
 typedef enum {
@@ -351,10 +358,10 @@ sbr_status sbr_synthesize_bwd(const sbr_paths* paths, const sbr_radar_cfg* radar
 /* Saved state of one point-cloud evaluation (needed by its adjoint) and its
  * scratch, carved from one region by sbr_pc_bind. */
 typedef struct {
-  int32_t n_virt, n_chirps, n_samples, n_theta, k_max, _pad;
+  int32_t n_virt, n_chirps, n_samples, n_theta, k_max, n_elev;
   float* spec;        /* [V*C*N_s*2] range+Doppler spectrum X */
-  float* power;       /* [n_theta*N_s] power map Pw */
-  int32_t* peak_cell; /* [k_max] linear cell a*N_s+k of each output point */
+  float* power;       /* [n_elev*n_theta*N_s] power map Pw, row e*n_theta+a */
+  int32_t* peak_cell; /* [k_max] linear cell rho*N_s+k of each output point */
   int32_t* n_points;  /* [1] number of points written (device) */
   int32_t* argmax;    /* [1] cell of max Pw */
   void* scratch;
@@ -365,26 +372,28 @@ sbr_status sbr_pc_bind(void* d_mem, size_t bytes, const sbr_radar_cfg* radar,
                        const sbr_cfar_cfg* cfar, sbr_pc_state* out);
 
 /* d_points [k_max][4] = (x, y, z, w) ordered by (w desc, cell asc); rows at
- * and beyond *n_points are zero.  The angle DFT runs on the tensor cores
- * (tcgen05, TF32 with a hi/lo operand split: ~1e-6 relative to FP32) when
- * n_theta <= 64, V <= 16 and N_s is a multiple of 64, on CUDA cores otherwise. */
+ * and beyond *n_points are zero.  Detection: 3x3x3 (elevation, azimuth, range)
+ * local maxima; each point is (r u, r w, r sqrt(1 - u^2 - w^2)) after a
+ * parabolic refine of ln Pw along each axis.  The angle DFT runs on the tensor
+ * cores (tcgen05, TF32 with a hi/lo operand split: ~1e-6 relative to FP32) when
+ * R <= 128, V <= 16 and N_s is a multiple of 128, on CUDA cores otherwise. */
 sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* radar,
                           const sbr_cfar_cfg* cfar, float* d_points, sbr_pc_state* state,
                           sbr_stream stream);
 
 /* Steps 1-4 of sbr_pointcloud only: range FFT, Doppler FFT, angle DFT and the
- * range-angle power map Pw [n_theta][N_s] = sum over Doppler bins of |Y|^2, left
+ * range-angle power map Pw [R][N_s] = sum over Doppler bins of |Y|^2, left
  * in state->power (and the spectrum in state->spec, for the adjoint); no
  * detection, no points.  This is the image T(y) of the spatial loss below. */
 sbr_status sbr_power_map(const float* d_cube, const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar,
                          sbr_pc_state* state, sbr_stream stream);
 
 /* Spatial multi-antenna loss (Section 3.4, Eq. 16):
- *   loss = (1/N) sum_i (T(y)_i - T(ybar)_i)^2,  N = n_theta x N_s,
+ *   loss = (1/N) sum_i (T(y)_i - T(ybar)_i)^2,  N = R x N_s,
  * with T(y) the power map Pw of the last sbr_power_map or sbr_pointcloud on
  * `state` (the paper names T only as a signal-processing map to a spatial
  * image; this library's image is the range-angle power map) and d_target
- * [n_theta][N_s] the target image T(ybar).  Writes *d_loss (device float) and,
+ * [R][N_s] the target image T(ybar).  Writes *d_loss (device float) and,
  * when d_gcube is not NULL, dloss/dcube [V][C][N_s] complex (overwritten)
  * through the adjoints of the power map, the angle DFT and the two FFTs.
  * Deterministic (fixed-order sums). */
@@ -393,8 +402,8 @@ sbr_status sbr_image_loss(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, 
 
 /* Synchronises the stream and reports the device-side status of the last
  * sbr_pointcloud on `state` (each call clears it on entry): SBR_ERR_TIMEOUT
- * when the tensor-core angle DFT (used for n_theta <= 64, at most 16 virtual
- * antennas and N_s a multiple of 64) gave up its bounded wait for its matrix
+ * when the tensor-core angle DFT (used for R <= 128, at most 16 virtual
+ * antennas and N_s a multiple of 128) gave up its bounded wait for its matrix
  * products, in which case the power map holds NaN. */
 sbr_status sbr_pc_check(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const sbr_pc_state* state,
                         sbr_stream stream);

@@ -42,7 +42,8 @@ class RayGrid(ctypes.Structure):
 
 class CfarCfg(ctypes.Structure):
     _fields_ = [("n_theta", c_i32), ("guard", c_i32), ("train", c_i32), ("k_max", c_i32),
-                ("alpha", c_f32), ("floor_rel", c_f32), ("beta", c_f32), ("w_min", c_f32)]
+                ("alpha", c_f32), ("floor_rel", c_f32), ("beta", c_f32), ("w_min", c_f32),
+                ("n_elev", c_i32), ("_pad", c_i32)]
 
 
 class Paths(ctypes.Structure):
@@ -68,7 +69,7 @@ class Materials(ctypes.Structure):
 
 class PcState(ctypes.Structure):
     _fields_ = [("n_virt", c_i32), ("n_chirps", c_i32), ("n_samples", c_i32), ("n_theta", c_i32),
-                ("k_max", c_i32), ("_pad", c_i32), ("spec", c_p), ("power", c_p), ("peak_cell", c_p),
+                ("k_max", c_i32), ("n_elev", c_i32), ("spec", c_p), ("power", c_p), ("peak_cell", c_p),
                 ("n_points", c_p), ("argmax", c_p), ("scratch", c_p)]
 
 

@@ -82,35 +82,47 @@ __global__ void k_fft_cols(float2* __restrict__ x, int C, int logc, int Ns, floa
   }
 }
 
-// x_v / lambda_c per virtual antenna, passed by value (no host-to-device copy,
-// so the entry points can be captured into CUDA graphs).
+// x_v / lambda_c and y_v / lambda_c per virtual antenna and the angle bins,
+// passed by value (no host-to-device copy, so the entry points can be captured
+// into CUDA graphs).  Angle row rho = e * A + a: azimuth cosine u_a = -1 + 2a/A,
+// elevation cosine w_e = (2e + 1 - E) / E (w = 0 with one elevation bin).
 struct Steer {
   float xl[SBR_MAX_VIRT];
+  float yl[SBR_MAX_VIRT];
+  int A, E;
 };
 
-// Steering matrix W[a][v] into shared memory.
-__device__ inline void load_w(float2* sw, const Steer& xl, int A, int V) {
-  for (int i = threadIdx.x; i < A * V; i += blockDim.x) {
-    const int a = i / V, v = i - a * V;
-    const float u = -1.f + 2.f * (float)a / (float)A;
+// Phase (in half-cycles, for sincospif) of antenna v in angle row rho.
+__device__ inline float steer_halfcycles(const Steer& st, int rho, int v) {
+  const int e = rho / st.A, a = rho - e * st.A;
+  const float u = -1.f + 2.f * (float)a / (float)st.A;
+  const float w = (float)(2 * e + 1 - st.E) / (float)st.E;
+  return 2.f * (st.xl[v] * u + st.yl[v] * w);
+}
+
+// Steering matrix W[rho][v] of the R = E * A angle rows into shared memory.
+__device__ inline void load_w(float2* sw, const Steer& xl, int R, int V) {
+  for (int i = threadIdx.x; i < R * V; i += blockDim.x) {
+    const int rho = i / V, v = i - rho * V;
     float sn, cs;
-    sincospif(2.f * xl.xl[v] * u, &sn, &cs);
+    sincospif(steer_halfcycles(xl, rho, v), &sn, &cs);
     sw[i] = make_float2(cs, sn);
   }
 }
 
 constexpr int kKT = 32;  // ranges per CTA in the angle kernels
 
-// Partial power map over one group of Doppler bins: part[g][a][k] = sum_{d in g} |Y|^2.
+// Partial power map over one group of Doppler bins: part[g][rho][k] = sum_{d in g} |Y|^2
+// for the R = 8 APT angle rows.
 template <int APT>
 __global__ void __launch_bounds__(256) k_angle_power(const float2* __restrict__ X,
                                                      const Steer xl, int V, int C,
                                                      int Ns, int dpg, float* __restrict__ part) {
   extern __shared__ float2 sm[];
-  constexpr int A = 8 * APT;
-  float2* sw = sm;                // [A][V]
-  float2* sx = sm + A * V;        // [V][kKT]
-  load_w(sw, xl, A, V);
+  constexpr int R = 8 * APT;
+  float2* sw = sm;                // [R][V]
+  float2* sx = sm + R * V;        // [V][kKT]
+  load_w(sw, xl, R, V);
   const int kk = threadIdx.x & (kKT - 1), ag = threadIdx.x >> 5;
   const int k0 = blockIdx.x * kKT, g = blockIdx.y;
   float acc[APT];
@@ -140,22 +152,23 @@ __global__ void __launch_bounds__(256) k_angle_power(const float2* __restrict__ 
     for (int i = 0; i < APT; ++i) acc[i] = fmaf(yr[i], yr[i], fmaf(yi[i], yi[i], acc[i]));
   }
 #pragma unroll
-  for (int i = 0; i < APT; ++i) part[((size_t)g * A + ag * APT + i) * Ns + k0 + kk] = acc[i];
+  for (int i = 0; i < APT; ++i) part[((size_t)g * R + ag * APT + i) * Ns + k0 + kk] = acc[i];
 }
 
 // ---- angle DFT on the tensor cores ------------------------------------------
 //
 // Per Doppler bin d the angle DFT of kTcM range bins is one real GEMM
 //   D[k][2a + part] = sum_j A[k][j] B[2a + part][j],   j = 2v + (0: Re, 1: Im)
-// with A = X^T (M = kTcM range bins, K = 2V) and B = the steering matrix as
-// N = 128 real rows: row 2a = (W_re, -W_im) and row 2a + 1 = (W_im, W_re) at
-// columns (2v, 2v + 1), so D[k][2a] = Re Y[a,d,k] and D[k][2a + 1] = Im Y[a,d,k].
+// with A = X^T (M = kTcM range bins, K = 2V) and B = the steering matrix of the
+// R <= NR angle rows (NR = 64 or 128) as N = 2 NR real rows: row 2a = (W_re, -W_im)
+// and row 2a + 1 = (W_im, W_re) at columns (2v, 2v + 1), so D[k][2a] = Re Y[a,d,k]
+// and D[k][2a + 1] = Im Y[a,d,k].
 // It runs as tcgen05.mma kind::tf32 from shared memory into TMEM.  Each
 // operand is split as hi = tf32(x), lo = x - hi, and three products
 // A_lo B_hi + A_hi B_lo + A_hi B_hi (small terms first) keep ~21 bits; the
 // dropped lo.lo term is ~2^-22 relative, so Y matches the FP32 CUDA-core
 // contraction to ~1e-6.  A CTA takes kTcM range bins of kTcDG Doppler bins, one
-// kTcM x 128 FP32 accumulator per Doppler bin in TMEM; thread t of the CTA owns
+// kTcM x 2 NR FP32 accumulator per Doppler bin in TMEM; thread t of the CTA owns
 // TMEM lane t (range bin k0 + t) and every angle, so |Y|^2 = D[2a]^2 + D[2a+1]^2
 // needs no data exchange, and its sum over the CTA's Doppler bins stays in
 // registers until one coalesced store per angle.
@@ -163,19 +176,23 @@ __global__ void __launch_bounds__(256) k_angle_power(const float2* __restrict__ 
 #define SBR_ANGLE_DG 2
 #endif
 constexpr int kTcM = 128;                      // range bins per CTA (MMA M: one TMEM lane each)
-constexpr int kTcN = 128;                      // 64 angles x (Re, Im) (MMA N)
 constexpr int kTcDG = SBR_ANGLE_DG;            // Doppler bins per CTA
-constexpr int kTcCols = kTcN * kTcDG;          // TMEM columns: a power of two >= 32
 constexpr int kTcThreads = 128;                // four warps: the four TMEM lane quadrants
 constexpr int kTcK = 32;                       // K capacity: up to 16 antennas
 constexpr uint32_t kTcTile = 128 * kTcK * 4;   // bytes of one 128-row operand (hi or lo)
 constexpr uint32_t kTcLbo = 128;               // K-adjacent core matrices
 constexpr uint32_t kTcSbo = (kTcK / 4) * 128;  // M/N-adjacent core matrices (8-row groups)
-constexpr size_t kTcSmem = 2 * (size_t)kTcTile * (1 + kTcDG) + 64;
 constexpr uint64_t kTcWaitNs = 200000000ull;   // bounded wait for the MMAs: 0.2 s
-static_assert(kTcCols >= 32 && kTcCols <= 512 && (kTcCols & (kTcCols - 1)) == 0, "TMEM columns");
+// NR angle rows (64 or 128): MMA N = 2 NR, TMEM columns 2 NR per Doppler bin, the
+// steering operand 2 NR rows; shared memory = steering + X^T per Doppler bin (hi, lo)
+template <int NR>
+constexpr int tc_cols() { return 2 * NR * kTcDG; }
+template <int NR>
+constexpr size_t tc_smem() { return 2 * (size_t)kTcTile * (2 * NR / 128 + kTcDG) + 64; }
+static_assert(tc_cols<64>() >= 32 && tc_cols<128>() <= 512, "TMEM columns");
 
-inline bool angle_tc_ok(int A, int V, int Ns) { return A <= 64 && V <= 16 && Ns % kTcM == 0; }
+inline int angle_tc_rows(int R) { return R <= 64 ? 64 : 128; }
+inline bool angle_tc_ok(int R, int V, int Ns) { return R <= 128 && V <= 16 && Ns % kTcM == 0; }
 
 // Byte offset of the 16-byte row chunk (row, k .. k + 3), k a multiple of 4, in
 // the no-swizzle K-major layout of a K = 32 operand: 8-row x 4-element core
@@ -192,23 +209,27 @@ __device__ inline void tc_put4(unsigned char* hi, unsigned char* lo, uint32_t of
   *reinterpret_cast<float4*>(lo + off) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
 }
 
-// part[g][a][k] = sum over the Doppler bins of group g of |Y[a,d,k]|^2; on a
-// timed-out wait the CTA writes NaN and sets bit 0 of *err.
-__global__ void __launch_bounds__(kTcThreads) k_angle_tc(const float2* __restrict__ X, const Steer xl, int A,
+// part[g][rho][k] = sum over the Doppler bins of group g of |Y[rho,d,k]|^2 for the R
+// angle rows (R <= NR); on a timed-out wait the CTA writes NaN and sets bit 0 of *err.
+template <int NR>
+__global__ void __launch_bounds__(kTcThreads) k_angle_tc(const float2* __restrict__ X, const Steer xl, int R,
                                                          int V, int C, int Ns, float* __restrict__ part,
                                                          int* __restrict__ err) {
+  constexpr int kN = 2 * NR;                         // MMA N
+  constexpr int kCols = tc_cols<NR>();
+  constexpr uint32_t kTileW = (uint32_t)kN * kTcK * 4;  // steering operand bytes (hi or lo)
   extern __shared__ __align__(1024) unsigned char tsm[];
   unsigned char* sw_hi = tsm;                  // B: steering rows
-  unsigned char* sw_lo = tsm + kTcTile;
-  unsigned char* sx_hi = tsm + 2 * kTcTile;    // A: X^T per Doppler bin, hi then lo
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + 2 * (size_t)kTcTile * (1 + kTcDG));
+  unsigned char* sw_lo = tsm + kTileW;
+  unsigned char* sx_hi = tsm + 2 * kTileW;     // A: X^T per Doppler bin, hi then lo
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sx_hi + 2 * (size_t)kTcTile * kTcDG);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int k0 = blockIdx.x * kTcM, g = blockIdx.y, d0 = g * kTcDG;
   const int nd = min(kTcDG, C - d0);  // Doppler bins of this CTA (>= 1)
   const int ks = (2 * V + 7) / 8;      // MMA K steps of 8 used
   if (warp == 0) {
-    tc::tmem_alloc(tslot, kTcCols);
+    tc::tmem_alloc(tslot, kCols);
     tc::tmem_relinquish();
   }
   if (tid == 0) tc::mbar_init(mbar, 1);
@@ -221,14 +242,13 @@ __global__ void __launch_bounds__(kTcThreads) k_angle_tc(const float2* __restric
 #pragma unroll
     for (int v = 0; v < kTcK / 2; ++v)
       xv[dd][v] = (dd < nd && v < V) ? X[((size_t)v * C + d0 + dd) * Ns + k0 + tid] : make_float2(0.f, 0.f);
-  // B: row pair (2a, 2a + 1) of angle a, antenna pair j: one 16-byte chunk per row
-  for (int i = tid; i < 64 * (kTcK / 4); i += kTcThreads) {
+  // B: row pair (2a, 2a + 1) of angle row a, antenna pair j: one 16-byte chunk per row
+  for (int i = tid; i < NR * (kTcK / 4); i += kTcThreads) {
     const int a = i >> 3, j = i & 7;
     float c0 = 0.f, s0 = 0.f, c1 = 0.f, s1 = 0.f;
-    if (a < A) {
-      const float u = -1.f + 2.f * (float)a / (float)A;
-      if (2 * j < V) sincospif(2.f * xl.xl[2 * j] * u, &s0, &c0);
-      if (2 * j + 1 < V) sincospif(2.f * xl.xl[2 * j + 1] * u, &s1, &c1);
+    if (a < R) {
+      if (2 * j < V) sincospif(steer_halfcycles(xl, a, 2 * j), &s0, &c0);
+      if (2 * j + 1 < V) sincospif(steer_halfcycles(xl, a, 2 * j + 1), &s1, &c1);
     }
     tc_put4(sw_hi, sw_lo, tc_off(2 * a, 4 * j), make_float4(c0, -s0, c1, -s1));
     tc_put4(sw_hi, sw_lo, tc_off(2 * a + 1, 4 * j), make_float4(s0, c0, s1, c1));
@@ -247,7 +267,7 @@ __global__ void __launch_bounds__(kTcThreads) k_angle_tc(const float2* __restric
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
   if (tid == 0) {
-    constexpr uint32_t idesc = tc::idesc_tf32(kTcM, kTcN);
+    constexpr uint32_t idesc = tc::idesc_tf32(kTcM, kN);
     const uint32_t wh = tc::smem_u32(sw_hi), wl = tc::smem_u32(sw_lo);
     for (int dd = 0; dd < nd; ++dd) {
       const uint32_t xh = tc::smem_u32(sx_hi + 2 * (size_t)kTcTile * dd), xlo = xh + kTcTile;
@@ -255,7 +275,7 @@ __global__ void __launch_bounds__(kTcThreads) k_angle_tc(const float2* __restric
       for (int pass = 0; pass < 3; ++pass) {  // lo.hi, hi.lo, hi.hi
         const uint32_t pa = pass == 0 ? xlo : xh, pb = pass == 1 ? wl : wh;
         for (int j = 0; j < ks; ++j) {  // K step j covers columns 8j .. 8j + 7: two core matrices
-          tc::mma_tf32(tbase + (uint32_t)(dd * kTcN), tc::smem_desc(pa + 256u * j, kTcLbo, kTcSbo),
+          tc::mma_tf32(tbase + (uint32_t)(dd * kN), tc::smem_desc(pa + 256u * j, kTcLbo, kTcSbo),
                        tc::smem_desc(pb + 256u * j, kTcLbo, kTcSbo), idesc, acc);
           acc = true;
         }
@@ -265,35 +285,35 @@ __global__ void __launch_bounds__(kTcThreads) k_angle_tc(const float2* __restric
   }
   const bool ok = __all_sync(0xffffffffu, tc::mbar_wait_bounded(mbar, 0, kTcWaitNs));
   tc::fence_after_sync();
-  float acc[64];
+  float acc[NR];
 #pragma unroll
-  for (int a = 0; a < 64; ++a) acc[a] = 0.f;
+  for (int a = 0; a < NR; ++a) acc[a] = 0.f;
   if (ok) {
     const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
     for (int dd = 0; dd < nd; ++dd) {
 #pragma unroll
-      for (int h = 0; h < kTcN / 32; ++h) {
+      for (int h = 0; h < kN / 32; ++h) {
         float y[32];
-        tc::tmem_ld32(lane_base + (uint32_t)(dd * kTcN + h * 32), y);
+        tc::tmem_ld32(lane_base + (uint32_t)(dd * kN + h * 32), y);
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[h * 16 + j] = fmaf(y[2 * j], y[2 * j], fmaf(y[2 * j + 1], y[2 * j + 1], acc[h * 16 + j]));
       }
     }
   } else {
 #pragma unroll
-    for (int a = 0; a < 64; ++a) acc[a] = __int_as_float(0x7fc00000);
+    for (int a = 0; a < NR; ++a) acc[a] = __int_as_float(0x7fc00000);
     if ((tid & 31) == 0) atomicOr(err, 1);
     if (tid == 0) tc::mbar_wait_bounded(mbar, 0, kTcWaitNs);  // the MMAs' own completion, once more
   }
-  float* out = part + (size_t)g * A * Ns + k0 + tid;
+  float* out = part + (size_t)g * R * Ns + k0 + tid;
 #pragma unroll
-  for (int a = 0; a < 64; ++a)
-    if (a < A) out[(size_t)a * Ns] = acc[a];
+  for (int a = 0; a < NR; ++a)
+    if (a < R) out[(size_t)a * Ns] = acc[a];
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tbase, kTcCols);
+    tc::tmem_dealloc(tbase, kCols);
   }
 }
 
@@ -324,6 +344,7 @@ __device__ inline int amax_cell(const unsigned long long* key) {
 struct CfarArg {
   int A, Ns, guard, train;
   float alpha, floor_rel, beta, w_min;
+  int E;  // elevation bins: the map has E * A angle rows (row e * A + a) of Ns range cells
 };
 
 __device__ inline float lnp(float p) { return logf(fmaxf(p, 1e-30f)); }
@@ -356,28 +377,30 @@ __device__ inline float soft_w(const float* __restrict__ Pw, const CfarArg& c, i
   return 1.f / (1.f + expf(-z));
 }
 
-// Detection test of cell i: a 3x3 local maximum above the floor (equal values:
-// the lower cell wins) whose soft CFAR weight reaches w_min; returns the sort key
-// (w descending), or 0xffffffff.
+// Detection test of cell i: a 3x3x3 (elevation, azimuth, range) local maximum
+// above the floor (equal values: the lower cell wins) whose soft CFAR weight
+// reaches w_min; returns the sort key (w descending), or 0xffffffff.
 __device__ inline uint32_t detect_key(const float* __restrict__ Pw, const CfarArg& c, int i, float floor_v) {
-  const int a = i / c.Ns, k = i - a * c.Ns;
+  const int rho = i / c.Ns, k = i - rho * c.Ns;
+  const int e = rho / c.A, a = rho - e * c.A;
   const float p = Pw[i];
   bool peak = p > floor_v;
-  for (int da = -1; da <= 1 && peak; ++da)
-    for (int dk = -1; dk <= 1; ++dk) {
-      if (da == 0 && dk == 0) continue;
-      const int aa = a + da, kk = k + dk;
-      if (aa < 0 || aa >= c.A || kk < 0 || kk >= c.Ns) continue;
-      const float q = Pw[(size_t)aa * c.Ns + kk];
-      const bool earlier = da < 0 || (da == 0 && dk < 0);
-      if (earlier ? !(p > q) : !(p >= q)) {
-        peak = false;
-        break;
+  for (int de = -1; de <= 1 && peak; ++de)
+    for (int da = -1; da <= 1 && peak; ++da)
+      for (int dk = -1; dk <= 1; ++dk) {
+        if (de == 0 && da == 0 && dk == 0) continue;
+        const int ee = e + de, aa = a + da, kk = k + dk;
+        if (ee < 0 || ee >= c.E || aa < 0 || aa >= c.A || kk < 0 || kk >= c.Ns) continue;
+        const int j = ((ee * c.A) + aa) * c.Ns + kk;
+        const float q = Pw[j];
+        if (j < i ? !(p > q) : !(p >= q)) {
+          peak = false;
+          break;
+        }
       }
-    }
   if (!peak) return 0xffffffffu;
   int cnt;
-  const float w = soft_w(Pw, c, a, k, floor_v, nullptr, nullptr, &cnt);
+  const float w = soft_w(Pw, c, rho, k, floor_v, nullptr, nullptr, &cnt);
   return w >= c.w_min ? 0xffffffffu - __float_as_uint(w) : 0xffffffffu;
 }
 
@@ -386,7 +409,7 @@ __global__ void k_detect(const float* __restrict__ Pw, CfarArg c, const unsigned
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int am = amax_cell(amax_key);
   if (i == 0) *amax = am;
-  if (i >= c.A * c.Ns) return;
+  if (i >= c.E * c.A * c.Ns) return;
   const uint32_t kk = detect_key(Pw, c, i, c.floor_rel * Pw[am]);
   if (flag) flag[i] = kk != 0xffffffffu ? 1 : 0;
   key[i] = kk;
@@ -449,21 +472,26 @@ struct PointArg {
 };
 
 // Point i of the cloud from detected cell `cell`: parabolic refine of ln Pw per
-// axis, then (r u, 0, r sqrt(1 - u^2)) with its soft weight.
+// axis (range, azimuth, elevation), then (r u, r v, r sqrt(1 - u^2 - v^2)) with
+// its soft weight (v = 0 with one elevation bin).
 __device__ inline float4 emit_point(const float* __restrict__ Pw, const PointArg& pa, float floor_v, int cell) {
   const CfarArg& c = pa.c;
-  const int a = cell / c.Ns, k = cell - a * c.Ns;
+  const int rho = cell / c.Ns, k = cell - rho * c.Ns;
+  const int e = rho / c.A, a = rho - e * c.A;
   int cnt;
-  const float w = soft_w(Pw, c, a, k, floor_v, nullptr, nullptr, &cnt);
-  const float* row = Pw + (size_t)a * c.Ns;
+  const float w = soft_w(Pw, c, rho, k, floor_v, nullptr, nullptr, &cnt);
+  const float* row = Pw + (size_t)rho * c.Ns;
   const float l0 = lnp(row[k]);
-  float t0, t1, t2, dk = 0.f, da = 0.f;
+  float t0, t1, t2, dk = 0.f, da = 0.f, de = 0.f;
   if (k > 0 && k < c.Ns - 1) dk = refine(lnp(row[k - 1]), l0, lnp(row[k + 1]), &t0, &t1, &t2);
   if (a > 0 && a < c.A - 1)
-    da = refine(lnp(Pw[(size_t)(a - 1) * c.Ns + k]), l0, lnp(Pw[(size_t)(a + 1) * c.Ns + k]), &t0, &t1, &t2);
+    da = refine(lnp(Pw[(size_t)(rho - 1) * c.Ns + k]), l0, lnp(Pw[(size_t)(rho + 1) * c.Ns + k]), &t0, &t1, &t2);
+  if (e > 0 && e < c.E - 1)
+    de = refine(lnp(Pw[(size_t)(rho - c.A) * c.Ns + k]), l0, lnp(Pw[(size_t)(rho + c.A) * c.Ns + k]), &t0, &t1, &t2);
   const float r = ((float)k + dk) * pa.range_bin;
   const float u = fminf(fmaxf(-1.f + 2.f * ((float)a + da) / (float)c.A, -1.f), 1.f);
-  return make_float4(r * u, 0.f, r * sqrtf(fmaxf(1.f - u * u, 0.f)), w);
+  const float v = (2.f * ((float)e + de) + 1.f - (float)c.E) / (float)c.E;
+  return make_float4(r * u, r * v, r * sqrtf(fmaxf(1.f - u * u - v * v, 0.f)), w);
 }
 
 __global__ void k_points(const float* __restrict__ Pw, PointArg pa, const int32_t* __restrict__ amax,
@@ -498,7 +526,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const float* __restrict_
   extern __shared__ __align__(16) uint32_t sel_sm[];  // cta::kSortSmemWords
   __shared__ uint32_t wt[32];
   const CfarArg& c = pa.c;
-  const int cells = c.A * c.Ns, t = threadIdx.x;
+  const int cells = c.E * c.A * c.Ns, t = threadIdx.x;
   const float floor_v = c.floor_rel * Pw[amax_cell(amax_key)];
   // rounds of 4 x kSelThreads cells (cells is a multiple of 8): thread t loads
   // cells 4t .. 4t + 3 of the round as one coalesced 16-B load, up to four
@@ -579,13 +607,14 @@ __device__ void point_adjoint(int i, const float* __restrict__ Pw, const PointAr
                               const DpwScatter<kPass>& sc) {
   const CfarArg& c = pa.c;
   const int cell = cells[i];
-  const int a = cell / c.Ns, k = cell - a * c.Ns;
+  const int rho = cell / c.Ns, k = cell - rho * c.Ns;
+  const int e = rho / c.A, a = rho - e * c.A;
   const int am = *amax;
   const float floor_v = c.floor_rel * Pw[am];
   const float4 g = gpts[i];
   float z, N;
   int cnt;
-  const float w = soft_w(Pw, c, a, k, floor_v, &z, &N, &cnt);
+  const float w = soft_w(Pw, c, rho, k, floor_v, &z, &N, &cnt);
   // soft weight: w = sigmoid(z), z = (l0 - ln(alpha N + F)) / beta
   const float gz = g.w * w * (1.f - w) / c.beta;
   const float den = c.alpha * N + floor_v;
@@ -596,34 +625,46 @@ __device__ void point_adjoint(int i, const float* __restrict__ Pw, const PointAr
   if (cnt > 0) {
     int lo0, lo1, hi0, hi1;
     noise_cells(c, k, lo0, lo1, hi0, hi1);
-    const float e = dN / (float)cnt;
-    for (int j = lo0; j < lo1; ++j) sc.add((size_t)a * c.Ns + j, e);
-    for (int j = hi0; j < hi1; ++j) sc.add((size_t)a * c.Ns + j, e);
+    const float en = dN / (float)cnt;
+    for (int j = lo0; j < lo1; ++j) sc.add((size_t)rho * c.Ns + j, en);
+    for (int j = hi0; j < hi1; ++j) sc.add((size_t)rho * c.Ns + j, en);
   }
-  // position: r = (k + dk) bin, u = -1 + 2 (a + da) / A, p = (r u, 0, r sqrt(1 - u^2))
-  const float* row = Pw + (size_t)a * c.Ns;
+  // position: r = (k + dk) bin, u = -1 + 2 (a + da) / A, v = (2 (e + de) + 1 - E) / E,
+  // p = (r u, r v, r sqrt(1 - u^2 - v^2))
+  const float* row = Pw + (size_t)rho * c.Ns;
   const float l0 = lnp(row[k]);
-  float rm = 0.f, r0 = 0.f, rp = 0.f, am_ = 0.f, a0 = 0.f, ap = 0.f, dk = 0.f, da = 0.f;
-  if (k > 0 && k < c.Ns - 1) dk = refine(lnp(row[k - 1]), l0, lnp(row[k + 1]), &rm, &r0, &rp);
-  if (a > 0 && a < c.A - 1)
-    da = refine(lnp(Pw[(size_t)(a - 1) * c.Ns + k]), l0, lnp(Pw[(size_t)(a + 1) * c.Ns + k]), &am_, &a0, &ap);
+  float rm = 0.f, r0 = 0.f, rp = 0.f, am_ = 0.f, a0 = 0.f, ap = 0.f, em = 0.f, e0 = 0.f, ep = 0.f;
+  float dk = 0.f, da = 0.f, de = 0.f;
+  const bool rk = k > 0 && k < c.Ns - 1, ra = a > 0 && a < c.A - 1, re = e > 0 && e < c.E - 1;
+  const size_t up = (size_t)c.A * c.Ns;  // one elevation bin in the map
+  if (rk) dk = refine(lnp(row[k - 1]), l0, lnp(row[k + 1]), &rm, &r0, &rp);
+  if (ra) da = refine(lnp(Pw[(size_t)cell - c.Ns]), l0, lnp(Pw[(size_t)cell + c.Ns]), &am_, &a0, &ap);
+  if (re) de = refine(lnp(Pw[(size_t)cell - up]), l0, lnp(Pw[(size_t)cell + up]), &em, &e0, &ep);
   const float r = ((float)k + dk) * pa.range_bin;
   const float ur = -1.f + 2.f * ((float)a + da) / (float)c.A;
   const float u = fminf(fmaxf(ur, -1.f), 1.f);
-  const float sq = sqrtf(fmaxf(1.f - u * u, 0.f));
-  const float dr = g.x * u + g.z * sq;
-  const float du = (ur > -1.f && ur < 1.f && sq > 0.f) ? (g.x * r - g.z * r * u / sq) : 0.f;
+  const float v = (2.f * ((float)e + de) + 1.f - (float)c.E) / (float)c.E;
+  const float sq = sqrtf(fmaxf(1.f - u * u - v * v, 0.f));
+  const float dr = g.x * u + g.y * v + g.z * sq;
+  // the clamps of u and of sqrt's argument pass no gradient
+  const float du = (ur > -1.f && ur < 1.f) ? (sq > 0.f ? g.x * r - g.z * r * u / sq : g.x * r) : 0.f;
+  const float dv = sq > 0.f ? g.y * r - g.z * r * v / sq : g.y * r;
   const float ddk = dr * pa.range_bin;
   const float dda = du * 2.f / (float)c.A;
-  dl0 += ddk * r0 + dda * a0;
+  const float dde = dv * 2.f / (float)c.E;
+  dl0 += ddk * r0 + dda * a0 + dde * e0;
   add_dl(sc, Pw, (size_t)cell, dl0);
-  if (k > 0 && k < c.Ns - 1) {
+  if (rk) {
     add_dl(sc, Pw, (size_t)cell - 1, ddk * rm);
     add_dl(sc, Pw, (size_t)cell + 1, ddk * rp);
   }
-  if (a > 0 && a < c.A - 1) {
+  if (ra) {
     add_dl(sc, Pw, (size_t)cell - c.Ns, dda * am_);
     add_dl(sc, Pw, (size_t)cell + c.Ns, dda * ap);
+  }
+  if (re) {
+    add_dl(sc, Pw, (size_t)cell - up, dde * em);
+    add_dl(sc, Pw, (size_t)cell + up, dde * ep);
   }
 }
 
@@ -644,18 +685,19 @@ __global__ void k_fix_finish(FixScatter fs, int n, float* __restrict__ out) {
   if (i < n) out[i] = fix_get(fs.acc[i], fix_exp(*fs.max_bits, fs.log2n));
 }
 
-// dX[v,d,k] = sum_a conj(W[a,v]) 2 Y[a,d,k] dPw[a,k], Y recomputed from X.
+// dX[v,d,k] = sum_rho conj(W[rho,v]) 2 Y[rho,d,k] dPw[rho,k] over the R = 8 APT angle
+// rows, Y recomputed from X.
 template <int APT>
 __global__ void __launch_bounds__(256) k_angle_bwd(const float2* __restrict__ X,
                                                    const Steer xl,
                                                    const float* __restrict__ dPw, int V, int C,
                                                    int Ns, float2* __restrict__ dX) {
   extern __shared__ float2 sm[];
-  constexpr int A = 8 * APT;
-  float2* sw = sm;               // [A][V]
-  float2* sx = sw + A * V;       // [V][kKT]
-  float2* sg = sx + V * kKT;     // [A][kKT]
-  load_w(sw, xl, A, V);
+  constexpr int R = 8 * APT;
+  float2* sw = sm;               // [R][V]
+  float2* sx = sw + R * V;       // [V][kKT]
+  float2* sg = sx + V * kKT;     // [R][kKT]
+  load_w(sw, xl, R, V);
   const int kk = threadIdx.x & (kKT - 1), ag = threadIdx.x >> 5;
   const int k0 = blockIdx.x * kKT, d = blockIdx.y;
   for (int i = threadIdx.x; i < V * kKT; i += blockDim.x) {
@@ -679,7 +721,7 @@ __global__ void __launch_bounds__(256) k_angle_bwd(const float2* __restrict__ X,
   for (int i = threadIdx.x; i < V * kKT; i += blockDim.x) {
     const int v = i / kKT, q = i - v * kKT;
     float gr = 0.f, gi = 0.f;
-    for (int a = 0; a < A; ++a) {
+    for (int a = 0; a < R; ++a) {
       const float2 w = sw[a * V + v], g = sg[a * kKT + q];  // conj(w) * g
       gr = fmaf(w.x, g.x, fmaf(w.y, g.y, gr));
       gi = fmaf(w.x, g.y, fmaf(-w.y, g.x, gi));
@@ -737,16 +779,21 @@ cudaError_t angle_tc_attr() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 64 && ((done.load() >> dev) & 1u)) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_angle_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  e = cudaFuncSetAttribute(k_angle_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<64>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_angle_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<128>());
   if (e == cudaSuccess && dev < 64) done.fetch_or(1ull << dev);
   return e;
 }
 
+inline int n_elev(const sbr_cfar_cfg* f) { return f->n_elev > 0 ? f->n_elev : 1; }
+inline int angle_rows(const sbr_cfar_cfg* f) { return n_elev(f) * f->n_theta; }
+
 size_t pc_layout(Layout* L, void* mem, const sbr_radar_cfg* r, const sbr_cfar_cfg* f) {
   Carver c(mem);
-  const int V = r->n_tx * r->n_rx, C = r->n_chirps, Ns = r->n_samples, A = f->n_theta;
-  const int64_t cells = (int64_t)A * Ns;
-  L->groups = angle_tc_ok(A, V, Ns) ? (C + kTcDG - 1) / kTcDG : dgroups(C);
+  const int V = r->n_tx * r->n_rx, C = r->n_chirps, Ns = r->n_samples, R = angle_rows(f);
+  const int64_t cells = (int64_t)R * Ns;
+  L->groups = angle_tc_ok(R, V, Ns) ? (C + kTcDG - 1) / kTcDG : dgroups(C);
   L->spec = c.take<float2>((size_t)V * C * Ns);
   L->power = c.take<float>(cells);
   L->peak_cell = c.take<int32_t>(f->k_max > 0 ? f->k_max : 1);
@@ -775,27 +822,39 @@ sbr_status check_cfar(const sbr_cfar_cfg* f, const sbr_radar_cfg* r, const char*
   const int V = r->n_tx * r->n_rx;
   SBR_ARG(f->n_theta >= 8 && f->n_theta <= 256 && (f->n_theta & (f->n_theta - 1)) == 0,
           "%s: n_theta=%d must be a power of two in [8, 256]", who, f->n_theta);
-  SBR_ARG(f->n_theta * V <= 4096, "%s: n_theta * V = %d above 4096", who, f->n_theta * V);
+  SBR_ARG(f->n_elev >= 0 && f->n_elev <= 256 && (f->n_elev & (f->n_elev - 1)) == 0,
+          "%s: n_elev=%d must be 0 or a power of two", who, f->n_elev);
+  SBR_ARG(angle_rows(f) <= 256, "%s: n_elev * n_theta = %d above 256", who, angle_rows(f));
+  SBR_ARG(angle_rows(f) * V <= 4096, "%s: n_elev * n_theta * V = %d above 4096", who, angle_rows(f) * V);
   SBR_ARG(f->guard >= 0 && f->train >= 0 && f->guard + f->train < 4096, "%s: bad guard/train", who);
   SBR_ARG(f->k_max >= 1 && f->k_max <= (1 << 20), "%s: k_max=%d outside [1, 2^20]", who, f->k_max);
   SBR_ARG(f->alpha > 0.f && f->beta > 0.f && f->floor_rel >= 0.f, "%s: alpha, beta > 0 needed", who);
   return SBR_OK;
 }
 
-// x_v / lambda_c per virtual antenna, uploaded into the state's small table.
-Steer steering_table(const sbr_radar_cfg* r) {
+// x_v / lambda_c and y_v / lambda_c per virtual antenna and the angle bins.
+Steer steering_table(const sbr_radar_cfg* r, const sbr_cfar_cfg* f) {
   Steer s{};
   const double lam = kC / (r->f0 + 0.5 * r->bandwidth);
   for (int t = 0; t < r->n_tx; ++t)
-    for (int q = 0; q < r->n_rx; ++q) s.xl[t * r->n_rx + q] = (float)((r->tx[t][0] + r->rx[q][0]) / lam);
+    for (int q = 0; q < r->n_rx; ++q) {
+      s.xl[t * r->n_rx + q] = (float)((r->tx[t][0] + r->rx[q][0]) / lam);
+      s.yl[t * r->n_rx + q] = (float)((r->tx[t][1] + r->rx[q][1]) / lam);
+    }
+  s.A = f->n_theta;
+  s.E = n_elev(f);
   return s;
+}
+
+inline CfarArg cfar_arg(const sbr_radar_cfg* r, const sbr_cfar_cfg* f) {
+  return CfarArg{f->n_theta, r->n_samples, f->guard, f->train, f->alpha, f->floor_rel, f->beta, f->w_min, n_elev(f)};
 }
 
 template <int APT>
 void launch_angle_power(const float2* X, const Steer& xl, int V, int C, int Ns, int groups, float* part,
                         cudaStream_t st) {
-  const int A = 8 * APT;
-  const size_t sm = sizeof(float2) * ((size_t)A * V + (size_t)V * kKT);
+  const int R = 8 * APT;
+  const size_t sm = sizeof(float2) * ((size_t)R * V + (size_t)V * kKT);
   dim3 grid(Ns / kKT, groups);
   ::sbr::note_launch();
   k_angle_power<APT><<<grid, 256, sm, st>>>(X, xl, V, C, Ns, (C + groups - 1) / groups, part);
@@ -804,8 +863,8 @@ void launch_angle_power(const float2* X, const Steer& xl, int V, int C, int Ns, 
 template <int APT>
 void launch_angle_bwd(const float2* X, const Steer& xl, const float* dpw, int V, int C, int Ns, float2* dX,
                       cudaStream_t st) {
-  const int A = 8 * APT;
-  const size_t sm = sizeof(float2) * ((size_t)A * V + (size_t)V * kKT + (size_t)A * kKT);
+  const int R = 8 * APT;
+  const size_t sm = sizeof(float2) * ((size_t)R * V + (size_t)V * kKT + (size_t)R * kKT);
   dim3 grid(Ns / kKT, C);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_angle_bwd<APT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ::sbr::note_launch();
@@ -868,6 +927,7 @@ extern "C" sbr_status sbr_pc_bind(void* d_mem, size_t bytes, const sbr_radar_cfg
   out->n_samples = radar->n_samples;
   out->n_theta = cfar->n_theta;
   out->k_max = cfar->k_max;
+  out->n_elev = n_elev(cfar);
   out->spec = reinterpret_cast<float*>(L.spec);
   out->power = L.power;
   out->peak_cell = L.peak_cell;
@@ -882,7 +942,7 @@ sbr_status state_layout(const sbr_pc_state* s, const sbr_radar_cfg* r, const sbr
                         const char* who) {
   SBR_ARG(s && s->scratch, "%s: state is NULL or unbound", who);
   SBR_ARG(s->n_virt == r->n_tx * r->n_rx && s->n_chirps == r->n_chirps && s->n_samples == r->n_samples &&
-              s->n_theta == f->n_theta && s->k_max == f->k_max,
+              s->n_theta == f->n_theta && s->k_max == f->k_max && s->n_elev == n_elev(f),
           "%s: state bound for another configuration", who);
   pc_layout(L, s->scratch, r, f);
   return SBR_OK;
@@ -894,26 +954,30 @@ namespace {
 // Steps 1-4 of T: range FFT, Doppler FFT, angle DFT, power map Pw (and its argmax key).
 sbr_status power_map_impl(const float* d_cube, const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const Layout& L,
                           cudaStream_t st) {
-  const int V = radar->n_tx * radar->n_rx, C = radar->n_chirps, Ns = radar->n_samples, A = cfar->n_theta;
-  const int cells = A * Ns;
-  const Steer xl = steering_table(radar);
+  const int V = radar->n_tx * radar->n_rx, C = radar->n_chirps, Ns = radar->n_samples, R = angle_rows(cfar);
+  const int cells = R * Ns;
+  const Steer xl = steering_table(radar, cfar);
   // 1-2: range FFT over samples, Doppler FFT over chirps
   SBR_CUDA(fft_rows(reinterpret_cast<const float2*>(d_cube), L.spec, V * C, Ns, -1.f, st));
   SBR_CUDA(fft_cols(L.spec, V, C, Ns, -1.f, st));
   // 3-4: angle DFT and power map (partials per Doppler group, fixed-order sum)
   SBR_CUDA(cudaMemsetAsync(L.amax_key, 0, 2 * sizeof(unsigned long long), st));
-  if (angle_tc_ok(A, V, Ns)) {
+  if (angle_tc_ok(R, V, Ns)) {
     SBR_CUDA(angle_tc_attr());
     ::sbr::note_launch();
-    k_angle_tc<<<dim3(Ns / kTcM, L.groups), kTcThreads, kTcSmem, st>>>(L.spec, xl, A, V, C, Ns, L.part, L.err);
-  } else switch (A / 8) {
+    const dim3 grid(Ns / kTcM, L.groups);
+    if (angle_tc_rows(R) == 64)
+      k_angle_tc<64><<<grid, kTcThreads, tc_smem<64>(), st>>>(L.spec, xl, R, V, C, Ns, L.part, L.err);
+    else
+      k_angle_tc<128><<<grid, kTcThreads, tc_smem<128>(), st>>>(L.spec, xl, R, V, C, Ns, L.part, L.err);
+  } else switch (R / 8) {
     case 1: launch_angle_power<1>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
     case 2: launch_angle_power<2>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
     case 4: launch_angle_power<4>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
     case 8: launch_angle_power<8>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
     case 16: launch_angle_power<16>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
     case 32: launch_angle_power<32>(L.spec, xl, V, C, Ns, L.groups, L.part, st); break;
-    default: set_error("sbr_pointcloud: n_theta=%d unsupported", A); return SBR_ERR_UNSUPPORTED;
+    default: set_error("sbr_pointcloud: %d angle rows unsupported", R); return SBR_ERR_UNSUPPORTED;
   }
   SBR_CUDA(cudaGetLastError());
   ::sbr::note_launch();
@@ -949,12 +1013,12 @@ extern "C" sbr_status sbr_pointcloud(const float* d_cube, const sbr_radar_cfg* r
   rs = state_layout(state, radar, cfar, &L, "sbr_pointcloud");
   if (rs != SBR_OK) return rs;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int A = cfar->n_theta, Ns = radar->n_samples;
-  const int cells = A * Ns;
+  const int Ns = radar->n_samples;
+  const int cells = angle_rows(cfar) * Ns;
   rs = power_map_impl(d_cube, radar, cfar, L, st);
   if (rs != SBR_OK) return rs;
   // 5-9: soft CFAR, peaks, compaction in cell order, stable sort by weight, points
-  CfarArg ca{A, Ns, cfar->guard, cfar->train, cfar->alpha, cfar->floor_rel, cfar->beta, cfar->w_min};
+  const CfarArg ca = cfar_arg(radar, cfar);
   PointArg pa{ca, cfar->k_max, (float)(kC / (2.0 * radar->bandwidth))};
   if (cells <= kSortOneCta) {
     SBR_CUDA(select_attr());
@@ -1011,17 +1075,17 @@ namespace {
 // forward DFTs (unnormalised inverse transforms, in place).
 sbr_status cube_adjoint(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const Layout& L, float* d_gcube,
                         cudaStream_t st) {
-  const int V = radar->n_tx * radar->n_rx, C = radar->n_chirps, Ns = radar->n_samples, A = cfar->n_theta;
-  const Steer xl = steering_table(radar);
+  const int V = radar->n_tx * radar->n_rx, C = radar->n_chirps, Ns = radar->n_samples, R = angle_rows(cfar);
+  const Steer xl = steering_table(radar, cfar);
   float2* g = reinterpret_cast<float2*>(d_gcube);
-  switch (A / 8) {
+  switch (R / 8) {
     case 1: launch_angle_bwd<1>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
     case 2: launch_angle_bwd<2>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
     case 4: launch_angle_bwd<4>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
     case 8: launch_angle_bwd<8>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
     case 16: launch_angle_bwd<16>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
     case 32: launch_angle_bwd<32>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
-    default: set_error("n_theta=%d unsupported", A); return SBR_ERR_UNSUPPORTED;
+    default: set_error("%d angle rows unsupported", R); return SBR_ERR_UNSUPPORTED;
   }
   SBR_CUDA(cudaGetLastError());
   SBR_CUDA(fft_cols(g, V, C, Ns, +1.f, st));
@@ -1067,7 +1131,7 @@ extern "C" sbr_status sbr_image_loss(const sbr_radar_cfg* radar, const sbr_cfar_
   rs = state_layout(state, radar, cfar, &L, "sbr_image_loss");
   if (rs != SBR_OK) return rs;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int cells = cfar->n_theta * radar->n_samples;
+  const int cells = angle_rows(cfar) * radar->n_samples;
   ::sbr::note_launch();
   k_image_mse<<<1, kMseThreads, 0, st>>>(L.power, d_target, cells, d_loss, d_gcube ? L.dpw : nullptr);
   SBR_CUDA(cudaGetLastError());
@@ -1087,14 +1151,15 @@ extern "C" sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_c
   rs = state_layout(state, radar, cfar, &L, "sbr_pointcloud_bwd");
   if (rs != SBR_OK) return rs;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int Ns = radar->n_samples, A = cfar->n_theta;
-  const int cells = A * Ns;
+  const int cells = angle_rows(cfar) * radar->n_samples;
   // accumulator and max word are adjacent: one memset clears both
   SBR_CUDA(cudaMemsetAsync(L.dpw_acc, 0,
                            reinterpret_cast<char*>(L.dpw_max + 1) - reinterpret_cast<char*>(L.dpw_acc), st));
-  CfarArg ca{A, Ns, cfar->guard, cfar->train, cfar->alpha, cfar->floor_rel, cfar->beta, cfar->w_min};
+  const CfarArg ca = cfar_arg(radar, cfar);
   PointArg pa{ca, cfar->k_max, (float)(kC / (2.0 * radar->bandwidth))};
-  FixScatter fs{L.dpw_acc, L.dpw_max, ceil_log2((int64_t)cfar->k_max * (6 + 2 * (int64_t)cfar->train))};
+  // adds per point: floor, 2 train windows, the cell, 2 neighbours per refined axis
+  const int64_t per_point = 6 + 2 * (int64_t)cfar->train + (ca.E > 1 ? 2 : 0);
+  FixScatter fs{L.dpw_acc, L.dpw_max, ceil_log2((int64_t)cfar->k_max * per_point)};
   const float4* gp = reinterpret_cast<const float4*>(d_gpoints);
   const int nb = (cfar->k_max + 255) / 256;
   ::sbr::note_launch();

@@ -83,6 +83,7 @@ def cfar_struct(cfg) -> L.CfarCfg:
     c = L.CfarCfg()
     c.n_theta, c.guard, c.train, c.k_max = cfg.n_theta, cfg.guard, cfg.train, cfg.k_max
     c.alpha, c.floor_rel, c.beta, c.w_min = cfg.alpha, cfg.floor_rel, cfg.beta, cfg.w_min
+    c.n_elev = int(getattr(cfg, "n_elev", 1))
     return c
 
 
@@ -299,7 +300,7 @@ class PcState:
                ctypes.byref(self.s))
         self.k_max = cfar.k_max
         self.shape = (radar.n_virt, radar.n_chirps, radar.n_samples)
-        self.A = cfar.n_theta
+        self.rows = max(1, int(getattr(cfar, "n_elev", 1))) * cfar.n_theta  # angle rows e * n_theta + a
 
     def n_points_tensor(self):
         return _region(self.mem, self.s.n_points, torch.int32, (1,))
@@ -308,7 +309,7 @@ class PcState:
         return int(self.n_points_tensor().item())
 
     def power(self):
-        return _region(self.mem, self.s.power, torch.float32, (self.A, self.shape[2]))
+        return _region(self.mem, self.s.power, torch.float32, (self.rows, self.shape[2]))
 
     def spectrum(self):
         return _region(self.mem, self.s.spec, torch.float32, (*self.shape, 2))
@@ -335,7 +336,8 @@ def pointcloud(cube: torch.Tensor, radar, cfar, state: PcState | None = None, ou
 
 
 def power_map(cube: torch.Tensor, radar, cfar, state: PcState | None = None, stream=None) -> PcState:
-    """sbr_power_map: the range-angle power map [n_theta, N_s] of the cube, left in ``state.power()``."""
+    """sbr_power_map: the range-angle power map [n_elev * n_theta, N_s] of the cube (row
+    e * n_theta + a), left in ``state.power()``."""
     _need_cuda(cube, torch.float32, "cube")
     if state is None:
         state = PcState(radar, cfar, device=cube.device)
@@ -349,6 +351,8 @@ def image_loss(state: PcState, target: torch.Tensor, loss: torch.Tensor | None =
     """sbr_image_loss (Eq. 16): loss [1] = mean (Pw - target)^2 over the power map of ``state``,
     and dloss/dcube [V, C, N_s, 2] when ``want_grad``."""
     _need_cuda(target, torch.float32, "target")
+    if target.numel() != state.rows * state.shape[2]:
+        raise ValueError(f"target of {target.numel()} cells, the power map has {state.rows * state.shape[2]}")
     if loss is None:
         loss = torch.empty(1, dtype=torch.float32, device=target.device)
     if want_grad and gcube is None:

@@ -75,3 +75,28 @@ def test_every_status_code_has_a_name():
     txt = open(os.path.join(ROOT, "include", "sbr.h")).read()
     codes = {int(v): n for n, v in re.findall(r"\b(SBR_(?:OK|ERR_[A-Z_]+))\s*=\s*(\d+)", txt)}
     assert codes and all(_lib.STATUS.get(v) == n for v, n in codes.items()), (codes, _lib.STATUS)
+
+
+def test_pointcloud_config_validation(lib):
+    """Angle-row limits of the point-cloud configuration are checked on the host: n_elev a power of
+    two (0 reads as 1), n_elev * n_theta <= 256 and n_elev * n_theta * V <= 4096."""
+    from paper_2311_13182_gb300 import _lib
+    L = _lib.load()
+    r = _lib.RadarCfg()
+    r.n_tx, r.n_rx, r.n_samples, r.n_chirps, r.f0, r.bandwidth, r.chirp_time = 3, 4, 256, 4, 77e9, 4e9, 4e-5
+    r.chirp_rep = 4e-5
+
+    def size(n_theta, n_elev):
+        c = _lib.CfarCfg()
+        c.n_theta, c.guard, c.train, c.k_max, c.alpha, c.floor_rel, c.beta, c.w_min = n_theta, 2, 8, 100, 16., 1e-4, .5, .01
+        c.n_elev = n_elev
+        return L.sbr_pc_bytes(ctypes.byref(r), ctypes.byref(c))
+
+    base = size(64, 0)
+    assert base > 0 and size(64, 1) == base
+    assert size(64, 4) > size(64, 2) > base          # the map and its scratch grow with the rows
+    assert size(64, 3) == 0 and "n_elev" in _lib.last_error()
+    assert size(64, 8) == 0 and "256" in _lib.last_error()   # 512 rows
+    assert size(256, 2) == 0                                  # 512 rows
+    r.n_tx, r.n_rx = 4, 8                                     # V = 32: 256 rows x 32 > 4096
+    assert size(32, 8) == 0 and "4096" in _lib.last_error()
