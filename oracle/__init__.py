@@ -349,12 +349,56 @@ def trace_frozen(verts, faces, tr_ref: dict, grid) -> dict:
     reference trace).  Hit k is the intersection of the ray with the plane of its
     recorded triangle (Moller-Trumbore's t), then specular reflection as in ``trace``.
     The interior derivative of Eq. 4-5 is the derivative of this function."""
+    return _frozen(verts, faces, tr_ref, grid, tr_ref["din"][:, 0].copy(), tr_ref["omega"].copy())
+
+
+def trace_reparam(verts, faces, tr_ref: dict, grid, verts_ref) -> dict:
+    """The ray samples of ``tr_ref`` under the change of variables of Eq. 6, for new vertex
+    positions: T attaches each ray's first hit to its triangle at the reference barycentrics
+    (u, v), so the launch direction follows the surface,
+        d_1 = (x - o) / |x - o|,  x = (1 - u - v) a + u b + v c   (the moved triangle),
+    and the ray's solid-angle weight takes the factor |det J_T|, the change of the solid angle
+    the attached surface element subtends: with N = (b - a) x (c - a) (twice the area times the
+    unit normal; an affine map of the triangle scales every area element with |N|),
+        omega' = omega * J(verts) / J(verts_ref),  J = |N . (x - o)| / |x - o|^3.
+    Later bounces follow as in ``trace_frozen`` (triangle sequence held).  At verts = verts_ref
+    this is the reference trace; the derivative of a path sum under it is Eq. 7's integrand
+    (df/dtheta with the sample moving along, plus f dlog|det J_T|/dtheta).  Rays without a first
+    hit keep their direction and weight."""
+    v = np.asarray(verts, dtype=np.float64)
+    v0 = np.asarray(verts_ref, dtype=np.float64)
+    f = np.asarray(faces)
+    tri0 = tr_ref["tri"][:, 0]
+    n = tri0.shape[0]
+    o = np.asarray(grid.origin, np.float64)
+    d = tr_ref["din"][:, 0].copy()
+    omega = tr_ref["omega"].astype(np.float64).copy()
+    idx = np.where(tri0 >= 0)[0]
+    if idx.size:
+        fa = f[tri0[idx]]
+        u, w = tr_ref["tuv"][idx, 0, 1], tr_ref["tuv"][idx, 0, 2]
+
+        def point_and_density(vv):
+            a, b, c = vv[fa[:, 0]], vv[fa[:, 1]], vv[fa[:, 2]]
+            x = (1.0 - u - w)[:, None] * a + u[:, None] * b + w[:, None] * c
+            N = np.cross(b - a, c - a)
+            r = np.linalg.norm(x - o, axis=1)
+            return x, np.abs((N * (x - o)).sum(-1)) / r ** 3, r
+
+        x, J, r = point_and_density(v)
+        _, J0, _ = point_and_density(v0)
+        d[idx] = (x - o) / r[:, None]
+        omega[idx] *= J / J0
+    return _frozen(verts, faces, tr_ref, grid, d, omega)
+
+
+def _frozen(verts, faces, tr_ref: dict, grid, d, omega) -> dict:
+    """Hits and reflections of ``tr_ref``'s triangle sequences from launch directions d."""
     v = np.asarray(verts, dtype=np.float64)
     f = np.asarray(faces)
     tri = tr_ref["tri"]
     n, K = tri.shape
     o = np.repeat(np.asarray(grid.origin, np.float64)[None], n, axis=0)
-    d = tr_ref["din"][:, 0].copy()
     hit = np.zeros((n, K, 3))
     din = np.zeros((n, K, 3))
     nrm = np.zeros((n, K, 3))
@@ -379,5 +423,5 @@ def trace_frozen(verts, faces, tr_ref: dict, grid) -> dict:
         dd = d[idx]
         d[idx] = dd - 2.0 * (dd * nh).sum(-1, keepdims=True) * nh
         o[idx] = h
-    return dict(tri=tri.copy(), tuv=tuv, hit=hit, din=din, nrm=nrm, omega=tr_ref["omega"].copy(),
+    return dict(tri=tri.copy(), tuv=tuv, hit=hit, din=din, nrm=nrm, omega=omega,
                 flag=np.zeros(n, np.int32), ray_ids=tr_ref["ray_ids"], K=K)
