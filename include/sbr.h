@@ -416,8 +416,21 @@ sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cf
                               float* d_gcube, sbr_stream stream);
 
 /* ------------------------------------------------------------------------ */
-/* Trace adjoint (Section 3.3, Eq. 13; interior derivative, Eq. 4-5)        */
+/* Trace adjoint (Section 3.3, Eq. 13; interior derivative, Eq. 4-5; the    */
+/* reparameterised samples of Eq. 6-7 with SBR_BWD_REPARAM)                 */
 /* ------------------------------------------------------------------------ */
+
+/* sbr_trace_bwd flags.  SBR_BWD_REPARAM: differentiate under the change of
+ * variables of Eq. 6-7 instead of with fixed launch directions.  T attaches each
+ * ray's first hit to its triangle at the forward hit's barycentrics (u, v), so
+ * the launch direction follows the surface, d_1 = (x - o)/|x - o| with
+ * x = (1 - u - v) a + u b + v c, and the ray's solid-angle weight takes the
+ * factor |det J_T| = J / J_0, J = |N.(x - o)| / |x - o|^3 (N = (b - a) x (c - a)):
+ * the gradient gains the motion of the sample with the surface and the term
+ * f dlog|det J_T| of Eq. 7.  This carries the silhouette (boundary) term of a
+ * surface seen against empty space, which fixed directions miss; occlusion
+ * edges between two surfaces are not reparameterised. */
+#define SBR_BWD_REPARAM 0x1
 
 /* Scratch bytes of sbr_trace_bwd for a scene of nv vertices (a 64-bit
  * accumulator per vertex coordinate and per material parameter, status words). */
@@ -437,13 +450,14 @@ size_t sbr_trace_bwd_ws_bytes(int32_t nv);
  * angle, and d_geps, when not NULL, receives (added) dL/d eps_re[m] and
  * dL/d eps_im[m] at [2m], [2m + 1] for m < n_materials (eps = eps_re - j eps_im),
  * summed the same deterministic way.
+ * flags: 0 or SBR_BWD_REPARAM (above); other bits SBR_ERR_INVALID_ARG.
  * d_ws (256-byte aligned) holds sbr_trace_bwd_ws_bytes(nv) bytes, else
  * SBR_ERR_OOM.  max_bounces <= 8. */
 sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts, const sbr_radar_cfg* radar,
                          const sbr_ray_grid* grid, const int32_t* d_ray_ids,
                          const sbr_paths* paths, const float* d_glen, const float* d_gamp,
-                         const float* d_gphase, float* d_gverts, float* d_geps, void* d_ws, size_t ws_bytes,
-                         sbr_stream stream);
+                         const float* d_gphase, float* d_gverts, float* d_geps, int32_t flags, void* d_ws,
+                         size_t ws_bytes, sbr_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Reconstruction loss and optimiser (Section 3.4: Eq. 14 objective and the */

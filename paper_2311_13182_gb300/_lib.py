@@ -56,6 +56,7 @@ class Paths(ctypes.Structure):
 MAX_MATERIALS = 16
 MAX_OBJECTS = 16
 SYNTH_MOVING = 0x100
+BWD_REPARAM = 0x1
 
 
 class Motion(ctypes.Structure):
@@ -136,8 +137,8 @@ _SIGS = {
     "sbr_power_map": (c_i32, [c_p, P(RadarCfg), P(CfarCfg), P(PcState), c_p]),
     "sbr_image_loss": (c_i32, [P(RadarCfg), P(CfarCfg), P(PcState), c_p, c_p, c_p, c_p]),
     "sbr_trace_bwd_ws_bytes": (c_sz, [c_i32]),
-    "sbr_trace_bwd": (c_i32, [c_p, c_p, P(RadarCfg), P(RayGrid), c_p, P(Paths), c_p, c_p, c_p, c_p, c_p, c_p, c_sz,
-                              c_p]),
+    "sbr_trace_bwd": (c_i32, [c_p, c_p, P(RadarCfg), P(RayGrid), c_p, P(Paths), c_p, c_p, c_p, c_p, c_p, c_i32, c_p,
+                              c_sz, c_p]),
     "sbr_chamfer": (c_i32, [c_p, c_p, c_i32, c_p, c_i32, c_p, c_p, c_p]),
     "sbr_mesh_adjacency": (c_i32, [c_p, c_i32, c_i32, c_p, c_p, c_i32, P(c_i32)]),
     "sbr_laplacian_ws_bytes": (c_sz, [c_i32]),

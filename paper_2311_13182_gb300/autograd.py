@@ -25,13 +25,16 @@ from . import sim
 class Simulator:
     def __init__(self, faces: np.ndarray, nv: int, radar, grid, max_bounces: int, cfar, ray_ids=None,
                  phase_mode: int = sim.PHASE_SPLIT, recompute: bool = False, materials=None, motion=None,
-                 device="cuda"):
+                 reparam: bool = False, device="cuda"):
         """materials: None (perfect conductors) or (eps, tri_material): complex relative
         permittivities (eps_re - j eps_im; eps_re <= 0 a perfect conductor) and each triangle's
         material index (None: all material 0), Section 3.2.2 Eq. 9-10.
         motion: None (a static scene) or (velocities, tri_object): a velocity [m/s] per object
         and each triangle's object; the forward pass then synthesises every chirp from the
-        moving delays (no gradients through the motion)."""
+        moving delays (no gradients through the motion).
+        reparam: differentiate the trace under the reparameterised samples of Eq. 6-7 (first
+        hits attached to their surfaces) instead of with fixed launch directions."""
+        self.reparam = reparam
         self.velocities = None
         self.tri_object = None
         if motion is not None:
@@ -113,7 +116,7 @@ class Simulator:
         else:
             glen, gamp = sim.synthesize_bwd(paths, self.radar, gcube, ws=self.synth_ws)
         sim.trace_bwd(self.scene, verts, self.radar, self.grid, paths, glen, gamp, self.ray_ids, gverts=gverts,
-                      ws=self.bwd_ws, gphase=gph, geps=geps)
+                      ws=self.bwd_ws, gphase=gph, geps=geps, reparam=self.reparam)
         return gverts
 
 

@@ -441,8 +441,8 @@ sbr_status enqueue_recon(sbr_server* s, Req* q, Slot& sl) {
     ENQ(sbr_laplacian(dv, r.nv, aoff, adj, r.lap_weight, loss, grad, lap, lws, ss));
     ENQ(sbr_pointcloud_bwd(&s->radar, &s->cfar, &pc, gpts, gcube, ss));
     ENQ(sbr_synthesize_bwd(&paths, &s->radar, gcube, glen, gamp, nullptr, ws, q->sz.ws, ss));
-    ENQ(sbr_trace_bwd(scene, dv, &s->radar, &r.grid, nullptr, &paths, glen, gamp, nullptr, grad, nullptr, bwd, bws,
-                      ss));
+    ENQ(sbr_trace_bwd(scene, dv, &s->radar, &r.grid, nullptr, &paths, glen, gamp, nullptr, grad, nullptr, 0, bwd,
+                      bws, ss));
     ENQ(sbr_adam_step(dv, grad, m1, m2, 3 * (int64_t)r.nv, step, r.lr, 0.9f, 0.999f, 1e-8f, ss));
   }
   float* hp = reinterpret_cast<float*>(sl.pinned);

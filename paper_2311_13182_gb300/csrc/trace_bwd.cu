@@ -2,7 +2,7 @@
 // the continuous-integrand derivative of Eq. 4-5).
 //
 // With the triangle sequence of every ray held fixed (visibility changes are
-// the discontinuous part that Eq. 6-7 reparameterises; not included), each hit
+// the discontinuous part; see the reparameterisation below), each hit
 // is a smooth function of the vertices:
 //   h_k = o_k + t_k d_k,  t_k = N_k.(a_k - o_k) / (N_k.d_k),  N_k = (b_k - a_k) x (c_k - a_k)
 //   d_{k+1} = d_k - 2 (d_k.n_k) n_k,  n_k = N_k / |N_k|,  o_{k+1} = h_k
@@ -16,6 +16,13 @@
 //   dL/d cos_j += G_A Re(q) + G_o Im(q) / (2 pi),  q = d log r_s / d cos = -2 / w,
 //   dL/d eps_m += the same with q = d log r_s / d eps = cos / (w (eps - 1)),
 // w = sqrt(eps - 1 + cos^2), for eps = eps_re - j eps_im (d eps / d eps_im = -j).
+// Reparameterised samples (Eq. 6-7, SBR_BWD_REPARAM): the first hit is attached
+// to its triangle at the forward barycentrics, x = (1 - u - v) a + u b + v c,
+// d_1 = (x - o) / r, r = |x - o|, and the ray's weight carries |det J_T| =
+// J / J_0 with J = |s| / r^3, s = N_1.(x - o).  The sweep's adjoint of d_1 then
+// flows into x, dL/dx += (I - d_1 d_1^T) dL/dd_1 / r, and with
+// G_w = sum over the ray's paths of dL/dA A (A is linear in the weight),
+//   dL/dx += G_w (N_1 / s - 3 (x - o) / r^2),  dL/dN_1 += G_w (x - o) / s.
 // One thread per ray accumulates the adjoints of its path lengths and
 // strengths onto the hit points and |d.n| terms, then sweeps the bounces in
 // reverse, and adds the per-corner vertex gradients to the vertices with the
@@ -78,8 +85,8 @@ __device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, cons
                             int K, const sbr_hit* __restrict__ hits, const float4* __restrict__ hit_pos,
                             const int32_t* __restrict__ first, const float4* __restrict__ prep, int64_t cap,
                             const float* __restrict__ glen, const float* __restrict__ gamp,
-                            const float* __restrict__ gphase, const FixScatter& fs, int E, float& lmax,
-                            const FixScatter& fe, int Ee, float& emax) {
+                            const float* __restrict__ gphase, bool reparam, const FixScatter& fs, int E,
+                            float& lmax, const FixScatter& fe, int Ee, float& emax) {
   const int p0 = first[i], m = first[i + 1] - p0;
   if (m <= 0) return;
   // launch direction in FP32 (cell centre a = start + col step, likewise b with row)
@@ -103,6 +110,24 @@ __device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, cons
   int mj[kMaxK];        // material of bounce j (-1: perfect conductor or no materials)
   float2 wj[kMaxK];     // w = sqrt(eps - 1 + cos^2) of bounce j
   d[0] = f3(wx * wl, wy * wl, wz * wl);
+  const float3 org = f3(g.o[0], g.o[1], g.o[2]);
+  float3 x0 = org;
+  float bu = 0.f, bv = 0.f;
+  if (reparam) {  // the launch direction attached to the first hit's surface point
+    const size_t s0 = (size_t)i * K;
+    bu = hits[s0].u;
+    bv = hits[s0].v;
+    const int id = hits[s0].tri;
+    int q[3];
+    for (int c = 0; c < 3; ++c) {
+      q[c] = faces[3 * id + c];
+      q[c] = (q[c] >= 0 && q[c] < nv) ? q[c] : 0;
+    }
+    x0 = ld3(verts, q[0]) * (1.f - bu - bv) + ld3(verts, q[1]) * bu + ld3(verts, q[2]) * bv;
+    const float3 e = x0 - org;
+    d[0] = e * rsqrtf(dot(e, e));
+  }
+  float gw = 0.f;  // sum over the ray's paths of dL/dA A
   for (int k = 0; k < m; ++k) {
     const size_t sl = (size_t)i * K + k;
     const int id = hits[sl].tri;
@@ -169,6 +194,7 @@ __device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, cons
       lin_sum_b += linb;
     }
     for (int j = 1; j <= k; ++j) segb[j] += lin_sum_b;
+    gw += g_a;
     if (mat.n > 0) {  // the Fresnel factor: every bounce j <= k of this path
       const float go = g_o * (float)(0.5 / M_PI);
       for (int j = 0; j <= k; ++j) {
@@ -228,6 +254,20 @@ __device__ void ray_adjoint(int i, const float* __restrict__ verts, int nv, cons
     db_next = db;
     ob_next = ob;
   }
+  if (reparam) {  // d_1 and the weight as functions of the attached point x and of N_1
+    const float3 e = x0 - org;
+    const float r2 = dot(e, e), r = sqrtf(r2);
+    const float3 u = e * (1.f / r);
+    const float s = dot(N[0], e);
+    float3 xb = (db_next - u * dot(u, db_next)) * (1.f / r);
+    add3(xb, (N[0] * (1.f / s) - e * (3.f / r2)) * gw);
+    const float3 Nb = e * (gw / s);
+    const float3 va = A[0], vb = ld3(verts, fv[0][1]), vc = ld3(verts, fv[0][2]);
+    const float3 e1b = cross(vc - va, Nb), e2b = cross(Nb, vb - va);
+    scatter<kPass>(fs, E, lmax, fv[0][0], xb * (1.f - bu - bv) - e1b - e2b);
+    scatter<kPass>(fs, E, lmax, fv[0][1], xb * bu + e1b);
+    scatter<kPass>(fs, E, lmax, fv[0][2], xb * bv + e2b);
+  }
 }
 
 template <int kPass>
@@ -236,14 +276,14 @@ __global__ void __launch_bounds__(128) k_trace_bwd(
     const int32_t* __restrict__ ray_ids, int n_rays, int K, const sbr_hit* __restrict__ hits,
     const float4* __restrict__ hit_pos, const int32_t* __restrict__ first,
     const float4* __restrict__ prep, int64_t cap, const float* __restrict__ glen,
-    const float* __restrict__ gamp, const float* __restrict__ gphase, FixScatter fs, FixScatter fe) {
+    const float* __restrict__ gamp, const float* __restrict__ gphase, bool reparam, FixScatter fs, FixScatter fe) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int E = kPass == 0 ? 0 : fix_exp(*fs.max_bits, fs.log2n);
   const int Ee = kPass == 0 ? 0 : fix_exp(*fe.max_bits, fe.log2n);
   float lmax = 0.f, emax = 0.f;
   if (i < n_rays)
     ray_adjoint<kPass>(i, verts, nv, faces, g, rd, mat, ray_ids, K, hits, hit_pos, first, prep, cap, glen, gamp,
-                       gphase, fs, E, lmax, fe, Ee, emax);
+                       gphase, reparam, fs, E, lmax, fe, Ee, emax);
   if (kPass == 0) {  // every lane of the warp reaches this
     fix_note_warp(fs.max_bits, lmax);
     if (mat.n > 0) fix_note_warp(fe.max_bits, emax);
@@ -286,9 +326,11 @@ extern "C" size_t sbr_trace_bwd_ws_bytes(int32_t nv) {
 extern "C" sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts, const sbr_radar_cfg* radar,
                                     const sbr_ray_grid* grid, const int32_t* d_ray_ids,
                                     const sbr_paths* paths, const float* d_glen, const float* d_gamp,
-                                    const float* d_gphase, float* d_gverts, float* d_geps, void* d_ws,
-                                    size_t ws_bytes, sbr_stream stream) {
+                                    const float* d_gphase, float* d_gverts, float* d_geps, int32_t flags,
+                                    void* d_ws, size_t ws_bytes, sbr_stream stream) {
   SBR_ARG(scene && paths && d_verts && d_glen && d_gamp && d_gverts, "sbr_trace_bwd: NULL argument");
+  SBR_ARG((flags & ~SBR_BWD_REPARAM) == 0, "sbr_trace_bwd: unknown flags 0x%x", (unsigned)flags);
+  const bool reparam = (flags & SBR_BWD_REPARAM) != 0;
   SBR_ARG(scene->n_mat == 0 || d_gphase,
           "sbr_trace_bwd: the scene has materials: d_gphase (sbr_synthesize_bwd's phase gradient) is required");
   SBR_ARG(d_ws && aligned256(d_ws), "sbr_trace_bwd: workspace NULL or not 256-byte aligned");
@@ -329,7 +371,7 @@ extern "C" sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts
   const int R = paths->n_rays;
   BwdWs w;
   bwd_ws_layout(d_ws, scene->nv, &w);
-  w.fs.log2n = ceil_log2(3 * (int64_t)R * paths->max_bounces);  // contributions per axis, at most
+  w.fs.log2n = ceil_log2(3 * (int64_t)R * (paths->max_bounces + (reparam ? 1 : 0)));  // contributions per axis, at most
   w.fe.log2n = ceil_log2((int64_t)R * paths->max_bounces * paths->max_bounces);  // per material, at most
   const MatArg mat = mat_arg(scene);
   SBR_CUDA(cudaMemsetAsync(d_ws, 0, sbr_trace_bwd_ws_bytes(scene->nv), st));
@@ -338,11 +380,11 @@ extern "C" sbr_status sbr_trace_bwd(const sbr_scene* scene, const float* d_verts
   ::sbr::note_launch();
   k_trace_bwd<0><<<(R + 127) / 128, 128, 0, st>>>(d_verts, scene->nv, scene->faces, g, rd, mat, d_ray_ids, R,
                                                    paths->max_bounces, paths->hits, hp, paths->ray_first, pr,
-                                                   paths->path_cap, d_glen, d_gamp, d_gphase, w.fs, w.fe);
+                                                   paths->path_cap, d_glen, d_gamp, d_gphase, reparam, w.fs, w.fe);
   ::sbr::note_launch();
   k_trace_bwd<1><<<(R + 127) / 128, 128, 0, st>>>(d_verts, scene->nv, scene->faces, g, rd, mat, d_ray_ids, R,
                                                    paths->max_bounces, paths->hits, hp, paths->ray_first, pr,
-                                                   paths->path_cap, d_glen, d_gamp, d_gphase, w.fs, w.fe);
+                                                   paths->path_cap, d_glen, d_gamp, d_gphase, reparam, w.fs, w.fe);
   const int n3 = 3 * scene->nv;
   if (n3 > 0) {
     ::sbr::note_launch();

@@ -5,6 +5,7 @@ One iteration (Eq. 14 objective, Eq. 15 update; Adam in place of plain SGD):
   loss = weighted squared Chamfer(points, target) + w_lap * uniform Laplacian
   point-cloud adjoint -> synthesis adjoint (Eq. 11-12) -> trace adjoint (Eq. 13)
   Adam step on the vertex positions
+(reparam=True: the trace adjoint under the reparameterised samples of Eq. 6-7)
 or, with loss="image", the paper's spatial multi-antenna loss (Eq. 16): the
 target is a range-angle power map [n_theta, N_s], the forward stops at the power
 map, and loss = mean squared image difference + w_lap * Laplacian, whose adjoint
@@ -23,14 +24,15 @@ from .autograd import Simulator
 
 class Reconstruction:
     def __init__(self, verts0: np.ndarray, faces: np.ndarray, target: torch.Tensor, radar, grid, max_bounces,
-                 cfar, lr=1e-3, lap_weight=0.1, ray_ids=None, recompute=False, loss="chamfer", device="cuda"):
+                 cfar, lr=1e-3, lap_weight=0.1, ray_ids=None, recompute=False, loss="chamfer", reparam=False,
+                 device="cuda"):
         if loss not in ("chamfer", "image"):
             raise ValueError(f"loss must be 'chamfer' or 'image', not {loss!r}")
         self.kind = loss
         self.verts = torch.from_numpy(np.ascontiguousarray(verts0, np.float32)).to(device)
         self.nv = self.verts.shape[0]
         self.sim = Simulator(faces, self.nv, radar, grid, max_bounces, cfar, ray_ids=ray_ids,
-                             recompute=recompute, device=device)
+                             recompute=recompute, reparam=reparam, device=device)
         self.adj = sim.Adjacency(faces, self.nv, device)
         self.target = target.contiguous().float().to(device)
         self.lr, self.lap_weight = lr, lap_weight

@@ -14,6 +14,7 @@ from . import _lib as L
 
 PHASE_SPLIT, PHASE_FP64, PHASE_NAIVE = L.PHASE_SPLIT, L.PHASE_FP64, L.PHASE_NAIVE
 SYNTH_MOVING = L.SYNTH_MOVING  # OR into a phase mode: every chirp from the paths' dL/dt
+BWD_REPARAM = L.BWD_REPARAM    # sbr_trace_bwd: reparameterised samples (Eq. 6-7)
 
 
 def _vp(t):
@@ -379,10 +380,11 @@ def trace_bwd_ws_bytes(nv: int) -> int:
 def trace_bwd(scene: Scene, verts: torch.Tensor, radar, grid, paths: PathBuffers, glen: torch.Tensor,
               gamp: torch.Tensor, ray_ids: torch.Tensor | None = None, gverts: torch.Tensor | None = None,
               ws: torch.Tensor | None = None, gphase: torch.Tensor | None = None, geps: torch.Tensor | None = None,
-              stream=None):
+              reparam: bool = False, stream=None):
     """sbr_trace_bwd: adds dL/dverts [nv, 3] from per-path (dL/dlength, dL/dA) and, on a scene
     with materials, the Fresnel terms from dL/d(phase offset) ``gphase``; adds dL/d eps
-    [n_materials, 2] (d eps_re, d eps_im) to ``geps`` when given."""
+    [n_materials, 2] (d eps_re, d eps_im) to ``geps`` when given.  ``reparam``: the
+    reparameterised samples of Eq. 6-7 (SBR_BWD_REPARAM) instead of fixed launch directions."""
     _need_cuda(verts, torch.float32, "verts")
     if gverts is None:
         gverts = torch.zeros_like(verts)
@@ -391,8 +393,8 @@ def trace_bwd(scene: Scene, verts: torch.Tensor, radar, grid, paths: PathBuffers
         ws = torch.empty(nb, dtype=torch.uint8, device=verts.device)
     r, g = radar_struct(radar), grid_struct(grid)
     L.call("sbr_trace_bwd", scene.handle, _vp(verts), ctypes.byref(r), ctypes.byref(g), _vp(ray_ids),
-           ctypes.byref(paths.s), _vp(glen), _vp(gamp), _vp(gphase), _vp(gverts), _vp(geps), _vp(ws), nb,
-           _stream(stream))
+           ctypes.byref(paths.s), _vp(glen), _vp(gamp), _vp(gphase), _vp(gverts), _vp(geps),
+           BWD_REPARAM if reparam else 0, _vp(ws), nb, _stream(stream))
     return gverts
 
 

@@ -21,8 +21,12 @@ def weights(ray, k, v):
     return np.sin(1.3 * ray + 0.7 * k + 2.1 * v), np.cos(0.9 * ray - 1.1 * k + 0.5 * v) * 1e4
 
 
-def oracle_L(verts, wl, tr_ref, gl, ga):
-    pa = oracle.paths(oracle.trace_frozen(verts, wl.faces, tr_ref, wl.grid), wl.radar)
+def oracle_L(verts, wl, tr_ref, gl, ga, reparam=False):
+    if reparam:
+        tr = oracle.trace_reparam(verts, wl.faces, tr_ref, wl.grid, wl.verts)
+    else:
+        tr = oracle.trace_frozen(verts, wl.faces, tr_ref, wl.grid)
+    pa = oracle.paths(tr, wl.radar)
     return float((gl * pa["tau"] * C_LIGHT).sum() + (ga * pa["amp"]).sum())
 
 
@@ -30,7 +34,7 @@ def rel_err(g, fd):
     return np.abs(g - fd) / np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max())
 
 
-def check_trace_adjoint(sbr, wl, ids=None, n_vert_checks=12):
+def check_trace_adjoint(sbr, wl, ids=None, n_vert_checks=12, reparam=False):
     tr = oracle.trace(wl.verts, wl.faces, wl.grid, wl.max_bounces, ray_ids=ids)
     scene, paths = gpu_trace(sbr, wl, ray_ids=ids)
     P = paths.count()
@@ -45,7 +49,7 @@ def check_trace_adjoint(sbr, wl, ids=None, n_vert_checks=12):
     vt = torch.from_numpy(wl.verts).cuda()
     ids_t = None if ids is None else torch.from_numpy(ids).cuda()
     g = sbr.trace_bwd(scene, vt, wl.radar, wl.grid, paths, torch.from_numpy(gl).cuda(),
-                      torch.from_numpy(ga).cuda(), ray_ids=ids_t).cpu().numpy().astype(np.float64)
+                      torch.from_numpy(ga).cuda(), ray_ids=ids_t, reparam=reparam).cpu().numpy().astype(np.float64)
     pa = oracle.paths(tr, wl.radar)
     glo = np.stack([weights(pa["ray"], pa["bounce"], v)[0] for v in range(V)])
     gao = np.stack([weights(pa["ray"], pa["bounce"], v)[1] for v in range(V)])
@@ -59,17 +63,67 @@ def check_trace_adjoint(sbr, wl, ids=None, n_vert_checks=12):
             vp, vm = v64.copy(), v64.copy()
             vp[vi, ax] += H
             vm[vi, ax] -= H
-            fd = (oracle_L(vp, wl, tr, glo, gao) - oracle_L(vm, wl, tr, glo, gao)) / (2 * H)
+            fd = (oracle_L(vp, wl, tr, glo, gao, reparam) - oracle_L(vm, wl, tr, glo, gao, reparam)) / (2 * H)
             scale = max(abs(fd), 1e-3 * np.abs(g).max())
             assert abs(g[vi, ax] - fd) <= 1e-3 * scale, (vi, ax, g[vi, ax], fd)
     # a random direction over all vertices
     D = rng.normal(size=v64.shape)
-    fd = (oracle_L(v64 + H * D, wl, tr, glo, gao) - oracle_L(v64 - H * D, wl, tr, glo, gao)) / (2 * H)
+    fd = (oracle_L(v64 + H * D, wl, tr, glo, gao, reparam) - oracle_L(v64 - H * D, wl, tr, glo, gao, reparam)) / (2 * H)
     assert abs((g * D).sum() - fd) <= 1e-3 * abs(fd)
+    return g
 
 
 def test_trace_adjoint_sphere(sbr):
     check_trace_adjoint(sbr, sphere_scene(G=48))
+
+
+def test_trace_adjoint_reparam_sphere(sbr):
+    """SBR_BWD_REPARAM (Eq. 6-7: first hits attached to the surface, weights with |det J_T|) against
+    FP64 central differences of the oracle's reparameterised samples; differs from the interior one."""
+    wl = sphere_scene(G=48)
+    g = check_trace_adjoint(sbr, wl, reparam=True)
+    g0 = check_trace_adjoint(sbr, wl, n_vert_checks=2)
+    assert np.abs(g - g0).max() > 1e-3 * np.abs(g0).max()
+
+
+def test_trace_adjoint_reparam_corner_three_bounces(sbr):
+    from tests.test_oracle_pins import axis_grid, corner_reflector
+    C = np.array([0.25, 0.125, 2.0])
+    v, f = corner_reflector(C, 0.75)
+    wl = Workload("corner", v, f, radar_single_tx(), axis_grid(24, 0.12, axis=C), 3, {})
+    check_trace_adjoint(sbr, wl, n_vert_checks=8, reparam=True)
+
+
+def test_trace_adjoint_reparam_plate_integral(sbr):
+    """With dL/dA = 1 on one antenna's paths the trace adjoint is the gradient of the
+    Monte-Carlo estimate of the plate's integral of Eq. 1's strength.  Under the
+    reparameterised samples its derivative along random vertex motions follows the derivative
+    of the exact integral (quadrature) within 0.5 %, silhouette motion included; with fixed
+    launch directions it does not (the boundary term is missing)."""
+    from tests.test_oracle_pins import axis_grid, plate_integral, square
+    v, f = square((-0.35, -0.25, 1.2), (0.7, 0.05, 0.15), (-0.05, 0.6, 0.1))
+    wl = Workload("plate", v, f, radar_single_tx(), axis_grid(256, 0.5), 1, {})
+    scene, paths = gpu_trace(sbr, wl)
+    P = paths.count()
+    V = wl.radar.n_virt
+    gl = torch.zeros((V, paths.cap), device="cuda")
+    ga = torch.zeros((V, paths.cap), device="cuda")
+    ga[0, :P] = 1.0
+    vt = torch.from_numpy(v).cuda()
+    g = sbr.trace_bwd(scene, vt, wl.radar, wl.grid, paths, gl, ga, reparam=True).cpu().numpy().astype(np.float64)
+    g0 = sbr.trace_bwd(scene, vt, wl.radar, wl.grid, paths, gl, ga).cpu().numpy().astype(np.float64)
+    v64 = v.astype(np.float64)
+    est = float(paths.prep()[0, :P, 3].double().sum())
+    assert abs(est - plate_integral(v64, f, wl.radar)) < 0.01 * est
+    rng = np.random.default_rng(7)
+    miss = 0.0
+    for _ in range(3):
+        D = rng.normal(size=v64.shape)
+        h = 1e-6
+        ex = (plate_integral(v64 + h * D, f, wl.radar) - plate_integral(v64 - h * D, f, wl.radar)) / (2 * h)
+        assert abs((g * D).sum() - ex) < 0.005 * abs(ex), ((g * D).sum(), ex)
+        miss = max(miss, abs((g0 * D).sum() - ex) / abs(ex))
+    assert miss > 0.05  # the fixed-direction gradient misses the boundary term
 
 
 def test_trace_adjoint_corner_three_bounces(sbr):
@@ -149,18 +203,20 @@ def test_reconstruction_gradient_fd(sbr):
     assert (err <= 1e-3).all(), err.max()
 
 
-def test_image_loss_gradient_fd(sbr):
+@pytest.mark.parametrize("reparam", [False, True])
+def test_image_loss_gradient_fd(sbr, reparam):
     """The paper's spatial loss (Eq. 16) end to end: dloss/dverts of the mean squared
     range-angle power-map difference (no Laplacian) against FP64 central differences of the
     oracle chain (frozen triangle sequences, paths, Eq. 8, direct DFTs, power map) on 12
-    seeded template vertices x 3 axes."""
+    seeded template vertices x 3 axes; with reparam, the oracle chain samples under the
+    change of variables of Eq. 6-7 (trace_reparam) and the simulator differentiates the same."""
     from paper_2311_13182_gb300.autograd import Simulator
     sv, sf, tv, tf, radar, grid = recon_setup()
     cfg = CfarParams()
     K = 2
     tcube, _, _ = oracle.simulate_cube(Workload("t", sv, sf, radar, grid, K, {}))
     _, _, target = opc.power_map(tcube, radar, cfg)
-    s = Simulator(tf, tv.shape[0], radar, grid, K, cfg)
+    s = Simulator(tf, tv.shape[0], radar, grid, K, cfg, reparam=reparam)
     vt = torch.from_numpy(tv).cuda()
     s.forward_image(vt)
     loss, gcube = sbr.image_loss(s.state, torch.from_numpy(target.astype(np.float32)).cuda())
@@ -171,7 +227,8 @@ def test_image_loss_gradient_fd(sbr):
     tr = oracle.trace(tv, tf, grid, K)
 
     def L(verts):
-        pa = oracle.paths(oracle.trace_frozen(verts, tf, tr, grid), radar)
+        trv = oracle.trace_reparam(verts, tf, tr, grid, tv) if reparam else oracle.trace_frozen(verts, tf, tr, grid)
+        pa = oracle.paths(trv, radar)
         return opc.image_loss(oracle.synthesize(pa["tau"], pa["amp"], radar), target, radar, cfg)
 
     v64 = tv.astype(np.float64)

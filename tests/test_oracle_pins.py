@@ -905,3 +905,57 @@ def test_reparam_weights_follow_the_exact_solid_angle():
         assert abs(fd - ex) < 0.01 * abs(ex), (fd, ex)
         fz = oracle.trace_frozen(v + h * D, f, tr, grid)["omega"][hit].sum() - tr["omega"][hit].sum()
         assert fz == 0.0
+
+
+def plate_integral(vv, faces, radar, n=24):
+    """int over the plate of Eq. 1's single-bounce strength per unit solid angle,
+    |n.u_tx| / (4 pi |y - Tx| |y - Rx|) dOmega (Tx 0, Rx 0, sample origin at Tx), by a
+    Gauss-Legendre product rule on each triangle (Duffy map y = a + s (b - a) + s t (c - b),
+    dA = s |N| ds dt): converged far below the Monte-Carlo estimate's error."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    x, w = 0.5 * (x + 1.0), 0.5 * w
+    S, T = np.meshgrid(x, x, indexing="ij")
+    W = np.outer(w, w)
+    tx, rx = np.asarray(radar.tx[0], float), np.asarray(radar.rx[0], float)
+    total = 0.0
+    for tri in faces:
+        a, b, c = vv[tri]
+        N = np.cross(b - a, c - a)
+        nn = N / np.linalg.norm(N)
+        y = a + S[..., None] * (b - a) + (S * T)[..., None] * (c - b)
+        e = y - tx
+        r = np.linalg.norm(e, axis=-1)
+        cos = np.abs((e * nn).sum(-1)) / r
+        f = cos / (4.0 * np.pi * r * np.linalg.norm(y - rx, axis=-1))
+        dOmega = cos / r ** 2 * np.linalg.norm(N) * S
+        total += (W * f * dOmega).sum()
+    return total
+
+
+def test_reparam_derivative_follows_the_exact_strength_integral():
+    """The single-bounce strength summed over a plate's rays (Eq. 1's cos and spreading, one
+    antenna) estimates the integral of that strength over the plate's solid angle; under the
+    reparameterised samples its derivative along random vertex motions matches the derivative of
+    the exact integral (Gauss-Legendre quadrature) within 0.1 %, while the fixed-direction
+    derivative misses the silhouette term by more than 30 %."""
+    from sbr_inputs import radar_single_tx
+    v, f = square((-0.35, -0.25, 1.2), (0.7, 0.05, 0.15), (-0.05, 0.6, 0.1))
+    radar = radar_single_tx()
+    grid = axis_grid(256, 0.5)
+    tr = oracle.trace(v, f, grid, 1)
+    v64 = v.astype(np.float64)
+
+    def est(vv, reparam):
+        t = oracle.trace_reparam(vv, f, tr, grid, v64) if reparam else oracle.trace_frozen(vv, f, tr, grid)
+        return oracle.paths(t, radar)["amp"][0].sum()
+
+    assert abs(est(v64, True) - plate_integral(v64, f, radar)) < 0.01 * est(v64, True)
+    rng = np.random.default_rng(7)
+    h = 1e-6
+    for _ in range(3):
+        D = rng.normal(size=v64.shape)
+        ex = (plate_integral(v64 + h * D, f, radar) - plate_integral(v64 - h * D, f, radar)) / (2 * h)
+        rp = (est(v64 + h * D, True) - est(v64 - h * D, True)) / (2 * h)
+        fz = (est(v64 + h * D, False) - est(v64 - h * D, False)) / (2 * h)
+        assert abs(rp - ex) < 1e-3 * abs(ex), (rp, ex)
+        assert abs(fz - ex) > 0.3 * abs(ex)
