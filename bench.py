@@ -230,7 +230,7 @@ def gpu_arm(args, rank, world, local):
     stage_ms = dict(zip(["scene_build", "trace", "synthesize", "pointcloud"], stage.mean(0).round(4).tolist()))
 
     # ---- end to end through the public API with host buffers
-    e2e = e2e_arm(sbr, torch, wl, cfg, args, world)
+    e2e = e2e_arm(sbr, torch, wl, cfg, args, world, flush)
 
     # ---- rooflines (work counters from one counting trace, outside the timed region)
     from paper_2311_13182_gb300 import sim as _sim
@@ -269,49 +269,33 @@ def gpu_arm(args, rank, world, local):
     return out
 
 
-def e2e_arm(sbr, torch, wl, cfg, args, world):
-    """Same step through the public API from pinned host buffers: H2D of the mesh each step, the
-    scene created from it, trace, synthesis, point cloud, D2H of the points and their count."""
-    hv = torch.from_numpy(wl.verts).pin_memory()
-    hf = torch.from_numpy(wl.faces).pin_memory()
-    hp = torch.empty((cfg.k_max, 4), dtype=torch.float32).pin_memory()
-    hn = torch.empty(1, dtype=torch.int32).pin_memory()
-    dv = torch.empty_like(hv, device="cuda")
-    df = torch.empty_like(hf, device="cuda")
-    paths = sbr.PathBuffers(wl.grid.n_rays, wl.max_bounces, wl.radar.n_virt)
-    ws = torch.empty(sbr.synth_ws_bytes(wl.radar, paths.cap), dtype=torch.uint8, device="cuda")
-    cube = torch.empty((wl.radar.n_virt, wl.radar.n_chirps, wl.radar.n_samples, 2), device="cuda")
-    state = sbr.PcState(wl.radar, cfg)
-    pts = torch.empty((cfg.k_max, 4), device="cuda")
-
-    def step():
-        dv.copy_(hv, non_blocking=True)
-        df.copy_(hf, non_blocking=True)
-        scene = sbr.Scene(dv, df)
-        sbr.trace(scene, wl.radar, wl.grid, wl.max_bounces, out=paths)
-        sbr.synthesize(paths, wl.radar, sbr.PHASE_SPLIT, out=cube, ws=ws)
-        sbr.pointcloud(cube, wl.radar, cfg, state=state, out=pts)
-        hp.copy_(pts, non_blocking=True)
-        hn.copy_(state.n_points_tensor(), non_blocking=True)
-        return scene
-
+def e2e_arm(sbr, torch, wl, cfg, args, world, flush):
+    """Same step through the public API from page-locked host buffers: sbr.Forward with host_io,
+    whose graph copies the vertex positions host-to-device at its start (the topology fixed at
+    construction), rebuilds the scene, traces, synthesises and extracts the points, and copies
+    the points and their count device-to-host at its end; one run_host call per step, L2 flushed
+    between steps outside the per-step events as in the device-timed arm."""
+    fwd = sbr.Forward(torch.from_numpy(wl.verts).cuda(), torch.from_numpy(wl.faces).cuda(), wl.radar, wl.grid,
+                      wl.max_bounces, cfg, host_io=True)
     for _ in range(3):
-        step()
+        fwd.run_host(wl.verts)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier(world)
     torch.cuda.synchronize()
-    e0.record()
-    keep = []
-    for _ in range(args.steps):
-        keep.append(step())
-    e1.record()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        fwd.run_host()
+        ev[i][1].record()
     torch.cuda.synchronize()
-    ms = reduce_max(e0.elapsed_time(e1) / args.steps, world)
-    bi = hv.numel() * 4 + hf.numel() * 4
-    bo = hp.numel() * 4 + 4
+    ms = reduce_max(float(np.mean([a.elapsed_time(b) for a, b in ev])), world)
+    bi = fwd.h_verts.numel() * 4
+    bo = fwd.h_points.numel() * 4 + 4
     return {"value": reduce_sum(wl.grid.n_rays, world) / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
-            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+            "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+            "path": "sbr.Forward(host_io=True).run_host: H2D of the vertices, the step, D2H of the points, "
+                    "one CUDA graph per step"}
 
 
 # Counters per launch of each roofline stage (DRAM bytes, warp instructions), from ncu captures

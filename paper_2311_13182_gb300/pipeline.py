@@ -7,7 +7,10 @@ buffers.  ``Forward`` captures the sequence once and replays it, so a step costs
 one graph launch on the host and no gaps between dependent kernels on the GPU.
 New vertex positions of the same topology are written into ``verts`` between
 replays (``set_vertices``); everything else (radar, grid, bounce count, CFAR
-settings) is fixed at construction.
+settings) is fixed at construction.  With ``host_io`` the graph also holds the
+step's host traffic: the copy of the vertex positions from a page-locked host
+buffer at its start, and the copies of the points and their count into
+page-locked host buffers at its end (``run_host``).
 """
 from __future__ import annotations
 
@@ -18,7 +21,7 @@ from . import sim
 
 class Forward:
     def __init__(self, verts: torch.Tensor, faces: torch.Tensor, radar, grid, max_bounces: int, cfar,
-                 mode: int = sim.PHASE_SPLIT, graph: bool = True):
+                 mode: int = sim.PHASE_SPLIT, graph: bool = True, host_io: bool = False):
         self.radar, self.grid, self.max_bounces, self.cfar, self.mode = radar, grid, max_bounces, cfar, mode
         self.verts = verts.detach().clone().contiguous()
         self.faces = faces.detach().contiguous()
@@ -28,6 +31,13 @@ class Forward:
         self.cube = torch.empty((radar.n_virt, radar.n_chirps, radar.n_samples, 2), device=self.verts.device)
         self.state = sim.PcState(radar, cfar)
         self.points = torch.empty((cfar.k_max, 4), device=self.verts.device)
+        self.host_io = host_io
+        if host_io:
+            self.h_verts = torch.empty(self.verts.shape, dtype=torch.float32).pin_memory()
+            self.h_verts.copy_(self.verts)
+            self.h_points = torch.empty((cfar.k_max, 4), dtype=torch.float32).pin_memory()
+            self.h_n = torch.empty(1, dtype=torch.int32).pin_memory()
+            self.done = torch.cuda.Event()
         self.graph = None
         if graph:
             # first calls outside the capture: they set per-device kernel attributes
@@ -40,7 +50,12 @@ class Forward:
             torch.cuda.synchronize()
             self.graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(self.graph):
+                if host_io:
+                    self.verts.copy_(self.h_verts, non_blocking=True)
                 self.run_eager()
+                if host_io:
+                    self.h_points.copy_(self.points, non_blocking=True)
+                    self.h_n.copy_(self.state.n_points_tensor(), non_blocking=True)
             torch.cuda.synchronize()
 
     def set_vertices(self, verts: torch.Tensor):
@@ -68,6 +83,19 @@ class Forward:
             self.graph.replay()
         else:
             self.run_eager()
+
+    def run_host(self, verts=None):
+        """One step from host memory (requires host_io and the graph): ``verts`` (array-like
+        [nv, 3], or None to keep the page-locked buffer's contents) go into the page-locked input
+        buffer once the previous step has finished with it, then the graph replays; the points
+        and their count land in ``h_points`` / ``h_n`` when ``done`` (an event) completes."""
+        if not self.host_io or self.graph is None:
+            raise RuntimeError("run_host needs Forward(..., graph=True, host_io=True)")
+        if verts is not None:
+            self.done.synchronize()  # the previous replay has read the buffer
+            self.h_verts.copy_(torch.as_tensor(verts, dtype=torch.float32))
+        self.graph.replay()
+        self.done.record()
 
     def n_points(self) -> int:
         return self.state.n_points()

@@ -31,6 +31,30 @@ def test_graph_replay_matches_eager(sbr):
     assert r_moved.min() > 0
 
 
+def test_host_io_graph_matches_eager(sbr):
+    """Forward(host_io=True).run_host: the graph copies the vertices in and the points and their
+    count out; the host buffers hold exactly what the separate launches compute, for the first
+    vertex set and after new host vertices (moved 1 cm) go in."""
+    wl = superquadric_scene(seed=6, G=256)
+    cfg = CfarParams()
+    v = torch.from_numpy(wl.verts).cuda()
+    f = torch.from_numpy(wl.faces).cuda()
+    h = sbr.Forward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg, host_io=True)
+    e = sbr.Forward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg, graph=False)
+    for shift in (0.0, 0.01):
+        moved = wl.verts + np.array([0.0, 0.0, shift], np.float32)
+        h.run_host(moved)
+        e.set_vertices(torch.from_numpy(moved).cuda())
+        e.run()
+        h.done.synchronize()
+        torch.cuda.synchronize()
+        n = int(h.h_n.item())
+        assert n == e.n_points() > 0
+        assert torch.equal(h.h_points, e.points.cpu())
+    with pytest.raises(RuntimeError):
+        e.run_host(wl.verts)
+
+
 def test_bench_step_full_cube_and_points_against_oracle(sbr):
     """The bench workload at full size (20,002 triangles, all 1,048,576 rays, 3 bounces,
     12 x 128 x 256 cube), run as the bench runs it (the graph-replayed sbr.Forward step):
