@@ -746,12 +746,16 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
   bool cross = false;
   if (i < n - 1) {
     int left, right, lo, hi;
-    karras_node(
-        [&](int j) {
-          const unsigned r = (unsigned)(j - wlo);
-          return r < (unsigned)wlen ? s_keys[r] : __ldcg(&keys[j]);
-        },
-        n, i, &left, &right, &lo, &hi);
+    if (wlen == n) {  // every key in shared memory: plain shared loads in the searches
+      karras_node([&](int j) { return s_keys[j]; }, n, i, &left, &right, &lo, &hi);
+    } else {  // a window: a lookup that may read either space becomes a generic load, ~3x slower
+      karras_node(
+          [&](int j) {
+            const unsigned r = (unsigned)(j - wlo);
+            return r < (unsigned)wlen ? s_keys[r] : __ldcg(&keys[j]);
+          },
+          n, i, &left, &right, &lo, &hi);
+    }
     B.nodes[i].child = make_int4(left, right, 0, 0);
     B.parent[left >= 0 ? left : (n - 1 + ~left)] = i;
     B.parent[right >= 0 ? right : (n - 1 + ~right)] = i;

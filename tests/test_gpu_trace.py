@@ -136,6 +136,18 @@ def test_tree_tile_boundaries(sbr, nt):
     check_paths(wl, tr, paths)
 
 
+def test_fused_build_with_key_window(sbr):
+    """50,000 triangles: inside the fused build's limit but above the 40,960 sorted keys it holds
+    in shared memory, so the tree searches read a window of keys and global memory beyond it."""
+    c = (0.0, 0.03, 1.1)
+    v, f = icosphere(6, 0.25, c)
+    wl = Workload("window", v, np.ascontiguousarray(f[:50000]), radar_single_tx(), ray_grid_for_sphere(c, 0.25, 32),
+                  2, {})
+    tr = oracle.trace(wl.verts, wl.faces, wl.grid, 2)
+    _, paths = gpu_trace(sbr, wl)
+    check_paths(wl, tr, paths)
+
+
 def test_large_mesh_multi_cta_build(sbr):
     """81,920 triangles: above the fused build's limit, so the Morton sort runs over many CTAs
     and the tree is refitted by global arrival counters."""
