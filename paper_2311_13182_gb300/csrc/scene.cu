@@ -269,8 +269,10 @@ constexpr int kBuildTile = 1024;
 constexpr int kTiledMax = 65536;
 // Sorted keys staged in shared memory for the tree searches: all of them up to
 // kKeyWindow, else a window around the tile (a local node's searches stay
-// within twice its range of it; the rest read global memory).
-constexpr int kKeyWindow = 40960;
+// within twice its range of it; the rest read global memory).  Sized so the
+// window, the tile's leaf boxes and k_build_scene's static arrays fit the
+// 227 KB of a CTA.
+constexpr int kKeyWindow = 38912;
 
 // exclusive scan of one value per thread over a CTA of whole warps
 __device__ inline uint32_t block_exclusive_u32(uint32_t v, uint32_t* total, uint32_t* warp_tot) {
@@ -347,8 +349,12 @@ inline size_t top_smem(int n) {
   const int slots = top_slots(n) > 0 ? top_slots(n) : 1;
   return (size_t)words * 8 + (size_t)slots * (sizeof(SBox) + 4 + 4 + 4 + 4);
 }
+// the tree phase's key window, then the tile's leaf boxes (16-byte aligned)
+inline __host__ __device__ size_t window_bytes(int n) {
+  return ((size_t)(n < kKeyWindow ? n : kKeyWindow) * sizeof(uint32_t) + 15) / 16 * 16;
+}
 inline size_t tree_smem(int n) {
-  const size_t keys = (size_t)(n < kKeyWindow ? n : kKeyWindow) * sizeof(uint32_t);
+  const size_t keys = window_bytes(n) + (size_t)kBuildTile * sizeof(SBox);
   const size_t top = top_smem(n);
   return keys > top ? keys : top;
 }
@@ -742,6 +748,8 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
     bx.hi = f3(fmaxf(fmaxf(p0.x, p1.x), p2.x) + pad, fmaxf(fmaxf(p0.y, p1.y), p2.y) + pad,
                fmaxf(fmaxf(p0.z, p1.z), p2.z) + pad);
   }
+  SBox* s_leaf = reinterpret_cast<SBox*>(build_sm + window_bytes(n));  // box of leaf c0+t
+  s_leaf[t] = sbox(bx);
   __syncthreads();
   bool cross = false;
   if (i < n - 1) {
@@ -783,7 +791,7 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
     const int2 ch = s_child[lp];
     const bool is_left = ch.x == me;
     const int sib = is_left ? ch.y : ch.x;
-    const Box sb = sib < 0 ? tri_box_cg(B.tris, ~sib, pad) : unsbox(s_box[sib - c0]);
+    const Box sb = unsbox(sib < 0 ? s_leaf[~sib - c0] : s_box[sib - c0]);  // both in this tile
     if (is_left) write_node(B.nodes, pn, bx, sb);
     else write_node(B.nodes, pn, sb, bx);
     bx = box_union(bx, sb);

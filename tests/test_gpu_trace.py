@@ -137,7 +137,7 @@ def test_tree_tile_boundaries(sbr, nt):
 
 
 def test_fused_build_with_key_window(sbr):
-    """50,000 triangles: inside the fused build's limit but above the 40,960 sorted keys it holds
+    """50,000 triangles: inside the fused build's limit but above the 38,912 sorted keys it holds
     in shared memory, so the tree searches read a window of keys and global memory beyond it."""
     c = (0.0, 0.03, 1.1)
     v, f = icosphere(6, 0.25, c)
@@ -183,3 +183,25 @@ def test_jittered_sampling_matches_oracle(sbr):
     tr = oracle.trace(sqj.verts, sqj.faces, sqj.grid, 3, ray_ids=ids)
     _, paths = gpu_trace(sbr, sqj, ray_ids=ids)
     check_paths(sqj, tr, paths)
+
+
+@pytest.mark.parametrize("nt", [20002, 65536])
+def test_fused_build_is_taken(sbr, nt):
+    """The one-launch cooperative build (k_build_scene, then the 4-wide collapse: two launches)
+    runs for the bench mesh and at its size limit: its shared memory fits a CTA, so it does not
+    fall back to the multi-kernel build."""
+    from sbr_inputs import superquadric_scene
+    if nt == 20002:
+        wl = superquadric_scene(seed=0, G=32)
+        v, f = wl.verts, wl.faces
+    else:
+        v, f = icosphere(6, 0.25, (0.0, 0.0, 1.0))
+        f = np.ascontiguousarray(f[:nt])
+    vt, ft = torch.from_numpy(v).cuda(), torch.from_numpy(f).cuda()
+    scene = sbr.Scene(vt, ft)
+    L = sbr.load()
+    torch.cuda.synchronize()
+    n0 = int(L.sbr_launch_count())
+    scene.update(vt)
+    torch.cuda.synchronize()
+    assert int(L.sbr_launch_count()) - n0 == 2
