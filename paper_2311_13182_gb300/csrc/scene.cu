@@ -461,10 +461,11 @@ __device__ void refit_crossing(int n, const float4* tris, float pad, Node* nodes
 // One CTA of 1024 threads per tile of 1024 triangles, all resident at once
 // (cooperative launch), with grid-wide barriers between the phases: centroid
 // bounds; Morton keys and their digit counts; four stable passes of an 8-bit
-// LSD radix sort (each CTA ranks its tile by digit, publishes the tile's digit
-// counts, and after a barrier scatters with the counts of the tiles before it);
-// then the tiled tree build above.  Data written by other CTAs is read through
-// L2 (ld.cg), never through the non-coherent L1 path.
+// LSD radix sort (each CTA ranks its tile by digit and scatters with the digit
+// counts of the tiles before it, which the previous pass's scatter counted by
+// destination tile: one barrier per pass); then the tiled tree build above.
+// Data written by other CTAs is read through L2 (ld.cg), never through the
+// non-coherent L1 path.
 
 constexpr int kBarrierSpins = 1 << 22;  // ~0.3 s of polling before a barrier gives up
 constexpr int kSortStride = 257;        // padded per-warp row of 256 digit counters
@@ -478,7 +479,7 @@ struct BuildBufs {
   uint32_t* crossing;
   int32_t* bounds;    // [8] ordered ints: centroid min xyz, max xyz, max |coord|
   uint32_t* hist;     // [4*256] digit counts of all keys
-  uint32_t* tile_hist;  // [tiles*256] digit counts per tile (current pass)
+  uint32_t* tile_hist;  // [3][tiles*256] digit counts per tile: pass p's in buffer p % 3
   uint32_t* bar;      // [2] grid barrier: arrivals, generation
   uint32_t* done;     // [1] CTAs finished with the tree
   int32_t* err;
@@ -625,6 +626,14 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
   }
   __syncthreads();
   if (goff[t]) atomicAdd(&B.hist[t], goff[t]);
+  // per-tile digit counts of pass p live in tile_hist[p % 3]: pass 0's are this tile's own
+  // keys; the other two buffers start at zero and collect the scatters' counts
+  const size_t hrow = (size_t)blockIdx.x * 256, hbuf = (size_t)nb * 256;
+  if (t < 256) {
+    B.tile_hist[hrow + t] = goff[t];
+    B.tile_hist[hbuf + hrow + t] = 0u;
+    B.tile_hist[2 * hbuf + hrow + t] = 0u;
+  }
   if (!grid_sync(B.bar, nb, B.err)) return;
   if (w < 4) {  // warp p: start of each digit of place p in the sorted array
     uint32_t c8[8], sum = 0;
@@ -647,7 +656,9 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
     }
   }
 
-  // 3. four stable passes; pass p moves keys[p & 1] to keys[(p + 1) & 1]
+  // 3. four stable passes; pass p moves keys[p & 1] to keys[(p + 1) & 1], one grid barrier
+  // each: the tile counts it needs were added by the previous pass's scatter, which also
+  // adds those of the next pass, by destination tile, into tile_hist[(p + 1) % 3]
   const uint32_t lt = (1u << lane) - 1u;
   const int rn = min(n - c0, kBuildTile);
   uint32_t* row = cnt + w * kSortStride;
@@ -681,7 +692,6 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
       if (lane == 31) tot[dd] = x;
     }
     __syncthreads();
-    if (t < 256) B.tile_hist[(size_t)blockIdx.x * 256 + t] = tot[t];
     if (w == 0) warp_scan256(tot, lstart);
     __syncthreads();
     if (live) {
@@ -689,19 +699,23 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
       stage_k[q] = key;
       stage_v[q] = val;
     }
-    if (!grid_sync(B.bar, nb, B.err)) return;
+    const uint32_t* th = B.tile_hist + (size_t)(p % 3) * hbuf;
     if (t < 256) {  // digit t's output start for this tile: whole-array start + earlier tiles
       uint32_t pre = 0;
-      for (uint32_t c2 = 0; c2 < blockIdx.x; ++c2) pre += __ldcg(&B.tile_hist[(size_t)c2 * 256 + t]);
+      for (uint32_t c2 = 0; c2 < blockIdx.x; ++c2) pre += __ldcg(&th[(size_t)c2 * 256 + t]);
       gbase[t] = goff[256 * p + t] + pre - lstart[t];
+      // this tile's row of the buffer pass p + 1 fills, read last by pass p - 2
+      if (p == 1) B.tile_hist[hrow + t] = 0u;
     }
     __syncthreads();
+    uint32_t* th_next = B.tile_hist + (size_t)((p + 1) % 3) * hbuf;
     if (t < rn) {
       const uint32_t k2 = stage_k[t];
       const uint32_t pos = gbase[(k2 >> shift) & 255u] + (uint32_t)t;
       if (pos < (uint32_t)n) {  // always true when the counts match the keys
         ((p & 1) ? B.keys[0] : B.keys[1])[pos] = k2;
         ((p & 1) ? B.vals[0] : B.vals[1])[pos] = stage_v[t];
+        if (p < 3) atomicAdd(&th_next[(size_t)(pos / kBuildTile) * 256 + ((k2 >> (shift + 8)) & 255u)], 1u);
       }
     }
     if (!grid_sync(B.bar, nb, B.err)) return;
@@ -957,7 +971,7 @@ size_t layout(sbr_scene* s, void* mem, int32_t nt) {
   s->hist = c.take<uint32_t>(4 * 256);
   s->done = c.take<uint32_t>(1);
   s->bar = c.take<uint32_t>(2);
-  s->tile_hist = c.take<uint32_t>((size_t)256 * ((n + kBuildTile - 1) / kBuildTile));
+  s->tile_hist = c.take<uint32_t>((size_t)3 * 256 * ((n + kBuildTile - 1) / kBuildTile));
   s->sort_scratch = c.take<char>(sort_scratch_bytes(n));
   return c.bytes();
 }

@@ -58,7 +58,7 @@ struct sbr_scene {
   uint32_t* hist;      // [4*256] Morton key digit counts (8-bit places) for the sort
   uint32_t* done;      // [1] CTAs of the cooperative build that have finished the tree
   uint32_t* bar;       // [2] grid barrier of the cooperative build: arrivals, generation
-  uint32_t* tile_hist; // [tiles*256] per-tile digit counts of the cooperative sort
+  uint32_t* tile_hist; // [3][tiles*256] per-tile digit counts of the cooperative sort (pass p: p % 3)
   int coop;            // build with one cooperative launch (all tiles resident at once)
   void* sort_scratch;
   size_t bytes;
