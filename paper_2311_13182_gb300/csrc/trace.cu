@@ -796,6 +796,76 @@ __global__ void __launch_bounds__(128) k_trace_coop(const float4* __restrict__ t
   }
 }
 
+// Few rays (reconstruction steps, small requests): one warp per ray from its
+// first bounce on, every nearest-hit search a cooperative traversal.  A
+// thread per ray would leave most SMs idle and end when the longest ray's
+// dependent node fetches end; a warp per ray fills the GPU and splits each
+// search over 32 lanes.  The candidates are ordered by the same total rule as
+// in k_trace, so the hits are the same.
+#ifndef SBR_TRACE_WARP_MAX
+#define SBR_TRACE_WARP_MAX 32768
+#endif
+constexpr int64_t kWarpRaysMax = SBR_TRACE_WARP_MAX;  // rays up to which k_trace_warp runs
+
+template <bool kCount>
+__global__ void __launch_bounds__(128) k_trace_warp(const float4* __restrict__ tris,
+                                                    const Node4* __restrict__ nodes, int nt, GridArg g,
+                                                    const int32_t* __restrict__ ray_ids, int n_rays, int K,
+                                                    sbr_hit* __restrict__ hits, float4* __restrict__ hit_pos,
+                                                    float* __restrict__ ray_w, int32_t* __restrict__ nvalid,
+                                                    unsigned long long* __restrict__ counts) {
+  __shared__ int lists[4][kCoopList];
+  const int lane = threadIdx.x & 31;
+  int* list = lists[threadIdx.x >> 5];
+  int n_nodes = 0, n_tris = 0, n_trav = 0;
+  const int slot = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (slot < n_rays) {  // the same for the whole warp
+    ff3 ray_o, ray_d;
+    Ray r(ray_o, ray_d);
+    r.g = &g;
+    r.rid = ray_ids ? ray_ids[slot] : slot;
+    r.has_ff = false;
+    r.skip = -1;
+    r.o = ff3_arr(g.o);
+    r.of = ff3_hi(r.o);
+    float omega;
+    r.df = grid_dir_f32(g, r.rid, omega);
+    set_idir(r);
+    if (lane == 0) ray_w[slot] = omega;
+    int nh = 0;
+    for (int k = 0; k < K; ++k) {
+      Best b;
+      init_best(b);
+      if (nt > 0) {
+        if (kCount && lane == 0) ++n_trav;
+        if (lane == 0) list[0] = nt > 1 ? 0 : ~0;
+        __syncwarp();
+        b = coop_nearest<kCount>(tris, nodes, nt, r, b, list, 1, n_nodes, n_tris);
+        __syncwarp();  // every lane is done with the list
+      }
+      if (b.id < 0) {
+        if (lane == 0) record_miss(hits, hit_pos, slot, k, K);
+        break;
+      }
+      record_hit(tris, r, b, hits, hit_pos, (size_t)slot * K + k, lane == 0);
+      ++nh;
+    }
+    if (lane == 0) nvalid[slot] = nh;
+  }
+  if (kCount) {
+    for (int o = 16; o; o >>= 1) {
+      n_nodes += __shfl_xor_sync(0xffffffffu, n_nodes, o);
+      n_tris += __shfl_xor_sync(0xffffffffu, n_tris, o);
+      n_trav += __shfl_xor_sync(0xffffffffu, n_trav, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&counts[0], (unsigned long long)n_nodes);
+      atomicAdd(&counts[1], (unsigned long long)n_tris);
+      atomicAdd(&counts[2], (unsigned long long)n_trav);
+    }
+  }
+}
+
 __device__ inline ff3 ld_hit(const float4* __restrict__ hp, size_t sl, float& cosv) {
   const float4 p = hp[2 * sl], q = hp[2 * sl + 1];
   cosv = q.z;
@@ -1132,9 +1202,20 @@ static sbr_status trace_impl(const sbr_scene* scene, const sbr_radar_cfg* radar,
   unsigned int* dctr = dump_counters(paths);
   SBR_CUDA(cudaMemsetAsync(dctr, 0, 2 * sizeof(unsigned int), st));
   float4* hp = reinterpret_cast<float4*>(paths->hit_pos);
-  ::sbr::note_launch();
-  if (d_counts) {
-    SBR_CUDA(cudaMemsetAsync(d_counts, 0, 4 * sizeof(unsigned long long), st));
+  if (d_counts) SBR_CUDA(cudaMemsetAsync(d_counts, 0, 4 * sizeof(unsigned long long), st));
+  if (R <= kWarpRaysMax) {  // one warp per ray (no hand-over needed)
+    const int nbw = blocks(R * 32, 128);
+    ::sbr::note_launch();
+    if (d_counts)
+      k_trace_warp<true><<<nbw, 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, d_ray_ids, (int)R,
+                                               max_bounces, paths->hits, hp, paths->ray_weight, paths->ray_first,
+                                               d_counts);
+    else
+      k_trace_warp<false><<<nbw, 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, d_ray_ids, (int)R,
+                                                max_bounces, paths->hits, hp, paths->ray_weight, paths->ray_first,
+                                                nullptr);
+  } else if (d_counts) {
+    ::sbr::note_launch();
     k_trace<true><<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, d_ray_ids, (int)R,
                                                   max_bounces, paths->hits, hp, paths->ray_weight, paths->ray_first,
                                                   dumps, dctr, d_counts, scene->top, scene->top_n);
@@ -1142,6 +1223,7 @@ static sbr_status trace_impl(const sbr_scene* scene, const sbr_radar_cfg* radar,
     k_trace_coop<true><<<coop_grid(), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, max_bounces, dumps,
                                                     dctr, dctr + 1, paths->hits, hp, paths->ray_first, d_counts);
   } else {
+    ::sbr::note_launch();
     k_trace<false><<<blocks(R, 128), 128, 0, st>>>(scene->tris, scene->nodes4, scene->nt, g, d_ray_ids, (int)R,
                                                    max_bounces, paths->hits, hp, paths->ray_weight,
                                                    paths->ray_first, dumps, dctr, nullptr, scene->top, scene->top_n);
