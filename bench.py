@@ -391,7 +391,7 @@ def rooflines(stage_ms, wl, P, counts, peaks, src):
       antenna) + 4 B per path) per second against the HBM copy rate: the working set is L2-resident,
       so these bytes are served mostly by L1/L2 (a bytes-served rate, not DRAM);
       dram: the call's DRAM bytes (ncu) per second against the HBM copy rate.
-    synthesis (k_nufft_spread + k_nufft_finish + k_reduce; Eq. 8 as a type-1 non-uniform FFT):
+    synthesis (k_nufft_spread + k_nufft_finish; Eq. 8 as a type-1 non-uniform FFT):
       dram as above; speedup_vs_direct_sum: Eq. 8 terms (path, antenna, sample) per second over the
       FP32-pipe bound of a term-by-term kernel (152 SMs x 128 lanes x f_max / 4 lane-ops per term)."""
     V, Ns = wl.radar.n_virt, wl.radar.n_samples
@@ -429,7 +429,7 @@ def rooflines(stage_ms, wl, P, counts, peaks, src):
     ach, frac = issue("synthesize", t_sy)
     fp32_terms = 152 * 128 * mhz * 1e6 / 4
     rec = P * V * 16
-    synth = {"kernel": "k_nufft_spread (+ k_nufft_finish, k_reduce)", "bound": "alu", "limiter": "issue slots",
+    synth = {"kernel": "k_nufft_spread (+ k_nufft_finish)", "bound": "alu", "limiter": "issue slots",
              "achieved": ach, "peak": issue_peak, "unit": "warp-inst/s", "frac": frac,
              "inst_per_launch": ctr.get("synthesize", {}).get("inst_per_launch"),
              "traffic": ctr.get("synthesize", {}).get("dram_bytes_per_launch"),

@@ -132,9 +132,18 @@ __global__ void k_lap_delta(const float* __restrict__ v, int nv, const int32_t* 
   sq[i] = dx * dx + dy * dy + dz * dz;
 }
 
-// dL/dv_k = weight (2 / nv) (delta_k - sum_{i in N(k)} delta_i / deg_i)
+// dL/dv_k = weight (2 / nv) (delta_k - sum_{i in N(k)} delta_i / deg_i); the first
+// CTA also adds lscale * sum_i sq_i (the loss term) to *loss, in a fixed order.
 __global__ void k_lap_grad(const float* __restrict__ delta, int nv, const int32_t* __restrict__ off,
-                           const int32_t* __restrict__ adj, float scale, float* __restrict__ g) {
+                           const int32_t* __restrict__ adj, float scale, float* __restrict__ g,
+                           const float* __restrict__ sq, float lscale, float* __restrict__ loss) {
+  __shared__ float red[32];
+  if (blockIdx.x == 0) {
+    float s = 0.f;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) s += sq[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) *loss += lscale * s;
+  }
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nv) return;
   float gx = delta[3 * k], gy = delta[3 * k + 1], gz = delta[3 * k + 2];
@@ -148,14 +157,6 @@ __global__ void k_lap_grad(const float* __restrict__ delta, int nv, const int32_
   g[3 * k] += scale * gx;
   g[3 * k + 1] += scale * gy;
   g[3 * k + 2] += scale * gz;
-}
-
-__global__ void k_sum_into(const float* __restrict__ x, int n, float scale, float* __restrict__ out) {
-  __shared__ float red[32];
-  float s = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) *out += scale * s;
 }
 
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -251,9 +252,8 @@ extern "C" sbr_status sbr_laplacian(const float* d_verts, int32_t nv, const int3
   ::sbr::note_launch();
   k_lap_delta<<<b, 256, 0, st>>>(d_verts, nv, d_off, d_adj, delta, sq);
   ::sbr::note_launch();
-  k_sum_into<<<1, 1024, 0, st>>>(sq, nv, weight / (float)nv, d_loss);
-  ::sbr::note_launch();
-  k_lap_grad<<<b, 256, 0, st>>>(delta, nv, d_off, d_adj, 2.f * weight / (float)nv, d_gverts);
+  k_lap_grad<<<b, 256, 0, st>>>(delta, nv, d_off, d_adj, 2.f * weight / (float)nv, d_gverts, sq, weight / (float)nv,
+                                d_loss);
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;
 }

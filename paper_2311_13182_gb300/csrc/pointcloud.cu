@@ -679,18 +679,13 @@ __global__ void k_points_bwd(const float* __restrict__ Pw, PointArg pa, const in
   if (kPass == 0) fix_note_warp(fs.max_bits, lmax);  // every lane of the warp reaches this
 }
 
-// dPw[i] = acc[i] 2^-E
-__global__ void k_fix_finish(FixScatter fs, int n, float* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = fix_get(fs.acc[i], fix_exp(*fs.max_bits, fs.log2n));
-}
-
 // dX[v,d,k] = sum_rho conj(W[rho,v]) 2 Y[rho,d,k] dPw[rho,k] over the R = 8 APT angle
-// rows, Y recomputed from X.
+// rows, Y recomputed from X.  dPw is read as floats, or, when fs.acc is set, straight
+// from the point adjoint's fixed-point sums (acc 2^-E).
 template <int APT>
 __global__ void __launch_bounds__(256) k_angle_bwd(const float2* __restrict__ X,
                                                    const Steer xl,
-                                                   const float* __restrict__ dPw, int V, int C,
+                                                   const float* __restrict__ dPw, FixScatter fs, int V, int C,
                                                    int Ns, float2* __restrict__ dX) {
   extern __shared__ float2 sm[];
   constexpr int R = 8 * APT;
@@ -714,7 +709,8 @@ __global__ void __launch_bounds__(256) k_angle_bwd(const float2* __restrict__ X,
       yr = fmaf(w.x, x.x, fmaf(-w.y, x.y, yr));
       yi = fmaf(w.x, x.y, fmaf(w.y, x.x, yi));
     }
-    const float s = 2.f * dPw[(size_t)a * Ns + k0 + kk];
+    const size_t cell = (size_t)a * Ns + k0 + kk;
+    const float s = 2.f * (fs.acc ? fix_get(fs.acc[cell], fix_exp(*fs.max_bits, fs.log2n)) : dPw[cell]);
     sg[a * kKT + kk] = make_float2(s * yr, s * yi);
   }
   __syncthreads();
@@ -861,14 +857,15 @@ void launch_angle_power(const float2* X, const Steer& xl, int V, int C, int Ns, 
 }
 
 template <int APT>
-void launch_angle_bwd(const float2* X, const Steer& xl, const float* dpw, int V, int C, int Ns, float2* dX,
+void launch_angle_bwd(const float2* X, const Steer& xl, const float* dpw, const FixScatter& fs, int V, int C, int Ns,
+                      float2* dX,
                       cudaStream_t st) {
   const int R = 8 * APT;
   const size_t sm = sizeof(float2) * ((size_t)R * V + (size_t)V * kKT + (size_t)R * kKT);
   dim3 grid(Ns / kKT, C);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_angle_bwd<APT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ::sbr::note_launch();
-  k_angle_bwd<APT><<<grid, 256, sm, st>>>(X, xl, dpw, V, C, Ns, dX);
+  k_angle_bwd<APT><<<grid, 256, sm, st>>>(X, xl, dpw, fs, V, C, Ns, dX);
 }
 
 cudaError_t fft_rows(const float2* in, float2* out, int rows, int n, float sign, cudaStream_t st) {
@@ -1071,20 +1068,21 @@ extern "C" sbr_status sbr_pc_check(const sbr_radar_cfg* radar, const sbr_cfar_cf
 
 namespace sbr {
 namespace {
-// dL/dcube from dL/dPw (L.dpw): dY = 2 Y dPw, dX = W^H dY, then the adjoints of the
-// forward DFTs (unnormalised inverse transforms, in place).
-sbr_status cube_adjoint(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const Layout& L, float* d_gcube,
-                        cudaStream_t st) {
+// dL/dcube from dL/dPw (L.dpw, or the fixed-point sums in fs when fs.acc is set):
+// dY = 2 Y dPw, dX = W^H dY, then the adjoints of the forward DFTs (unnormalised
+// inverse transforms, in place).
+sbr_status cube_adjoint(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const Layout& L, const FixScatter& fs,
+                        float* d_gcube, cudaStream_t st) {
   const int V = radar->n_tx * radar->n_rx, C = radar->n_chirps, Ns = radar->n_samples, R = angle_rows(cfar);
   const Steer xl = steering_table(radar, cfar);
   float2* g = reinterpret_cast<float2*>(d_gcube);
   switch (R / 8) {
-    case 1: launch_angle_bwd<1>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
-    case 2: launch_angle_bwd<2>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
-    case 4: launch_angle_bwd<4>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
-    case 8: launch_angle_bwd<8>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
-    case 16: launch_angle_bwd<16>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
-    case 32: launch_angle_bwd<32>(L.spec, xl, L.dpw, V, C, Ns, g, st); break;
+    case 1: launch_angle_bwd<1>(L.spec, xl, L.dpw, fs, V, C, Ns, g, st); break;
+    case 2: launch_angle_bwd<2>(L.spec, xl, L.dpw, fs, V, C, Ns, g, st); break;
+    case 4: launch_angle_bwd<4>(L.spec, xl, L.dpw, fs, V, C, Ns, g, st); break;
+    case 8: launch_angle_bwd<8>(L.spec, xl, L.dpw, fs, V, C, Ns, g, st); break;
+    case 16: launch_angle_bwd<16>(L.spec, xl, L.dpw, fs, V, C, Ns, g, st); break;
+    case 32: launch_angle_bwd<32>(L.spec, xl, L.dpw, fs, V, C, Ns, g, st); break;
     default: set_error("%d angle rows unsupported", R); return SBR_ERR_UNSUPPORTED;
   }
   SBR_CUDA(cudaGetLastError());
@@ -1136,7 +1134,7 @@ extern "C" sbr_status sbr_image_loss(const sbr_radar_cfg* radar, const sbr_cfar_
   k_image_mse<<<1, kMseThreads, 0, st>>>(L.power, d_target, cells, d_loss, d_gcube ? L.dpw : nullptr);
   SBR_CUDA(cudaGetLastError());
   if (!d_gcube) return SBR_OK;
-  return cube_adjoint(radar, cfar, L, d_gcube, st);
+  return cube_adjoint(radar, cfar, L, FixScatter{nullptr, nullptr, 0}, d_gcube, st);
 }
 
 extern "C" sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar,
@@ -1166,7 +1164,5 @@ extern "C" sbr_status sbr_pointcloud_bwd(const sbr_radar_cfg* radar, const sbr_c
   k_points_bwd<0><<<nb, 256, 0, st>>>(L.power, pa, L.argmax, L.peak_cell, L.n_points, gp, fs);
   ::sbr::note_launch();
   k_points_bwd<1><<<nb, 256, 0, st>>>(L.power, pa, L.argmax, L.peak_cell, L.n_points, gp, fs);
-  ::sbr::note_launch();
-  k_fix_finish<<<(cells + 255) / 256, 256, 0, st>>>(fs, cells, L.dpw);
-  return cube_adjoint(radar, cfar, L, d_gcube, st);
+  return cube_adjoint(radar, cfar, L, fs, d_gcube, st);
 }

@@ -705,14 +705,15 @@ __global__ void __launch_bounds__(kNuThreads) k_nufft_spread(const float4* __res
 // point, each over every such CTA with four interleaved sums, then the threads'
 // sums in order) into bsum; the last CTA of the antenna to finish (a counter per
 // antenna, zeroed by the spreading kernel) runs the M-point FFT and the division
-// by Psi(n'/M) and writes S[v][n] (one chirp).
+// by Psi(n'/M) and writes S[v][n] into the cube: chirp `only` (a moving scene),
+// else every chirp (a static scene's chirps are equal).
 constexpr int kNuFinThreads = 1024;
 constexpr int kNuFinSlice = 128;
 __global__ void __launch_bounds__(kNuFinThreads) k_nufft_finish(const float2* __restrict__ grids, int V, int Q,
                                                                 int Ns, int log_m, PsiQuad pq,
                                                                 float2* __restrict__ bsum,
                                                                 unsigned int* __restrict__ cnt,
-                                                                float2* __restrict__ samples) {
+                                                                float2* __restrict__ cube, int C, int only) {
   extern __shared__ float2 sg[];  // [M] grid, [M / 2] twiddles, [kNuFinThreads] per-thread sums
   __shared__ int s_last;
   const int M = 1 << log_m, slice = M < kNuFinSlice ? M : kNuFinSlice, S = M / slice;
@@ -770,7 +771,12 @@ __global__ void __launch_bounds__(kNuFinThreads) k_nufft_finish(const float2* __
     for (int i = 0; i < kNuQuad; ++i) ph = fmaf(pq.wpsi[i], cospif(2.f * xi * pq.x[i]), ph);
     const float2 B = sg[(n - h) & (M - 1)];
     const float inv = 1.f / ph;
-    samples[(size_t)v * Ns + n] = make_float2(B.x * inv, B.y * inv);
+    const float2 val = make_float2(B.x * inv, B.y * inv);
+    if (only >= 0) {
+      cube[((size_t)v * C + only) * Ns + n] = val;
+    } else {
+      for (int c = 0; c < C; ++c) cube[((size_t)v * C + c) * Ns + n] = val;
+    }
   }
 }
 
@@ -924,7 +930,7 @@ void nufft_shape(int V, int Ns, int64_t cap, int* Qn) {
 
 // Workspace: per-CTA partial sums of the direct kernels, the chirp-summed
 // upstream gradient of the adjoint, and, for the non-uniform FFT, the CTAs'
-// grids and the finished samples of one chirp.
+// grids, their sum and the finishing counters.
 size_t ws_layout(const sbr_radar_cfg* radar, int64_t cap, int* Q, int* Qn = nullptr) {
   const int V = radar->n_tx * radar->n_rx, Ns = radar->n_samples;
   grid_shape(V, Ns, cap, Q);
@@ -935,7 +941,6 @@ size_t ws_layout(const sbr_radar_cfg* radar, int64_t cap, int* Q, int* Qn = null
   c.take<float2>((size_t)V * (*Q) * Ns);       // per-CTA partial sums
   c.take<float2>((size_t)V * Ns);              // chirp-summed upstream gradient
   c.take<float2>((size_t)V * qn * 2 * Ns);     // non-uniform FFT: the CTAs' grids
-  c.take<float2>((size_t)V * Ns);              // non-uniform FFT: samples of one chirp
   c.take<float2>((size_t)V * 2 * Ns);          // non-uniform FFT: the summed grids
   c.take<unsigned int>((size_t)V);             // non-uniform FFT: finishing counters
   return c.bytes();
@@ -957,7 +962,6 @@ struct SynthWs {
   float2* partial;
   float2* gsum;
   float2* grids;
-  float2* samples;
   float2* bsum;
   unsigned int* fin_cnt;
   int Q, Qn;
@@ -977,7 +981,6 @@ sbr_status bind_ws(const sbr_radar_cfg* radar, int64_t cap, void* ws, size_t byt
   w->partial = c.take<float2>((size_t)V * Q * Ns);
   w->gsum = c.take<float2>((size_t)V * Ns);
   w->grids = c.take<float2>((size_t)V * Qn * 2 * Ns);
-  w->samples = c.take<float2>((size_t)V * Ns);
   w->bsum = c.take<float2>((size_t)V * 2 * Ns);
   w->fin_cnt = c.take<unsigned int>((size_t)V);
   w->Q = Q;
@@ -1005,9 +1008,7 @@ sbr_status launch_moving(sbr_phase_mode mode, const sbr_paths* p, const sbr_rada
                                                                    w.fin_cnt, p->path_rate, cnu, ceps);
       ::sbr::note_launch();
       k_nufft_finish<<<V * slices, kNuFinThreads, sizeof(float2) * (3 * (size_t)Ns + kNuFinThreads), st>>>(
-          w.grids, V, w.Qn, Ns, log_m, psi_quad(), w.bsum, w.fin_cnt, w.samples);
-      ::sbr::note_launch();
-      k_reduce<<<dim3((V * Ns + 255) / 256, 1), 256, 0, st>>>(w.samples, V, 1, Ns, C, cube, c);
+          w.grids, V, w.Qn, Ns, log_m, psi_quad(), w.bsum, w.fin_cnt, cube, C, c);
     }
     return SBR_OK;
   }
@@ -1035,7 +1036,7 @@ sbr_status launch_moving(sbr_phase_mode mode, const sbr_paths* p, const sbr_rada
   return SBR_ERR_UNSUPPORTED;
 }
 
-// Split-phase samples by the non-uniform FFT: spread, finish, one chirp -> all chirps.
+// Split-phase samples by the non-uniform FFT: spread, then finish (one chirp, written to all chirps).
 void launch_nufft(const sbr_paths* p, const sbr_radar_cfg* r, const SynthWs& w, float2* cube, cudaStream_t st) {
   const int V = p->n_virt, Ns = r->n_samples;
   int log_m = 0;
@@ -1049,9 +1050,7 @@ void launch_nufft(const sbr_paths* p, const sbr_radar_cfg* r, const SynthWs& w, 
   const int M = 2 * Ns, slices = M < kNuFinSlice ? 1 : M / kNuFinSlice;
   ::sbr::note_launch();
   k_nufft_finish<<<V * slices, kNuFinThreads, sizeof(float2) * (3 * (size_t)Ns + kNuFinThreads), st>>>(
-      w.grids, V, w.Qn, Ns, log_m, psi_quad(), w.bsum, w.fin_cnt, w.samples);
-  ::sbr::note_launch();
-  k_reduce<<<reduce_grid(V, Ns, r->n_chirps), 256, 0, st>>>(w.samples, V, 1, Ns, r->n_chirps, cube);
+      w.grids, V, w.Qn, Ns, log_m, psi_quad(), w.bsum, w.fin_cnt, cube, r->n_chirps, -1);
 }
 
 template <int M>
@@ -1215,9 +1214,13 @@ extern "C" sbr_status sbr_synthesize_bwd(const sbr_paths* paths, const sbr_radar
   if (rs != SBR_OK) return rs;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int V = paths->n_virt, Ns = radar->n_samples, C = radar->n_chirps;
-  ::sbr::note_launch();
-  k_chirp_sum<<<(V * Ns + 255) / 256, 256, 0, st>>>(reinterpret_cast<const float2*>(d_gcube), V, C,
-                                                     Ns, w.gsum);
+  // the upstream gradient summed over the (equal) chirps; one chirp needs no sum
+  const float2* gs = reinterpret_cast<const float2*>(d_gcube);
+  if (C > 1) {
+    ::sbr::note_launch();
+    k_chirp_sum<<<(V * Ns + 255) / 256, 256, 0, st>>>(gs, V, C, Ns, w.gsum);
+    gs = w.gsum;
+  }
   const int64_t cap = paths->path_cap;
   if (cap > 0) {
     dim3 grid((unsigned)((cap + 255) / 256), (unsigned)V);
@@ -1225,7 +1228,7 @@ extern "C" sbr_status sbr_synthesize_bwd(const sbr_paths* paths, const sbr_radar
     const double bcn = radar->bandwidth / (kC * Ns);
     ::sbr::note_launch();
     k_synth_bwd<<<grid, 256, Ns * sizeof(float2), st>>>(
-        reinterpret_cast<const float4*>(paths->prep), cap, paths->count, Ns, w.gsum,
+        reinterpret_cast<const float4*>(paths->prep), cap, paths->count, Ns, gs,
         (float)lam_inv, (float)bcn, d_glen, d_gamp, d_gphase);
   }
   SBR_CUDA(cudaGetLastError());
