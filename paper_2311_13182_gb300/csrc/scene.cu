@@ -513,6 +513,18 @@ __device__ bool grid_sync(uint32_t* bar, uint32_t nblocks, int32_t* err) {
   return s_ok != 0;
 }
 
+// Barrier between the build's phases: a thread-block cluster's hardware barrier
+// (release / acquire at cluster scope) when the whole grid is one cluster, else
+// the grid-wide barrier above.  A cluster's CTAs are resident together and take
+// no early exit before the last barrier, so the cluster barrier always completes.
+__device__ inline bool build_sync(uint32_t* bar, uint32_t nblocks, int32_t* err, bool cluster) {
+  if (cluster) {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    return true;
+  }
+  return grid_sync(bar, nblocks, err);
+}
+
 // exclusive scan of 256 counts held in shared memory, by one warp (8 per lane)
 __device__ inline void warp_scan256(const uint32_t* in, uint32_t* out) {
   const int lane = threadIdx.x & 31;
@@ -546,7 +558,7 @@ inline size_t build_smem(int n) {
 
 __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restrict__ verts, int nv,
                                                             const int32_t* __restrict__ faces, int n,
-                                                            BuildBufs B, int slots) {
+                                                            BuildBufs B, int slots, bool cluster) {
   __shared__ int32_t s_par_leaf[kBuildTile];  // in-tile parent of leaf c0+t, else -1
   __shared__ int32_t s_par_node[kBuildTile];  // in-tile local parent of node c0+t, else -1
   __shared__ int2 s_child[kBuildTile];
@@ -604,7 +616,7 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
       else if (lane < 7) atomicMax(&B.bounds[lane], mine);
     }
   }
-  if (!grid_sync(B.bar, nb, B.err)) return;
+  if (!build_sync(B.bar, nb, B.err, cluster)) return;
 
   // 2. Morton keys and the digit counts of all four places
   uint32_t* cnt = reinterpret_cast<uint32_t*>(build_sm);  // [32][kSortStride]
@@ -634,7 +646,7 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
     B.tile_hist[hbuf + hrow + t] = 0u;
     B.tile_hist[2 * hbuf + hrow + t] = 0u;
   }
-  if (!grid_sync(B.bar, nb, B.err)) return;
+  if (!build_sync(B.bar, nb, B.err, cluster)) return;
   if (w < 4) {  // warp p: start of each digit of place p in the sorted array
     uint32_t c8[8], sum = 0;
 #pragma unroll
@@ -718,7 +730,7 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
         if (p < 3) atomicAdd(&th_next[(size_t)(pos / kBuildTile) * 256 + ((k2 >> (shift + 8)) & 255u)], 1u);
       }
     }
-    if (!grid_sync(B.bar, nb, B.err)) return;
+    if (!build_sync(B.bar, nb, B.err, cluster)) return;
   }
 
   // 4. tree: this tile's triangles in sorted order, its nodes, the local refit
@@ -983,7 +995,33 @@ sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
                 s->bounds, s->hist, s->tile_hist, s->bar, s->done, s->err};
     int slots = top_slots(nt), n = nt, nvv = nv;
     const int32_t* faces = s->faces;
-    void* args[] = {(void*)&verts, (void*)&nvv, (void*)&faces, (void*)&n, (void*)&B, (void*)&slots};
+    if (s->cluster) {  // the whole grid one cluster: hardware barriers between the phases
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(blocks(nt, kBuildTile));
+      cfg.blockDim = dim3(kBuildTile);
+      cfg.dynamicSmemBytes = build_smem(nt);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = blocks(nt, kBuildTile);
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      ::sbr::note_launch();
+      SBR_CUDA(cudaLaunchKernelEx(&cfg, k_build_scene, verts, nv, faces, nt, B, slots, true));
+      ::sbr::note_launch();
+      k_collapse4<<<blocks(nt - 1, 128), 128, 0, st>>>(s->nodes, nt, s->nodes4);
+      if (kTopLevels > 0) {
+        ::sbr::note_launch();
+        k_top_table<<<1, 128, 0, st>>>(s->nodes4, nt, s->top, s->top_n);
+      }
+      SBR_CUDA(cudaGetLastError());
+      return SBR_OK;
+    }
+    bool no_cluster = false;
+    void* args[] = {(void*)&verts, (void*)&nvv, (void*)&faces, (void*)&n, (void*)&B, (void*)&slots,
+                    (void*)&no_cluster};
     ::sbr::note_launch();
     SBR_CUDA(cudaLaunchCooperativeKernel((const void*)k_build_scene, dim3(blocks(nt, kBuildTile)),
                                          dim3(kBuildTile), args, build_smem(nt), st));
@@ -1078,6 +1116,27 @@ extern "C" sbr_status sbr_scene_create(const float* d_verts, int32_t nv, const i
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_scene, kBuildTile, build_smem(nt));
       s->coop = e == cudaSuccess && coop && (int64_t)per_sm * sms >= blocks(nt, kBuildTile);
       if (e != cudaSuccess) (void)cudaGetLastError();  // not fatal: the multi-kernel build runs
+      // up to 16 tiles the grid can run as one cluster, when the GPU can hold it
+      const int tiles = blocks(nt, kBuildTile);
+      s->cluster = 0;
+      if (s->coop && tiles <= 16) {
+        cudaError_t ce = cudaFuncSetAttribute(k_build_scene, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(tiles);
+        cfg.blockDim = dim3(kBuildTile);
+        cfg.dynamicSmemBytes = build_smem(nt);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = tiles;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveClusters(&clusters, k_build_scene, &cfg);
+        if (ce == cudaSuccess && clusters >= 1) s->cluster = 1;
+        else (void)cudaGetLastError();  // the cooperative launch stays
+      }
       e = cudaSuccess;
     }
     // counters of the cooperative build start cleared; bounds start empty

@@ -60,6 +60,7 @@ struct sbr_scene {
   uint32_t* bar;       // [2] grid barrier of the cooperative build: arrivals, generation
   uint32_t* tile_hist; // [3][tiles*256] per-tile digit counts of the cooperative sort (pass p: p % 3)
   int coop;            // build with one cooperative launch (all tiles resident at once)
+  int cluster;         // ... launched as one thread-block cluster (at most 16 tiles): hardware barriers
   void* sort_scratch;
   size_t bytes;
   // materials (sbr_scene_set_materials): 0 = perfect conductors everywhere
