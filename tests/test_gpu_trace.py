@@ -205,3 +205,23 @@ def test_fused_build_is_taken(sbr, nt):
     scene.update(vt)
     torch.cuda.synchronize()
     assert int(L.sbr_launch_count()) - n0 == 2
+
+
+@pytest.mark.parametrize("G", [64, 200])
+def test_trace_counts_variant(sbr, G):
+    """sbr_trace_counts (the counting variant of the trace, warp per ray at 64^2 rays, thread per
+    ray at 200^2): the same hits as sbr_trace, and exactly one traversal per ray and bounce until
+    the ray's first miss; node and triangle counts positive."""
+    from sbr_inputs import superquadric_scene
+    wl = superquadric_scene(seed=2, G=G)
+    v, f = torch.from_numpy(wl.verts).cuda(), torch.from_numpy(wl.faces).cuda()
+    scene = sbr.Scene(v, f)
+    a = sbr.trace(scene, wl.radar, wl.grid, wl.max_bounces)
+    b = sbr.PathBuffers(wl.grid.n_rays, wl.max_bounces, wl.radar.n_virt)
+    counts = sbr.sim.trace_counts(scene, wl.radar, wl.grid, wl.max_bounces, out=b)
+    torch.cuda.synchronize()
+    assert torch.equal(a.hits()[0], b.hits()[0])
+    nh = (a.hits()[0] >= 0).sum(dim=1).cpu().numpy()
+    expect = int(np.minimum(nh + 1, wl.max_bounces).sum())
+    nodes, tris, trav = counts
+    assert trav == expect and nodes > 0 and tris > 0
