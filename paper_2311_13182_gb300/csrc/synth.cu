@@ -818,7 +818,15 @@ const PsiQuad& psi_quad() {
   return pq;
 }
 
-inline bool nufft_for(sbr_phase_mode mode, int Ns) { return mode == SBR_PHASE_SPLIT && Ns <= kNuMaxSamples; }
+// Few (path, antenna) records: the direct kernels, whose one pass over the records
+// costs less than the non-uniform FFT's spreading, finishing sum and FFT chain.
+#ifndef SBR_NUFFT_MIN_RECORDS
+#define SBR_NUFFT_MIN_RECORDS 65536
+#endif
+constexpr int64_t kNuMinRecords = SBR_NUFFT_MIN_RECORDS;
+inline bool nufft_for(sbr_phase_mode mode, int Ns, int64_t records) {
+  return mode == SBR_PHASE_SPLIT && Ns <= kNuMaxSamples && records >= kNuMinRecords;
+}
 
 // Launch-shape queries are cached per device ordinal (kernel attributes such as
 // a raised shared-memory limit are per device too); ordinals at or beyond
@@ -1104,7 +1112,7 @@ extern "C" sbr_status sbr_synthesize(const sbr_paths* paths, const sbr_radar_cfg
     SBR_CUDA(cudaGetLastError());
     return SBR_OK;
   }
-  if (nufft_for(mode, Ns)) {
+  if (nufft_for(mode, Ns, paths->path_cap * paths->n_virt)) {
     launch_nufft(paths, radar, w, reinterpret_cast<float2*>(d_cube), st);
     SBR_CUDA(cudaGetLastError());
     return SBR_OK;
