@@ -319,13 +319,19 @@ COUNTER_METRICS = {"dram__bytes_read.sum": "dram", "dram__bytes_write.sum": "dra
 
 
 def sources_sha1(stage: str) -> str:
+    """SHA-1 of the stage's kernel sources and of the C header without its comments (the
+    header's declarations and constants reach the kernels; its documentation does not)."""
     import hashlib
+    import re
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2311_13182_gb300", "csrc")
     for f in [os.path.join(csrc, n) for n in COUNTER_SOURCES[stage]] + [os.path.join(ROOT, "include", "sbr.h")]:
         if os.path.exists(f):
             with open(f, "rb") as fh:
-                h.update(os.path.basename(f).encode() + fh.read())
+                data = fh.read()
+            if f.endswith(".h"):
+                data = re.sub(rb"/\*.*?\*/", b"", data, flags=re.S)
+            h.update(os.path.basename(f).encode() + data)
     return h.hexdigest()
 
 

@@ -303,10 +303,11 @@ size_t sbr_synth_ws_bytes(const sbr_radar_cfg* radar, int64_t path_cap);
 /* d_cube [V][C][N_s] complex64 (interleaved re, im) =
  *   sum_p A_{p,v} exp(j 2 pi (f_c tau_{p,v} + mu tau_{p,v} t_n)),
  * broadcast over the C chirps of a static scene.  Deterministic: partial sums
- * per CTA are reduced in a fixed order.  SBR_PHASE_SPLIT with N_s <= 512 is
- * evaluated as a type-1 non-uniform FFT (spreading onto 2 N_s grid points with
- * a width-8 exponential-of-semicircle kernel, one FFT, deconvolution; ~1e-6
- * relative to the FP64 sum), term by term otherwise.  SBR_PHASE_FP64 forms each
+ * per CTA are reduced in a fixed order.  SBR_PHASE_SPLIT with N_s <= 512 and
+ * at least 65536 record slots (path_cap * n_virt) is evaluated as a type-1
+ * non-uniform FFT (spreading onto 2 N_s grid points with a width-8
+ * exponential-of-semicircle kernel, one FFT, deconvolution; ~1e-6 relative to
+ * the FP64 sum), term by term otherwise.  SBR_PHASE_FP64 forms each
  * sample's phase in FP64 from paths->path_len; SBR_PHASE_NAIVE rounds the delay
  * to FP32.  With SBR_SYNTH_MOVING OR'ed into mode (paths traced on a scene with
  * motion) every chirp c is synthesised from the delays tau + c chirp_rep
