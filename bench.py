@@ -615,7 +615,8 @@ def recon_arm(sbr, torch, args):
     ms = e0.elapsed_time(e1) / n
     return {"iters_per_s": 1e3 / ms, "ms_per_iter": ms, "iterations": n + 4, "loss_first": loss0,
             "loss_last": float(rec.loss.item()), "vertices": int(tv.shape[0]), "rays": grid.n_rays,
-            "mode": "CUDA graph of one full iteration (forward, loss, adjoints, Adam)"}
+            "mode": "CUDA graph of one full iteration (forward, loss, adjoints, Adam); the tree refitted each "
+                    "iteration and rebuilt every 50 (rec.rebuild_every)"}
 
 
 def serve_arm(sbr, torch, args):

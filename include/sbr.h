@@ -173,6 +173,15 @@ sbr_status sbr_scene_create(const float* d_verts, int32_t nv, const int32_t* d_f
  * tree would leave loose boxes, and the cooperative build costs about as much
  * as a refit pass. */
 sbr_status sbr_scene_update(sbr_scene* scene, const float* d_verts, sbr_stream stream);
+/* New vertex positions of the same mesh into the tree of the last create or
+ * update: the triangles are re-packed in that build's order and every box is
+ * recomputed bottom-up, the topology (Morton order, children) kept.  The trace
+ * of a refitted scene finds the same hits as that of a rebuilt one (the nearest
+ * hit does not depend on the tree); it only slows down as the positions drift
+ * from those the tree was built for, so callers moving vertices far rebuild
+ * now and then.  Cheaper than sbr_scene_update (no Morton codes, sort or tree
+ * construction).  Same errors as sbr_scene_update. */
+sbr_status sbr_scene_refit(sbr_scene* scene, const float* d_verts, sbr_stream stream);
 /* Synchronises the stream and reports a device-side error word set by the
  * build: bit 0 (a face index outside [0, nv)) gives SBR_ERR_INVALID_ARG; bit 1
  * (the crossing-node bound of the tiled refit exceeded, which a radix tree

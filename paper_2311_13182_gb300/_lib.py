@@ -117,6 +117,7 @@ _SIGS = {
     "sbr_scene_bytes": (c_sz, [c_i32]),
     "sbr_scene_create": (c_i32, [c_p, c_i32, c_p, c_i32, c_p, c_sz, c_p, P(c_p)]),
     "sbr_scene_update": (c_i32, [c_p, c_p, c_p]),
+    "sbr_scene_refit": (c_i32, [c_p, c_p, c_p]),
     "sbr_scene_check": (c_i32, [c_p, c_p]),
     "sbr_scene_destroy": (None, [c_p]),
     "sbr_paths_bytes": (c_sz, [c_i32, c_i32, c_i32]),

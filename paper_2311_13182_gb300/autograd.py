@@ -57,6 +57,9 @@ class Simulator:
         self.n_rays = grid.G * grid.G if ray_ids is None else int(self.ray_ids.shape[0])
         self.mode, self.recompute, self.device = phase_mode, recompute, device
         self.scene = None
+        # after the first build: True refits the tree for new vertex positions
+        # (sbr_scene_refit: same hits, no rebuild), False rebuilds it (sbr_scene_update)
+        self.bvh_refit = False
         self.paths = None if recompute else sim.PathBuffers(self.n_rays, max_bounces, radar.n_virt, device)
         cap = self.n_rays * max_bounces
         self.synth_ws = torch.empty(sim.synth_ws_bytes(radar, cap), dtype=torch.uint8, device=device)
@@ -76,6 +79,8 @@ class Simulator:
                 self.scene.set_materials(self.eps, self.tri_material)
             if self.velocities:
                 self.scene.set_motion(self.velocities, self.tri_object)
+        elif self.bvh_refit:
+            self.scene.refit(verts)
         else:
             self.scene.update(verts)
         paths = self.paths if self.paths is not None else sim.PathBuffers(self.n_rays, self.K, self.radar.n_virt,

@@ -322,11 +322,10 @@ __device__ inline void write_node(Node* nodes, int i, const Box& l, const Box& r
   nodes[i].rxy = make_float4(r.lo.x, r.hi.x, r.lo.y, r.hi.y);
   nodes[i].lrz = make_float4(l.lo.z, l.hi.z, r.lo.z, r.hi.z);
 }
-__device__ inline float refit_pad(const int32_t* bounds) {
-  // conservative pad: covers the FP32 ray's deviation from its exact source and
-  // slab-test rounding for rays within the scene's coordinate range
-  return ldexpf(1.f + unord(bounds[6]), -18);
-}
+// conservative pad: covers the FP32 ray's deviation from its exact source and
+// slab-test rounding for rays within the scene's coordinate range (bounds[6]:
+// the largest |x| + |y| + |z| of a vertex, written by other CTAs: read through L2)
+__device__ inline float refit_pad(const int32_t* bounds) { return ldexpf(1.f + unord(__ldcg(&bounds[6])), -18); }
 
 __device__ inline Box tri_box_cg(const float4* tris, int slot, float pad) {  // written in this kernel
   const float4 a = __ldcg(&tris[3 * slot]), b = __ldcg(&tris[3 * slot + 1]), c = __ldcg(&tris[3 * slot + 2]);
@@ -556,6 +555,10 @@ inline size_t build_smem(int n) {
   return t > kSortSmem ? t : kSortSmem;
 }
 
+// kRefit: the boxes of the tree of the last build for new vertex positions of the
+// same mesh (phases 1, 4 and 5: the bounds for the pads, then the packing and the
+// refit with the kept triangle order, children and crossing marks).
+template <bool kRefit>
 __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restrict__ verts, int nv,
                                                             const int32_t* __restrict__ faces, int n,
                                                             BuildBufs B, int slots, bool cluster) {
@@ -618,6 +621,7 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
   }
   if (!build_sync(B.bar, nb, B.err, cluster)) return;
 
+  if (!kRefit) {
   // 2. Morton keys and the digit counts of all four places
   uint32_t* cnt = reinterpret_cast<uint32_t*>(build_sm);  // [32][kSortStride]
   uint32_t* goff = cnt + 32 * kSortStride;                 // [4][256] start of each digit, whole array
@@ -733,12 +737,14 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
     if (!build_sync(B.bar, nb, B.err, cluster)) return;
   }
 
+  }  // !kRefit
+
   // 4. tree: this tile's triangles in sorted order, its nodes, the local refit
   const uint32_t* keys = B.keys[0];
   uint32_t* s_keys = reinterpret_cast<uint32_t*>(build_sm);
   const int wlen = min(n, kKeyWindow);
   const int wlo = min(max(c0 + kBuildTile / 2 - kKeyWindow / 2, 0), n - wlen);
-  {
+  if (!kRefit) {
     // window copy with every load in flight before the stores (a plain loop
     // would wait out one L2 round trip per element it moves)
     constexpr int kU = 8;
@@ -759,7 +765,7 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
   s_par_leaf[t] = -1;
   s_par_node[t] = -1;
   s_arr[t] = 0u;
-  const float pad = ldexpf(1.f + unord(__ldcg(&B.bounds[6])), -18);  // as refit_pad
+  const float pad = refit_pad(B.bounds);
   Box bx{};
   if (live) {
     const int f = __ldcg(&B.vals[0][i]);
@@ -778,7 +784,19 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
   s_leaf[t] = sbox(bx);
   __syncthreads();
   bool cross = false;
-  if (i < n - 1) {
+  if (kRefit && i < n - 1) {  // the kept topology: children and crossing marks of the last build
+    const int4 ch = __ldcg(&B.nodes[i].child);
+    const int left = ch.x, right = ch.y;
+    s_child[t] = make_int2(left, right);
+    cross = (__ldcg(&B.crossing[i >> 5]) >> (i & 31)) & 1u;
+    if (!cross) {
+      if (left < 0) s_par_leaf[~left - c0] = i;
+      else s_par_node[left - c0] = i;
+      if (right < 0) s_par_leaf[~right - c0] = i;
+      else s_par_node[right - c0] = i;
+    }
+  }
+  if (!kRefit && i < n - 1) {
     int left, right, lo, hi;
     if (wlen == n) {  // every key in shared memory: plain shared loads in the searches
       karras_node([&](int j) { return s_keys[j]; }, n, i, &left, &right, &lo, &hi);
@@ -802,9 +820,11 @@ __global__ void __launch_bounds__(kBuildTile) k_build_scene(const float* __restr
       else s_par_node[right - c0] = i;
     }
   }
-  if (i == 0) B.parent[0] = -1;
-  const uint32_t mword = __ballot_sync(0xffffffffu, cross);
-  if (lane == 0 && i < n - 1) B.crossing[i >> 5] = mword;
+  if (!kRefit) {
+    if (i == 0) B.parent[0] = -1;
+    const uint32_t mword = __ballot_sync(0xffffffffu, cross);
+    if (lane == 0 && i < n - 1) B.crossing[i >> 5] = mword;
+  }
   __syncthreads();
   int me = ~i;  // child code of the subtree this thread holds
   int pn = live ? s_par_leaf[t] : -1;
@@ -988,7 +1008,9 @@ size_t layout(sbr_scene* s, void* mem, int32_t nt) {
   return c.bytes();
 }
 
-sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
+// The whole build, or with refit the boxes of the last build's tree for new vertex
+// positions (triangle order, children and crossing marks kept).
+sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st, bool refit = false) {
   const int nt = s->nt, nv = s->nv;
   if (s->coop) {  // one cooperative launch; it leaves its counters reset for the next build
     BuildBufs B{{s->keys[0], s->keys[1]}, {s->vals[0], s->vals[1]}, s->tris, s->nodes, s->parent, s->visits,
@@ -1009,7 +1031,8 @@ sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       ::sbr::note_launch();
-      SBR_CUDA(cudaLaunchKernelEx(&cfg, k_build_scene, verts, nv, faces, nt, B, slots, true));
+      if (refit) SBR_CUDA(cudaLaunchKernelEx(&cfg, k_build_scene<true>, verts, nv, faces, nt, B, slots, true));
+      else SBR_CUDA(cudaLaunchKernelEx(&cfg, k_build_scene<false>, verts, nv, faces, nt, B, slots, true));
       ::sbr::note_launch();
       k_collapse4<<<blocks(nt - 1, 128), 128, 0, st>>>(s->nodes, nt, s->nodes4);
       if (kTopLevels > 0) {
@@ -1023,8 +1046,8 @@ sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
     void* args[] = {(void*)&verts, (void*)&nvv, (void*)&faces, (void*)&n, (void*)&B, (void*)&slots,
                     (void*)&no_cluster};
     ::sbr::note_launch();
-    SBR_CUDA(cudaLaunchCooperativeKernel((const void*)k_build_scene, dim3(blocks(nt, kBuildTile)),
-                                         dim3(kBuildTile), args, build_smem(nt), st));
+    SBR_CUDA(cudaLaunchCooperativeKernel(refit ? (const void*)k_build_scene<true> : (const void*)k_build_scene<false>,
+                                         dim3(blocks(nt, kBuildTile)), dim3(kBuildTile), args, build_smem(nt), st));
     ::sbr::note_launch();
     k_collapse4<<<blocks(nt - 1, 128), 128, 0, st>>>(s->nodes, nt, s->nodes4);
     if (kTopLevels > 0) {
@@ -1042,15 +1065,19 @@ sbr_status rebuild(sbr_scene* s, const float* verts, cudaStream_t st) {
   }
   ::sbr::note_launch();
   k_bounds<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->bounds, s->err);
-  ::sbr::note_launch();
-  k_morton<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->bounds, s->keys[0],
-                                            s->vals[0], s->hist, s->err);
-  SBR_CUDA(radix_sort_pairs(s->keys, s->vals, nt, nullptr, 31, s->sort_scratch, st, s->hist));
+  if (!refit) {
+    ::sbr::note_launch();
+    k_morton<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->bounds, s->keys[0],
+                                              s->vals[0], s->hist, s->err);
+    SBR_CUDA(radix_sort_pairs(s->keys, s->vals, nt, nullptr, 31, s->sort_scratch, st, s->hist));
+  }
   ::sbr::note_launch();
   k_pack<<<blocks(nt, 256), 256, 0, st>>>(verts, nv, s->faces, nt, s->vals[0], s->tris, s->err);
   if (nt > 1) {
-    ::sbr::note_launch();
-    k_karras<<<blocks(nt - 1, 256), 256, 0, st>>>(s->keys[0], nt, s->nodes, s->parent);
+    if (!refit) {
+      ::sbr::note_launch();
+      k_karras<<<blocks(nt - 1, 256), 256, 0, st>>>(s->keys[0], nt, s->nodes, s->parent);
+    }
     SBR_CUDA(cudaMemsetAsync(s->visits, 0, sizeof(uint32_t) * (nt - 1), st));
     ::sbr::note_launch();
     k_refit<<<blocks(nt, 256), 256, 0, st>>>(s->tris, nt, s->nodes, s->parent, s->visits,
@@ -1110,17 +1137,22 @@ extern "C" sbr_status sbr_scene_create(const float* d_verts, int32_t nv, const i
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_build_scene, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_build_scene<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)build_smem(kTiledMax));  // the largest any scene asks
       if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_scene, kBuildTile, build_smem(nt));
+        e = cudaFuncSetAttribute(k_build_scene<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)build_smem(kTiledMax));
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_scene<false>, kBuildTile, build_smem(nt));
       s->coop = e == cudaSuccess && coop && (int64_t)per_sm * sms >= blocks(nt, kBuildTile);
       if (e != cudaSuccess) (void)cudaGetLastError();  // not fatal: the multi-kernel build runs
       // up to 16 tiles the grid can run as one cluster, when the GPU can hold it
       const int tiles = blocks(nt, kBuildTile);
       s->cluster = 0;
       if (s->coop && tiles <= 16) {
-        cudaError_t ce = cudaFuncSetAttribute(k_build_scene, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaError_t ce = cudaFuncSetAttribute(k_build_scene<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (ce == cudaSuccess)
+          ce = cudaFuncSetAttribute(k_build_scene<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(tiles);
         cfg.blockDim = dim3(kBuildTile);
@@ -1133,7 +1165,7 @@ extern "C" sbr_status sbr_scene_create(const float* d_verts, int32_t nv, const i
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveClusters(&clusters, k_build_scene, &cfg);
+        if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveClusters(&clusters, k_build_scene<false>, &cfg);
         if (ce == cudaSuccess && clusters >= 1) s->cluster = 1;
         else (void)cudaGetLastError();  // the cooperative launch stays
       }
@@ -1177,6 +1209,12 @@ extern "C" sbr_status sbr_scene_update(sbr_scene* scene, const float* d_verts, s
   SBR_ARG(scene != nullptr, "sbr_scene_update: scene is NULL");
   SBR_ARG(scene->nt == 0 || d_verts, "sbr_scene_update: d_verts is NULL");
   return rebuild(scene, d_verts, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" sbr_status sbr_scene_refit(sbr_scene* scene, const float* d_verts, sbr_stream stream) {
+  SBR_ARG(scene != nullptr, "sbr_scene_refit: scene is NULL");
+  SBR_ARG(scene->nt == 0 || d_verts, "sbr_scene_refit: d_verts is NULL");
+  return rebuild(scene, d_verts, reinterpret_cast<cudaStream_t>(stream), true);
 }
 
 extern "C" sbr_status sbr_scene_check(const sbr_scene* scene, sbr_stream stream) {

@@ -11,7 +11,10 @@ target is a range-angle power map [n_theta, N_s], the forward stops at the power
 map, and loss = mean squared image difference + w_lap * Laplacian, whose adjoint
 enters the synthesis adjoint directly.
 Every step is a library kernel on one stream with no host synchronisation, so
-the whole iteration is captured once into a CUDA graph and replayed.
+the whole iteration is captured into a CUDA graph and replayed.  The scene's tree
+is refitted to the new vertices each iteration (sbr_scene_refit: the same hits as
+a rebuild) and rebuilt every ``rebuild_every`` iterations (two captured graphs), so
+that its boxes stay tight as the mesh moves.
 """
 from __future__ import annotations
 
@@ -25,9 +28,13 @@ from .autograd import Simulator
 class Reconstruction:
     def __init__(self, verts0: np.ndarray, faces: np.ndarray, target: torch.Tensor, radar, grid, max_bounces,
                  cfar, lr=1e-3, lap_weight=0.1, ray_ids=None, recompute=False, loss="chamfer", reparam=False,
-                 device="cuda"):
+                 rebuild_every: int = 50, device="cuda"):
         if loss not in ("chamfer", "image"):
             raise ValueError(f"loss must be 'chamfer' or 'image', not {loss!r}")
+        if rebuild_every < 1:
+            raise ValueError("rebuild_every must be at least 1 (1: rebuild the tree every iteration)")
+        self.rebuild_every = int(rebuild_every)
+        self.iters = 0  # iterations run (eager or replayed): every rebuild_every-th rebuilds the tree
         self.kind = loss
         self.verts = torch.from_numpy(np.ascontiguousarray(verts0, np.float32)).to(device)
         self.nv = self.verts.shape[0]
@@ -43,8 +50,10 @@ class Reconstruction:
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
         self.gpoints = torch.zeros((cfar.k_max, 4), dtype=torch.float32, device=device)
         self.graph = None
+        self.graph_rebuild = None
 
-    def _iteration(self):
+    def _iteration(self, rebuild: bool = True):
+        self.sim.bvh_refit = not rebuild
         if self.kind == "image":
             self.sim.forward_image(self.verts)
             sim.image_loss(self.sim.state, self.target, loss=self.loss, gcube=self.sim.gcube)
@@ -59,21 +68,34 @@ class Reconstruction:
             self.sim.backward(self.verts, self.gpoints, self.grad)
         sim.adam_step(self.verts, self.grad, self.m, self.v, self.step_count, lr=self.lr)
 
+    def _rebuild_now(self) -> bool:
+        return self.iters % self.rebuild_every == 0
+
     def step(self):
         """One eager iteration (the first call also builds the scene)."""
-        self._iteration()
+        self._iteration(self._rebuild_now())
+        self.iters += 1
 
     def capture(self):
-        """Capture one iteration into a CUDA graph (after at least one eager step)."""
+        """Capture the iteration into CUDA graphs (after at least one eager step): one with
+        the tree refitted, one with it rebuilt.  Capturing runs no iteration."""
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
+        state = [t.clone() for t in (self.verts, self.m, self.v, self.step_count, self.loss)]
         with torch.cuda.stream(s):
-            self._iteration()  # warm the stream-local allocator state before capture
+            self._iteration(False)  # warm the stream-local allocator state before capture
+            self._iteration(True)
         torch.cuda.current_stream().wait_stream(s)
+        for t, t0 in zip((self.verts, self.m, self.v, self.step_count, self.loss), state):
+            t.copy_(t0)  # the warm-up iterations leave no trace
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
-            self._iteration()
+            self._iteration(False)
+        self.graph_rebuild = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph_rebuild):
+            self._iteration(True)
 
     def replay(self, n: int = 1):
         for _ in range(n):
-            self.graph.replay()
+            (self.graph_rebuild if self._rebuild_now() else self.graph).replay()
+            self.iters += 1

@@ -118,6 +118,11 @@ class Scene:
         _need_cuda(verts, torch.float32, "verts")
         L.call("sbr_scene_update", self.handle, _vp(verts), _stream(stream))
 
+    def refit(self, verts: torch.Tensor, stream=None):
+        """sbr_scene_refit: new positions into the last build's tree (same hits, no rebuild)."""
+        _need_cuda(verts, torch.float32, "verts")
+        L.call("sbr_scene_refit", self.handle, _vp(verts), _stream(stream))
+
     def check(self, stream=None):
         L.call("sbr_scene_check", self.handle, _stream(stream))
 
