@@ -166,12 +166,10 @@ size_t sbr_scene_bytes(int32_t nt);
 sbr_status sbr_scene_create(const float* d_verts, int32_t nv, const int32_t* d_faces,
                             int32_t nt, void* d_mem, size_t mem_bytes, sbr_stream stream,
                             sbr_scene** out);
-/* Rebuilds the scene for new vertex positions of the same topology (the
- * per-iteration update of the reconstruction loop).  This is the refit step of
- * a mesh-optimisation loop, done as a full rebuild (Morton order, tree and
- * boxes from the new positions): after large vertex moves a refit of the old
- * tree would leave loose boxes, and the cooperative build costs about as much
- * as a refit pass. */
+/* Rebuilds the scene for new vertex positions of the same topology (Morton
+ * order, tree and boxes from the new positions).  sbr_scene_refit below keeps
+ * the tree and costs less; a rebuild keeps the boxes tight after large vertex
+ * moves (the reconstruction loop refits each iteration and rebuilds now and then). */
 sbr_status sbr_scene_update(sbr_scene* scene, const float* d_verts, sbr_stream stream);
 /* New vertex positions of the same mesh into the tree of the last create or
  * update: the triangles are re-packed in that build's order and every box is
@@ -535,7 +533,8 @@ typedef struct {
   const int32_t* faces; /* host [nt][3] */
   int32_t nv, nt;
   sbr_ray_grid grid;
-  /* reconstruction: iterations of forward + loss + adjoints + Adam from verts */
+  /* reconstruction: iterations of forward + loss + adjoints + Adam from verts (the
+     tree refitted to the moved vertices each iteration, rebuilt every 50) */
   int32_t iterations;
   int32_t n_target;
   const float* target;  /* host [n_target][4] target points (x, y, z, w) */

@@ -174,6 +174,10 @@ struct sbr_server {
 namespace sbr {
 namespace {
 
+// Reconstruction requests refit the scene's tree to the moved vertices each
+// iteration and rebuild it every kRebuildEvery iterations (the hits are the same).
+constexpr int kRebuildEvery = 50;
+
 Sizes request_sizes(const sbr_radar_cfg* radar, const sbr_cfar_cfg* cfar, const sbr_request* q) {
   Sizes s{};
   const int V = radar->n_tx * radar->n_rx;
@@ -432,7 +436,8 @@ sbr_status enqueue_recon(sbr_server* s, Req* q, Slot& sl) {
   ENQ(sbr_scene_create(dv, r.nv, df, r.nt, dscene, q->sz.scene, ss, &scene));
   q->own_scene = scene;
   for (int it = 0; it < r.iterations; ++it) {
-    if (it > 0) ENQ(sbr_scene_update(scene, dv, ss));
+    // the moved vertices into the tree: refitted, rebuilt every kRebuildEvery iterations
+    if (it > 0) ENQ(it % kRebuildEvery == 0 ? sbr_scene_update(scene, dv, ss) : sbr_scene_refit(scene, dv, ss));
     ENQ(sbr_trace(scene, &s->radar, &r.grid, nullptr, -1, r.max_bounces, &paths, ss));
     ENQ(sbr_synthesize(&paths, &s->radar, SBR_PHASE_SPLIT, cube, ws, q->sz.ws, ss));
     ENQ(sbr_pointcloud(cube, &s->radar, &s->cfar, pts, &pc, ss));
