@@ -23,6 +23,8 @@
 // n * delta_hi is exact in FP32 for n < 4096) and delta_lo; and
 // A = omega (-1)^(k-1) |d_k . n_k| / (4 pi L_in L_out).
 #include <math.h>
+#include <stddef.h>
+#include <stdint.h>
 
 #include "ff.cuh"
 #include "scene.cuh"
@@ -112,6 +114,7 @@ struct Ray {
   __device__ Ray(ff3& o_, ff3& d_) : o(o_), d(d_) {}
   float3 of, df;  // FP32 ray driving the traversal
   float3 idir;
+  int near;  // byte offsets of a 4-wide entry's near-plane rows, x | y << 8 | z << 16 (set_idir)
   int skip;
   bool has_ff;        // primary rays build d in float-float only when needed
   int rid;
@@ -227,19 +230,54 @@ __device__ inline void test_tri(Best& b, const float4* __restrict__ tris, Ray& r
     consider(b, tris, r, id, slot, t.hi - fabsf(t.hi) * 2.4e-7f, t.hi + fabsf(t.hi) * 2.4e-7f, true, t);
 }
 
-// Entry and exit distances of a padded box.  t = lo idir - o idir, one FMA per
+// Entry and exit distances of a padded box from its planes along the ray: nx,
+// ny, nz the planes entered first (per axis the lower bound when the direction
+// component is positive, else the upper one), fx, fy, fz the planes left last;
+// tn the largest entry, tf the smallest exit.  t = p idir - o idir, one FMA per
 // plane: rounding o idir moves a plane by at most 2^-24 |o| along its axis, and
-// the final rounding by 2^-24 |lo - o|; both stay far inside the box pads
+// the final rounding by 2^-24 |p - o|; both stay far inside the box pads
 // (2^-18 (1 + max |coord|)) for origins within the scene's coordinate range.
-__device__ inline void slab(const float3& o, const float3& idir, float lox, float hix, float loy,
-                            float hiy, float loz, float hiz, float& tn, float& tf) {
-  const float nx = -(o.x * idir.x), ny = -(o.y * idir.y), nz = -(o.z * idir.z);
-  float tx0 = fmaf(lox, idir.x, nx), tx1 = fmaf(hix, idir.x, nx);
-  float ty0 = fmaf(loy, idir.y, ny), ty1 = fmaf(hiy, idir.y, ny);
-  float tz0 = fmaf(loz, idir.z, nz), tz1 = fmaf(hiz, idir.z, nz);
-  tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fminf(tz0, tz1));
-  tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+// An FMA is monotone in the plane, so for lo <= hi the chosen planes give the
+// min and max of each axis's pair; an unused slot is rejected by its link.
+__device__ inline void slab_nf(const float3& o, const float3& idir, float nx, float fx, float ny, float fy,
+                               float nz, float fz, float& tn, float& tf) {
+  const float ax = -(o.x * idir.x), ay = -(o.y * idir.y), az = -(o.z * idir.z);
+  tn = fmaxf(fmaxf(fmaf(nx, idir.x, ax), fmaf(ny, idir.y, ay)), fmaf(nz, idir.z, az));
+  tf = fminf(fminf(fmaf(fx, idir.x, ax), fmaf(fy, idir.y, ay)), fmaf(fz, idir.z, az));
   tf = tf * 1.0000005f + 1e-30f;
+}
+
+// A 4-wide entry's boxes as the ray meets them: per axis the plane entered first
+// (the lower bound when the direction component is positive, else the upper
+// one) and the plane left last, one float4 over the four slots each.  Entries
+// are 128-byte aligned, so a near row's byte offset (Ray::near) is OR-ed
+// into the entry's address, and the far row is the near one with bit 4 flipped.
+struct Planes4 {
+  float4 nx, fx, ny, fy, nz, fz;
+};
+
+static_assert(offsetof(Node4, lox) == 0 && offsetof(Node4, hix) == 16 && offsetof(Node4, loy) == 32 &&
+                  offsetof(Node4, hiy) == 48 && offsetof(Node4, loz) == 64 && offsetof(Node4, hiz) == 80 &&
+                  alignof(Node4) == 128,
+              "near/far plane rows assume this entry layout");
+
+template <bool kGlobal>
+__device__ inline float4 plane_row(const void* q, int off) {
+  const float4* a = reinterpret_cast<const float4*>(reinterpret_cast<uintptr_t>(q) | (uintptr_t)(unsigned)off);
+  return kGlobal ? __ldg(a) : *a;
+}
+
+template <bool kGlobal = true>
+__device__ inline Planes4 load_planes(const void* q, int near) {
+  const int nxo = near & 0xff, nyo = (near >> 8) & 0xff, nzo = near >> 16;
+  Planes4 p;
+  p.nx = plane_row<kGlobal>(q, nxo);
+  p.fx = plane_row<kGlobal>(q, nxo ^ 16);
+  p.ny = plane_row<kGlobal>(q, nyo);
+  p.fy = plane_row<kGlobal>(q, nyo ^ 16);
+  p.nz = plane_row<kGlobal>(q, nzo);
+  p.fz = plane_row<kGlobal>(q, nzo ^ 16);
+  return p;
 }
 
 constexpr int kStack = 192;  // 3 pending siblings per 4-wide level, 64 binary levels at most
@@ -356,28 +394,27 @@ __device__ Best nearest(const float4* __restrict__ tris, const Node4* __restrict
     }
     if (node >= 0) {
       if (kCount) ++n_nodes;
-      float4 lx, hx, ly, hy, lz, hz;
+      Planes4 p;
       int4 ch;
       if (kTopLevels > 0 && node >= kStaged) {
         const Node4& q = s_top[node - kStaged];
-        lx = q.lox, hx = q.hix, ly = q.loy, hy = q.hiy, lz = q.loz, hz = q.hiz;
+        p = load_planes<false>(&q, r.near);
         ch = q.child;
       } else {
         const Node4* q = nodes + node;
-        lx = __ldg(&q->lox), hx = __ldg(&q->hix), ly = __ldg(&q->loy), hy = __ldg(&q->hiy);
-        lz = __ldg(&q->loz), hz = __ldg(&q->hiz);
+        p = load_planes(q, r.near);
         ch = __ldg(&q->child);
       }
       const float lim = b.hi;
       float d0, d1, d2, d3, tf;
       int c0 = ch.x, c1 = ch.y, c2 = ch.z, c3 = ch.w;
-      slab(r.of, r.idir, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, d0, tf);
+      slab_nf(r.of, r.idir, p.nx.x, p.fx.x, p.ny.x, p.fy.x, p.nz.x, p.fz.x, d0, tf);
       d0 = (c0 != kEmpty && d0 <= tf && tf >= 0.f && d0 <= lim) ? d0 : INFINITY;
-      slab(r.of, r.idir, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, d1, tf);
+      slab_nf(r.of, r.idir, p.nx.y, p.fx.y, p.ny.y, p.fy.y, p.nz.y, p.fz.y, d1, tf);
       d1 = (c1 != kEmpty && d1 <= tf && tf >= 0.f && d1 <= lim) ? d1 : INFINITY;
-      slab(r.of, r.idir, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, d2, tf);
+      slab_nf(r.of, r.idir, p.nx.z, p.fx.z, p.ny.z, p.fy.z, p.nz.z, p.fz.z, d2, tf);
       d2 = (c2 != kEmpty && d2 <= tf && tf >= 0.f && d2 <= lim) ? d2 : INFINITY;
-      slab(r.of, r.idir, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, d3, tf);
+      slab_nf(r.of, r.idir, p.nx.w, p.fx.w, p.ny.w, p.fy.w, p.nz.w, p.fz.w, d3, tf);
       d3 = (c3 != kEmpty && d3 <= tf && tf >= 0.f && d3 <= lim) ? d3 : INFINITY;
       // sort the four entry distances (misses are +inf and sink to the end)
       cswap(d0, c0, d1, c1);
@@ -427,19 +464,18 @@ __device__ bool traverse(const float4* __restrict__ tris, const Node4* __restric
     if (node >= 0) {
       if (kCount) ++n_nodes;
       const Node4* q = nodes + node;
-      const float4 lx = __ldg(&q->lox), hx = __ldg(&q->hix), ly = __ldg(&q->loy), hy = __ldg(&q->hiy),
-                   lz = __ldg(&q->loz), hz = __ldg(&q->hiz);
+      const Planes4 p = load_planes(q, r.near);
       const int4 ch = __ldg(&q->child);
       const float lim = fminf(b.hi, ext_lim);
       float d0, d1, d2, d3, tf;
       int c0 = ch.x, c1 = ch.y, c2 = ch.z, c3 = ch.w;
-      slab(r.of, r.idir, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, d0, tf);
+      slab_nf(r.of, r.idir, p.nx.x, p.fx.x, p.ny.x, p.fy.x, p.nz.x, p.fz.x, d0, tf);
       d0 = (c0 != kEmpty && d0 <= tf && tf >= 0.f && d0 <= lim) ? d0 : INFINITY;
-      slab(r.of, r.idir, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, d1, tf);
+      slab_nf(r.of, r.idir, p.nx.y, p.fx.y, p.ny.y, p.fy.y, p.nz.y, p.fz.y, d1, tf);
       d1 = (c1 != kEmpty && d1 <= tf && tf >= 0.f && d1 <= lim) ? d1 : INFINITY;
-      slab(r.of, r.idir, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, d2, tf);
+      slab_nf(r.of, r.idir, p.nx.z, p.fx.z, p.ny.z, p.fy.z, p.nz.z, p.fz.z, d2, tf);
       d2 = (c2 != kEmpty && d2 <= tf && tf >= 0.f && d2 <= lim) ? d2 : INFINITY;
-      slab(r.of, r.idir, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, d3, tf);
+      slab_nf(r.of, r.idir, p.nx.w, p.fx.w, p.ny.w, p.fy.w, p.nz.w, p.fz.w, d3, tf);
       d3 = (c3 != kEmpty && d3 <= tf && tf >= 0.f && d3 <= lim) ? d3 : INFINITY;
       cswap(d0, c0, d1, c1);
       cswap(d2, c2, d3, c3);
@@ -466,6 +502,9 @@ __device__ bool traverse(const float4* __restrict__ tris, const Node4* __restric
 __device__ inline void set_idir(Ray& r) {
   auto inv = [](float x) { return 1.0f / (fabsf(x) < 1e-20f ? copysignf(1e-20f, x) : x); };
   r.idir = f3(inv(r.df.x), inv(r.df.y), inv(r.df.z));
+  // near rows: lo (bytes 0, 32, 64 of the entry) for a positive component, hi (16, 48, 80) otherwise
+  r.near = (__float_as_int(r.idir.x) < 0 ? 16 : 0) | (__float_as_int(r.idir.y) < 0 ? 48 : 32) << 8 |
+           (__float_as_int(r.idir.z) < 0 ? 80 : 64) << 16;
 }
 
 __device__ inline void set_f32(Ray& r) {
@@ -656,17 +695,16 @@ __device__ Best coop_nearest(const float4* __restrict__ tris, const Node4* __res
     if (expand) {
       if (kCount) ++n_nodes;
       const Node4* q = nodes + e;
-      const float4 lx = __ldg(&q->lox), hx = __ldg(&q->hix), ly = __ldg(&q->loy), hy = __ldg(&q->hiy),
-                   lz = __ldg(&q->loz), hz = __ldg(&q->hiz);
+      const Planes4 p = load_planes(q, r.near);
       const int4 ch = __ldg(&q->child);
       float tn, tf;
-      slab(r.of, r.idir, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, tn, tf);
+      slab_nf(r.of, r.idir, p.nx.x, p.fx.x, p.ny.x, p.fy.x, p.nz.x, p.fz.x, tn, tf);
       if (ch.x != kEmpty && tn <= tf && tf >= 0.f && tn <= b.hi) kid[nk++] = ch.x;
-      slab(r.of, r.idir, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, tn, tf);
+      slab_nf(r.of, r.idir, p.nx.y, p.fx.y, p.ny.y, p.fy.y, p.nz.y, p.fz.y, tn, tf);
       if (ch.y != kEmpty && tn <= tf && tf >= 0.f && tn <= b.hi) kid[nk++] = ch.y;
-      slab(r.of, r.idir, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, tn, tf);
+      slab_nf(r.of, r.idir, p.nx.z, p.fx.z, p.ny.z, p.fy.z, p.nz.z, p.fz.z, tn, tf);
       if (ch.z != kEmpty && tn <= tf && tf >= 0.f && tn <= b.hi) kid[nk++] = ch.z;
-      slab(r.of, r.idir, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, tn, tf);
+      slab_nf(r.of, r.idir, p.nx.w, p.fx.w, p.ny.w, p.fy.w, p.nz.w, p.fz.w, tn, tf);
       if (ch.w != kEmpty && tn <= tf && tf >= 0.f && tn <= b.hi) kid[nk++] = ch.w;
     }
     if (!__any_sync(0xffffffffu, expand)) break;  // only leaves left
