@@ -697,14 +697,27 @@ def oracle_sample(n_rays: int, seed: int):
     return time.perf_counter() - t0, pa["P"]
 
 
-def cpu_baseline(seed: int, budget_s: float = 20.0):
+def cpu_baseline(seed: int, budget_s: float = 20.0, single_s: float = 6.0):
+    """The oracle on every host core over a ~budget_s sample, and on one core over a ~single_s one."""
+    import oracle
     n = 2048
     dt, _ = oracle_sample(n, seed)
     n2 = int(min(1 << 20, max(n, n * budget_s / max(dt, 1e-3))))
     dt2, P = oracle_sample(n2, seed)
-    return {"value": n2 / dt2, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n2} of 1,048,576 rays (seeded subset): brute-force FP64 trace, paths, direct-sum "
-                      f"synthesis of their {P} paths x 12 antennas x 256 samples, point cloud; {dt2:.1f} s"}
+    out = {"value": n2 / dt2, "unit": "rays/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{n2} of 1,048,576 rays (seeded subset): brute-force FP64 trace, paths, direct-sum "
+                     f"synthesis of their {P} paths x 12 antennas x 256 samples, point cloud; {dt2:.1f} s"}
+    prev = oracle.set_threads(1)
+    try:
+        m = 256
+        dt1, _ = oracle_sample(m, seed)
+        m2 = int(min(n2, max(m, m * single_s / max(dt1, 1e-3))))
+        dt12, P1 = oracle_sample(m2, seed)
+    finally:
+        oracle.set_threads(prev)
+    out["single_thread"] = {"value": m2 / dt12, "unit": "rays/s", "cores": 1,
+                            "sample": f"{m2} rays of the same seeded subset order ({P1} paths); {dt12:.1f} s"}
+    return out
 
 
 def reference_arm(args, rank, world):

@@ -69,8 +69,15 @@ def _lib():
                                   ctypes.c_double, ctypes.c_int, P, P]
         lib.orc_synth_grad.argtypes = [P, P, ctypes.c_long, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P, P, P]
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads.restype = ctypes.c_int
         _LIB = lib
     return _LIB
+
+
+def set_threads(n: int) -> int:
+    """Threads the C oracle's loops use from now on (n >= 1); returns the previous count."""
+    return int(_lib().orc_set_threads(int(n)))
 
 
 def _ptr(a):

@@ -29,6 +29,9 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct { double x, y, z; } d3;
 
@@ -218,4 +221,17 @@ int orc_synth_grad(const double* tau, const double* amp, long P, int V, double f
     }
   }
   return 0;
+}
+
+/* Thread count of the OpenMP loops above (n >= 1; anything else leaves it); returns the count
+ * in force before the call.  Used to time the oracle on one core beside all of them. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  int prev = omp_get_max_threads();
+  if (n >= 1) omp_set_num_threads(n);
+  return prev;
+#else
+  (void)n;
+  return 1;
+#endif
 }
