@@ -6,6 +6,10 @@ mesh pack + LBVH build of a 20,002-triangle scene (seeded superquadric over a
 ground plane), the trace of 1024 x 1024 rays with up to 3 specular bounces and
 float-float path preparation, the synthesis of the [12, 128, 256] IF cube (Eq. 8),
 and the point cloud (range FFT, Doppler FFT, angle DFT, soft CFAR, refine).
+Steps are timed three batches deep (sbr.PipelinedForward: the next batch's
+build and the previous batch's point cloud beside this batch's trace and
+synthesis, every stage once per step); the serial step (one batch end to end
+per replay) is timed and printed beside it.
 
 Printed (rank 0, one JSON line): traced rays/s over all ranks (device-timed,
 inputs resident), the same end to end through the public API with host
@@ -203,6 +207,22 @@ def gpu_arm(args, rank, world, local):
     torch.cuda.synchronize()
     P = b["paths"].count()
     n_points = b["state"].n_points()
+    # one batch end to end per replay (the serial step's latency), L2 flushed between steps
+    ev = [(mk(), mk()) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        fw.run()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    ms_serial = reduce_max(float(np.mean([a.elapsed_time(e) for a, e in ev])), world)
+    # the step three batches deep (sbr.PipelinedForward): build of the next batch and point
+    # cloud of the previous one beside this batch's trace and synthesis
+    pf = sbr.PipelinedForward(torch.from_numpy(wl.verts).cuda(), torch.from_numpy(wl.faces).cuda(), wl.radar,
+                              wl.grid, wl.max_bounces, cfg)
+    for _ in range(max(args.warmup, 3)):
+        pf.run()
+    torch.cuda.synchronize()
 
     # ---- device-timed region: graph replays, inputs resident, L2 flushed between steps
     ev = [(mk(), mk()) for _ in range(args.steps)]
@@ -214,7 +234,7 @@ def gpu_arm(args, rank, world, local):
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record()
-        fw.run()
+        pf.run()
         ev[i][1].record()
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
@@ -223,6 +243,9 @@ def gpu_arm(args, rank, world, local):
     clk = clocks.stop()
     ms_step = float(np.mean([a.elapsed_time(e) for a, e in ev]))
     ms_step_all = reduce_max(ms_step, world)
+    if pf.n_points() != n_points:
+        raise RuntimeError(f"pipelined step found {pf.n_points()} points, the serial step {n_points}")
+    del pf
     rays = wl.grid.n_rays
     value = reduce_sum(rays, world) / (ms_step_all * 1e-3)
     samples = P * wl.radar.n_virt * wl.radar.n_samples
@@ -250,8 +273,12 @@ def gpu_arm(args, rank, world, local):
         "config": {"workload": WORKLOAD, "rays_per_step": rays, "paths_per_step": P, "points": n_points,
                    "parallelism": f"replicas x{world} (independent scenes per GPU, no collective)",
                    "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written between steps, outside the per-step events",
-                   "timing": "each step one CUDA-graph replay of the whole forward step (sbr.Forward); stage_ms "
-                             "from the same step as separate launches with events between the stages"},
+                   "timing": "each step one CUDA-graph replay of sbr.PipelinedForward: this batch's trace and "
+                             "synthesis, the next batch's LBVH build and the previous batch's point cloud on "
+                             "three streams (every stage once per step); serial = one batch end to end per "
+                             "replay (sbr.Forward); stage_ms from the serial step as separate launches with "
+                             "events between the stages"},
+        "serial": {"ms_per_step": ms_serial, "rays_per_s": reduce_sum(rays, world) / (ms_serial * 1e-3)},
         "path_samples_per_s": path_samples,
         "stage_ms": stage_ms,
         "recon_iters_per_s": None if recon is None else recon["iters_per_s"],
@@ -270,13 +297,13 @@ def gpu_arm(args, rank, world, local):
 
 
 def e2e_arm(sbr, torch, wl, cfg, args, world, flush):
-    """Same step through the public API from page-locked host buffers: sbr.Forward with host_io,
-    whose graph copies the vertex positions host-to-device at its start (the topology fixed at
-    construction), rebuilds the scene, traces, synthesises and extracts the points, and copies
-    the points and their count device-to-host at its end; one run_host call per step, L2 flushed
-    between steps outside the per-step events as in the device-timed arm."""
-    fwd = sbr.Forward(torch.from_numpy(wl.verts).cuda(), torch.from_numpy(wl.faces).cuda(), wl.radar, wl.grid,
-                      wl.max_bounces, cfg, host_io=True)
+    """Same step through the public API from page-locked host buffers: sbr.PipelinedForward with
+    host_io, whose graphs copy the vertex positions host-to-device for the batch they build (the
+    topology fixed at construction), build, trace, synthesise and extract points (three batches in
+    flight), and copy the points and their count device-to-host; one run_host call per step, L2
+    flushed between steps outside the per-step events as in the device-timed arm."""
+    fwd = sbr.PipelinedForward(torch.from_numpy(wl.verts).cuda(), torch.from_numpy(wl.faces).cuda(), wl.radar,
+                               wl.grid, wl.max_bounces, cfg, host_io=True)
     for _ in range(3):
         fwd.run_host(wl.verts)
     torch.cuda.synchronize()
@@ -294,8 +321,8 @@ def e2e_arm(sbr, torch, wl, cfg, args, world, flush):
     bo = fwd.h_points.numel() * 4 + 4
     return {"value": reduce_sum(wl.grid.n_rays, world) / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
             "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
-            "path": "sbr.Forward(host_io=True).run_host: H2D of the vertices, the step, D2H of the points, "
-                    "one CUDA graph per step"}
+            "path": "sbr.PipelinedForward(host_io=True).run_host: H2D of the vertices, the step, D2H of the "
+                    "points, one CUDA graph per step"}
 
 
 # Counters per launch of each roofline stage (DRAM bytes, warp instructions), from ncu captures

@@ -7,12 +7,12 @@ memory and streams into it.  Importing the package does not build anything;
 """
 from . import build
 from ._lib import SbrError, load
-from .pipeline import Forward
+from .pipeline import Forward, PipelinedForward
 from .sim import (PHASE_FP64, PHASE_NAIVE, PHASE_SPLIT, SYNTH_MOVING, Adjacency, PathBuffers, PcState, Scene, adam_step,
                   cfar_struct, chamfer, grid_struct, image_loss, laplacian, pointcloud, pointcloud_bwd, power_map,
                   radar_struct, synth_ws_bytes, synthesize, synthesize_bwd, trace, trace_bwd)
 
-__all__ = ["build", "load", "SbrError", "Forward", "Scene", "PathBuffers", "PcState", "Adjacency", "trace", "synthesize",
+__all__ = ["build", "load", "SbrError", "Forward", "PipelinedForward", "Scene", "PathBuffers", "PcState", "Adjacency", "trace", "synthesize",
            "synthesize_bwd", "pointcloud", "pointcloud_bwd", "power_map", "image_loss", "trace_bwd", "chamfer", "laplacian", "adam_step",
            "synth_ws_bytes", "radar_struct", "grid_struct", "cfar_struct", "PHASE_SPLIT", "PHASE_FP64",
            "PHASE_NAIVE", "SYNTH_MOVING"]

@@ -11,6 +11,10 @@ settings) is fixed at construction.  With ``host_io`` the graph also holds the
 step's host traffic: the copy of the vertex positions from a page-locked host
 buffer at its start, and the copies of the points and their count into
 page-locked host buffers at its end (``run_host``).
+
+``PipelinedForward`` keeps three batches in flight for throughput: the build of
+the next batch and the point cloud of the previous one run on two more streams
+beside the current batch's trace and synthesis.
 """
 from __future__ import annotations
 
@@ -95,6 +99,125 @@ class Forward:
             self.done.synchronize()  # the previous replay has read the buffer
             self.h_verts.copy_(torch.as_tensor(verts, dtype=torch.float32))
         self.graph.replay()
+        self.done.record()
+
+    def n_points(self) -> int:
+        return self.state.n_points()
+
+
+class PipelinedForward:
+    """The forward step three batches deep, for throughput.
+
+    A step j (one graph replay; the parity of j picks one of two captured graphs) runs three
+    independent branches on three streams:
+
+      * the trace and synthesis of batch j from tree ``scenes[j % 2]`` into ``cubes[j % 2]``
+        (capture stream);
+      * the LBVH build of batch j+1 from ``verts`` into ``scenes[(j + 1) % 2]``, the tree the
+        next step traces (a high-priority stream, so that its CTAs are placed as soon as SMs
+        free up);
+      * the point cloud of batch j-1 from ``cubes[(j + 1) % 2]`` into ``points`` (a second
+        high-priority stream).
+
+    The branches share no buffer, so the build's few dozen CTAs and the point cloud's small
+    kernels fill SMs beside the trace instead of running alone after it; every step still
+    builds, traces, synthesizes and images one batch each.  The points after step j are those of
+    the vertices set before step j-2 (steps 0 and 1: the constructor's vertices, whose cube the
+    constructor computes).  With ``host_io`` the graph also copies the vertices from the
+    page-locked ``h_verts`` at the build branch's start, and the points and their count into
+    ``h_points`` / ``h_n`` at the point-cloud branch's end (``run_host``).
+    """
+
+    def __init__(self, verts: torch.Tensor, faces: torch.Tensor, radar, grid, max_bounces: int, cfar,
+                 mode: int = sim.PHASE_SPLIT, graph: bool = True, host_io: bool = False):
+        dev = verts.device
+        self.radar, self.grid, self.max_bounces, self.cfar, self.mode = radar, grid, max_bounces, cfar, mode
+        self.verts = verts.detach().clone().contiguous()
+        self.faces = faces.detach().contiguous()
+        self.scenes = [sim.Scene(self.verts, self.faces), sim.Scene(self.verts, self.faces)]
+        self.paths = sim.PathBuffers(grid.n_rays, max_bounces, radar.n_virt)
+        self.ws = torch.empty(sim.synth_ws_bytes(radar, self.paths.cap), dtype=torch.uint8, device=dev)
+        self.cubes = [torch.zeros((radar.n_virt, radar.n_chirps, radar.n_samples, 2), device=dev) for _ in range(2)]
+        self.state = sim.PcState(radar, cfar)
+        self.points = torch.empty((cfar.k_max, 4), device=dev)
+        self.build_stream = torch.cuda.Stream(device=dev, priority=-1)
+        self.pc_stream = torch.cuda.Stream(device=dev, priority=-1)
+        self.host_io = host_io
+        if host_io:
+            self.h_verts = torch.empty(self.verts.shape, dtype=torch.float32).pin_memory()
+            self.h_verts.copy_(self.verts)
+            self.h_points = torch.empty((cfar.k_max, 4), dtype=torch.float32).pin_memory()
+            self.h_n = torch.empty(1, dtype=torch.int32).pin_memory()
+            self.done = torch.cuda.Event()
+        self.graphs = None
+        self._prime()  # the first point cloud images a real cube
+        if graph:
+            # first calls outside the capture: they set per-device kernel attributes
+            side = torch.cuda.Stream(device=dev)
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                for j in range(2):
+                    self._step(j, copies=False)
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            self.graphs = []
+            for p in range(2):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    self._step(p, copies=host_io)
+                self.graphs.append(g)
+            torch.cuda.synchronize()
+        self._prime()
+
+    def _prime(self):
+        """Step 0's state: tree 0 of the current vertices, and cube 1 (imaged by step 0) from it."""
+        self.scenes[0].update(self.verts)
+        sim.trace(self.scenes[0], self.radar, self.grid, self.max_bounces, out=self.paths)
+        sim.synthesize(self.paths, self.radar, self.mode, out=self.cubes[1], ws=self.ws)
+        self.j = 0
+
+    def _step(self, p: int, copies: bool):
+        main = torch.cuda.current_stream()
+        self.build_stream.wait_stream(main)
+        self.pc_stream.wait_stream(main)
+        with torch.cuda.stream(self.build_stream):
+            if copies:
+                self.verts.copy_(self.h_verts, non_blocking=True)
+            self.scenes[1 - p].update(self.verts)
+        with torch.cuda.stream(self.pc_stream):
+            sim.pointcloud(self.cubes[1 - p], self.radar, self.cfar, state=self.state, out=self.points)
+            if copies:
+                self.h_points.copy_(self.points, non_blocking=True)
+                self.h_n.copy_(self.state.n_points_tensor(), non_blocking=True)
+        sim.trace(self.scenes[p], self.radar, self.grid, self.max_bounces, out=self.paths)
+        sim.synthesize(self.paths, self.radar, self.mode, out=self.cubes[p], ws=self.ws)
+        main.wait_stream(self.build_stream)
+        main.wait_stream(self.pc_stream)
+
+    def set_vertices(self, verts: torch.Tensor):
+        """New positions for the same topology: the next step builds their tree, the step after
+        it traces them and the one after that images them."""
+        self.verts.copy_(verts, non_blocking=True)
+
+    def run(self):
+        """One step: a graph replay (or the launches themselves when built with graph=False)."""
+        if self.graphs is not None:
+            self.graphs[self.j % 2].replay()
+        else:
+            self._step(self.j % 2, copies=False)
+        self.j += 1
+
+    def run_host(self, verts=None):
+        """One step from host memory (requires host_io and the graphs): ``verts`` (array-like
+        [nv, 3], or None to keep the page-locked buffer's contents) go into the page-locked input
+        buffer once the previous step has finished with it, then the graph replays; ``h_points`` /
+        ``h_n`` hold the points of the vertices of two calls earlier when ``done`` completes."""
+        if not self.host_io or self.graphs is None:
+            raise RuntimeError("run_host needs PipelinedForward(..., graph=True, host_io=True)")
+        if verts is not None:
+            self.done.synchronize()  # the previous replay has read the buffer
+            self.h_verts.copy_(torch.as_tensor(verts, dtype=torch.float32))
+        self.run()
         self.done.record()
 
     def n_points(self) -> int:

@@ -55,6 +55,50 @@ def test_host_io_graph_matches_eager(sbr):
         e.run_host(wl.verts)
 
 
+def test_pipelined_lags_two_steps(sbr):
+    """sbr.PipelinedForward: step j traces batch j's tree, builds batch j+1's beside it and
+    images batch j-1's cube beside both.  With the vertices moving every step, step j's points
+    equal (bitwise) those the serial step gives for the vertices set before step j-2 (steps 0
+    and 1: the constructor's), replayed from the two graphs, run eagerly, and with host buffers;
+    the cube synthesized at step j is the serial cube of the vertices set before step j-1."""
+    wl = superquadric_scene(seed=6, G=256)
+    cfg = CfarParams()
+    v = torch.from_numpy(wl.verts).cuda()
+    f = torch.from_numpy(wl.faces).cuda()
+    e = sbr.Forward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg, graph=False)
+    pg = sbr.PipelinedForward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg)
+    pe = sbr.PipelinedForward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg, graph=False)
+    ph = sbr.PipelinedForward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg, host_io=True)
+    shifts = [0.0, 0.01, 0.03, -0.02, 0.02]
+    want = []
+    for sh in shifts:  # the serial step's outputs per vertex set
+        e.set_vertices(v + torch.tensor([0.0, 0.0, sh], device="cuda"))
+        e.run()
+        torch.cuda.synchronize()
+        want.append((e.cube.clone(), e.points.clone(), e.n_points()))
+    seq = shifts + [0.0, 0.0]  # the vertex set given before each step
+    out = dict(zip(shifts, want))
+    for j, sh in enumerate(seq):
+        moved = v + torch.tensor([0.0, 0.0, sh], device="cuda")
+        for fw in (pg, pe):
+            fw.set_vertices(moved)
+            fw.run()
+        ph.run_host(moved.cpu().numpy())
+        ph.done.synchronize()
+        torch.cuda.synchronize()
+        _, pts, n = out[seq[j - 2] if j >= 2 else 0.0]
+        traced = out[seq[j - 1] if j >= 1 else 0.0][0]
+        assert n > 0
+        for fw in (pg, pe):
+            assert fw.n_points() == n
+            assert torch.equal(fw.points, pts)
+            assert torch.equal(fw.cubes[j % 2], traced)
+        assert int(ph.h_n.item()) == n
+        assert torch.equal(ph.h_points, pts.cpu())
+    with pytest.raises(RuntimeError):
+        pe.run_host(wl.verts)
+
+
 def test_bench_step_full_cube_and_points_against_oracle(sbr):
     """The bench workload at full size (20,002 triangles, all 1,048,576 rays, 3 bounces,
     12 x 128 x 256 cube), run as the bench runs it (the graph-replayed sbr.Forward step):
