@@ -6,10 +6,10 @@ mesh pack + LBVH build of a 20,002-triangle scene (seeded superquadric over a
 ground plane), the trace of 1024 x 1024 rays with up to 3 specular bounces and
 float-float path preparation, the synthesis of the [12, 128, 256] IF cube (Eq. 8),
 and the point cloud (range FFT, Doppler FFT, angle DFT, soft CFAR, refine).
-Steps are timed three batches deep (sbr.PipelinedForward: the next batch's
-build and the previous batch's point cloud beside this batch's trace and
-synthesis, every stage once per step); the serial step (one batch end to end
-per replay) is timed and printed beside it.
+Steps are timed four batches deep (sbr.PipelinedForward: the next batch's
+build, the previous batch's synthesis and an earlier batch's point cloud beside
+this batch's trace, every stage once per step); the serial step (one batch end
+to end per replay) is timed and printed beside it.
 
 Printed (rank 0, one JSON line): traced rays/s over all ranks (device-timed,
 inputs resident), the same end to end through the public API with host
@@ -216,8 +216,8 @@ def gpu_arm(args, rank, world, local):
         ev[i][1].record()
     torch.cuda.synchronize()
     ms_serial = reduce_max(float(np.mean([a.elapsed_time(e) for a, e in ev])), world)
-    # the step three batches deep (sbr.PipelinedForward): build of the next batch and point
-    # cloud of the previous one beside this batch's trace and synthesis
+    # the step four batches deep (sbr.PipelinedForward): the next batch's build, the previous
+    # batch's synthesis and an earlier batch's point cloud beside this batch's trace
     pf = sbr.PipelinedForward(torch.from_numpy(wl.verts).cuda(), torch.from_numpy(wl.faces).cuda(), wl.radar,
                               wl.grid, wl.max_bounces, cfg)
     for _ in range(max(args.warmup, 3)):
@@ -273,11 +273,11 @@ def gpu_arm(args, rank, world, local):
         "config": {"workload": WORKLOAD, "rays_per_step": rays, "paths_per_step": P, "points": n_points,
                    "parallelism": f"replicas x{world} (independent scenes per GPU, no collective)",
                    "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written between steps, outside the per-step events",
-                   "timing": "each step one CUDA-graph replay of sbr.PipelinedForward: this batch's trace and "
-                             "synthesis, the next batch's LBVH build and the previous batch's point cloud on "
-                             "three streams (every stage once per step); serial = one batch end to end per "
-                             "replay (sbr.Forward); stage_ms from the serial step as separate launches with "
-                             "events between the stages"},
+                   "timing": "each step one CUDA-graph replay of sbr.PipelinedForward (depth 4): this batch's "
+                             "trace, the previous batch's synthesis, the next batch's LBVH build and the point "
+                             "cloud of the batch before the previous on four streams (every stage once per "
+                             "step); serial = one batch end to end per replay (sbr.Forward); stage_ms from the "
+                             "serial step as separate launches with events between the stages"},
         "serial": {"ms_per_step": ms_serial, "rays_per_s": reduce_sum(rays, world) / (ms_serial * 1e-3)},
         "path_samples_per_s": path_samples,
         "stage_ms": stage_ms,
@@ -299,7 +299,7 @@ def gpu_arm(args, rank, world, local):
 def e2e_arm(sbr, torch, wl, cfg, args, world, flush):
     """Same step through the public API from page-locked host buffers: sbr.PipelinedForward with
     host_io, whose graphs copy the vertex positions host-to-device for the batch they build (the
-    topology fixed at construction), build, trace, synthesise and extract points (three batches in
+    topology fixed at construction), build, trace, synthesise and extract points (four batches in
     flight), and copy the points and their count device-to-host; one run_host call per step, L2
     flushed between steps outside the per-step events as in the device-timed arm."""
     fwd = sbr.PipelinedForward(torch.from_numpy(wl.verts).cuda(), torch.from_numpy(wl.faces).cuda(), wl.radar,

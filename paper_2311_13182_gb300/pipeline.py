@@ -12,9 +12,10 @@ step's host traffic: the copy of the vertex positions from a page-locked host
 buffer at its start, and the copies of the points and their count into
 page-locked host buffers at its end (``run_host``).
 
-``PipelinedForward`` keeps three batches in flight for throughput: the build of
-the next batch and the point cloud of the previous one run on two more streams
-beside the current batch's trace and synthesis.
+``PipelinedForward`` keeps several batches in flight for throughput: the build
+of the next batch and the point cloud of an earlier one (and optionally the
+synthesis of the previous one) run on more streams beside the current batch's
+trace.
 """
 from __future__ import annotations
 
@@ -106,42 +107,57 @@ class Forward:
 
 
 class PipelinedForward:
-    """The forward step three batches deep, for throughput.
+    """The forward step several batches deep, for throughput.
 
-    A step j (one graph replay; the parity of j picks one of two captured graphs) runs three
-    independent branches on three streams:
+    A step j (one graph replay; the parity of j picks one of two captured graphs) runs
+    independent branches on separate streams, each on buffers of its own parity:
 
-      * the trace and synthesis of batch j from tree ``scenes[j % 2]`` into ``cubes[j % 2]``
-        (capture stream);
+      * the trace of batch j from tree ``scenes[j % 2]``;
       * the LBVH build of batch j+1 from ``verts`` into ``scenes[(j + 1) % 2]``, the tree the
-        next step traces (a high-priority stream, so that its CTAs are placed as soon as SMs
-        free up);
-      * the point cloud of batch j-1 from ``cubes[(j + 1) % 2]`` into ``points`` (a second
-        high-priority stream).
+        next step traces (highest priority: its cooperative launch needs all its CTAs resident
+        at once, and once the trace's CTAs are being placed it would wait for the trace to
+        drain);
+      * ``depth`` 4 (the default): the synthesis of batch j-1 from the other of two path
+        buffers (lowest priority) and the point cloud of batch j-2 (highest priority);
+        ``depth`` 3: the synthesis of batch j after its trace, and the point cloud of batch j-1.
 
-    The branches share no buffer, so the build's few dozen CTAs and the point cloud's small
-    kernels fill SMs beside the trace instead of running alone after it; every step still
-    builds, traces, synthesizes and images one batch each.  The points after step j are those of
-    the vertices set before step j-2 (steps 0 and 1: the constructor's vertices, whose cube the
-    constructor computes).  With ``host_io`` the graph also copies the vertices from the
-    page-locked ``h_verts`` at the build branch's start, and the points and their count into
-    ``h_points`` / ``h_n`` at the point-cloud branch's end (``run_host``).
+    The branches share no buffer, so the build's few dozen CTAs, the point cloud's small kernels
+    and (depth 4) the synthesis fill SMs beside the trace instead of running alone after it;
+    every step still builds, traces, synthesizes and images one batch each.  The synthesis call
+    starts with its one-wave spreading kernel while the trace's first kernel follows a memset;
+    three tiny ops at the head of the synthesis branch let the trace's CTAs be placed first, so
+    that the synthesis takes the SMs the trace's last CTAs leave idle rather than holding every
+    SM for a wave before the trace starts.  The points after step j are those of the vertices
+    set before step j - (depth - 1) (earlier steps: the constructor's vertices, whose paths and
+    cube the constructor computes).  With ``host_io`` the graph also copies the vertices from
+    the page-locked ``h_verts`` at its start, and the points and their count into ``h_points`` /
+    ``h_n`` at the point-cloud branch's end (``run_host``).
     """
 
+    SYNTH_DELAY = 3  # tiny ops ahead of the synthesis in its branch
+
     def __init__(self, verts: torch.Tensor, faces: torch.Tensor, radar, grid, max_bounces: int, cfar,
-                 mode: int = sim.PHASE_SPLIT, graph: bool = True, host_io: bool = False):
+                 mode: int = sim.PHASE_SPLIT, graph: bool = True, host_io: bool = False, depth: int = 4):
+        if depth not in (3, 4):
+            raise ValueError("depth must be 3 or 4")
         dev = verts.device
+        self.depth, self.lag = depth, depth - 1
         self.radar, self.grid, self.max_bounces, self.cfar, self.mode = radar, grid, max_bounces, cfar, mode
         self.verts = verts.detach().clone().contiguous()
         self.faces = faces.detach().contiguous()
         self.scenes = [sim.Scene(self.verts, self.faces), sim.Scene(self.verts, self.faces)]
-        self.paths = sim.PathBuffers(grid.n_rays, max_bounces, radar.n_virt)
-        self.ws = torch.empty(sim.synth_ws_bytes(radar, self.paths.cap), dtype=torch.uint8, device=dev)
+        self.paths = [sim.PathBuffers(grid.n_rays, max_bounces, radar.n_virt) for _ in range(depth - 2)]
+        self.ws = torch.empty(sim.synth_ws_bytes(radar, self.paths[0].cap), dtype=torch.uint8, device=dev)
         self.cubes = [torch.zeros((radar.n_virt, radar.n_chirps, radar.n_samples, 2), device=dev) for _ in range(2)]
         self.state = sim.PcState(radar, cfar)
         self.points = torch.empty((cfar.k_max, 4), device=dev)
-        self.build_stream = torch.cuda.Stream(device=dev, priority=-1)
-        self.pc_stream = torch.cuda.Stream(device=dev, priority=-1)
+        lo, hi = torch.cuda.Stream.priority_range()  # (lowest, highest): larger numbers run later
+        self.build_stream = torch.cuda.Stream(device=dev, priority=hi)
+        self.pc_stream = torch.cuda.Stream(device=dev, priority=hi)
+        if depth == 4:
+            self.trace_stream = torch.cuda.Stream(device=dev, priority=(lo + hi) // 2)
+            self.synth_stream = torch.cuda.Stream(device=dev, priority=lo)
+            self.delay = torch.zeros(1, dtype=torch.int32, device=dev)
         self.host_io = host_io
         if host_io:
             self.h_verts = torch.empty(self.verts.shape, dtype=torch.float32).pin_memory()
@@ -170,33 +186,51 @@ class PipelinedForward:
         self._prime()
 
     def _prime(self):
-        """Step 0's state: tree 0 of the current vertices, and cube 1 (imaged by step 0) from it."""
+        """Step 0's state from the current vertices: tree 0, and the paths and cube the first
+        step's synthesis and point cloud take (depth 3: cube 1; depth 4: paths 1 and cube 0)."""
         self.scenes[0].update(self.verts)
-        sim.trace(self.scenes[0], self.radar, self.grid, self.max_bounces, out=self.paths)
-        sim.synthesize(self.paths, self.radar, self.mode, out=self.cubes[1], ws=self.ws)
+        sim.trace(self.scenes[0], self.radar, self.grid, self.max_bounces, out=self.paths[-1])
+        sim.synthesize(self.paths[-1], self.radar, self.mode, out=self.cubes[1 if self.depth == 3 else 0], ws=self.ws)
         self.j = 0
 
     def _step(self, p: int, copies: bool):
         main = torch.cuda.current_stream()
-        self.build_stream.wait_stream(main)
-        self.pc_stream.wait_stream(main)
+        if copies:  # ahead of every branch, so that the build is not held behind it
+            self.verts.copy_(self.h_verts, non_blocking=True)
+        side = [self.build_stream, self.pc_stream]
+        if self.depth == 4:
+            side += [self.trace_stream, self.synth_stream]
+        for st in side:
+            st.wait_stream(main)
         with torch.cuda.stream(self.build_stream):
-            if copies:
-                self.verts.copy_(self.h_verts, non_blocking=True)
             self.scenes[1 - p].update(self.verts)
         with torch.cuda.stream(self.pc_stream):
-            sim.pointcloud(self.cubes[1 - p], self.radar, self.cfar, state=self.state, out=self.points)
+            sim.pointcloud(self.cubes[1 - p if self.depth == 3 else p], self.radar, self.cfar, state=self.state,
+                           out=self.points)
             if copies:
                 self.h_points.copy_(self.points, non_blocking=True)
                 self.h_n.copy_(self.state.n_points_tensor(), non_blocking=True)
-        sim.trace(self.scenes[p], self.radar, self.grid, self.max_bounces, out=self.paths)
-        sim.synthesize(self.paths, self.radar, self.mode, out=self.cubes[p], ws=self.ws)
-        main.wait_stream(self.build_stream)
-        main.wait_stream(self.pc_stream)
+        if self.depth == 3:
+            sim.trace(self.scenes[p], self.radar, self.grid, self.max_bounces, out=self.paths[0])
+            sim.synthesize(self.paths[0], self.radar, self.mode, out=self.cubes[p], ws=self.ws)
+        else:
+            with torch.cuda.stream(self.trace_stream):
+                sim.trace(self.scenes[p], self.radar, self.grid, self.max_bounces, out=self.paths[p])
+            with torch.cuda.stream(self.synth_stream):
+                for _ in range(self.SYNTH_DELAY):
+                    self.delay.zero_()
+                sim.synthesize(self.paths[1 - p], self.radar, self.mode, out=self.cubes[1 - p], ws=self.ws)
+        for st in side:
+            main.wait_stream(st)
+
+    def synthesized(self):
+        """The cube the last step synthesized (that of the vertices set before step j - depth + 2)."""
+        q = (self.j - 1) % 2
+        return self.cubes[q if self.depth == 3 else 1 - q]
 
     def set_vertices(self, verts: torch.Tensor):
-        """New positions for the same topology: the next step builds their tree, the step after
-        it traces them and the one after that images them."""
+        """New positions for the same topology: the next step builds their tree and the points
+        of the step ``depth`` - 1 steps after it are theirs."""
         self.verts.copy_(verts, non_blocking=True)
 
     def run(self):
@@ -211,7 +245,8 @@ class PipelinedForward:
         """One step from host memory (requires host_io and the graphs): ``verts`` (array-like
         [nv, 3], or None to keep the page-locked buffer's contents) go into the page-locked input
         buffer once the previous step has finished with it, then the graph replays; ``h_points`` /
-        ``h_n`` hold the points of the vertices of two calls earlier when ``done`` completes."""
+        ``h_n`` hold the points of the vertices of ``depth`` - 1 calls earlier when ``done``
+        completes."""
         if not self.host_io or self.graphs is None:
             raise RuntimeError("run_host needs PipelinedForward(..., graph=True, host_io=True)")
         if verts is not None:

@@ -55,20 +55,23 @@ def test_host_io_graph_matches_eager(sbr):
         e.run_host(wl.verts)
 
 
-def test_pipelined_lags_two_steps(sbr):
-    """sbr.PipelinedForward: step j traces batch j's tree, builds batch j+1's beside it and
-    images batch j-1's cube beside both.  With the vertices moving every step, step j's points
-    equal (bitwise) those the serial step gives for the vertices set before step j-2 (steps 0
-    and 1: the constructor's), replayed from the two graphs, run eagerly, and with host buffers;
-    the cube synthesized at step j is the serial cube of the vertices set before step j-1."""
+@pytest.mark.parametrize("depth", [3, 4])
+def test_pipelined_lags(sbr, depth):
+    """sbr.PipelinedForward: step j traces batch j's tree beside the build of batch j+1 and the
+    synthesis (depth 4) and point cloud of earlier batches.  With the vertices moving every step,
+    step j's points equal (bitwise) those the serial step gives for the vertices set before step
+    j - (depth - 1) (earlier steps: the constructor's), replayed from the two graphs, run eagerly,
+    and with host buffers; the cube synthesized at step j is the serial cube of the vertices set
+    before step j - depth + 2."""
     wl = superquadric_scene(seed=6, G=256)
     cfg = CfarParams()
     v = torch.from_numpy(wl.verts).cuda()
     f = torch.from_numpy(wl.faces).cuda()
     e = sbr.Forward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg, graph=False)
-    pg = sbr.PipelinedForward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg)
-    pe = sbr.PipelinedForward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg, graph=False)
-    ph = sbr.PipelinedForward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg, host_io=True)
+    kw = dict(depth=depth)
+    pg = sbr.PipelinedForward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg, **kw)
+    pe = sbr.PipelinedForward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg, graph=False, **kw)
+    ph = sbr.PipelinedForward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg, host_io=True, **kw)
     shifts = [0.0, 0.01, 0.03, -0.02, 0.02]
     want = []
     for sh in shifts:  # the serial step's outputs per vertex set
@@ -76,8 +79,12 @@ def test_pipelined_lags_two_steps(sbr):
         e.run()
         torch.cuda.synchronize()
         want.append((e.cube.clone(), e.points.clone(), e.n_points()))
-    seq = shifts + [0.0, 0.0]  # the vertex set given before each step
+    seq = shifts + [0.0] * depth  # the vertex set given before each step
     out = dict(zip(shifts, want))
+
+    def given(k):  # the vertex set before step k (the constructor's before step 0)
+        return seq[k] if k >= 0 else 0.0
+
     for j, sh in enumerate(seq):
         moved = v + torch.tensor([0.0, 0.0, sh], device="cuda")
         for fw in (pg, pe):
@@ -86,17 +93,19 @@ def test_pipelined_lags_two_steps(sbr):
         ph.run_host(moved.cpu().numpy())
         ph.done.synchronize()
         torch.cuda.synchronize()
-        _, pts, n = out[seq[j - 2] if j >= 2 else 0.0]
-        traced = out[seq[j - 1] if j >= 1 else 0.0][0]
+        _, pts, n = out[given(j - depth + 1)]
+        synthesized = out[given(j - depth + 2)][0]
         assert n > 0
         for fw in (pg, pe):
             assert fw.n_points() == n
             assert torch.equal(fw.points, pts)
-            assert torch.equal(fw.cubes[j % 2], traced)
+            assert torch.equal(fw.synthesized(), synthesized)
         assert int(ph.h_n.item()) == n
         assert torch.equal(ph.h_points, pts.cpu())
     with pytest.raises(RuntimeError):
         pe.run_host(wl.verts)
+    with pytest.raises(ValueError):
+        sbr.PipelinedForward(v, f, wl.radar, wl.grid, wl.max_bounces, cfg, graph=False, depth=5)
 
 
 def test_bench_step_full_cube_and_points_against_oracle(sbr):
