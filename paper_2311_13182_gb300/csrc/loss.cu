@@ -110,46 +110,84 @@ __global__ void __launch_bounds__(1024) k_chamfer(const float4* __restrict__ P, 
   }
 }
 
-// delta_i = v_i - mean_{j in N(i)} v_j ; sq_i = |delta_i|^2
-__global__ void k_lap_delta(const float* __restrict__ v, int nv, const int32_t* __restrict__ off,
-                            const int32_t* __restrict__ adj, float* __restrict__ delta, float* __restrict__ sq) {
+constexpr int kLapThreads = 256;
+constexpr int kLapFirst = 8;  // neighbour indices loaded together before their values
+
+// delta_i = v_i - mean_{j in N(i)} v_j; partial[blockIdx] = the CTA's sum of
+// |delta_i|^2 (fixed order).  The first kLapFirst neighbour indices are loaded
+// before any of their positions, so that the position loads overlap; the sums
+// run in neighbour order either way.
+__global__ void __launch_bounds__(kLapThreads) k_lap_delta(const float* __restrict__ v, int nv,
+                                                           const int32_t* __restrict__ off,
+                                                           const int32_t* __restrict__ adj, float* __restrict__ delta,
+                                                           float* __restrict__ partial) {
+  __shared__ float red[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nv) return;
-  const int b = off[i], e = off[i + 1];
-  float mx = 0.f, my = 0.f, mz = 0.f;
-  for (int q = b; q < e; ++q) {
-    const int j = adj[q];
-    mx += v[3 * j];
-    my += v[3 * j + 1];
-    mz += v[3 * j + 2];
+  float sq = 0.f;
+  if (i < nv) {
+    const int b = __ldg(&off[i]), e = __ldg(&off[i + 1]);
+    int nb[kLapFirst];
+#pragma unroll
+    for (int u = 0; u < kLapFirst; ++u) nb[u] = b + u < e ? __ldg(&adj[b + u]) : -1;
+    float mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+    for (int u = 0; u < kLapFirst; ++u)
+      if (nb[u] >= 0) {
+        mx += __ldg(&v[3 * nb[u]]);
+        my += __ldg(&v[3 * nb[u] + 1]);
+        mz += __ldg(&v[3 * nb[u] + 2]);
+      }
+    for (int q = b + kLapFirst; q < e; ++q) {
+      const int j = __ldg(&adj[q]);
+      mx += __ldg(&v[3 * j]);
+      my += __ldg(&v[3 * j + 1]);
+      mz += __ldg(&v[3 * j + 2]);
+    }
+    const float inv = e > b ? 1.f / (float)(e - b) : 0.f;
+    const float dx = e > b ? v[3 * i] - mx * inv : 0.f, dy = e > b ? v[3 * i + 1] - my * inv : 0.f,
+                dz = e > b ? v[3 * i + 2] - mz * inv : 0.f;
+    delta[3 * i] = dx;
+    delta[3 * i + 1] = dy;
+    delta[3 * i + 2] = dz;
+    sq = dx * dx + dy * dy + dz * dz;
   }
-  const float inv = e > b ? 1.f / (float)(e - b) : 0.f;
-  const float dx = e > b ? v[3 * i] - mx * inv : 0.f, dy = e > b ? v[3 * i + 1] - my * inv : 0.f,
-              dz = e > b ? v[3 * i + 2] - mz * inv : 0.f;
-  delta[3 * i] = dx;
-  delta[3 * i + 1] = dy;
-  delta[3 * i + 2] = dz;
-  sq[i] = dx * dx + dy * dy + dz * dz;
+  sq = block_sum(sq, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = sq;
 }
 
 // dL/dv_k = weight (2 / nv) (delta_k - sum_{i in N(k)} delta_i / deg_i); the first
-// CTA also adds lscale * sum_i sq_i (the loss term) to *loss, in a fixed order.
-__global__ void k_lap_grad(const float* __restrict__ delta, int nv, const int32_t* __restrict__ off,
-                           const int32_t* __restrict__ adj, float scale, float* __restrict__ g,
-                           const float* __restrict__ sq, float lscale, float* __restrict__ loss) {
+// CTA also adds lscale * (the sum of the nb CTA partials, fixed order) to *loss.
+__global__ void __launch_bounds__(kLapThreads) k_lap_grad(const float* __restrict__ delta, int nv,
+                                                          const int32_t* __restrict__ off,
+                                                          const int32_t* __restrict__ adj, float scale,
+                                                          float* __restrict__ g, const float* __restrict__ partial,
+                                                          int nb, float lscale, float* __restrict__ loss) {
   __shared__ float red[32];
   if (blockIdx.x == 0) {
     float s = 0.f;
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) s += sq[i];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
     s = block_sum(s, red);
     if (threadIdx.x == 0) *loss += lscale * s;
   }
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nv) return;
   float gx = delta[3 * k], gy = delta[3 * k + 1], gz = delta[3 * k + 2];
-  for (int q = off[k]; q < off[k + 1]; ++q) {
-    const int i = adj[q];
-    const float inv = 1.f / (float)(off[i + 1] - off[i]);
+  const int b = __ldg(&off[k]), e = __ldg(&off[k + 1]);
+  int nbr[kLapFirst];
+#pragma unroll
+  for (int u = 0; u < kLapFirst; ++u) nbr[u] = b + u < e ? __ldg(&adj[b + u]) : -1;
+#pragma unroll
+  for (int u = 0; u < kLapFirst; ++u)
+    if (nbr[u] >= 0) {
+      const int i = nbr[u];
+      const float inv = 1.f / (float)(__ldg(&off[i + 1]) - __ldg(&off[i]));
+      gx -= delta[3 * i] * inv;
+      gy -= delta[3 * i + 1] * inv;
+      gz -= delta[3 * i + 2] * inv;
+    }
+  for (int q = b + kLapFirst; q < e; ++q) {
+    const int i = __ldg(&adj[q]);
+    const float inv = 1.f / (float)(__ldg(&off[i + 1]) - __ldg(&off[i]));
     gx -= delta[3 * i] * inv;
     gy -= delta[3 * i + 1] * inv;
     gz -= delta[3 * i + 2] * inv;
@@ -246,14 +284,14 @@ extern "C" sbr_status sbr_laplacian(const float* d_verts, int32_t nv, const int3
   }
   Carver c(d_ws);
   float* delta = c.take<float>(3 * (size_t)nv);
-  float* sq = c.take<float>(nv);
+  float* partial = c.take<float>(nv);  // one per CTA (nb <= nv)
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int b = (nv + 255) / 256;
+  const int b = (nv + kLapThreads - 1) / kLapThreads;
   ::sbr::note_launch();
-  k_lap_delta<<<b, 256, 0, st>>>(d_verts, nv, d_off, d_adj, delta, sq);
+  k_lap_delta<<<b, kLapThreads, 0, st>>>(d_verts, nv, d_off, d_adj, delta, partial);
   ::sbr::note_launch();
-  k_lap_grad<<<b, 256, 0, st>>>(delta, nv, d_off, d_adj, 2.f * weight / (float)nv, d_gverts, sq, weight / (float)nv,
-                                d_loss);
+  k_lap_grad<<<b, kLapThreads, 0, st>>>(delta, nv, d_off, d_adj, 2.f * weight / (float)nv, d_gverts, partial, b,
+                                        weight / (float)nv, d_loss);
   SBR_CUDA(cudaGetLastError());
   return SBR_OK;
 }

@@ -517,6 +517,8 @@ __global__ void k_points(const float* __restrict__ Pw, PointArg pa, const int32_
 // block scan per round places them), the stable sort by weight, and the points.  Same
 // results as scan, k_compact, the sort and k_points, in one launch instead of four.
 constexpr int kSelThreads = 1024;
+constexpr int kRankMax = 256;  // candidates k_select ranks directly (shared memory: 2 KB)
+static_assert(2 * kRankMax <= cta::kSortSmemWords, "the rank buffers share the sort's shared memory");
 __global__ void __launch_bounds__(kSelThreads) k_select(const float* __restrict__ Pw, PointArg pa,
                                                         const unsigned long long* __restrict__ amax_key,
                                                         const uint32_t* __restrict__ key,
@@ -564,7 +566,29 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const float* __restrict_
   }
   const uint32_t total = base;
   __syncthreads();  // the compacted candidates are visible to the whole CTA
-  cta::sort_pairs(k0, v0, k1, v1, (int64_t)total, 32, nullptr, sel_sm);
+  if (total <= (uint32_t)kRankMax) {
+    // few candidates: each one's rank is the number of smaller keys plus the equal keys
+    // before it (they are in cell order), i.e. its place in the stable sort, found with
+    // two barriers instead of the sort network's dozens
+    uint32_t* rk = sel_sm;
+    int32_t* rv = reinterpret_cast<int32_t*>(sel_sm + kRankMax);
+    for (int i = t; i < (int)total; i += kSelThreads) {
+      rk[i] = k0[i];
+      rv[i] = v0[i];
+    }
+    __syncthreads();
+    if (t < (int)total) {
+      const uint32_t ki = rk[t];
+      int r = 0;
+      for (int j = 0; j < (int)total; ++j) {
+        const uint32_t kj = rk[j];
+        r += (kj < ki) | ((kj == ki) & (j < t));
+      }
+      v0[r] = rv[t];
+    }
+  } else {
+    cta::sort_pairs(k0, v0, k1, v1, (int64_t)total, 32, nullptr, sel_sm);
+  }
   __syncthreads();
   const int n = min((int)total, pa.k_max);
   if (t == 0) *n_out = n;

@@ -10,8 +10,9 @@ or, with loss="image", the paper's spatial multi-antenna loss (Eq. 16): the
 target is a range-angle power map [n_theta, N_s], the forward stops at the power
 map, and loss = mean squared image difference + w_lap * Laplacian, whose adjoint
 enters the synthesis adjoint directly.
-Every step is a library kernel on one stream with no host synchronisation, so
-the whole iteration is captured into a CUDA graph and replayed.  The scene's tree
+Every step is a library kernel with no host synchronisation (the Laplacian term
+on a second stream beside the forward pass), so the whole iteration is captured
+into a CUDA graph and replayed.  The scene's tree
 is refitted to the new vertices each iteration (sbr_scene_refit: the same hits as
 a rebuild) and rebuilt every ``rebuild_every`` iterations (two captured graphs), so
 that its boxes stay tight as the mesh moves.
@@ -48,25 +49,42 @@ class Reconstruction:
         self.v = torch.zeros_like(self.verts)
         self.step_count = torch.zeros(1, dtype=torch.int32, device=device)
         self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.loss_lap = torch.zeros(1, dtype=torch.float32, device=device)
+        self.lap_stream = torch.cuda.Stream(device=device)
         self.gpoints = torch.zeros((cfar.k_max, 4), dtype=torch.float32, device=device)
         self.graph = None
         self.graph_rebuild = None
 
     def _iteration(self, rebuild: bool = True):
         self.sim.bvh_refit = not rebuild
+        main = torch.cuda.current_stream()
+        # The smoothness term depends on the vertices alone, so it runs on a second stream
+        # beside the forward pass: it zeroes the gradient and adds its own term, which the
+        # adjoint of the data term then adds to (the same order as one stream), and keeps its
+        # loss term apart until the data term has written the loss (the same sum).
+        lap_done = torch.cuda.Event()
+        self.lap_stream.wait_stream(main)
+        with torch.cuda.stream(self.lap_stream):
+            self.grad.zero_()
+            self.loss_lap.zero_()
+            sim.laplacian(self.verts, self.adj, self.lap_weight, self.loss_lap, self.grad)
+            lap_done.record()
         if self.kind == "image":
             self.sim.forward_image(self.verts)
             sim.image_loss(self.sim.state, self.target, loss=self.loss, gcube=self.sim.gcube)
         else:
             pts, n = self.sim.forward(self.verts)
             sim.chamfer(pts, n, self.target, loss=self.loss, gpred=self.gpoints)
-        self.grad.zero_()
-        sim.laplacian(self.verts, self.adj, self.lap_weight, self.loss, self.grad)
+        self.lap_stream.wait_stream(main)  # the data term has written the loss
+        with torch.cuda.stream(self.lap_stream):
+            self.loss.add_(self.loss_lap)
+        main.wait_event(lap_done)
         if self.kind == "image":
             self.sim.backward_cube(self.verts, self.sim.gcube, self.grad)
         else:
             self.sim.backward(self.verts, self.gpoints, self.grad)
         sim.adam_step(self.verts, self.grad, self.m, self.v, self.step_count, lr=self.lr)
+        main.wait_stream(self.lap_stream)
 
     def _rebuild_now(self) -> bool:
         return self.iters % self.rebuild_every == 0

@@ -272,3 +272,51 @@ def test_trace_adjoint_jittered_grid(sbr):
     from sbr_inputs import jittered
     wl = sphere_scene(G=32)
     check_trace_adjoint(sbr, dataclasses.replace(wl, grid=jittered(wl.grid, 6)))
+
+
+def _fan(n_rim: int):
+    """A flat fan: centre vertex 0 joined to n_rim rim vertices (centre degree n_rim)."""
+    ang = np.linspace(0.0, 2 * np.pi, n_rim, endpoint=False)
+    rng = np.random.default_rng(7)
+    v = np.concatenate([[[0.0, 0.0, 0.1]], np.stack([np.cos(ang), np.sin(ang), 0.05 * rng.standard_normal(n_rim)], 1)])
+    f = np.array([[0, 1 + i, 1 + (i + 1) % n_rim] for i in range(n_rim)], np.int32)
+    return v.astype(np.float32), f
+
+
+@pytest.mark.parametrize("mesh", ["icosphere4", "fan24"])
+def test_laplacian_value_and_gradient(sbr, mesh):
+    """sbr_laplacian against the oracle's uniform Laplacian (weight x mean_i |v_i - mean of its
+    neighbours|^2): the value it adds to the loss within 1e-5 relative, and the gradient it adds
+    within 1e-4 of the largest component against FP64 central differences of the oracle (exact
+    for this quadratic up to rounding).  The icosphere (2,562 vertices) spans 11 CTAs with a
+    ragged last one; the fan's centre has 24 neighbours, past the neighbours loaded together."""
+    if mesh == "icosphere4":
+        v, f = icosphere(4, 0.2)
+        rng = np.random.default_rng(3)
+        v = (v * (1.0 + 0.05 * rng.standard_normal((v.shape[0], 1)))).astype(np.float32)
+    else:
+        v, f = _fan(24)
+    w = 0.1
+    vt = torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()
+    adj = sbr.Adjacency(f, v.shape[0])
+    l0, g0 = 2.0 ** -20, 2.0 ** -30  # the call adds to what is there (small, so no precision is lost)
+    loss = torch.full((1,), l0, device="cuda")
+    g = torch.full_like(vt, g0)
+    sbr.laplacian(vt, adj, w, loss, g)
+    torch.cuda.synchronize()
+    v64 = v.astype(np.float64)
+    ref = w * opc.laplacian(v64, f)
+    assert abs((float(loss.item()) - l0) - ref) <= 1e-5 * ref
+    gg = g.cpu().numpy().astype(np.float64) - g0
+    rng = np.random.default_rng(11)
+    chosen = np.unique(np.concatenate([[0], rng.choice(v.shape[0], size=min(20, v.shape[0]), replace=False)]))
+    H = 1e-5
+    fd = np.zeros((chosen.size, 3))
+    for i, vi in enumerate(chosen):
+        for ax in range(3):
+            vp, vm = v64.copy(), v64.copy()
+            vp[vi, ax] += H
+            vm[vi, ax] -= H
+            fd[i, ax] = w * (opc.laplacian(vp, f) - opc.laplacian(vm, f)) / (2 * H)
+    scale = np.abs(fd).max()
+    assert np.abs(gg[chosen] - fd).max() <= 1e-4 * scale, np.abs(gg[chosen] - fd).max() / scale
