@@ -128,8 +128,8 @@ class PipelinedForward:
     three tiny ops at the head of the synthesis branch let the trace's CTAs be placed first, so
     that the synthesis takes the SMs the trace's last CTAs leave idle rather than holding every
     SM for a wave before the trace starts.  The points after step j are those of the vertices
-    set before step j - (depth - 1) (earlier steps: the constructor's vertices, whose paths and
-    cube the constructor computes).  With ``host_io`` the graph also copies the vertices from
+    set before step j - ``lag`` (``lag`` = depth - 1; earlier steps: the constructor's vertices,
+    whose paths and cube the constructor computes).  With ``host_io`` the graph also copies the vertices from
     the page-locked ``h_verts`` at its start, and the points and their count into ``h_points`` /
     ``h_n`` at the point-cloud branch's end (``run_host``).
     """
