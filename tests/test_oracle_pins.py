@@ -959,3 +959,22 @@ def test_reparam_derivative_follows_the_exact_strength_integral():
         fz = (est(v64 + h * D, False) - est(v64 - h * D, False)) / (2 * h)
         assert abs(rp - ex) < 1e-3 * abs(ex), (rp, ex)
         assert abs(fz - ex) > 0.3 * abs(ex)
+
+
+def test_oracle_thread_count_leaves_results_unchanged():
+    """oracle.set_threads (used to time the oracle on one core): it reports the count in force,
+    ignores counts below 1, and the brute-force trace of a seeded ray sample is identical with one
+    thread and with the previous count (every ray is computed alone)."""
+    from sbr_inputs import ray_subset, sphere_scene
+    wl = sphere_scene()
+    ids = ray_subset(3, wl.grid.n_rays, 256)
+    prev = oracle.set_threads(1)
+    try:
+        assert prev >= 1
+        assert oracle.set_threads(0) == 1  # ignored: still one thread
+        one = oracle.trace(wl.verts, wl.faces, wl.grid, wl.max_bounces, ray_ids=ids)
+    finally:
+        oracle.set_threads(prev)
+    many = oracle.trace(wl.verts, wl.faces, wl.grid, wl.max_bounces, ray_ids=ids)
+    for k in ("tri", "tuv", "hit", "omega", "flag"):
+        assert np.array_equal(one[k], many[k])
