@@ -146,6 +146,11 @@ struct Req {
 
 struct Slot {
   cudaStream_t stream = nullptr;
+  // the slot's tree builds run on a stream of the greatest priority, joined to `stream` by
+  // events: a cooperative build needs all its CTAs resident at once, and beside another
+  // slot's trace it would otherwise find them only when that trace drains
+  cudaStream_t build_stream = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t start = nullptr, done = nullptr;
   Req* req = nullptr;
   char* pinned = nullptr;  // page-locked staging: the request's results, then its inputs
@@ -326,6 +331,25 @@ struct Staging {
     }                                                                        \
   } while (0)
 
+// Runs build(stream) on the slot's build stream, ordered after the slot stream's work so far
+// and before its next work.
+template <class F>
+sbr_status on_build_stream(Slot& sl, F build) {
+  if (cudaEventRecord(sl.fork, sl.stream) != cudaSuccess ||
+      cudaStreamWaitEvent(sl.build_stream, sl.fork, 0) != cudaSuccess) {
+    set_error("server: fork to the build stream failed");
+    return SBR_ERR_CUDA;
+  }
+  const sbr_status rs = build(reinterpret_cast<sbr_stream>(sl.build_stream));
+  if (rs != SBR_OK) return rs;
+  if (cudaEventRecord(sl.join, sl.build_stream) != cudaSuccess ||
+      cudaStreamWaitEvent(sl.stream, sl.join, 0) != cudaSuccess) {
+    set_error("server: join from the build stream failed");
+    return SBR_ERR_CUDA;
+  }
+  return SBR_OK;
+}
+
 // Enqueues a forward request's work on its slot stream.
 sbr_status enqueue_forward(sbr_server* s, Req* q, Slot& sl) {
   cudaStream_t st = sl.stream;
@@ -346,7 +370,9 @@ sbr_status enqueue_forward(sbr_server* s, Req* q, Slot& sl) {
     const int32_t* hf = in.put(q->faces);
     ENQ_CUDA(cudaMemcpyAsync(dv, hv, sizeof(float) * 3 * r.nv, cudaMemcpyHostToDevice, st));
     ENQ_CUDA(cudaMemcpyAsync(df, hf, sizeof(int32_t) * 3 * r.nt, cudaMemcpyHostToDevice, st));
-    ENQ(sbr_scene_create(dv, r.nv, df, r.nt, dmem, q->sz.scene, reinterpret_cast<sbr_stream>(st), &scene));
+    ENQ(on_build_stream(sl, [&](sbr_stream bs) {
+      return sbr_scene_create(dv, r.nv, df, r.nt, dmem, q->sz.scene, bs, &scene);
+    }));
     if (q->scene_ref) {
       q->scene_ref->scene = scene;
       ENQ_CUDA(cudaEventRecord(q->scene_ref->built, st));
@@ -433,11 +459,16 @@ sbr_status enqueue_recon(sbr_server* s, Req* q, Slot& sl) {
   ENQ_CUDA(cudaMemsetAsync(m2, 0, sizeof(float) * 3 * r.nv, st));
   ENQ_CUDA(cudaMemsetAsync(step, 0, sizeof(int32_t), st));
   sbr_scene* scene = nullptr;
-  ENQ(sbr_scene_create(dv, r.nv, df, r.nt, dscene, q->sz.scene, ss, &scene));
+  ENQ(on_build_stream(sl, [&](sbr_stream bs) {
+    return sbr_scene_create(dv, r.nv, df, r.nt, dscene, q->sz.scene, bs, &scene);
+  }));
   q->own_scene = scene;
   for (int it = 0; it < r.iterations; ++it) {
     // the moved vertices into the tree: refitted, rebuilt every kRebuildEvery iterations
-    if (it > 0) ENQ(it % kRebuildEvery == 0 ? sbr_scene_update(scene, dv, ss) : sbr_scene_refit(scene, dv, ss));
+    if (it > 0)
+      ENQ(on_build_stream(sl, [&](sbr_stream bs) {
+        return it % kRebuildEvery == 0 ? sbr_scene_update(scene, dv, bs) : sbr_scene_refit(scene, dv, bs);
+      }));
     ENQ(sbr_trace(scene, &s->radar, &r.grid, nullptr, -1, r.max_bounces, &paths, ss));
     ENQ(sbr_synthesize(&paths, &s->radar, SBR_PHASE_SPLIT, cube, ws, q->sz.ws, ss));
     ENQ(sbr_pointcloud(cube, &s->radar, &s->cfar, pts, &pc, ss));
@@ -640,6 +671,11 @@ extern "C" sbr_status sbr_server_create(void* d_arena, size_t arena_bytes, int32
   s->slots.resize(n_slots);
   for (auto& sl : s->slots) {
     SBR_CUDA(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
+    int least = 0, greatest = 0;
+    SBR_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    SBR_CUDA(cudaStreamCreateWithPriority(&sl.build_stream, cudaStreamNonBlocking, greatest));
+    SBR_CUDA(cudaEventCreateWithFlags(&sl.fork, cudaEventDisableTiming));
+    SBR_CUDA(cudaEventCreateWithFlags(&sl.join, cudaEventDisableTiming));
     SBR_CUDA(cudaEventCreate(&sl.start));
     SBR_CUDA(cudaEventCreate(&sl.done));
   }
@@ -778,6 +814,9 @@ extern "C" void sbr_server_destroy(sbr_server* s) {
     if (sl.start) cudaEventDestroy(sl.start);
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.stream) cudaStreamDestroy(sl.stream);
+    if (sl.build_stream) cudaStreamDestroy(sl.build_stream);
+    if (sl.fork) cudaEventDestroy(sl.fork);
+    if (sl.join) cudaEventDestroy(sl.join);
   }
   for (auto& kv : s->scenes) {
     sbr_scene_destroy(kv.second->scene);
